@@ -1,0 +1,294 @@
+"""FP64 CPU oracle for the volumetrically consistent Gaussian rasterizer (arXiv 2412.03378).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow reference the CUDA library is
+checked against.  Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline legs of
+`bench.py` may import it; the product package never does and shares no code with it.
+
+The arithmetic lives in `vg_oracle.c` (plain C, FP64, OpenMP over pixels); this module
+compiles it with gcc on first use (no floating-point contraction, so the FP32 key
+function is reproducible) and wraps it for numpy inputs produced by `synth`.
+
+Passages followed: Sec. 3.1-3.2 (Eq. 1-4), Sec. 4.1-4.2 (Eq. 8-19), Supp. B (the 1D
+Gaussian along the ray), Sec. 6.2 (Eq. 21, tomography), Sec. 7 ("per-tile sorting").
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vg_oracle.c")
+_HDR = os.path.join(_HERE, "vg_oracle.h")
+_SO = os.path.join(_HERE, "liboracle.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+#: exact mode: no alpha skip, no clamp, no early stop; footprint truncated at tau_cut.
+EXACT = dict(alpha_min=0.0, tau_cut=1e-6, tau_max=math.inf, T_stop=0.0, bg=(0.0, 0.0, 0.0), z_near=0.2)
+#: compat mode: the 3DGS thresholds (alpha >= 1/255 blended, alpha <= 0.99, stop at T < 1e-4).
+COMPAT = dict(alpha_min=1.0 / 255.0, tau_cut=-math.log1p(-1.0 / 255.0), tau_max=math.log(100.0),
+              T_stop=1e-4, bg=(0.0, 0.0, 0.0), z_near=0.2)
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to its source (gcc, FP64, OpenMP, no FP contraction)."""
+    with _LOCK:
+        stale = (not os.path.exists(_SO) or
+                 os.path.getmtime(_SO) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+        if force or stale:
+            tmp = _SO + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+                   "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        P = ctypes.c_void_p
+        i32, i64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+        L.orc_keys.restype = i64
+        L.orc_keys.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, f32, f32, P, P]
+        L.orc_tomo_keys.restype = i64
+        L.orc_tomo_keys.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, f32, P]
+        L.orc_bin.restype = i64
+        L.orc_bin.argtypes = [i32, i32, P, P, P, P, i64, i64, P, P]
+        L.orc_sh_basis.restype = None
+        L.orc_sh_basis.argtypes = [i32, P, P]
+        L.orc_tau.restype = None
+        L.orc_tau.argtypes = [P, P, P, ctypes.c_double, P, P, P]
+        L.orc_render.restype = None
+        L.orc_render.argtypes = [i32, P, P, P, P, P, i32, i32, P, P, i32, i32, P, P, P, P, i32, P, P, P, P, P, P, P]
+        L.orc_render_grad.restype = None
+        L.orc_render_grad.argtypes = [i32, P, P, P, P, P, i32, i32, P, P, i32, i32, P, P, P, P, P, P, P, P,
+                                      P, P, P, P, P]
+        L.orc_tomo.restype = None
+        L.orc_tomo.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, P, P, i32, P, P, P]
+        L.orc_tomo_grad.restype = None
+        L.orc_tomo_grad.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, P, P, P, P,
+                                    P, P, P, P]
+        L.orc_num_threads.restype = i32
+        _LIB = L
+    return _LIB
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _scene_arrays(scene, dt=np.float32):
+    """FP32 for the key functions (the values the GPU sees), FP64 for everything else."""
+    return (_c(scene.mu, dt), _c(scene.scale, dt), _c(scene.quat, dt), _c(scene.kappa, dt), _c(scene.sh, dt))
+
+
+def cam_arrays(cams):
+    cf = np.zeros((len(cams), 16), np.float32)
+    wh = np.zeros((len(cams), 2), np.int32)
+    for v, c in enumerate(cams):
+        cf[v, :9] = np.asarray(c.R, np.float32).reshape(9)
+        cf[v, 9:12] = np.asarray(c.t, np.float32)
+        cf[v, 12:16] = [c.fx, c.fy, c.cx, c.cy]
+        wh[v] = [c.width, c.height]
+    return cf, wh
+
+
+def tile_layout(cams, tile=(16, 16)):
+    tx = np.array([(c.width + tile[0] - 1) // tile[0] for c in cams], np.int32)
+    ty = np.array([(c.height + tile[1] - 1) // tile[1] for c in cams], np.int32)
+    base = np.zeros(len(cams), np.int32)
+    if len(cams) > 1:
+        base[1:] = np.cumsum(tx * ty)[:-1]
+    return tx, ty, base, int((tx * ty).sum())
+
+
+def pix_bases(cams):
+    sizes = np.array([c.width * c.height for c in cams], np.int64)
+    base = np.zeros(len(cams), np.int64)
+    if len(cams) > 1:
+        base[1:] = np.cumsum(sizes)[:-1]
+    return base, int(sizes.sum())
+
+
+def _opts_arr(opts):
+    o = dict(EXACT)
+    o.update(opts or {})
+    bg = o["bg"]
+    return np.array([o["alpha_min"], o["tau_cut"], o["tau_max"], o["T_stop"], bg[0], bg[1], bg[2],
+                     o["z_near"]], np.float64), o
+
+
+# ------------------------------------------------------------------------------------------
+def keys(scene, cams, opts=None, tile=(16, 16)):
+    """FP32 key function: depth key bits [V, N] (0xFFFFFFFF = invalid or behind z_near) and
+    tile rectangles [V, N, 4] = (tx0, ty0, tx1, ty1) inclusive, -1 when culled."""
+    _, o = _opts_arr(opts)
+    mu, sc, q, k, _sh = _scene_arrays(scene)
+    cf, wh = cam_arrays(cams)
+    V, N = len(cams), scene.n
+    depth = np.zeros((V, N), np.uint32)
+    rect = np.zeros((V, N, 4), np.int32)
+    lib().orc_keys(N, _p(mu), _p(sc), _p(q), _p(k), V, _p(cf), _p(wh), tile[0], tile[1],
+                   np.float32(o["z_near"]), np.float32(o["tau_cut"]), _p(depth), _p(rect))
+    return depth, rect
+
+
+def bin(scene_n, n_views, depth, rect, tiles_x, tile_base, n_tiles):
+    """Stable per-tile lists sorted by (tile, depth key, Gaussian index)."""
+    rect = _c(rect, np.int32)
+    dep = None if depth is None else _c(depth, np.uint32)
+    tiles_x = _c(tiles_x, np.int32)
+    tile_base = _c(tile_base, np.int32)
+    ts = np.zeros(n_tiles + 1, np.int64)
+    r = rect.reshape(-1, 4)
+    vis = r[:, 0] >= 0
+    total = int(((r[vis, 2] - r[vis, 0] + 1).astype(np.int64) * (r[vis, 3] - r[vis, 1] + 1)).sum())
+    sg = np.zeros(max(total, 1), np.int32)
+    got = lib().orc_bin(scene_n, n_views, _p(dep), _p(rect), _p(tiles_x), _p(tile_base), n_tiles, total,
+                        _p(ts), _p(sg))
+    assert got == total
+    return ts, sg[:total]
+
+
+def lists(scene, cams, opts=None, tile=(16, 16)):
+    depth, rect = keys(scene, cams, opts, tile)
+    tx, ty, base, nt = tile_layout(cams, tile)
+    ts, sg = bin(scene.n, len(cams), depth, rect, tx, base, nt)
+    return dict(depth=depth, rect=rect, tile_start=ts, sorted_g=sg, tiles_x=tx, tiles_y=ty, tile_base=base,
+                n_tiles=nt, tile=tile)
+
+
+def render(scene, cams, opts=None, L=None, brute=False, mask=None, tile=(16, 16)):
+    """Blend every pixel (Eq. 14 with the Eq. 19 alpha).  Returns per-view lists of
+    rgb [H, W, 3] and T_final [H, W] (float64) and the blended-Gaussian count."""
+    oa, o = _opts_arr(opts)
+    if L is None:
+        L = lists(scene, cams, o, tile)
+    mu, sc, q, k, sh = _scene_arrays(scene, np.float64)
+    cf, wh = cam_arrays(cams)
+    pb, P = pix_bases(cams)
+    rgb = np.zeros((P, 3), np.float64)
+    T = np.zeros(P, np.float64)
+    nb = np.zeros(P, np.int32)
+    m = None if mask is None else _c(mask, np.int32)
+    lib().orc_render(scene.n, _p(mu), _p(sc), _p(q), _p(k), _p(sh), scene.sh_degree, len(cams), _p(cf), _p(wh),
+                     L["tile"][0], L["tile"][1], _p(oa), _p(L["tile_start"]), _p(L["sorted_g"]),
+                     _p(_c(L["tile_base"], np.int32)), int(brute), _p(_c(L["depth"], np.uint32)),
+                     _p(_c(L["rect"], np.int32)), _p(pb), _p(m), _p(rgb), _p(T), _p(nb))
+    out_rgb, out_T, out_n = [], [], []
+    for v, c in enumerate(cams):
+        s = slice(pb[v], pb[v] + c.width * c.height)
+        out_rgb.append(rgb[s].reshape(c.height, c.width, 3))
+        out_T.append(T[s].reshape(c.height, c.width))
+        out_n.append(nb[s].reshape(c.height, c.width))
+    return out_rgb, out_T, out_n
+
+
+def render_grad(scene, cams, opts, L, dL_drgb, dL_dT=None, mask=None):
+    """Analytic FP64 gradient of sum(dL_drgb * rgb) + sum(dL_dT * T_final) with the tile
+    lists `L` held fixed.  dL_drgb / dL_dT are per-view lists (or flat arrays)."""
+    oa, o = _opts_arr(opts)
+    mu, sc, q, k, sh = _scene_arrays(scene, np.float64)
+    cf, wh = cam_arrays(cams)
+    pb, P = pix_bases(cams)
+    g_rgb = _c(np.concatenate([np.asarray(a, np.float64).reshape(-1, 3) for a in dL_drgb])
+               if isinstance(dL_drgb, (list, tuple)) else np.asarray(dL_drgb).reshape(-1, 3), np.float64)
+    g_T = None
+    if dL_dT is not None:
+        g_T = _c(np.concatenate([np.asarray(a, np.float64).reshape(-1) for a in dL_dT])
+                 if isinstance(dL_dT, (list, tuple)) else np.asarray(dL_dT).reshape(-1), np.float64)
+    N, K = scene.n, (scene.sh_degree + 1) ** 2
+    out = dict(mu=np.zeros((N, 3)), scale=np.zeros((N, 3)), quat=np.zeros((N, 4)), kappa=np.zeros(N),
+               sh=np.zeros((N, K, 3)))
+    m = None if mask is None else _c(mask, np.int32)
+    lib().orc_render_grad(N, _p(mu), _p(sc), _p(q), _p(k), _p(sh), scene.sh_degree, len(cams), _p(cf), _p(wh),
+                          L["tile"][0], L["tile"][1], _p(oa), _p(L["tile_start"]), _p(L["sorted_g"]),
+                          _p(_c(L["tile_base"], np.int32)), _p(pb), _p(g_rgb), _p(g_T), _p(m),
+                          _p(out["mu"]), _p(out["scale"]), _p(out["quat"]), _p(out["kappa"]), _p(out["sh"]))
+    return out
+
+
+def tau(scene, g, o, d):
+    """Closed-form line integral of Gaussian g along o + t d (d unit) and the Supp. B
+    quantities: dict(tau, a, b, c, gamma, beta, gmax)."""
+    out = np.zeros(7, np.float64)
+    mu = _c(scene.mu[g], np.float64)
+    sc = _c(scene.scale[g], np.float64)
+    q = _c(scene.quat[g], np.float64)
+    lib().orc_tau(_p(mu), _p(sc), _p(q), float(scene.kappa[g]), _p(_c(o, np.float64)),
+                  _p(_c(d, np.float64)), _p(out))
+    return dict(zip(("tau", "a", "b", "c", "gamma", "beta", "gmax"), out.tolist()))
+
+
+def sh_basis(degree, direction):
+    out = np.zeros(16, np.float64)
+    lib().orc_sh_basis(degree, _p(_c(direction, np.float64)), _p(out))
+    return out[: (degree + 1) ** 2]
+
+
+# ------------------------------------------------------------------------------ tomography
+def tomo_keys(scene, beam, tau_cut=1e-6, tile=(16, 16)):
+    mu, sc, q, k, _ = _scene_arrays(scene)
+    A, N = len(beam.angles), scene.n
+    rect = np.zeros((A, N, 4), np.int32)
+    lib().orc_tomo_keys(N, _p(mu), _p(sc), _p(q), _p(k), A, _p(_c(beam.angles, np.float32)), beam.det_w,
+                        beam.det_h, beam.pitch_u, beam.pitch_v, beam.u0, beam.v0, tile[0], tile[1],
+                        np.float32(tau_cut), _p(rect))
+    return rect
+
+
+def tomo_lists(scene, beam, tau_cut=1e-6, tile=(16, 16)):
+    rect = tomo_keys(scene, beam, tau_cut, tile)
+    A = len(beam.angles)
+    tx = (beam.det_w + tile[0] - 1) // tile[0]
+    ty = (beam.det_h + tile[1] - 1) // tile[1]
+    txs = np.full(A, tx, np.int32)
+    base = (np.arange(A) * tx * ty).astype(np.int32)
+    ts, sg = bin(scene.n, A, None, rect, txs, base, A * tx * ty)
+    return dict(rect=rect, tile_start=ts, sorted_g=sg, tiles_x=tx, tiles_y=ty, n_tiles=A * tx * ty, tile=tile)
+
+
+def tomo(scene, beam, L=None, brute=False, mask=None, tau_cut=1e-6, tile=(16, 16)):
+    """Parallel-beam projection: returns (line_sum, proj = exp(-line_sum)), each [A, H, W]."""
+    if L is None and not brute:
+        L = tomo_lists(scene, beam, tau_cut, tile)
+    mu, sc, q, k, _ = _scene_arrays(scene, np.float64)
+    A = len(beam.angles)
+    ls = np.zeros((A, beam.det_h, beam.det_w))
+    pr = np.zeros((A, beam.det_h, beam.det_w))
+    ts = L["tile_start"] if L is not None else np.zeros(1, np.int64)
+    sg = L["sorted_g"] if L is not None else np.zeros(1, np.int32)
+    tl = L["tile"] if L is not None else tile
+    m = None if mask is None else _c(mask, np.int32)
+    lib().orc_tomo(scene.n, _p(mu), _p(sc), _p(q), _p(k), A, _p(_c(beam.angles, np.float32)), beam.det_w,
+                   beam.det_h, beam.pitch_u, beam.pitch_v, beam.u0, beam.v0, tl[0], tl[1], _p(ts), _p(sg),
+                   int(brute), _p(m), _p(ls), _p(pr))
+    return ls, pr
+
+
+def tomo_grad(scene, beam, L, dL_dproj, mask=None):
+    mu, sc, q, k, _ = _scene_arrays(scene, np.float64)
+    A, N = len(beam.angles), scene.n
+    out = dict(mu=np.zeros((N, 3)), scale=np.zeros((N, 3)), quat=np.zeros((N, 4)), kappa=np.zeros(N))
+    m = None if mask is None else _c(mask, np.int32)
+    lib().orc_tomo_grad(N, _p(mu), _p(sc), _p(q), _p(k), A, _p(_c(beam.angles, np.float32)), beam.det_w,
+                        beam.det_h, beam.pitch_u, beam.pitch_v, beam.u0, beam.v0, L["tile"][0], L["tile"][1],
+                        _p(L["tile_start"]), _p(L["sorted_g"]), _p(_c(dL_dproj, np.float64)), _p(m),
+                        _p(out["mu"]), _p(out["scale"]), _p(out["quat"]), _p(out["kappa"]))
+    return out

@@ -1,0 +1,74 @@
+/* FP64 CPU oracle for the volumetrically consistent Gaussian rasterizer
+ * (arXiv 2412.03378).  TEST INFRASTRUCTURE ONLY: this library exists to check the
+ * CUDA path.  Only the tests, the smoke check and the benchmark's CPU-baseline leg
+ * may load it; the product path never does.  It shares no code, header, table or
+ * constant with the CUDA library.
+ *
+ * Camera records are float[16] = { R[9] (row-major, world->camera), t[3], fx, fy, cx, cy }
+ * with integer sizes in cam_wh[2] = { width, height }.  A world point x maps to camera
+ * coordinates R x + t (OpenCV axes: x right, y down, z forward).
+ *
+ * The FP64 paths (render, gradient, tomography, tau) take double parameters so that
+ * finite differences can perturb them; the key functions take the FP32 values the GPU sees.
+ *
+ * Options are double[8] = { alpha_min, tau_cut, tau_max, T_stop, bg_r, bg_g, bg_b, z_near }.
+ */
+#ifndef VG_ORACLE_H
+#define VG_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Key function (tile rectangle and depth key) in FP32 with a fixed operation order. */
+int64_t orc_keys(int n, const float *mu, const float *scale, const float *quat, const float *kappa,
+                 int n_views, const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
+                 float z_near, float tau_cut, uint32_t *depth_bits, int32_t *rect);
+int64_t orc_tomo_keys(int n, const float *mu, const float *scale, const float *quat,
+                      const float *kappa, int n_angles, const float *angles, int det_w, int det_h,
+                      float pitch_u, float pitch_v, float u0, float v0, int tile_w, int tile_h,
+                      float tau_cut, int32_t *rect);
+/* Stable sort of (tile, depth, Gaussian) instances; fills tile_start[n_tiles+1], sorted_g. */
+int64_t orc_bin(int n, int n_views, const uint32_t *depth_bits, const int32_t *rect,
+                const int32_t *view_tiles_x, const int32_t *view_tile_base, int64_t n_tiles_total,
+                int64_t capacity, int64_t *tile_start, int32_t *sorted_g);
+
+void orc_sh_basis(int degree, const double *dir, double *out);
+void orc_tau(const double *mu, const double *scale, const double *quat, double kappa,
+             const double *o, const double *d, double *out /* tau, a, b, c, gamma, beta, gmax */);
+
+void orc_render(int n, const double *mu, const double *scale, const double *quat,
+                const double *kappa, const double *sh, int sh_degree, int n_views, const float *cam_f,
+                const int32_t *cam_wh, int tile_w, int tile_h, const double *opts,
+                const int64_t *tile_start, const int32_t *sorted_g, const int32_t *view_tile_base,
+                int brute, const uint32_t *depth_bits, const int32_t *rect,
+                const int64_t *pix_base, const int32_t *pix_mask, double *rgb, double *T_final,
+                int32_t *n_blend);
+
+void orc_render_grad(int n, const double *mu, const double *scale, const double *quat,
+                     const double *kappa, const double *sh, int sh_degree, int n_views,
+                     const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
+                     const double *opts, const int64_t *tile_start, const int32_t *sorted_g,
+                     const int32_t *view_tile_base, const int64_t *pix_base,
+                     const double *dL_drgb, const double *dL_dT, const int32_t *pix_mask,
+                     double *dmu, double *dscale, double *dquat, double *dkappa, double *dsh);
+
+void orc_tomo(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
+              int n_angles, const float *angles, int det_w, int det_h, float pitch_u,
+              float pitch_v, float u0, float v0, int tile_w, int tile_h,
+              const int64_t *tile_start, const int32_t *sorted_g, int brute,
+              const int32_t *pix_mask, double *line_sum, double *proj);
+
+void orc_tomo_grad(int n, const double *mu, const double *scale, const double *quat,
+                   const double *kappa, int n_angles, const float *angles, int det_w, int det_h,
+                   float pitch_u, float pitch_v, float u0, float v0, int tile_w, int tile_h,
+                   const int64_t *tile_start, const int32_t *sorted_g, const double *dL_dproj,
+                   const int32_t *pix_mask, double *dmu, double *dscale, double *dquat, double *dkappa);
+
+int orc_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

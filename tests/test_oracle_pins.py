@@ -1,0 +1,390 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each check uses an independent route (numerical quadrature, a library rotation,
+brute force, closed forms) so that a dropped term, a wrong sign or a transposed
+operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.spatial.transform import Rotation
+
+import oracle
+import synth
+
+
+# ----------------------------------------------------------------------------- helpers
+def rot(q):
+    w, x, y, z = np.asarray(q, np.float64)
+    return Rotation.from_quat([x, y, z, w]).as_matrix()      # scipy is scalar-last
+
+
+def cov_world(scene, g):
+    R = rot(scene.quat[g])
+    return R @ np.diag(np.asarray(scene.scale[g], np.float64) ** 2) @ R.T
+
+
+def mahal(x, mu, Sig):
+    d = np.asarray(x, np.float64) - mu
+    return float(d @ np.linalg.solve(Sig, d))
+
+
+def pixel_rays(cam):
+    """Unit world directions through pixel centres (the camera model, written out)."""
+    R = np.asarray(cam.R, np.float64)
+    t = np.asarray(cam.t, np.float64)
+    fx, fy, cx, cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))   # stored as float32
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    dc = np.stack([(xs + 0.5 - cx) / fx, (ys + 0.5 - cy) / fy, np.ones_like(xs, float)], -1)
+    d = dc @ R          # R^T dc for row vectors
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    return -R.T @ t, d
+
+
+def one_gaussian(mu, scale, quat, kappa, sh0=(0.0, 0.0, 0.0)):
+    return synth.Scene(np.array([mu], np.float32), np.array([scale], np.float32), np.array([quat], np.float32),
+                       np.array([kappa], np.float32), np.array([[sh0]], np.float32), 0)
+
+
+def concat(*scenes):
+    return synth.Scene(*(np.concatenate([getattr(s, f) for s in scenes]) for f in ("mu", "scale", "quat", "kappa", "sh")),
+                       scenes[0].sh_degree)
+
+
+def tau_all_pixels(scene, cam):
+    """Test-side closed form for every (pixel, Gaussian): kappa sqrt(2pi/a) exp(-(c-b^2/a)/2)."""
+    o, d = pixel_rays(cam)
+    out = np.zeros((scene.n,) + d.shape[:2])
+    for g in range(scene.n):
+        P = np.linalg.inv(cov_world(scene, g))
+        p = o - scene.mu[g].astype(np.float64)
+        a = np.einsum("hwi,ij,hwj->hw", d, P, d)
+        b = d @ (P @ p)
+        c = p @ P @ p
+        out[g] = scene.kappa[g] * np.sqrt(2 * np.pi / a) * np.exp(-0.5 * (c - b * b / a))
+    return out
+
+
+# ------------------------------------------------------------------ Eq. 19 and Supp. B
+@pytest.mark.parametrize("seed", range(8))
+def test_tau_closed_form_equals_line_integral(seed):
+    """Eq. 19 is the integral of kappa G(o + t d) over the whole line (Sec. 4.2, Supp. B)."""
+    rng = np.random.default_rng(seed)
+    scene = synth.uniform_scene(6, 700 + seed, log_scale=(-3.0, -1.0), flatten_frac=0.5)
+    for g in range(scene.n):
+        mu = scene.mu[g].astype(np.float64)
+        Sig = cov_world(scene, g)
+        o = mu + rng.normal(size=3) * 2.0 + np.array([0, 0, -3.0])
+        target = mu + rng.normal(size=3) * float(scene.scale[g].max())
+        d = (target - o) / np.linalg.norm(target - o)
+        # -log G along the ray is exactly quadratic in t: fit it from three points.
+        q = [mahal(o + t * d, mu, Sig) for t in (-1.0, 0.0, 1.0)]
+        A = 0.5 * (q[0] + q[2]) - q[1]
+        B = 0.5 * (q[2] - q[0])
+        t_star = -B / (2 * A)
+        beta_star = 1.0 / math.sqrt(A)
+        kap = float(scene.kappa[g])
+        f = lambda t: kap * math.exp(-0.5 * mahal(o + t * d, mu, Sig))
+        val, err = integrate.quad(f, t_star - 40 * beta_star, t_star + 40 * beta_star, points=[t_star],
+                                  epsabs=0.0, epsrel=1e-13, limit=400)
+        res = oracle.tau(scene, g, o, d)
+        assert res["tau"] == pytest.approx(val, rel=1e-10)
+        # Supp. B: the maximiser gamma, the width beta and the peak value G(o + gamma d)
+        assert res["gamma"] == pytest.approx(t_star, rel=1e-9, abs=1e-12)
+        assert res["beta"] == pytest.approx(beta_star, rel=1e-9)
+        assert res["gmax"] == pytest.approx(math.exp(-0.5 * mahal(o + t_star * d, mu, Sig)), rel=1e-9, abs=1e-300)
+
+
+def test_isotropic_alpha_is_analytic():
+    """Sigma = s^2 I: alpha = 1 - exp(-kappa sqrt(2 pi) s exp(-r^2 / 2 s^2)), r = ray-to-mean distance."""
+    s, kap = 0.1, 7.0
+    mu = np.array([0.05, -0.03, 0.2])
+    q = synth.random_unit_quats(np.random.default_rng(3), 1)[0]
+    for bg in [(0.0, 0.0, 0.0), (0.2, 0.7, 0.1)]:
+        scene = one_gaussian(mu, (s, s, s), q, kap, sh0=(0.0, 0.0, 0.0))
+        cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 32, 32, 20.0)
+        opts = dict(oracle.EXACT, bg=bg)
+        rgb, T, _ = oracle.render(scene, [cam], opts, brute=True)
+        o, d = pixel_rays(cam)
+        m32 = scene.mu[0].astype(np.float64)
+        pm = m32 - o
+        r2 = np.sum(pm * pm) - (d @ pm) ** 2
+        s32 = float(scene.scale[0, 0])                      # the stored (float32) scale
+        alpha = 1.0 - np.exp(-kap * math.sqrt(2 * math.pi) * s32 * np.exp(-r2 / (2 * s32 * s32)))
+        assert np.max(np.abs((1.0 - T[0]) - alpha)) < 1e-12
+        # a single Gaussian: C = c alpha + (1 - alpha) bg with c = 0.5 for zero SH coefficients
+        for ch in range(3):
+            assert np.max(np.abs(rgb[0][..., ch] - (0.5 * alpha + (1 - alpha) * bg[ch]))) < 1e-12
+
+
+# ------------------------------------------------------------------ Eq. 14 vs Eq. 1
+def _ray_march(scene, cam, t_lo, t_hi, n):
+    """Supp. A: march Eq. 1 with sigma(x) = sum kappa_i G_i, c(x) = sum kappa_i c_i G_i / sigma."""
+    o, d = pixel_rays(cam)
+    d = d.reshape(-1, 3)
+    dt = (t_hi - t_lo) / n
+    ts = t_lo + (np.arange(n) + 0.5) * dt
+    Y00 = oracle.sh_basis(0, np.array([0.0, 0.0, 1.0]))[0]
+    col = np.clip(scene.sh[:, 0, :].astype(np.float64) * Y00 + 0.5, 0, None)
+    out = np.zeros((d.shape[0], 3))
+    for r in range(d.shape[0]):
+        x = o[None, :] + ts[:, None] * d[r][None, :]
+        sig = np.zeros(n)
+        csum = np.zeros((n, 3))
+        for g in range(scene.n):
+            P = np.linalg.inv(cov_world(scene, g))
+            dx = x - scene.mu[g].astype(np.float64)
+            Gv = scene.kappa[g] * np.exp(-0.5 * np.einsum("ni,ij,nj->n", dx, P, dx))
+            sig += Gv
+            csum += Gv[:, None] * col[g][None, :]
+        cx = csum / np.maximum(sig, 1e-300)[:, None]
+        tau = sig * dt
+        T = np.exp(-np.concatenate([[0.0], np.cumsum(tau)[:-1]]))
+        out[r] = np.sum((T * (1.0 - np.exp(-tau)))[:, None] * cx, axis=0)
+    return out.reshape(cam.height, cam.width, 3)
+
+
+def test_blend_equals_volume_rendering_without_overlap():
+    """Sorted, non-overlapping Gaussians: the Eq. 14 blend equals the ray-marched Eq. 1
+    (Supp. A, rows 1-2); with heavy overlap it does not (row 3)."""
+    q = synth.random_unit_quats(np.random.default_rng(5), 3)
+    sep = concat(one_gaussian((0.01, 0.0, -1.0), (0.08, 0.06, 0.1), q[0], 3.0, (1.0, -0.5, 0.2)),
+                 one_gaussian((-0.02, 0.01, 0.0), (0.07, 0.09, 0.05), q[1], 6.0, (-0.4, 0.9, 0.3)),
+                 one_gaussian((0.0, -0.01, 1.0), (0.1, 0.08, 0.09), q[2], 1.5, (0.3, 0.3, -0.8)))
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 6, 6, 4.0)
+    rgb, _, _ = oracle.render(sep, [cam], oracle.EXACT, brute=True)
+    ref = _ray_march(sep, cam, 1.0, 7.0, 120000)
+    assert np.max(np.abs(rgb[0] - ref)) < 2e-6
+    ovl = concat(one_gaussian((0.0, 0.0, 0.0), (0.1, 0.1, 0.1), q[0], 4.0, (1.0, -0.5, 0.2)),
+                 one_gaussian((0.0, 0.0, 0.02), (0.1, 0.1, 0.1), q[1], 4.0, (-0.4, 0.9, 0.3)))
+    rgb2, _, _ = oracle.render(ovl, [cam], oracle.EXACT, brute=True)
+    ref2 = _ray_march(ovl, cam, 2.0, 6.0, 60000)
+    assert np.max(np.abs(rgb2[0] - ref2)) > 1e-2
+
+
+def test_transmittance_is_monotone_and_bounded():
+    scene, cams = synth.config1(0.25)
+    rgb, T, _ = oracle.render(scene, cams, oracle.EXACT, brute=True)
+    assert np.all(T[0] >= 0) and np.all(T[0] <= 1)
+    # removing Gaussians can only raise the transmittance (each one multiplies T by e^-tau <= 1)
+    sub = scene.subset(np.arange(0, scene.n, 2))
+    _, Ts, _ = oracle.render(sub, cams, oracle.EXACT, brute=True)
+    assert np.all(T[0] <= Ts[0] * (1 + 1e-12))
+    assert np.all(rgb[0] >= 0)
+
+
+# ------------------------------------------------------------------ footprint and sort
+@pytest.mark.parametrize("mode", ["compat", "exact"])
+def test_footprint_is_conservative(mode):
+    """Every (pixel, Gaussian) pair with tau >= tau_cut lies in the pixel's tile list
+    (brute force over all pairs of the 2,000-Gaussian 128x128 scene)."""
+    opts = oracle.COMPAT if mode == "compat" else oracle.EXACT
+    scene, cams = synth.config1()
+    cam = cams[0]
+    L = oracle.lists(scene, cams, opts)
+    tau = tau_all_pixels(scene, cam)
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    tile = (ys // 16) * L["tiles_x"][0] + xs // 16
+    member = np.zeros((scene.n, L["n_tiles"]), bool)
+    for t in range(L["n_tiles"]):
+        member[L["sorted_g"][L["tile_start"][t]:L["tile_start"][t + 1]], t] = True
+    zc = (scene.mu.astype(np.float64) @ np.asarray(cam.R, np.float64).T + cam.t)[:, 2]
+    need = (tau >= opts["tau_cut"]) & (zc > opts["z_near"])[:, None, None]
+    g_idx, py, px = np.nonzero(need)
+    assert g_idx.size > 1000
+    missing = ~member[g_idx, tile[py, px]]
+    assert missing.sum() == 0
+    # and the blend over tile lists equals the blend over all Gaussians up to truncation
+    rgb, T, _ = oracle.render(scene, cams, opts, L)
+    rgbb, Tb, _ = oracle.render(scene, cams, opts, L, brute=True)
+    bound = 0.0 if mode == "compat" else opts["tau_cut"] * scene.n
+    assert np.max(np.abs(rgb[0] - rgbb[0])) <= bound + 1e-15
+
+
+def test_sort_order_and_depth_keys():
+    scene, cams = synth.config1(0.5)
+    cams = cams + synth.small_views(2, 0, [(40, 24), (33, 17)])
+    L = oracle.lists(scene, cams, oracle.COMPAT)
+    inst = []
+    for v in range(len(cams)):
+        for g in range(scene.n):
+            r = L["rect"][v, g]
+            if r[0] < 0:
+                continue
+            for ty in range(r[1], r[3] + 1):
+                for tx in range(r[0], r[2] + 1):
+                    inst.append((int(L["tile_base"][v] + ty * L["tiles_x"][v] + tx), int(L["depth"][v, g]), g))
+    inst.sort()
+    assert np.array_equal(np.array([i[2] for i in inst], np.int32), L["sorted_g"])
+    counts = np.bincount(np.array([i[0] for i in inst]), minlength=L["n_tiles"])
+    assert np.array_equal(np.diff(L["tile_start"]), counts)
+    # depth key = FP32 view-space z of the mean, within one ulp of the FP64 value
+    for v, cam in enumerate(cams):
+        z = (scene.mu.astype(np.float64) @ np.asarray(cam.R, np.float64).T + cam.t.astype(np.float64))[:, 2]
+        ok = L["depth"][v] != 0xFFFFFFFF
+        zf = L["depth"][v][ok].view(np.float32).astype(np.float64)
+        assert np.all(np.abs(zf - z[ok]) <= 2 * np.spacing(np.float32(z[ok]).astype(np.float32)))
+        assert np.all(z[~ok] <= 0.2 + 1e-6)
+
+
+def test_invalid_and_behind_camera_are_culled():
+    q = [1.0, 0.0, 0.0, 0.0]
+    bad = [one_gaussian((0, 0, 0), (0.1, 0.1, 0.1), q, float("nan")),
+           one_gaussian((0, 0, 0), (0.1, -0.1, 0.1), q, 1.0),
+           one_gaussian((0, 0, 0), (0.1, 0.1, 0.1), [0, 0, 0, 0], 1.0),
+           one_gaussian((0, 0, 0), (0.1, 0.1, 0.1), q, 0.0),
+           one_gaussian((0, 0, -4.1), (0.1, 0.1, 0.1), q, 1.0),         # behind the camera
+           one_gaussian((0, 0, float("inf")), (0.1, 0.1, 0.1), q, 1.0)]
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 16, 16, 60.0)
+    for sc in bad:
+        depth, rect = oracle.keys(sc, [cam], oracle.COMPAT)
+        assert rect[0, 0, 0] == -1
+    # an empty scene renders the background with T = 1
+    empty = synth.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.zeros((0, 4), np.float32),
+                        np.zeros(0, np.float32), np.zeros((0, 1, 3), np.float32), 0)
+    rgb, T, _ = oracle.render(empty, [cam], dict(oracle.EXACT, bg=(0.1, 0.2, 0.3)))
+    assert np.all(T[0] == 1.0) and np.allclose(rgb[0], [0.1, 0.2, 0.3])
+
+
+# ------------------------------------------------------------------ Fig. 2 properties
+def test_opacity_grows_with_density_and_depth_scale():
+    """Sec. 4.3 / Fig. 2: alpha rises with kappa and with the scale along the ray; tau is
+    linear in kappa."""
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 8, 8, 10.0)
+    o, d = pixel_rays(cam)
+    centre = d[4, 4]
+    prev = -1.0
+    for kap in [0.5, 1.0, 2.0, 4.0, 8.0]:
+        sc = one_gaussian((0, 0, 0), (0.05, 0.05, 0.05), [1, 0, 0, 0], kap)
+        t1 = oracle.tau(sc, 0, o, centre)["tau"]
+        assert t1 > prev
+        t2 = oracle.tau(one_gaussian((0, 0, 0), (0.05, 0.05, 0.05), [1, 0, 0, 0], 2 * kap), 0, o, centre)["tau"]
+        assert t2 == pytest.approx(2 * t1, rel=1e-14)
+        prev = t1
+    prev = -1.0
+    for sz in [0.01, 0.03, 0.1, 0.3]:                     # scale along the optical axis (world z)
+        sc = one_gaussian((0, 0, 0), (0.05, 0.05, sz), [1, 0, 0, 0], 3.0)
+        a = 1 - math.exp(-oracle.tau(sc, 0, o, centre)["tau"])
+        assert a > prev
+        prev = a
+
+
+def test_sh_basis_is_orthonormal():
+    """Real spherical harmonics to degree 3: Gram matrix over the sphere is the identity
+    (Gauss-Legendre in cos(theta) times a uniform grid in phi, exact for these degrees)."""
+    xg, wg = np.polynomial.legendre.leggauss(12)
+    phis = np.arange(24) * 2 * np.pi / 24
+    Gm = np.zeros((16, 16))
+    for zc, w in zip(xg, wg):
+        r = math.sqrt(1 - zc * zc)
+        for ph in phis:
+            Y = oracle.sh_basis(3, np.array([r * math.cos(ph), r * math.sin(ph), zc]))
+            Gm += w * (2 * np.pi / 24) * np.outer(Y, Y)
+    assert np.max(np.abs(Gm - np.eye(16))) < 1e-12
+    # the degree-1 block is proportional to (-y, z, -x)
+    Y = oracle.sh_basis(1, np.array([0.0, 0.0, 1.0]))
+    assert Y[2] > 0 and abs(Y[1]) < 1e-15 and abs(Y[3]) < 1e-15
+    Y = oracle.sh_basis(1, np.array([1.0, 0.0, 0.0]))
+    assert Y[3] < 0
+
+
+# ------------------------------------------------------------------ gradients
+def _fd_check(f, x, g_an, idx, h_rel=1e-5, rtol=1e-6):
+    scale = max(1e-300, float(np.max(np.abs(g_an))))
+    for i in idx:
+        x0 = x.flat[i]
+        h = h_rel * max(1.0, abs(x0))
+        x.flat[i] = x0 + h
+        fp = f()
+        x.flat[i] = x0 - h
+        fm = f()
+        x.flat[i] = x0
+        fd = (fp - fm) / (2 * h)
+        den = max(abs(fd), 1e-3 * scale)
+        assert abs(fd - g_an.flat[i]) / den < rtol, (i, fd, g_an.flat[i])
+
+
+@pytest.mark.parametrize("variant", ["exact", "clamped"])
+def test_render_gradient_matches_finite_differences(variant):
+    """Analytic FP64 gradient of the blend (tile lists held fixed) vs central differences."""
+    rng = np.random.default_rng(11)
+    scene = synth.uniform_scene(9, 321, log_scale=(-2.5, -1.5), kappa=(0.5, 6.0), sh_degree=3, sh_std=0.3,
+                                flatten_frac=0.3, extent=0.4)
+    scene = synth.Scene(*(np.asarray(getattr(scene, f), np.float64) for f in ("mu", "scale", "quat", "kappa", "sh")),
+                        3)
+    scene.quat = scene.quat * rng.uniform(0.7, 1.3, (scene.n, 1))   # unnormalised input quaternions
+    cams = synth.small_views(2, 0, [(20, 18), (17, 23)])
+    opts = dict(oracle.EXACT, bg=(0.3, 0.1, 0.6))
+    if variant == "clamped":
+        opts["tau_max"] = 1.2
+    L = oracle.lists(scene, cams, opts)
+    wr = [rng.normal(size=(c.height, c.width, 3)) for c in cams]
+    wT = [rng.normal(size=(c.height, c.width)) for c in cams]
+
+    def loss():
+        rgb, T, _ = oracle.render(scene, cams, opts, L)
+        return sum(float(np.sum(a * b)) for a, b in zip(rgb, wr)) + sum(float(np.sum(a * b)) for a, b in zip(T, wT))
+
+    g = oracle.render_grad(scene, cams, opts, L, wr, wT)
+    for name, arr in (("mu", scene.mu), ("scale", scene.scale), ("quat", scene.quat), ("kappa", scene.kappa),
+                      ("sh", scene.sh)):
+        idx = range(arr.size) if arr.size <= 40 else rng.choice(arr.size, 40, replace=False)
+        assert np.max(np.abs(g[name])) > 0, name
+        _fd_check(loss, arr, g[name], idx, rtol=2e-6)
+
+
+# ------------------------------------------------------------------ tomography (Eq. 21)
+def test_tomography_detector_integral_and_marginal():
+    """Parallel beam: the detector integral of the line integrals of one Gaussian is
+    kappa (2 pi)^(3/2) sqrt(det Sigma); each pixel equals the 2D marginal Gaussian."""
+    q = synth.random_unit_quats(np.random.default_rng(9), 1)[0]
+    s = np.array([0.06, 0.045, 0.07])
+    kap = 3.0
+    g = one_gaussian((0.03, -0.02, 0.05), s, q, kap)
+    beam = synth.parallel_beam(3, det=96, extent=2.0, angles=np.array([0.0, 0.7, 2.9]))
+    ls, proj = oracle.tomo(g, beam, brute=True)
+    want = kap * (2 * np.pi) ** 1.5 * float(np.prod(g.scale[0].astype(np.float64)))
+    Sig = cov_world(g, 0)
+    mu = g.mu[0].astype(np.float64)
+    for a, th in enumerate(beam.angles.astype(np.float64)):
+        assert float(ls[a].sum()) * beam.pitch_u * beam.pitch_v == pytest.approx(want, rel=1e-9)
+        assert np.allclose(proj[a], np.exp(-ls[a]), rtol=1e-15, atol=0)
+        E = np.array([[-math.sin(th), 0.0], [math.cos(th), 0.0], [0.0, 1.0]])
+        S2 = E.T @ Sig @ E
+        u = beam.u0 + (np.arange(beam.det_w) + 0.5) * beam.pitch_u
+        v = beam.v0 + (np.arange(beam.det_h) + 0.5) * beam.pitch_v
+        D = np.stack(np.meshgrid(u, v), -1) - (E.T @ mu)
+        amp = want / (2 * np.pi * math.sqrt(np.linalg.det(S2)))
+        ref = amp * np.exp(-0.5 * np.einsum("hwi,ij,hwj->hw", D, np.linalg.inv(S2), D))
+        assert np.max(np.abs(ls[a] - ref)) <= 1e-10 * ref.max()
+
+
+def test_tomography_order_independent_and_tiled():
+    scene, beam, _ = synth.config4(frac=0.002, n_angles=3, det=64)
+    L = oracle.tomo_lists(scene, beam)
+    ls, _ = oracle.tomo(scene, beam, L)
+    perm = np.random.default_rng(1).permutation(scene.n)
+    ls2, _ = oracle.tomo(scene.subset(perm), beam)
+    assert np.max(np.abs(ls - ls2)) <= 1e-12 * max(1.0, ls.max())
+    lsb, _ = oracle.tomo(scene, beam, brute=True)
+    assert np.max(np.abs(ls - lsb)) <= 1e-6 * scene.n
+
+
+def test_tomography_gradient_matches_finite_differences():
+    rng = np.random.default_rng(4)
+    scene = synth.tomo_scene(7, 77, log_scale=(-2.5, -1.8))
+    scene = synth.Scene(*(np.asarray(getattr(scene, f), np.float64) for f in ("mu", "scale", "quat", "kappa", "sh")), 0)
+    beam = synth.parallel_beam(2, det=24, extent=2.4)
+    L = oracle.tomo_lists(scene, beam)
+    w = rng.normal(size=(2, 24, 24))
+
+    def loss():
+        _, pr = oracle.tomo(scene, beam, L)
+        return float(np.sum(pr * w))
+
+    g = oracle.tomo_grad(scene, beam, L, w)
+    for name, arr in (("mu", scene.mu), ("scale", scene.scale), ("quat", scene.quat), ("kappa", scene.kappa)):
+        assert np.max(np.abs(g[name])) > 0
+        _fd_check(loss, arr, g[name], range(arr.size), rtol=2e-6)
