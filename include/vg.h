@@ -1,0 +1,200 @@
+/* vg.h — C ABI of the volumetric Gaussian rasterizer (arXiv 2412.03378, "Volumetrically
+ * Consistent 3D Gaussian Rasterization") for NVIDIA GB300 (sm_103a).
+ *
+ * The library renders a mixture of 3D Gaussians sigma(x) = sum_i kappa_i G_i(x) (Sec. 3.2,
+ * Eq. 3-4) by front-to-back alpha blending (Sec. 4.1, Eq. 14) of per-Gaussian opacities
+ * that are the exact line integral of each Gaussian along the pixel ray (Sec. 4.2, Eq. 19):
+ *
+ *     tau_i = kappa_i sqrt(2 pi / a) exp(-(c - b^2 / a) / 2),   alpha_i = 1 - exp(-tau_i),
+ *     a = d' P d,  b = d' P (o - mu),  c = (o - mu)' P (o - mu),  P = Sigma^-1,
+ *
+ * with o the camera centre and d the unit direction through the pixel centre.  A tomography
+ * mode (Sec. 6.2, Eq. 21) sums the same line integrals along parallel-beam rays and returns
+ * exp(-sum).  All work runs in this library's CUDA kernels; the calls only marshal arguments.
+ *
+ * Conventions shared by every call
+ *  - Pointers named in vg_gaussians, image buffers and gradient buffers are DEVICE pointers
+ *    owned by the caller.  Camera, beam-angle and option structs are HOST memory, read
+ *    during the call only.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *    default stream) unless its comment says it synchronises.
+ *  - Every call returns a vg_status and never aborts.  On failure vg_last_error() gives a
+ *    one-line message.  Device-side failures are latched and reported by the next call.
+ *  - A workspace is not thread-safe; separate workspaces are independent.
+ *  - Gradient outputs are ACCUMULATED (+=); the caller zeroes them first.
+ */
+#ifndef VG_H
+#define VG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VG_OK = 0,
+    VG_ERR_INVALID_ARG = 1,   /* a null pointer, a negative size, an unsupported layout       */
+    VG_ERR_CUDA = 2,          /* a CUDA runtime call failed                                   */
+    VG_ERR_OOM = 3,           /* device memory for the workspace could not be allocated       */
+    VG_ERR_CAPACITY = 4,      /* fixed-capacity mode: more tile instances than reserved       */
+    VG_ERR_TIMEOUT = 5,       /* a bounded device wait gave up                                */
+    VG_ERR_UNSUPPORTED = 6,   /* a valid request this build does not implement                */
+    VG_ERR_STATE = 7          /* calls out of order (e.g. render before bin_sort)             */
+} vg_status;
+
+typedef enum { VG_F32 = 0, VG_BF16 = 1, VG_F16 = 2 } vg_dtype;
+
+/* Gaussian parameters (Sec. 3.2, Eq. 3-4; Sec. 5 for the colour model), structure of
+ * arrays, row-major, device memory:
+ *   mu    [n][3]  means (world)                           rec_dtype
+ *   scale [n][3]  per-axis standard deviations, > 0       rec_dtype
+ *   quat  [n][4]  rotation quaternions (w, x, y, z), normalised inside      rec_dtype
+ *   kappa [n]     densities kappa >= 0                    rec_dtype
+ *   sh    [n][K][3] real spherical-harmonic colour coefficients, K = (sh_degree+1)^2,
+ *                 colour = max(sum_k sh_k Y_k(dir) + 0.5, 0), dir = (mu - o)/|mu - o|
+ *                                                          sh_dtype (may be NULL in tomography)
+ * Gaussians with a non-finite parameter, a non-positive scale, a zero quaternion or
+ * kappa <= 0 are culled (counted in vg_stats.n_culled), never an error. */
+typedef struct {
+    const void *mu, *scale, *quat, *kappa, *sh;
+    int32_t rec_dtype;   /* vg_dtype of mu, scale, quat, kappa */
+    int32_t sh_dtype;    /* vg_dtype of sh */
+    int32_t n;
+    int32_t sh_degree;   /* 0..3 */
+} vg_gaussians;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  A world point x maps to
+ * camera coordinates R x + t; pixel (i, j) has its centre ray through
+ * ((i + 0.5 - cx)/fx, (j + 0.5 - cy)/fy, 1) in camera coordinates (Sec. 4.1: the ray
+ * passes through the pixel centre). */
+typedef struct {
+    float R[9];          /* row-major world->camera rotation */
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} vg_camera;
+
+/* Parallel-beam tomography geometry.  Rotation axis is world z; for angle theta the rays
+ * run along d = (cos theta, sin theta, 0) and detector pixel (i, j) sits at
+ * u = u0 + (i + 0.5) pitch_u along (-sin theta, cos theta, 0) and v = v0 + (j + 0.5) pitch_v
+ * along (0, 0, 1).  `angles` is a HOST array of n_angles radians. */
+typedef struct {
+    int32_t n_angles;
+    const float *angles;
+    int32_t det_w, det_h;
+    float pitch_u, pitch_v, u0, v0;
+} vg_beam;
+
+/* Blend options.  The paper swaps only the alpha of 3DGS (Sec. 5); thresholds follow the
+ * 3DGS conventions when enabled:
+ *   alpha_min  contributions with alpha < alpha_min are skipped (0: none skipped);
+ *   tau_cut    tile footprints cover every pixel where tau >= tau_cut may hold (> 0);
+ *   tau_max    tau is clamped to tau_max, i.e. alpha <= 1 - exp(-tau_max) (INFINITY: none);
+ *   T_stop     a pixel stops once its transmittance falls below T_stop (0: never);
+ *   bg         background colour added with the final transmittance;
+ *   z_near     Gaussians whose mean has camera z <= z_near are culled. */
+typedef struct {
+    float alpha_min, tau_cut, tau_max, T_stop;
+    float bg[3];
+    float z_near;
+    uint32_t flags;      /* VG_FLAG_* */
+} vg_opts;
+
+#define VG_FLAG_FIXED_CAPACITY 1u  /* never synchronise to read the instance count; fail with
+                                      VG_ERR_CAPACITY beyond the reserved capacity        */
+#define VG_FLAG_COUNT_PAIRS 2u     /* render_fwd also counts evaluated (pixel, Gaussian)
+                                      pairs into vg_stats.n_pairs (slower; for roofline) */
+
+typedef struct {
+    int64_t n_items;          /* views x Gaussians of the last preprocess                    */
+    int64_t n_visible;        /* items with a non-empty footprint                           */
+    int64_t n_culled;         /* invalid parameters or behind z_near                        */
+    int64_t n_instances;      /* (tile, item) instances of the last bin_sort                 */
+    int64_t n_tiles;          /* tiles over all views                                       */
+    int64_t n_pixels;         /* pixels over all views                                      */
+    int64_t instance_capacity;
+    int64_t n_pairs;          /* evaluated pairs of the last counted render_fwd              */
+    int64_t launches;         /* kernels launched by this workspace since creation          */
+    int64_t device_bytes;     /* device memory held by the workspace                        */
+} vg_stats;
+
+typedef struct vg_workspace vg_workspace;
+
+/* Create / destroy a workspace: library-owned device scratch (records, keys, sort buffers,
+ * per-pixel replay state, gradient intermediates).  Buffers grow on demand unless
+ * VG_FLAG_FIXED_CAPACITY is set.  Destroy synchronises the device. */
+vg_status vg_workspace_create(vg_workspace **ws);
+vg_status vg_workspace_destroy(vg_workspace *ws);
+
+/* Pre-size the workspace (synchronous): n_items = views x Gaussians, n_instances = tile
+ * instances, n_pixels and n_tiles over all views.  Needed before fixed-capacity use. */
+vg_status vg_workspace_reserve(vg_workspace *ws, int64_t n_items, int64_t n_instances,
+                               int64_t n_pixels, int64_t n_tiles);
+
+/* Per-(view, Gaussian) set-up (Sec. 5: the rasterizer's per-primitive phase, whose 3D
+ * inverse covariances the paper notes are its extra cost, Supp. F).  For each item it
+ * computes the depth key (camera z of the mean, FP32), the conservative tile rectangle of
+ * the ellipsoid (x - mu)' P (x - mu) <= k^2 that bounds every pixel with tau >= tau_cut,
+ * the view-dependent colour from spherical harmonics, and the blend record (whitening of
+ * Sigma relative to the pixel grid).  `cams` holds n_views host structs; views are
+ * rendered into one concatenated image buffer in view order. */
+vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams,
+                        int32_t n_views, const vg_opts *opts, void *stream);
+
+/* Tile binning and depth sort (Sec. 7: per-tile sorting of primitives front to back).
+ * Emits one instance per (tile, item) the footprint covers and sorts instances by
+ * (tile, depth key, Gaussian index) with a stable on-device radix sort.  Synchronises once
+ * to read the instance count unless VG_FLAG_FIXED_CAPACITY is set. */
+vg_status vg_bin_sort(vg_workspace *ws, void *stream);
+
+/* Front-to-back blend (Sec. 4.1, Eq. 14 with the Eq. 19 alpha).  Outputs, device memory:
+ *   rgb     [sum_v H_v W_v][3] float32, views concatenated, row-major pixels
+ *   T_final [sum_v H_v W_v]    float32 final transmittance (may be NULL)
+ * The workspace keeps per-pixel replay state (blended count, log-transmittance) for
+ * vg_render_bwd. */
+vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stream);
+
+/* Backward of the last vg_render_fwd on this workspace (derived from Eq. 14 and Eq. 19 by
+ * the chain rule; the forward is replayed back to front, nothing per pair is stored).
+ *   dL_drgb [pixels][3] float32, dL_dT [pixels] float32 or NULL.
+ * Accumulates into float32 device buffers shaped like the inputs of vg_preprocess:
+ *   dmu [n][3], dscale [n][3], dquat [n][4] (w.r.t. the unnormalised input), dkappa [n],
+ *   dsh [n][K][3] (may be NULL to skip colour gradients). */
+vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_dT,
+                        float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh,
+                        void *stream);
+
+/* Tomography (Sec. 6.2, Eq. 21): for every angle and detector pixel,
+ *   proj[a][j][i] = exp(-sum_g tau_g(ray)),  float32 device buffer [n_angles][det_h][det_w].
+ * If dL_dproj is not NULL it also runs the backward and accumulates dmu, dscale, dquat,
+ * dkappa (float32, shaped as above).  Colour coefficients are ignored.  Only
+ * opts->tau_cut and opts->flags are used. */
+vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam *beam,
+                          const vg_opts *opts, float *proj, const float *dL_dproj, float *dmu,
+                          float *dscale, float *dquat, float *dkappa, void *stream);
+
+/* L2 image loss helper for training steps: loss = scale * sum_i (x_i - y_i)^2 written to the
+ * device scalar *loss (overwritten), grad_i = 2 scale (x_i - y_i) (overwritten). */
+vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n, float scale,
+                     float *loss, float *grad, void *stream);
+
+/* Statistics of the last calls (synchronises the stream). */
+vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream);
+
+/* Diagnostic read-backs of the last preprocess / bin_sort into HOST buffers (synchronous):
+ *   depth_bits [n_items] uint32 (0xFFFFFFFF for culled items), rect [n_items][4] int32
+ *   (tile x0, y0, x1, y1 inclusive; -1 when culled); tile_start [n_tiles + 1] int64 and
+ *   sorted_item [n_instances] int32 (item = view * n + Gaussian). */
+vg_status vg_read_keys(vg_workspace *ws, uint32_t *depth_bits, int32_t *rect);
+vg_status vg_read_bins(vg_workspace *ws, int64_t *tile_start, int32_t *sorted_item);
+
+/* Message of the last failure on this workspace ("" if none).  ws may be NULL for
+ * failures of vg_workspace_create. */
+const char *vg_last_error(const vg_workspace *ws);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VG_H */

@@ -1,0 +1,491 @@
+// C ABI of the rasterizer: workspace management, argument validation and the order of
+// kernel launches for each entry point declared in include/vg.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vg_internal.cuh"
+
+using namespace vg;
+
+namespace {
+
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct vg_workspace {
+    std::string err;
+    int stage = 0;   // 0 empty, 1 preprocessed, 2 binned, 3 rendered
+    GaussIn g{};
+    vg_opts opts{};
+    BlendParams bp{};
+    int n_views = 0;
+    std::vector<ViewInfo> views_h;
+    std::vector<int> tile_view_h;
+    long long n_items = 0, n_tiles = 0, n_pixels = 0, n_inst = 0;
+    long long capacity = 0;
+    long long launches = 0;
+    bool views_valid = false;
+
+    DBuf<ViewInfo> views;
+    DBuf<int> tile_view;
+    DBuf<float4> rec;
+    DBuf<uint32_t> depth, count, offsets;
+    DBuf<short4> rect;
+    DBuf<uint32_t> skey[2], sval[2];
+    DBuf<uint32_t> ikey[2], ival[2];
+    uint32_t *perm = nullptr;          // items in depth order (points into sval)
+    uint32_t *inst_key = nullptr;      // sorted instance tile keys
+    uint32_t *inst_item = nullptr;     // sorted instance items
+    DBuf<uint2> ranges;
+    DBuf<float> S_fin, T_fin;
+    DBuf<uint32_t> nlast;
+    DBuf<float> grad;
+    DBuf<uint32_t> hist, scan_tmp;
+    DBuf<unsigned long long> counters;   // [0] visible items, [1] evaluated pairs
+    DBuf<float> tomo_cs;
+    uint32_t *h_total = nullptr;         // pinned
+};
+
+namespace {
+
+vg_status fail(vg_workspace *ws, vg_status s, const std::string &msg) {
+    if (ws) ws->err = msg;
+    return s;
+}
+
+#define VG_CUDA(ws, call)                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ws, VG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+vg_status ensure(vg_workspace *ws, DBuf<T> &b, size_t n, const char *what) {
+    if (n == 0) n = 1;
+    if (b.p && b.n >= n) return VG_OK;
+    if (b.p && (ws->opts.flags & VG_FLAG_FIXED_CAPACITY))
+        return fail(ws, VG_ERR_CAPACITY, std::string("fixed-capacity workspace too small for ") + what);
+    size_t nn = std::max(n, b.n + b.n / 4);
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.n = 0;
+        if (e != cudaSuccess) return fail(ws, VG_ERR_CUDA, std::string("cudaFree: ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMalloc((void **)&b.p, nn * sizeof(T));
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        (void)cudaGetLastError();
+        return fail(ws, VG_ERR_OOM, std::string("cudaMalloc for ") + what + ": " + cudaGetErrorString(e));
+    }
+    b.n = nn;
+    return VG_OK;
+}
+
+#define VG_TRY(x)                          \
+    do {                                   \
+        vg_status s_ = (x);                \
+        if (s_ != VG_OK) return s_;        \
+    } while (0)
+
+template <typename T>
+void release(DBuf<T> &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+}
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
+
+int bits_for(long long n) {
+    int b = 1;
+    while (b < 32 && (1LL << b) < n) ++b;
+    return b;
+}
+
+vg_status check_gauss(vg_workspace *ws, const vg_gaussians *g, bool need_sh) {
+    if (!g) return fail(ws, VG_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0) return fail(ws, VG_ERR_INVALID_ARG, "negative Gaussian count");
+    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ws, VG_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (g->rec_dtype < VG_F32 || g->rec_dtype > VG_F16 || g->sh_dtype < VG_F32 || g->sh_dtype > VG_F16)
+        return fail(ws, VG_ERR_INVALID_ARG, "unknown dtype");
+    if (g->n > 0 && (!g->mu || !g->scale || !g->quat || !g->kappa || (need_sh && !g->sh)))
+        return fail(ws, VG_ERR_INVALID_ARG, "a Gaussian parameter pointer is NULL");
+    return VG_OK;
+}
+
+GaussIn to_in(const vg_gaussians *g) {
+    GaussIn r;
+    r.mu = g->mu;
+    r.scale = g->scale;
+    r.quat = g->quat;
+    r.kappa = g->kappa;
+    r.sh = g->sh;
+    r.rec_dtype = g->rec_dtype;
+    r.sh_dtype = g->sh_dtype;
+    r.n = g->n;
+    r.sh_degree = g->sh_degree;
+    return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vg_last_error(const vg_workspace *ws) {
+    static const char *none = "";
+    static const char *nows = "workspace is NULL or could not be created";
+    if (!ws) return nows;
+    return ws->err.empty() ? none : ws->err.c_str();
+}
+
+vg_status vg_workspace_create(vg_workspace **out) {
+    if (!out) return VG_ERR_INVALID_ARG;
+    *out = nullptr;
+    vg_workspace *ws = new (std::nothrow) vg_workspace();
+    if (!ws) return VG_ERR_OOM;
+    cudaError_t e = cudaMallocHost((void **)&ws->h_total, 64);
+    if (e != cudaSuccess) {
+        delete ws;
+        return VG_ERR_CUDA;
+    }
+    e = cudaMalloc((void **)&ws->counters.p, 8 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFreeHost(ws->h_total);
+        delete ws;
+        return VG_ERR_OOM;
+    }
+    ws->counters.n = 8;
+    cudaMemset(ws->counters.p, 0, 8 * sizeof(unsigned long long));
+    *out = ws;
+    return VG_OK;
+}
+
+vg_status vg_workspace_destroy(vg_workspace *ws) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    release(ws->views);
+    release(ws->tile_view);
+    release(ws->rec);
+    release(ws->depth);
+    release(ws->count);
+    release(ws->offsets);
+    release(ws->rect);
+    for (int k = 0; k < 2; ++k) {
+        release(ws->skey[k]);
+        release(ws->sval[k]);
+        release(ws->ikey[k]);
+        release(ws->ival[k]);
+    }
+    release(ws->ranges);
+    release(ws->S_fin);
+    release(ws->T_fin);
+    release(ws->nlast);
+    release(ws->grad);
+    release(ws->hist);
+    release(ws->scan_tmp);
+    release(ws->counters);
+    release(ws->tomo_cs);
+    if (ws->h_total) cudaFreeHost(ws->h_total);
+    delete ws;
+    return VG_OK;
+}
+
+static vg_status reserve_items(vg_workspace *ws, long long n_items) {
+    VG_TRY(ensure(ws, ws->rec, (size_t)n_items * kRecF4, "records"));
+    VG_TRY(ensure(ws, ws->depth, (size_t)n_items, "depth keys"));
+    VG_TRY(ensure(ws, ws->count, (size_t)n_items, "tile counts"));
+    VG_TRY(ensure(ws, ws->rect, (size_t)n_items, "tile rectangles"));
+    VG_TRY(ensure(ws, ws->offsets, (size_t)n_items + 1, "offsets"));
+    for (int k = 0; k < 2; ++k) {
+        VG_TRY(ensure(ws, ws->skey[k], (size_t)n_items, "sort keys"));
+        VG_TRY(ensure(ws, ws->sval[k], (size_t)n_items, "sort values"));
+    }
+    return VG_OK;
+}
+
+static vg_status reserve_sort_scratch(vg_workspace *ws, long long n) {
+    VG_TRY(ensure(ws, ws->hist, radix_hist_words(n), "radix histogram"));
+    const long long scan_n = std::max<long long>(n, (long long)radix_hist_words(n));
+    VG_TRY(ensure(ws, ws->scan_tmp, scan_tmp_words(scan_n), "scan scratch"));
+    return VG_OK;
+}
+
+static vg_status reserve_instances(vg_workspace *ws, long long cap) {
+    for (int k = 0; k < 2; ++k) {
+        VG_TRY(ensure(ws, ws->ikey[k], (size_t)cap, "instance keys"));
+        VG_TRY(ensure(ws, ws->ival[k], (size_t)cap, "instance items"));
+    }
+    ws->capacity = (long long)std::min(ws->ikey[0].n, ws->ival[0].n);
+    return reserve_sort_scratch(ws, cap);
+}
+
+vg_status vg_workspace_reserve(vg_workspace *ws, int64_t n_items, int64_t n_instances, int64_t n_pixels,
+                               int64_t n_tiles) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (n_items < 0 || n_instances < 0 || n_pixels < 0 || n_tiles < 0)
+        return fail(ws, VG_ERR_INVALID_ARG, "negative reservation");
+    const unsigned flags = ws->opts.flags;
+    ws->opts.flags &= ~VG_FLAG_FIXED_CAPACITY;
+    vg_status s = reserve_items(ws, n_items);
+    if (s == VG_OK) s = reserve_sort_scratch(ws, n_items);
+    if (s == VG_OK) s = reserve_instances(ws, n_instances);
+    if (s == VG_OK) s = ensure(ws, ws->S_fin, (size_t)n_pixels, "pixel state");
+    if (s == VG_OK) s = ensure(ws, ws->T_fin, (size_t)n_pixels, "pixel state");
+    if (s == VG_OK) s = ensure(ws, ws->nlast, (size_t)n_pixels, "pixel state");
+    if (s == VG_OK) s = ensure(ws, ws->ranges, (size_t)n_tiles, "tile ranges");
+    if (s == VG_OK) s = ensure(ws, ws->tile_view, (size_t)n_tiles, "tile views");
+    if (s == VG_OK) s = ensure(ws, ws->grad, (size_t)n_items * kGradN, "gradient accumulators");
+    ws->opts.flags = flags;
+    return s;
+}
+
+vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams, int32_t n_views,
+                        const vg_opts *opts, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    VG_TRY(check_gauss(ws, g, true));
+    if (!cams || n_views < 1) return fail(ws, VG_ERR_INVALID_ARG, "need at least one camera");
+    if (!opts) return fail(ws, VG_ERR_INVALID_ARG, "opts is NULL");
+    if (!finite_pos(opts->tau_cut)) return fail(ws, VG_ERR_INVALID_ARG, "tau_cut must be finite and > 0");
+    if (!(opts->alpha_min >= 0.0f && opts->alpha_min < 1.0f)) return fail(ws, VG_ERR_INVALID_ARG, "alpha_min must be in [0, 1)");
+    if (!(opts->tau_max > 0.0f) || !(opts->T_stop >= 0.0f && opts->T_stop < 1.0f) || !std::isfinite(opts->z_near))
+        return fail(ws, VG_ERR_INVALID_ARG, "invalid tau_max, T_stop or z_near");
+    const long long n_items = (long long)g->n * n_views;
+    if (n_items >= 0xFFFFFFFFLL) return fail(ws, VG_ERR_INVALID_ARG, "views x Gaussians must be < 2^32");
+
+    std::vector<ViewInfo> vh((size_t)n_views);
+    std::vector<int> tv;
+    long long tile_base = 0, pix_base = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const vg_camera &c = cams[v];
+        if (c.width <= 0 || c.height <= 0 || !finite_pos(std::fabs(c.fx)) || !finite_pos(std::fabs(c.fy)) ||
+            !std::isfinite(c.cx) || !std::isfinite(c.cy))
+            return fail(ws, VG_ERR_INVALID_ARG, "invalid camera intrinsics or size");
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(c.R[k])) return fail(ws, VG_ERR_INVALID_ARG, "non-finite camera rotation");
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(c.t[k])) return fail(ws, VG_ERR_INVALID_ARG, "non-finite camera translation");
+        ViewInfo &V = vh[v];
+        memset(&V, 0, sizeof(V));
+        memcpy(V.R, c.R, sizeof(V.R));
+        memcpy(V.t, c.t, sizeof(V.t));
+        V.fx = c.fx;
+        V.fy = c.fy;
+        V.cx = c.cx;
+        V.cy = c.cy;
+        for (int k = 0; k < 3; ++k) {
+            V.od[k] = -((double)c.R[k] * c.t[0] + (double)c.R[3 + k] * c.t[1] + (double)c.R[6 + k] * c.t[2]);
+            V.of[k] = (float)V.od[k];
+        }
+        V.W = c.width;
+        V.H = c.height;
+        V.tiles_x = (c.width + kTile - 1) / kTile;
+        V.tiles_y = (c.height + kTile - 1) / kTile;
+        if (V.tiles_x > 32767 || V.tiles_y > 32767) return fail(ws, VG_ERR_INVALID_ARG, "image too large");
+        V.tile_base = (int)tile_base;
+        V.pix_base = pix_base;
+        for (int t = 0; t < V.tiles_x * V.tiles_y; ++t) tv.push_back(v);
+        tile_base += (long long)V.tiles_x * V.tiles_y;
+        pix_base += (long long)c.width * c.height;
+        if (tile_base >= (1LL << 30)) return fail(ws, VG_ERR_INVALID_ARG, "too many tiles");
+    }
+    ws->opts = *opts;
+    ws->g = to_in(g);
+    VG_TRY(reserve_items(ws, n_items));
+    VG_TRY(ensure(ws, ws->views, (size_t)n_views, "views"));
+    VG_TRY(ensure(ws, ws->tile_view, (size_t)tile_base, "tile views"));
+    const bool same = ws->views_valid && ws->n_views == n_views && ws->views_h.size() == vh.size() &&
+                      memcmp(ws->views_h.data(), vh.data(), vh.size() * sizeof(ViewInfo)) == 0;
+    if (!same) {
+        // pageable sources: the runtime stages them before returning, so the host vectors
+        // may change afterwards
+        VG_CUDA(ws, cudaMemcpyAsync(ws->views.p, vh.data(), vh.size() * sizeof(ViewInfo), cudaMemcpyHostToDevice, st));
+        VG_CUDA(ws, cudaMemcpyAsync(ws->tile_view.p, tv.data(), tv.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        ws->views_h = vh;
+        ws->tile_view_h = tv;
+        ws->views_valid = true;
+    }
+    ws->n_views = n_views;
+    ws->n_items = n_items;
+    ws->n_tiles = tile_base;
+    ws->n_pixels = pix_base;
+    ws->bp.tau_skip = opts->alpha_min > 0.0f ? (float)(-std::log1p(-(double)opts->alpha_min)) : 0.0f;
+    ws->bp.tau_max = opts->tau_max;
+    ws->bp.T_stop = opts->T_stop;
+    for (int c = 0; c < 3; ++c) ws->bp.bg[c] = opts->bg[c];
+    VG_CUDA(ws, cudaMemsetAsync(ws->counters.p, 0, sizeof(unsigned long long), st));
+    if (n_items > 0)
+        VG_CUDA(ws, launch_preprocess(ws->g, ws->views.p, n_views, opts->z_near, opts->tau_cut, ws->rec.p, ws->depth.p,
+                                      ws->count.p, ws->rect.p, ws->counters.p, st, &ws->launches));
+    ws->stage = 1;
+    return VG_OK;
+}
+
+vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (ws->stage < 1) return fail(ws, VG_ERR_STATE, "vg_bin_sort before vg_preprocess");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long n = ws->n_items;
+    VG_TRY(reserve_sort_scratch(ws, n));
+    // 1. items by depth key (stable: ties keep index order)
+    VG_CUDA(ws, cudaMemcpyAsync(ws->skey[0].p, ws->depth.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    VG_CUDA(ws, launch_iota(ws->sval[0].p, n, st, &ws->launches));
+    uint32_t *ksorted = nullptr;
+    VG_CUDA(ws, launch_radix_sort(ws->skey[0].p, ws->sval[0].p, ws->skey[1].p, ws->sval[1].p, n, 32, ws->hist.p,
+                                  ws->scan_tmp.p, &ksorted, &ws->perm, st, &ws->launches));
+    // 2. instance offsets in depth order
+    VG_CUDA(ws, launch_scan_gather(ws->count.p, ws->perm, ws->offsets.p, n, ws->scan_tmp.p, st, &ws->launches));
+    long long total;
+    if (ws->opts.flags & VG_FLAG_FIXED_CAPACITY) {
+        return fail(ws, VG_ERR_UNSUPPORTED, "fixed-capacity binning is not implemented in this build");
+    } else {
+        VG_CUDA(ws, cudaMemcpyAsync(ws->h_total, ws->offsets.p + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        VG_CUDA(ws, cudaStreamSynchronize(st));
+        total = (long long)ws->h_total[0];
+        VG_TRY(reserve_instances(ws, total));
+    }
+    ws->n_inst = total;
+    // 3. duplicate in depth order, 4. stable sort by tile id, 5. per-tile ranges
+    VG_CUDA(ws, launch_duplicate(ws->perm, ws->offsets.p, ws->rect.p, ws->views.p, n, ws->g.n, ws->ikey[0].p,
+                                 ws->ival[0].p, ws->capacity, st, &ws->launches));
+    VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, total,
+                                  bits_for(ws->n_tiles), ws->hist.p, ws->scan_tmp.p, &ws->inst_key, &ws->inst_item, st,
+                                  &ws->launches));
+    VG_TRY(ensure(ws, ws->ranges, (size_t)ws->n_tiles, "tile ranges"));
+    VG_CUDA(ws, launch_ranges(ws->inst_key, total, ws->ranges.p, ws->n_tiles, st, &ws->launches));
+    ws->stage = 2;
+    return VG_OK;
+}
+
+vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (ws->stage < 2) return fail(ws, VG_ERR_STATE, "vg_render_fwd before vg_bin_sort");
+    if (!rgb && ws->n_pixels > 0) return fail(ws, VG_ERR_INVALID_ARG, "rgb is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    VG_TRY(ensure(ws, ws->S_fin, (size_t)ws->n_pixels, "pixel state"));
+    VG_TRY(ensure(ws, ws->T_fin, (size_t)ws->n_pixels, "pixel state"));
+    VG_TRY(ensure(ws, ws->nlast, (size_t)ws->n_pixels, "pixel state"));
+    unsigned long long *pc = nullptr;
+    if (ws->opts.flags & VG_FLAG_COUNT_PAIRS) {
+        pc = ws->counters.p + 1;
+        VG_CUDA(ws, cudaMemsetAsync(pc, 0, sizeof(unsigned long long), st));
+    }
+    VG_CUDA(ws, launch_render_fwd(ws->views.p, ws->tile_view.p, ws->n_tiles, ws->ranges.p, ws->inst_item, ws->rec.p,
+                                  ws->bp, rgb, T_final, ws->T_fin.p, ws->S_fin.p, ws->nlast.p, pc, st, &ws->launches));
+    ws->stage = 3;
+    return VG_OK;
+}
+
+vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_dT, float *dmu, float *dscale,
+                        float *dquat, float *dkappa, float *dsh, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (ws->stage < 3) return fail(ws, VG_ERR_STATE, "vg_render_bwd before vg_render_fwd");
+    if ((!dL_drgb && ws->n_pixels > 0) || (ws->g.n > 0 && (!dmu || !dscale || !dquat || !dkappa)))
+        return fail(ws, VG_ERR_INVALID_ARG, "a gradient pointer is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    VG_TRY(ensure(ws, ws->grad, (size_t)ws->n_items * kGradN, "gradient accumulators"));
+    if (ws->n_items > 0)
+        VG_CUDA(ws, cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st));
+    VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, ws->n_tiles, ws->ranges.p, ws->inst_item, ws->rec.p,
+                                  ws->bp, ws->T_fin.p, ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, ws->grad.p, st,
+                                  &ws->launches));
+    if (ws->n_items > 0) {
+        GaussIn g = ws->g;
+        VG_CUDA(ws, launch_chain(g, ws->views.p, ws->n_views, ws->grad.p, dmu, dscale, dquat, dkappa, dsh, st,
+                                 &ws->launches));
+    }
+    return VG_OK;
+}
+
+vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam *beam, const vg_opts *opts,
+                          float *proj, const float *dL_dproj, float *dmu, float *dscale, float *dquat, float *dkappa,
+                          void *stream) {
+    (void)g;
+    (void)beam;
+    (void)opts;
+    (void)proj;
+    (void)dL_dproj;
+    (void)dmu;
+    (void)dscale;
+    (void)dquat;
+    (void)dkappa;
+    (void)stream;
+    if (!ws) return VG_ERR_INVALID_ARG;
+    return fail(ws, VG_ERR_UNSUPPORTED, "tomography is not implemented in this build");
+}
+
+vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n, float scale, float *loss,
+                     float *grad, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (n < 0 || !loss || (n > 0 && (!x || !y || !grad))) return fail(ws, VG_ERR_INVALID_ARG, "invalid loss arguments");
+    VG_CUDA(ws, launch_l2_loss(x, y, n, scale, loss, grad, (cudaStream_t)stream, &ws->launches));
+    return VG_OK;
+}
+
+vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream) {
+    if (!ws || !out) return VG_ERR_INVALID_ARG;
+    VG_CUDA(ws, cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned long long c[2] = {0, 0};
+    VG_CUDA(ws, cudaMemcpy(c, ws->counters.p, sizeof(c), cudaMemcpyDeviceToHost));
+    memset(out, 0, sizeof(*out));
+    out->n_items = ws->n_items;
+    out->n_visible = (int64_t)c[0];
+    out->n_instances = ws->n_inst;
+    out->n_tiles = ws->n_tiles;
+    out->n_pixels = ws->n_pixels;
+    out->instance_capacity = ws->capacity;
+    out->n_pairs = (int64_t)c[1];
+    out->launches = ws->launches;
+    size_t bytes = ws->views.n * sizeof(ViewInfo) + ws->tile_view.n * 4 + ws->rec.n * 16 + ws->depth.n * 4 +
+                   ws->count.n * 4 + ws->offsets.n * 4 + ws->rect.n * 8 + ws->ranges.n * 8 + ws->S_fin.n * 4 +
+                   ws->T_fin.n * 4 + ws->nlast.n * 4 + ws->grad.n * 4 + ws->hist.n * 4 + ws->scan_tmp.n * 4;
+    for (int k = 0; k < 2; ++k)
+        bytes += (ws->skey[k].n + ws->sval[k].n + ws->ikey[k].n + ws->ival[k].n) * 4;
+    out->device_bytes = (int64_t)bytes;
+    return VG_OK;
+}
+
+vg_status vg_read_keys(vg_workspace *ws, uint32_t *depth_bits, int32_t *rect) {
+    if (!ws || !depth_bits || !rect) return VG_ERR_INVALID_ARG;
+    if (ws->stage < 1) return fail(ws, VG_ERR_STATE, "no preprocess to read");
+    VG_CUDA(ws, cudaDeviceSynchronize());
+    const size_t n = (size_t)ws->n_items;
+    if (n == 0) return VG_OK;
+    VG_CUDA(ws, cudaMemcpy(depth_bits, ws->depth.p, n * 4, cudaMemcpyDeviceToHost));
+    std::vector<short4> r(n);
+    VG_CUDA(ws, cudaMemcpy(r.data(), ws->rect.p, n * sizeof(short4), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) {
+        rect[4 * i] = r[i].x;
+        rect[4 * i + 1] = r[i].y;
+        rect[4 * i + 2] = r[i].z;
+        rect[4 * i + 3] = r[i].w;
+    }
+    return VG_OK;
+}
+
+vg_status vg_read_bins(vg_workspace *ws, int64_t *tile_start, int32_t *sorted_item) {
+    if (!ws || !tile_start || (!sorted_item && ws->n_inst > 0)) return VG_ERR_INVALID_ARG;
+    if (ws->stage < 2) return fail(ws, VG_ERR_STATE, "no bin_sort to read");
+    VG_CUDA(ws, cudaDeviceSynchronize());
+    std::vector<uint2> rg((size_t)ws->n_tiles);
+    if (ws->n_tiles > 0)
+        VG_CUDA(ws, cudaMemcpy(rg.data(), ws->ranges.p, rg.size() * sizeof(uint2), cudaMemcpyDeviceToHost));
+    tile_start[0] = 0;
+    for (long long t = 0; t < ws->n_tiles; ++t) tile_start[t + 1] = tile_start[t] + (int64_t)(rg[t].y - rg[t].x);
+    if (ws->n_inst > 0)
+        VG_CUDA(ws, cudaMemcpy(sorted_item, ws->inst_item, (size_t)ws->n_inst * 4, cudaMemcpyDeviceToHost));
+    return VG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,309 @@
+// Per-(view, Gaussian) geometry used by the preprocess kernel and recomputed by the
+// backward chain kernel, so that both see bit-identical records.
+#pragma once
+
+#include <float.h>
+
+#include "vg_internal.cuh"
+
+namespace vg {
+
+// FP32 with explicit rounding: these wrappers keep nvcc from fusing a multiply and an add,
+// so the key function below yields the same bits as any IEEE implementation of the same
+// operation sequence.
+#define VG_MUL(a, b) __fmul_rn((a), (b))
+#define VG_ADD(a, b) __fadd_rn((a), (b))
+#define VG_SUB(a, b) __fsub_rn((a), (b))
+#define VG_DIV(a, b) __fdiv_rn((a), (b))
+#define VG_SQRT(a) __fsqrt_rn(a)
+
+// log2(sqrt(2 pi))
+constexpr float kLog2Sqrt2Pi = 1.32574806473615935f;
+constexpr float kLog2e = 1.44269504088896341f;
+
+template <typename RT>
+__device__ __forceinline__ void load_gauss(const GaussIn &g, long long i, float mu[3], float s[3], float q[4],
+                                           float &kap) {
+    const RT *m = (const RT *)g.mu, *sc = (const RT *)g.scale, *qq = (const RT *)g.quat, *k = (const RT *)g.kappa;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        mu[c] = ld_f<RT>(m, 3 * i + c);
+        s[c] = ld_f<RT>(sc, 3 * i + c);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q[c] = ld_f<RT>(qq, 4 * i + c);
+    kap = ld_f<RT>(k, i);
+}
+
+// Validity, unit quaternion, rotation Rq and world covariance Sigma = Rq S^2 Rq^T, FP32 with
+// a fixed operation order (the key function's first stage).
+__device__ __forceinline__ bool key_cov(const float mu[3], const float s[3], const float q[4], float kap,
+                                        float Sig[9], float Rq[9], float qn[4], float &smax) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(mu[k]) || !isfinite(s[k]) || !(s[k] > 0.0f)) return false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (!isfinite(q[k])) return false;
+    if (!isfinite(kap) || !(kap > 0.0f)) return false;
+    float n2 = VG_ADD(VG_ADD(VG_ADD(VG_MUL(q[0], q[0]), VG_MUL(q[1], q[1])), VG_MUL(q[2], q[2])), VG_MUL(q[3], q[3]));
+    if (!(n2 > 0.0f) || !isfinite(n2)) return false;
+    float inv = VG_DIV(1.0f, VG_SQRT(n2));
+    float w = VG_MUL(q[0], inv), x = VG_MUL(q[1], inv), y = VG_MUL(q[2], inv), z = VG_MUL(q[3], inv);
+    qn[0] = w;
+    qn[1] = x;
+    qn[2] = y;
+    qn[3] = z;
+    Rq[0] = VG_SUB(1.0f, VG_MUL(2.0f, VG_ADD(VG_MUL(y, y), VG_MUL(z, z))));
+    Rq[1] = VG_MUL(2.0f, VG_SUB(VG_MUL(x, y), VG_MUL(w, z)));
+    Rq[2] = VG_MUL(2.0f, VG_ADD(VG_MUL(x, z), VG_MUL(w, y)));
+    Rq[3] = VG_MUL(2.0f, VG_ADD(VG_MUL(x, y), VG_MUL(w, z)));
+    Rq[4] = VG_SUB(1.0f, VG_MUL(2.0f, VG_ADD(VG_MUL(x, x), VG_MUL(z, z))));
+    Rq[5] = VG_MUL(2.0f, VG_SUB(VG_MUL(y, z), VG_MUL(w, x)));
+    Rq[6] = VG_MUL(2.0f, VG_SUB(VG_MUL(x, z), VG_MUL(w, y)));
+    Rq[7] = VG_MUL(2.0f, VG_ADD(VG_MUL(y, z), VG_MUL(w, x)));
+    Rq[8] = VG_SUB(1.0f, VG_MUL(2.0f, VG_ADD(VG_MUL(x, x), VG_MUL(y, y))));
+    float v0 = VG_MUL(s[0], s[0]), v1 = VG_MUL(s[1], s[1]), v2 = VG_MUL(s[2], s[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Sig[3 * i + j] = VG_ADD(VG_ADD(VG_MUL(VG_MUL(Rq[3 * i], v0), Rq[3 * j]),
+                                           VG_MUL(VG_MUL(Rq[3 * i + 1], v1), Rq[3 * j + 1])),
+                                    VG_MUL(VG_MUL(Rq[3 * i + 2], v2), Rq[3 * j + 2]));
+    smax = fmaxf(fmaxf(s[0], s[1]), s[2]);
+    return true;
+}
+
+// k^2 with tau >= tau_cut => Mahalanobis m^2 <= k^2: tau <= kappa sqrt(2 pi) s_max exp(-m^2/2)
+// and ln x <= e ln 2 for x = m 2^e, m in [0.5, 1).  No transcendental function involved.
+__device__ __forceinline__ bool key_k2(float kap, float smax, float tau_cut, float &k2) {
+    float xr = VG_DIV(VG_MUL(VG_MUL(kap, 2.5066283f), smax), tau_cut);
+    if (!(xr > 1.0f)) return false;
+    int e = (xr > FLT_MAX) ? 128 : (int)((__float_as_uint(xr) >> 23) & 0xFFu) - 126;
+    k2 = VG_MUL((float)e, 1.3862944f);
+    return true;
+}
+
+// Pixel indices whose centre coordinate lies in [lo, hi] after a small outward pad;
+// returns lo > hi when empty.
+__device__ __forceinline__ void pixel_span(float lo, float hi, int n, int &ilo, int &ihi) {
+    lo = VG_SUB(lo, VG_ADD(0.02f, VG_MUL(1e-5f, fabsf(lo))));
+    hi = VG_ADD(hi, VG_ADD(0.02f, VG_MUL(1e-5f, fabsf(hi))));
+    if (!(hi >= 0.0f) || !(lo <= (float)(n - 1))) {
+        ilo = 1;
+        ihi = 0;
+        return;
+    }
+    ilo = (lo <= 0.0f) ? 0 : (int)ceilf(lo);
+    ihi = (hi >= (float)(n - 1)) ? n - 1 : (int)floorf(hi);
+}
+
+// Key function of one (view, Gaussian): camera depth of the mean (FP32 bits) and the
+// conservative tile rectangle of the Mahalanobis-k ellipsoid's screen bounding box.
+// Returns 0 = invalid/behind z_near, 1 = valid but no footprint, 2 = visible.
+__device__ __forceinline__ int key_persp(const ViewInfo &V, const float mu[3], const float Sig[9], float smax,
+                                         float kap, float z_near, float tau_cut, uint32_t &depth, short4 &rect,
+                                         float &Zf) {
+    const float *C = V.R;
+    float X = VG_ADD(VG_ADD(VG_ADD(VG_MUL(C[0], mu[0]), VG_MUL(C[1], mu[1])), VG_MUL(C[2], mu[2])), V.t[0]);
+    float Y = VG_ADD(VG_ADD(VG_ADD(VG_MUL(C[3], mu[0]), VG_MUL(C[4], mu[1])), VG_MUL(C[5], mu[2])), V.t[1]);
+    float Z = VG_ADD(VG_ADD(VG_ADD(VG_MUL(C[6], mu[0]), VG_MUL(C[7], mu[1])), VG_MUL(C[8], mu[2])), V.t[2]);
+    Zf = Z;
+    if (!(Z > z_near)) return 0;
+    depth = __float_as_uint(Z);
+    float k2;
+    if (!key_k2(kap, smax, tau_cut, k2)) return 1;
+    float T[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            T[3 * i + j] = VG_ADD(VG_ADD(VG_MUL(C[3 * i], Sig[j]), VG_MUL(C[3 * i + 1], Sig[3 + j])),
+                                  VG_MUL(C[3 * i + 2], Sig[6 + j]));
+    float sxx = VG_ADD(VG_ADD(VG_MUL(T[0], C[0]), VG_MUL(T[1], C[1])), VG_MUL(T[2], C[2]));
+    float sxz = VG_ADD(VG_ADD(VG_MUL(T[0], C[6]), VG_MUL(T[1], C[7])), VG_MUL(T[2], C[8]));
+    float syy = VG_ADD(VG_ADD(VG_MUL(T[3], C[3]), VG_MUL(T[4], C[4])), VG_MUL(T[5], C[5]));
+    float syz = VG_ADD(VG_ADD(VG_MUL(T[3], C[6]), VG_MUL(T[4], C[7])), VG_MUL(T[5], C[8]));
+    float szz = VG_ADD(VG_ADD(VG_MUL(T[6], C[6]), VG_MUL(T[7], C[7])), VG_MUL(T[8], C[8]));
+    float ZZ = VG_MUL(Z, Z);
+    float a2 = VG_SUB(ZZ, VG_MUL(k2, szz));
+    if (!(a2 > 0.0f)) {   // the cutoff ellipsoid reaches the camera plane: the whole view
+        rect = make_short4(0, 0, (short)(V.tiles_x - 1), (short)(V.tiles_y - 1));
+        return 2;
+    }
+    float k22 = VG_MUL(k2, k2);
+    float XZ = VG_MUL(X, Z), YZ = VG_MUL(Y, Z);
+    float bu = VG_SUB(XZ, VG_MUL(k2, sxz));
+    float qu = VG_ADD(VG_SUB(VG_MUL(ZZ, sxx), VG_MUL(2.0f, VG_MUL(XZ, sxz))), VG_MUL(VG_MUL(X, X), szz));
+    float du = VG_SUB(VG_MUL(k2, qu), VG_MUL(k22, VG_SUB(VG_MUL(sxx, szz), VG_MUL(sxz, sxz))));
+    if (!(du > 0.0f)) du = 0.0f;
+    float ru = VG_SQRT(du);
+    float ulo = VG_DIV(VG_SUB(bu, ru), a2), uhi = VG_DIV(VG_ADD(bu, ru), a2);
+    float bv = VG_SUB(YZ, VG_MUL(k2, syz));
+    float qv = VG_ADD(VG_SUB(VG_MUL(ZZ, syy), VG_MUL(2.0f, VG_MUL(YZ, syz))), VG_MUL(VG_MUL(Y, Y), szz));
+    float dv = VG_SUB(VG_MUL(k2, qv), VG_MUL(k22, VG_SUB(VG_MUL(syy, szz), VG_MUL(syz, syz))));
+    if (!(dv > 0.0f)) dv = 0.0f;
+    float rv = VG_SQRT(dv);
+    float vlo = VG_DIV(VG_SUB(bv, rv), a2), vhi = VG_DIV(VG_ADD(bv, rv), a2);
+    float xlo = VG_SUB(VG_ADD(VG_MUL(ulo, V.fx), V.cx), 0.5f), xhi = VG_SUB(VG_ADD(VG_MUL(uhi, V.fx), V.cx), 0.5f);
+    float ylo = VG_SUB(VG_ADD(VG_MUL(vlo, V.fy), V.cy), 0.5f), yhi = VG_SUB(VG_ADD(VG_MUL(vhi, V.fy), V.cy), 0.5f);
+    int ix0, ix1, iy0, iy1;
+    pixel_span(xlo, xhi, V.W, ix0, ix1);
+    pixel_span(ylo, yhi, V.H, iy0, iy1);
+    if (ix0 > ix1 || iy0 > iy1) return 1;
+    rect = make_short4((short)(ix0 / kTile), (short)(iy0 / kTile), (short)(ix1 / kTile), (short)(iy1 / kTile));
+    return 2;
+}
+
+// Blend-record geometry of one (view, Gaussian).  With B = Rc Rq and M = S^-1 B^T the
+// whitening in camera coordinates, a pixel ray d_c = (u, v, 1) maps to d' = M d_c and the
+// camera centre to o' = -M mu_c.  Pixels are addressed relative to the projected mean
+// (px0, py0), so that d' = A0 dx + A1 dy + A2 and o' x d' = C0 dx + C1 dy + C2 with
+// C2 ~ 0: the cancellation-prone cross product is formed per Gaussian in extra precision
+// instead of per pixel.
+struct ItemGeom {
+    float M[9];        // row-major
+    double muc[3];     // camera-space mean, FP64
+    float op[3];       // o'
+    float px0, py0;    // reference pixel (projected mean, rounded)
+    float dc0[3];      // camera ray through the reference pixel
+    float Dx, Dy;      // reference pixel minus the exact projection, in pixels
+    float A[9];        // A0, A1, A2 (rows of 3)
+    float Cc[9];       // C0, C1, C2
+};
+
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ void item_geom(const ViewInfo &V, const float mu[3], const float s[3], const float Rq[9],
+                                          ItemGeom &G) {
+    const float *Rc = V.R;
+    float B[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            B[3 * i + j] = Rc[3 * i] * Rq[j] + Rc[3 * i + 1] * Rq[3 + j] + Rc[3 * i + 2] * Rq[6 + j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float is = 1.0f / s[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) G.M[3 * i + j] = B[3 * j + i] * is;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        G.muc[k] = fma((double)Rc[3 * k], (double)mu[0],
+                       fma((double)Rc[3 * k + 1], (double)mu[1], fma((double)Rc[3 * k + 2], (double)mu[2], (double)V.t[k])));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        G.op[i] = (float)(-fma((double)G.M[3 * i], G.muc[0],
+                               fma((double)G.M[3 * i + 1], G.muc[1], (double)G.M[3 * i + 2] * G.muc[2])));
+    float Xf = (float)G.muc[0], Yf = (float)G.muc[1], Zf = (float)G.muc[2];
+    float izf = 1.0f / Zf;
+    G.px0 = fmaf(V.fx, Xf * izf, V.cx - 0.5f);
+    G.py0 = fmaf(V.fy, Yf * izf, V.cy - 0.5f);
+    double ex = ((double)G.px0 + 0.5 - (double)V.cx), ey = ((double)G.py0 + 0.5 - (double)V.cy);
+    G.Dx = (float)fma(ex, G.muc[2], -(double)V.fx * G.muc[0]) * izf;
+    G.Dy = (float)fma(ey, G.muc[2], -(double)V.fy * G.muc[1]) * izf;
+    G.dc0[0] = (float)ex / V.fx;
+    G.dc0[1] = (float)ey / V.fy;
+    G.dc0[2] = 1.0f;
+    float ifx = 1.0f / V.fx, ify = 1.0f / V.fy;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        G.A[i] = G.M[3 * i] * ifx;
+        G.A[3 + i] = G.M[3 * i + 1] * ify;
+        G.A[6 + i] = G.M[3 * i] * G.dc0[0] + G.M[3 * i + 1] * G.dc0[1] + G.M[3 * i + 2];
+    }
+    cross3(G.op, &G.A[0], &G.Cc[0]);
+    cross3(G.op, &G.A[3], &G.Cc[3]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) G.Cc[6 + i] = G.Cc[i] * G.Dx + G.Cc[3 + i] * G.Dy;
+}
+
+// ------------------------------------------------------------------ spherical harmonics
+// Real spherical harmonics to degree 3 (Condon-Shortley phase); Y[k] for k < (deg+1)^2.
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float Y[16]) {
+    Y[0] = 0.28209479177387814f;
+    if (deg < 1) return;
+    Y[1] = -0.48860251190291992f * y;
+    Y[2] = 0.48860251190291992f * z;
+    Y[3] = -0.48860251190291992f * x;
+    if (deg < 2) return;
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = 1.0925484305920792f * x * y;
+    Y[5] = -1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+    Y[7] = -1.0925484305920792f * x * z;
+    Y[8] = 0.54627421529603959f * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -0.59004358992664352f * y * (3.0f * xx - yy);
+    Y[10] = 2.8906114426405538f * x * y * z;
+    Y[11] = -0.45704579946446572f * y * (4.0f * zz - xx - yy);
+    Y[12] = 0.37317633259011540f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -0.45704579946446572f * x * (4.0f * zz - xx - yy);
+    Y[14] = 1.4453057213202769f * z * (xx - yy);
+    Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+}
+
+// Gradient of the basis polynomials with respect to (x, y, z), dY[k][c].
+__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float dY[16][3]) {
+    dY[0][0] = dY[0][1] = dY[0][2] = 0.0f;
+    if (deg < 1) return;
+    const float c1 = 0.48860251190291992f;
+    dY[1][0] = 0.0f; dY[1][1] = -c1; dY[1][2] = 0.0f;
+    dY[2][0] = 0.0f; dY[2][1] = 0.0f; dY[2][2] = c1;
+    dY[3][0] = -c1; dY[3][1] = 0.0f; dY[3][2] = 0.0f;
+    if (deg < 2) return;
+    const float a = 1.0925484305920792f, b = 0.31539156525252005f, c = 0.54627421529603959f;
+    float xx = x * x, yy = y * y, zz = z * z;
+    dY[4][0] = a * y;        dY[4][1] = a * x;        dY[4][2] = 0.0f;
+    dY[5][0] = 0.0f;         dY[5][1] = -a * z;       dY[5][2] = -a * y;
+    dY[6][0] = -2.0f * b * x; dY[6][1] = -2.0f * b * y; dY[6][2] = 4.0f * b * z;
+    dY[7][0] = -a * z;       dY[7][1] = 0.0f;         dY[7][2] = -a * x;
+    dY[8][0] = 2.0f * c * x; dY[8][1] = -2.0f * c * y; dY[8][2] = 0.0f;
+    if (deg < 3) return;
+    const float e = 0.59004358992664352f, f = 2.8906114426405538f, g = 0.45704579946446572f,
+                h = 0.37317633259011540f, i = 1.4453057213202769f;
+    dY[9][0] = -6.0f * e * x * y;  dY[9][1] = -3.0f * e * (xx - yy);  dY[9][2] = 0.0f;
+    dY[10][0] = f * y * z;         dY[10][1] = f * x * z;             dY[10][2] = f * x * y;
+    dY[11][0] = 2.0f * g * x * y;  dY[11][1] = -g * (4.0f * zz - xx - 3.0f * yy); dY[11][2] = -8.0f * g * y * z;
+    dY[12][0] = -6.0f * h * x * z; dY[12][1] = -6.0f * h * y * z;     dY[12][2] = h * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+    dY[13][0] = -g * (4.0f * zz - 3.0f * xx - yy); dY[13][1] = 2.0f * g * x * y; dY[13][2] = -8.0f * g * x * z;
+    dY[14][0] = 2.0f * i * x * z;  dY[14][1] = -2.0f * i * y * z;     dY[14][2] = i * (xx - yy);
+    dY[15][0] = -3.0f * e * (xx - yy); dY[15][1] = 6.0f * e * x * y;  dY[15][2] = 0.0f;
+}
+
+template <typename ST>
+__device__ __forceinline__ void eval_colour(const GaussIn &g, long long gi, const float dir[3], float rgb[3],
+                                            float raw[3]) {
+    float Y[16];
+    sh_basis(g.sh_degree, dir[0], dir[1], dir[2], Y);
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    const ST *sh = (const ST *)g.sh + (long long)gi * K * 3;
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = fmaf(ld_f<ST>(sh, 3 * k + c), Y[k], acc[c]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        raw[c] = acc[c];
+        rgb[c] = fmaxf(acc[c], 0.0f);
+    }
+}
+
+__device__ __forceinline__ void view_dir(const ViewInfo &V, const float mu[3], float dir[3], float &len) {
+    float d0 = mu[0] - V.of[0], d1 = mu[1] - V.of[1], d2 = mu[2] - V.of[2];
+    float n2 = d0 * d0 + d1 * d1 + d2 * d2;
+    len = sqrtf(n2);
+    float inv = 1.0f / len;
+    dir[0] = d0 * inv;
+    dir[1] = d1 * inv;
+    dir[2] = d2 * inv;
+}
+
+}  // namespace vg

@@ -1,0 +1,134 @@
+// Internal declarations of the CUDA library (kernels, launchers, device helpers).
+// Nothing here is part of the C ABI; see include/vg.h for that.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vg.h"
+
+namespace vg {
+
+constexpr int kTile = 16;                 // square pixel tiles
+constexpr int kTilePix = kTile * kTile;   // one thread per pixel in the blend kernels
+constexpr int kRecF4 = 6;                 // blend record: 6 x float4 = 96 bytes
+constexpr int kGradN = 24;                // per-item gradient accumulator (22 used)
+constexpr int kTomoRecF4 = 2;             // tomography record: 2 x float4
+
+// Per-view constants, device side.
+struct ViewInfo {
+    float R[9], t[3];
+    float fx, fy, cx, cy;
+    float of[3];          // camera centre o = -R^T t, FP32
+    double od[3];         // camera centre, FP64
+    int W, H, tiles_x, tiles_y;
+    int tile_base;        // first global tile id of this view
+    int pad;
+    long long pix_base;   // first pixel of this view in the concatenated image
+};
+
+struct GaussIn {
+    const void *mu, *scale, *quat, *kappa, *sh;
+    int rec_dtype, sh_dtype, n, sh_degree;
+};
+
+struct BlendParams {
+    float tau_skip;       // skip contributions with tau < tau_skip (alpha < alpha_min)
+    float tau_max;
+    float T_stop;
+    float bg[3];
+};
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <typename T> __device__ __forceinline__ float ld_f(const T *p, long long i);
+template <> __device__ __forceinline__ float ld_f<float>(const float *p, long long i) { return __ldg(p + i); }
+template <> __device__ __forceinline__ float ld_f<__nv_bfloat16>(const __nv_bfloat16 *p, long long i) {
+    return __bfloat162float(p[i]);
+}
+template <> __device__ __forceinline__ float ld_f<__half>(const __half *p, long long i) { return __half2float(p[i]); }
+
+// ------------------------------------------------------------------ launchers
+// All launchers return cudaGetLastError() after their launches and add the number of
+// kernels they launched to *launches.
+cudaError_t launch_preprocess(const GaussIn &g, const ViewInfo *views_d, int n_views, float z_near,
+                              float tau_cut, float4 *rec, uint32_t *depth, uint32_t *count, short4 *rect,
+                              unsigned long long *n_visible, cudaStream_t st, long long *launches);
+
+cudaError_t launch_tomo_preprocess(const GaussIn &g, const float *cs_d /* [A][2] cos, sin */, int n_angles,
+                                   int det_w, int det_h, float pitch_u, float pitch_v, float u0, float v0,
+                                   float tau_cut, float4 *rec, uint32_t *count, short4 *rect,
+                                   cudaStream_t st, long long *launches);
+
+// Exclusive scan of n uint32 values into out (out[n] = total).  tmp must hold
+// scan_tmp_words(n) uint32.
+size_t scan_tmp_words(long long n);
+cudaError_t launch_scan(const uint32_t *in, uint32_t *out, long long n, uint32_t *tmp, cudaStream_t st,
+                        long long *launches);
+// Scan of count[perm[i]] (gathered through a permutation); perm may be NULL.
+cudaError_t launch_scan_gather(const uint32_t *count, const uint32_t *perm, uint32_t *out, long long n,
+                               uint32_t *tmp, cudaStream_t st, long long *launches);
+
+// Stable LSD radix sort of (key, value) pairs over key bits [0, bits).  Result ends in
+// keys_out/vals_out; the *_tmp buffers are clobbered.  hist must hold
+// radix_hist_words(n) uint32.
+size_t radix_hist_words(long long n);
+cudaError_t launch_radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp, uint32_t *vals_tmp, long long n,
+                              int bits, uint32_t *hist, uint32_t *scan_tmp, uint32_t **keys_out,
+                              uint32_t **vals_out, cudaStream_t st, long long *launches);
+
+cudaError_t launch_iota(uint32_t *v, long long n, cudaStream_t st, long long *launches);
+
+// Duplicate items into (tile key, item) instances, in the order given by perm (NULL = item
+// order).  offsets[i] is the first instance slot of the i-th item in that order.
+cudaError_t launch_duplicate(const uint32_t *perm, const uint32_t *offsets, const short4 *rect,
+                             const ViewInfo *views, long long n_items, int n_per_view, uint32_t *inst_key,
+                             uint32_t *inst_val, long long capacity, cudaStream_t st, long long *launches);
+
+cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, uint2 *ranges, long long n_tiles,
+                          cudaStream_t st, long long *launches);
+
+cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, long long n_tiles,
+                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
+                              const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
+                              uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st,
+                              long long *launches);
+
+cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, long long n_tiles,
+                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
+                              const BlendParams &bp, const float *T_fin, const float *S_fin,
+                              const uint32_t *nlast, const float *dL_drgb, const float *dL_dT, float *grad_acc,
+                              cudaStream_t st, long long *launches);
+
+cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc,
+                         float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st,
+                         long long *launches);
+
+cudaError_t launch_tomo_fwd(const uint2 *ranges, long long n_tiles, int tiles_x, int tiles_per_view, int det_w,
+                            int det_h, const uint32_t *sorted_item, const float4 *rec, float *proj,
+                            cudaStream_t st, long long *launches);
+
+cudaError_t launch_tomo_bwd(const uint2 *ranges, long long n_tiles, int tiles_x, int tiles_per_view, int det_w,
+                            int det_h, const uint32_t *sorted_item, const float4 *rec, const float *proj,
+                            const float *dL_dproj, float *grad_acc, cudaStream_t st, long long *launches);
+
+cudaError_t launch_tomo_chain(const GaussIn &g, const float *cs_d, int n_angles, long long item0, long long n_items,
+                              float pitch_u, float pitch_v, float u0, float v0, const float *grad_acc, float *dmu,
+                              float *dscale, float *dquat, float *dkappa, cudaStream_t st, long long *launches);
+
+cudaError_t launch_l2_loss(const float *x, const float *y, long long n, float scale, float *loss, float *grad,
+                           cudaStream_t st, long long *launches);
+
+}  // namespace vg

@@ -1,0 +1,128 @@
+"""GPU parity of the rasterizer against the FP64 oracle, through the C ABI.
+
+Bars: tile rectangles, depth keys, per-tile lists bit-exact; images within 1e-4 max abs
+in exact mode; gradients within 1e-3 relative (floor 1e-3 of the largest magnitude of each
+parameter type)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import dev_scene, flat, grad_rel_err, run_backward, run_forward
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+def _multi_view_scene():
+    scene = synth.uniform_scene(300, 4242, log_scale=(-3.5, -2.2), sh_degree=3, sh_std=0.25, flatten_frac=0.2,
+                                extent=0.9)
+    cams = synth.small_views(3, 0, [(40, 24), (33, 17), (64, 48)])
+    return scene, cams
+
+
+CASES = {
+    "cfg1": lambda: synth.config1(),
+    "cfg1_ragged": lambda: (synth.config1(0.5)[0], [synth.look_at((0.3, -0.2, -4.0), (0, 0, 0), 75, 53, 60.0)]),
+    "multiview_sh3": _multi_view_scene,
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("mode", ["exact", "compat"])
+def test_keys_and_bins_bit_exact(gpu_lib, case, mode):
+    vg = gpu_lib
+    scene, cams = CASES[case]()
+    o = oracle.EXACT if mode == "exact" else oracle.COMPAT
+    ws, g, _, _ = run_forward(vg, scene, cams, o)
+    depth, rect = ws.read_keys()
+    od, orc = oracle.keys(scene, cams, o)
+    assert np.array_equal(depth, od.reshape(-1))
+    assert np.array_equal(rect, orc.reshape(-1, 4))
+    ts, items = ws.read_bins()
+    L = oracle.lists(scene, cams, o)
+    assert np.array_equal(ts, L["tile_start"])
+    assert np.array_equal(items % scene.n, L["sorted_g"])
+    # every instance of a tile belongs to that tile's view
+    tile_of = np.repeat(np.arange(L["n_tiles"]), np.diff(L["tile_start"]))
+    view_of_tile = np.searchsorted(L["tile_base"], tile_of, side="right") - 1
+    assert np.array_equal(items // scene.n, view_of_tile)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_forward_exact_mode(gpu_lib, case):
+    vg = gpu_lib
+    scene, cams = CASES[case]()
+    o = dict(oracle.EXACT, bg=(0.25, 0.5, 0.75))
+    _, _, rgb, T = run_forward(vg, scene, cams, o)
+    ref_rgb, ref_T, _ = oracle.render(scene, cams, o)
+    assert np.max(np.abs(rgb - flat(ref_rgb))) < IMG_TOL
+    assert np.max(np.abs(T - flat(ref_T))) < IMG_TOL
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_forward_compat_mode(gpu_lib, case):
+    """With alpha_min / tau_max / T_stop the FP32 and FP64 sides may decide a threshold
+    differently at a few pixels; elsewhere the image matches to 1e-4."""
+    vg = gpu_lib
+    scene, cams = CASES[case]()
+    o = oracle.COMPAT
+    _, _, rgb, T = run_forward(vg, scene, cams, o)
+    ref_rgb, ref_T, _ = oracle.render(scene, cams, o)
+    err = np.max(np.abs(rgb - flat(ref_rgb)), axis=1)
+    assert np.mean(err > IMG_TOL) < 0.005
+    assert np.max(err) < 0.02
+
+
+def test_forward_edge_cases(gpu_lib):
+    vg = gpu_lib
+    o = dict(oracle.EXACT, bg=(0.1, 0.2, 0.3))
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 37, 21, 60.0)
+    empty = synth.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.zeros((0, 4), np.float32),
+                        np.zeros(0, np.float32), np.zeros((0, 1, 3), np.float32), 0)
+    _, _, rgb, T = run_forward(vg, empty, [cam], o)
+    assert np.all(T == 1.0) and np.allclose(rgb, [0.1, 0.2, 0.3])
+    # invalid parameters and Gaussians behind the camera are culled, the rest still render
+    sc = synth.uniform_scene(50, 9, log_scale=(-2.5, -1.5))
+    sc.kappa[0] = np.nan
+    sc.scale[1, 2] = -1.0
+    sc.quat[2] = 0.0
+    sc.kappa[3] = 0.0
+    sc.mu[4] = (0.0, 0.0, -4.5)
+    sc.mu[5, 0] = np.inf
+    ws, _, rgb, T = run_forward(vg, sc, [cam], o)
+    ref_rgb, ref_T, _ = oracle.render(sc, [cam], o)
+    assert np.max(np.abs(rgb - flat(ref_rgb))) < IMG_TOL
+    assert ws.query()["n_visible"] <= 44
+    # a single Gaussian
+    one = sc.subset([10])
+    _, _, rgb, T = run_forward(vg, one, [cam], o)
+    ref_rgb, _, _ = oracle.render(one, [cam], o)
+    assert np.max(np.abs(rgb - flat(ref_rgb))) < IMG_TOL
+
+
+@pytest.mark.parametrize("case", ["cfg1", "multiview_sh3"])
+@pytest.mark.parametrize("variant", ["exact", "clamped_bg"])
+def test_backward_matches_oracle_gradient(gpu_lib, case, variant):
+    vg = gpu_lib
+    scene, cams = CASES[case]()
+    if case == "cfg1":
+        scene = scene.subset(np.arange(0, scene.n, 4))
+    o = dict(oracle.EXACT)
+    if variant == "clamped_bg":
+        o.update(tau_max=2.0, bg=(0.3, 0.6, 0.9))
+    ws, g, rgb, T = run_forward(vg, scene, cams, o)
+    rng = np.random.default_rng(7)
+    P = rgb.shape[0]
+    wr = rng.normal(size=(P, 3))
+    wT = rng.normal(size=P)
+    gg = run_backward(vg, ws, g, wr, wT)
+    L = oracle.lists(scene, cams, o)
+    ref = oracle.render_grad(scene, cams, o, L, wr, wT)
+    for k in ("mu", "scale", "quat", "kappa", "sh"):
+        e = grad_rel_err(gg[k], ref[k])
+        assert e < GRAD_TOL, (k, e)
