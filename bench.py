@@ -1,0 +1,426 @@
+"""Benchmark of the volumetric Gaussian rasterizer (arXiv 2412.03378) on GB300.
+
+Workload (the view-synthesis configuration): 1,000,000 Gaussians from a mixture of 64
+anisotropic clusters (20% flattened 100x), SH degree 3, densities log-uniform in
+[0.1, 100], one 1280x832 camera; one step = preprocess + bin/sort + forward blend + L2
+loss against a random target + backward (gradients w.r.t. means, scales, quaternions,
+densities and SH), FP32, inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  For N > 1 (torchrun, one rank per GPU) each rank renders its own
+replica (a single view does not split; see the design notes), value = all ranks' steps
+divided by the slowest rank's time.  `--impl reference` times the FP64 CPU oracle (the
+reference implementation of this build) on a bounded sample of the same step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd steps/s & frames/s, 1M Gaussians @1280×832, vs plain FP32, % of pipe peak"
+WORKLOAD = "1M Gaussians (64-cluster mixture, 20% flattened, SH deg 3), 1280x832, fwd+bwd, L2 loss, FP32"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SMS, FP32_LANES, MUFU_PER_SM = 152, 128, 16
+# Algorithmic FP32 work per evaluated (pixel, Gaussian) pair, FMA counted as 2, each
+# transcendental (rsqrt, exp2) as 1; derived operation by operation in the design notes.
+FLOPS_FWD_PAIR = 53
+FLOPS_BWD_PAIR = 95
+CPU_SAMPLE_TILES = 96
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [[x.strip() for x in l.split(",")] for l in self.lines if l]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- setup
+def make_workload(frac):
+    import synth
+
+    scene, cams, target = synth.config2(frac)
+    return scene, cams, target
+
+
+def traffic_record():
+    """DRAM bytes per launch of the backward blend kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged (null otherwise)."""
+    p = os.path.join(ROOT, "profiles", "render_bwd_cfg2_traffic.txt")
+    src = os.path.join(ROOT, "paper_2412_03378_gb300", "csrc", "render_bwd.cu")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    if kv.get("source_sha1") != sha:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_PATH))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2412_03378_gb300 as vg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vg.load()
+
+    scene, cams, target = make_workload(args.frac)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev).contiguous()
+    g = vg.Gaussians(t(scene.mu), t(scene.scale), t(scene.quat), t(scene.kappa), t(scene.sh), scene.sh_degree)
+    tgt = t(target.reshape(-1, 3))
+    P = cams[0].width * cams[0].height
+    ws = vg.Workspace()
+    opts = vg.Opts.compat(flags=vg.FLAG_GRAD_ZERO)
+    rgb = torch.empty(P, 3, device=dev)
+    T = torch.empty(P, device=dev)
+    dldrgb = torch.empty(P, 3, device=dev)
+    loss = torch.zeros(1, device=dev)
+    grads = [torch.zeros(g.n, 3, device=dev), torch.zeros(g.n, 3, device=dev), torch.zeros(g.n, 4, device=dev),
+             torch.zeros(g.n, device=dev), torch.zeros(tuple(g.sh.shape), device=dev)]
+    scale = 1.0 / float(rgb.numel())
+
+    def step(gg=g):
+        ws.preprocess(gg, cams, opts)
+        ws.bin_sort()
+        ws.render_fwd(rgb, T)
+        ws.l2_loss(rgb, tgt, scale, loss, dldrgb)
+        ws.render_bwd(dldrgb, None, *grads)
+
+    def fwd_only():
+        ws.preprocess(g, cams, opts)
+        ws.bin_sort()
+        ws.render_fwd(rgb, T)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- warm-up, then exactly K timed steps bracketed by barrier + synchronize
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [x for x in cvd.split(",") if x.strip()]
+    gpu_id = ids[local] if local < len(ids) else (ids[0] if ids else str(local))
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    l0 = ws.query()["launches"]
+    ws.profile_enable(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    stages = ws.profile_read()
+    ws.profile_enable(False)
+    launches = ws.query()["launches"] - l0
+    ms = e0.elapsed_time(e1)
+    t_local = ms / 1e3
+    if world > 1:
+        tt = torch.tensor([t_local], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    else:
+        t_max = t_local
+    total_steps = args.steps * world
+    value = total_steps / t_max
+
+    # ---- forward-only frames/s (same protocol, not part of the headline value)
+    for _ in range(2):
+        fwd_only()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        fwd_only()
+    f1.record(stream)
+    barrier()
+    frames = args.steps * world / (f0.elapsed_time(f1) / 1e3)
+
+    # ---- pair counts for the roofline (separate, counted launches outside the timed region)
+    ws.preprocess(g, cams, vg.Opts.compat(flags=vg.FLAG_GRAD_ZERO | vg.FLAG_COUNT_PAIRS))
+    ws.bin_sort()
+    ws.render_fwd(rgb, T)
+    ws.l2_loss(rgb, tgt, scale, loss, dldrgb)
+    ws.render_bwd(dldrgb, None, *grads)
+    q = ws.query()
+
+    # ---- end to end through the public API with host buffers (pinned), copies timed
+    host = [torch.as_tensor(np.ascontiguousarray(a)).pin_memory() for a in
+            (scene.mu, scene.scale, scene.quat, scene.kappa, scene.sh, target.reshape(-1, 3))]
+    dbufs = [g.mu, g.scale, g.quat, g.kappa, g.sh, tgt]
+    loss_host = torch.zeros(1).pin_memory()
+    h2d = sum(h.numel() * h.element_size() for h in host)
+
+    def e2e_step():
+        for d, h in zip(dbufs, host):
+            d.copy_(h, non_blocking=True)
+        step()
+        loss_host.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return float(loss_host[0])
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_t = time.perf_counter() - w0
+    if world > 1:
+        tt = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+    e2e_value = args.steps * world / e2e_t
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (the backward blend), measured live
+    calls_bwd, ms_bwd = stages.get("render_bwd", (0, 0.0))
+    dominant = "render_bwd"
+    per_launch_s = (ms_bwd / max(1, calls_bwd)) / 1e3
+    flops = q["n_pairs_bwd"] * FLOPS_BWD_PAIR
+    achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else None
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tf = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    traffic = traffic_record()
+    roofline = {"bound": "alu", "kernel": "k_render_bwd", "achieved": achieved, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": (achieved / peak_tf) if achieved else None, "traffic": traffic,
+                "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+                "pairs_per_launch": q["n_pairs_bwd"], "flops_per_pair": FLOPS_BWD_PAIR,
+                "launch_ms": per_launch_s * 1e3}
+    if clk and clk.get("sm_mhz"):
+        roofline["frac_at_observed_clock"] = achieved / (peak_tf * clk["sm_mhz"] / sm_max) if achieved else None
+
+    stage_ms = {k: round(v[1] / max(1, v[0]), 4) for k, v in stages.items()}
+    fwd_pairs = q["n_pairs"]
+    calls_f, ms_f = stages.get("render_fwd", (0, 0.0))
+    fwd_tf = fwd_pairs * FLOPS_FWD_PAIR / ((ms_f / max(1, calls_f)) / 1e3) / 1e12 if ms_f > 0 else None
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": g.n, "width": cams[0].width, "height": cams[0].height,
+                   "sh_degree": scene.sh_degree, "mode": "alpha_min 1/255, tau_max ln100, T_stop 1e-4",
+                   "l2": "inputs larger than L2 (236 MB Gaussian parameters + 12.8 MB target per step)",
+                   "parallelism": f"replicas x{world}", "frac": args.frac},
+        "frames_per_s": frames,
+        "stages_ms": stage_ms,
+        "roofline": roofline,
+        "fwd_blend_tflops": fwd_tf,
+        "counts": {"visible": q["n_visible"], "instances": q["n_instances"], "pairs_fwd": q["n_pairs"],
+                   "pairs_bwd": q["n_pairs_bwd"], "workspace_bytes": q["device_bytes"]},
+        "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = cpu_baseline(scene, cams, target)
+        except Exception as e:  # the baseline is reported, never the headline
+            out["cpu_baseline"] = {"error": str(e)}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_step(scene, cams, target, n_sample, seed, oracle):
+    """One oracle step on a bounded sample: keys + binning of every Gaussian, then the
+    forward blend and the analytic gradient on n_sample seeded random tiles.  Returns the
+    per-step time extrapolated to all tiles."""
+    o = dict(oracle.COMPAT)
+    t0 = time.perf_counter()
+    L = oracle.lists(scene, cams, o)
+    t1 = time.perf_counter()
+    cam = cams[0]
+    ntx, nty = L["tiles_x"][0], L["tiles_y"][0]
+    n_tiles = int(ntx * nty)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(n_tiles, size=min(n_sample, n_tiles), replace=False)
+    tile_of_pix = ((np.arange(cam.height)[:, None] // 16) * ntx + (np.arange(cam.width)[None, :] // 16)).reshape(-1)
+    mask = np.isin(tile_of_pix, pick).astype(np.int32)
+    empty = np.zeros_like(mask)
+    # fixed per-call set-up of the oracle (FP64 parameters, colours) measured separately
+    s0 = time.perf_counter()
+    oracle.render(scene, cams, o, L, mask=empty)
+    s1 = time.perf_counter()
+    rgb, _, _ = oracle.render(scene, cams, o, L, mask=mask)
+    s2 = time.perf_counter()
+    g = np.zeros_like(rgb[0].reshape(-1, 3))
+    sel = mask.astype(bool)
+    g[sel] = 2.0 * (rgb[0].reshape(-1, 3)[sel] - target.reshape(-1, 3)[sel]) / float(target.size)
+    s3 = time.perf_counter()
+    oracle.render_grad(scene, cams, o, L, g, None, mask=empty)
+    s4 = time.perf_counter()
+    oracle.render_grad(scene, cams, o, L, g, None, mask=mask)
+    s5 = time.perf_counter()
+    fixed = (t1 - t0) + (s1 - s0) + (s4 - s3)
+    per_tile = ((s2 - s1) - (s1 - s0) + (s5 - s4) - (s4 - s3)) / len(pick)
+    est = fixed + max(per_tile, 0.0) * n_tiles
+    wall = (t1 - t0) + (s5 - s0)
+    return est, wall, len(pick), n_tiles
+
+
+def cpu_baseline(scene, cams, target, n_sample=CPU_SAMPLE_TILES):
+    import oracle
+
+    est, wall, k, n_tiles = oracle_step(scene, cams, target, n_sample, 5, oracle)
+    return {"value": 1.0 / est, "unit": "steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle: keys+binning of all {scene.n} Gaussians, forward+gradient on {k} of "
+                      f"{n_tiles} tiles (seeded), per-tile time extrapolated to the full frame; "
+                      f"{wall:.1f} s wall for the sample"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    scene, cams, target = make_workload(args.frac)
+    for w in range(args.warmup):
+        oracle_step(scene, cams, target, 8, 100 + w, oracle)
+    ests = []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        est, _, _, n_tiles = oracle_step(scene, cams, target, 16, 200 + k, oracle)
+        ests.append(est)
+    wall = time.perf_counter() - t0
+    value = args.steps / sum(ests)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ests) / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "gaussians": scene.n, "width": cams[0].width,
+                      "height": cams[0].height, "frac": args.frac},
+           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"each step: keys+binning of all {scene.n} Gaussians, forward+gradient "
+                                      f"on 16 seeded tiles of {n_tiles}, extrapolated to the full frame; "
+                                      f"{wall:.1f} s wall in total"},
+           "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frac", type=float, default=1.0, help="scale the Gaussian count (parity/smoke use only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        log("note: fewer than 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -104,8 +104,10 @@ typedef struct {
 
 #define VG_FLAG_FIXED_CAPACITY 1u  /* never synchronise to read the instance count; fail with
                                       VG_ERR_CAPACITY beyond the reserved capacity        */
-#define VG_FLAG_COUNT_PAIRS 2u     /* render_fwd also counts evaluated (pixel, Gaussian)
-                                      pairs into vg_stats.n_pairs (slower; for roofline) */
+#define VG_FLAG_GRAD_ZERO 4u       /* render_bwd / project_tomo zero their gradient outputs
+                                      before accumulating into them                        */
+#define VG_FLAG_COUNT_PAIRS 2u     /* render_fwd / render_bwd also count evaluated (pixel,
+                                      Gaussian) pairs into vg_stats (slower; for roofline) */
 
 typedef struct {
     int64_t n_items;          /* views x Gaussians of the last preprocess                    */
@@ -118,7 +120,18 @@ typedef struct {
     int64_t n_pairs;          /* evaluated pairs of the last counted render_fwd              */
     int64_t launches;         /* kernels launched by this workspace since creation          */
     int64_t device_bytes;     /* device memory held by the workspace                        */
+    int64_t n_pairs_bwd;      /* pairs replayed by the last counted render_bwd              */
 } vg_stats;
+
+/* Per-stage device time recorded with CUDA events on the launching stream while
+ * profiling is enabled (vg_profile_enable).  Stage names: "preprocess", "depth_sort",
+ * "scan", "duplicate", "tile_sort", "ranges", "render_fwd", "render_bwd", "chain",
+ * "l2_loss", "tomo_fwd", "tomo_bwd". */
+typedef struct {
+    char name[24];
+    int64_t calls;
+    double total_ms;
+} vg_stage_time;
 
 typedef struct vg_workspace vg_workspace;
 
@@ -182,6 +195,14 @@ vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n
 
 /* Statistics of the last calls (synchronises the stream). */
 vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream);
+
+/* Enable (1) or disable (0) per-stage event timing; enabling clears earlier records. */
+vg_status vg_profile_enable(vg_workspace *ws, int32_t enable);
+
+/* Aggregate the recorded stage times (synchronises on the recorded events) into `out`
+ * (capacity entries, HOST memory); *n_out receives the number of stages written.  The
+ * records are cleared. */
+vg_status vg_profile_read(vg_workspace *ws, vg_stage_time *out, int32_t capacity, int32_t *n_out);
 
 /* Diagnostic read-backs of the last preprocess / bin_sort into HOST buffers (synchronous):
  *   depth_bits [n_items] uint32 (0xFFFFFFFF for culled items), rect [n_items][4] int32

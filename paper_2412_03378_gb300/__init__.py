@@ -23,6 +23,7 @@ _LIB = None
 VG_F32, VG_BF16, VG_F16 = 0, 1, 2
 FLAG_FIXED_CAPACITY = 1
 FLAG_COUNT_PAIRS = 2
+FLAG_GRAD_ZERO = 4
 _STATUS = {0: "VG_OK", 1: "VG_ERR_INVALID_ARG", 2: "VG_ERR_CUDA", 3: "VG_ERR_OOM", 4: "VG_ERR_CAPACITY",
            5: "VG_ERR_TIMEOUT", 6: "VG_ERR_UNSUPPORTED", 7: "VG_ERR_STATE"}
 TILE = 16
@@ -58,10 +59,14 @@ class _Opts(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
+class _StageTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("calls", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("n_items", "n_visible", "n_culled", "n_instances", "n_tiles",
                                               "n_pixels", "instance_capacity", "n_pairs", "launches",
-                                              "device_bytes")]
+                                              "device_bytes", "n_pairs_bwd")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -82,6 +87,8 @@ _SIGS = {
                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_query": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_read_keys": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "vg_profile_enable": [ctypes.c_void_p, ctypes.c_int32],
+    "vg_profile_read": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "vg_read_bins": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
 }
 
@@ -264,6 +271,16 @@ class Workspace:
         s = Stats()
         self._chk(self._L.vg_query(self.h, ctypes.byref(s), _stream(stream)))
         return s.as_dict()
+
+    def profile_enable(self, on=True):
+        self._chk(self._L.vg_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        """{stage: (calls, total_ms)} of the event-timed stages since profile_enable."""
+        arr = (_StageTime * 32)()
+        n = ctypes.c_int32()
+        self._chk(self._L.vg_profile_read(self.h, arr, 32, ctypes.byref(n)))
+        return {arr[i].name.decode(): (int(arr[i].calls), float(arr[i].total_ms)) for i in range(n.value)}
 
     def read_keys(self):
         import numpy as np

@@ -53,9 +53,52 @@ struct vg_workspace {
     DBuf<unsigned long long> counters;   // [0] visible items, [1] evaluated pairs
     DBuf<float> tomo_cs;
     uint32_t *h_total = nullptr;         // pinned
+
+    // per-stage event timing (vg_profile_enable)
+    bool prof_on = false;
+    struct ProfRec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> prof_pool;
 };
 
 namespace {
+
+enum Stage { ST_PRE, ST_DEPTH, ST_SCAN, ST_DUP, ST_TILE, ST_RANGES, ST_FWD, ST_BWD, ST_CHAIN, ST_LOSS, ST_TFWD,
+             ST_TBWD, ST_COUNT };
+const char *kStageName[ST_COUNT] = {"preprocess", "depth_sort", "scan",     "duplicate", "tile_sort", "ranges",
+                                    "render_fwd", "render_bwd", "chain",    "l2_loss",   "tomo_fwd",  "tomo_bwd"};
+
+cudaEvent_t prof_event(vg_workspace *ws) {
+    if (!ws->prof_pool.empty()) {
+        cudaEvent_t e = ws->prof_pool.back();
+        ws->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records an event pair around a stage on the launching stream while profiling is on.
+struct ProfScope {
+    vg_workspace *ws;
+    cudaStream_t st;
+    int idx = -1;
+    ProfScope(vg_workspace *w, int stage, cudaStream_t s) : ws(w), st(s) {
+        if (!ws->prof_on) return;
+        cudaEvent_t a = prof_event(ws), b = prof_event(ws);
+        if (!a || !b) return;
+        cudaEventRecord(a, st);
+        ws->prof.push_back({stage, a, b});
+        idx = (int)ws->prof.size() - 1;
+    }
+    ~ProfScope() {
+        if (idx >= 0) cudaEventRecord(ws->prof[idx].b, st);
+    }
+};
 
 vg_status fail(vg_workspace *ws, vg_status s, const std::string &msg) {
     if (ws) ws->err = msg;
@@ -197,6 +240,11 @@ vg_status vg_workspace_destroy(vg_workspace *ws) {
     release(ws->counters);
     release(ws->tomo_cs);
     if (ws->h_total) cudaFreeHost(ws->h_total);
+    for (auto &r : ws->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ws->prof_pool) cudaEventDestroy(e);
     delete ws;
     return VG_OK;
 }
@@ -325,9 +373,11 @@ vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera
     ws->bp.T_stop = opts->T_stop;
     for (int c = 0; c < 3; ++c) ws->bp.bg[c] = opts->bg[c];
     VG_CUDA(ws, cudaMemsetAsync(ws->counters.p, 0, sizeof(unsigned long long), st));
-    if (n_items > 0)
+    if (n_items > 0) {
+        ProfScope ps(ws, ST_PRE, st);
         VG_CUDA(ws, launch_preprocess(ws->g, ws->views.p, n_views, opts->z_near, opts->tau_cut, ws->rec.p, ws->depth.p,
                                       ws->count.p, ws->rect.p, ws->counters.p, st, &ws->launches));
+    }
     ws->stage = 1;
     return VG_OK;
 }
@@ -339,13 +389,20 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
     const long long n = ws->n_items;
     VG_TRY(reserve_sort_scratch(ws, n));
     // 1. items by depth key (stable: ties keep index order)
-    VG_CUDA(ws, cudaMemcpyAsync(ws->skey[0].p, ws->depth.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    VG_CUDA(ws, launch_iota(ws->sval[0].p, n, st, &ws->launches));
-    uint32_t *ksorted = nullptr;
-    VG_CUDA(ws, launch_radix_sort(ws->skey[0].p, ws->sval[0].p, ws->skey[1].p, ws->sval[1].p, n, 32, ws->hist.p,
-                                  ws->scan_tmp.p, &ksorted, &ws->perm, st, &ws->launches));
+    {
+        ProfScope ps(ws, ST_DEPTH, st);
+        VG_CUDA(ws, cudaMemcpyAsync(ws->skey[0].p, ws->depth.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice,
+                                    st));
+        VG_CUDA(ws, launch_iota(ws->sval[0].p, n, st, &ws->launches));
+        uint32_t *ksorted = nullptr;
+        VG_CUDA(ws, launch_radix_sort(ws->skey[0].p, ws->sval[0].p, ws->skey[1].p, ws->sval[1].p, n, 32, ws->hist.p,
+                                      ws->scan_tmp.p, &ksorted, &ws->perm, st, &ws->launches));
+    }
     // 2. instance offsets in depth order
-    VG_CUDA(ws, launch_scan_gather(ws->count.p, ws->perm, ws->offsets.p, n, ws->scan_tmp.p, st, &ws->launches));
+    {
+        ProfScope ps(ws, ST_SCAN, st);
+        VG_CUDA(ws, launch_scan_gather(ws->count.p, ws->perm, ws->offsets.p, n, ws->scan_tmp.p, st, &ws->launches));
+    }
     long long total;
     if (ws->opts.flags & VG_FLAG_FIXED_CAPACITY) {
         return fail(ws, VG_ERR_UNSUPPORTED, "fixed-capacity binning is not implemented in this build");
@@ -357,13 +414,22 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
     }
     ws->n_inst = total;
     // 3. duplicate in depth order, 4. stable sort by tile id, 5. per-tile ranges
-    VG_CUDA(ws, launch_duplicate(ws->perm, ws->offsets.p, ws->rect.p, ws->views.p, n, ws->g.n, ws->ikey[0].p,
-                                 ws->ival[0].p, ws->capacity, st, &ws->launches));
-    VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, total,
-                                  bits_for(ws->n_tiles), ws->hist.p, ws->scan_tmp.p, &ws->inst_key, &ws->inst_item, st,
-                                  &ws->launches));
+    {
+        ProfScope ps(ws, ST_DUP, st);
+        VG_CUDA(ws, launch_duplicate(ws->perm, ws->offsets.p, ws->rect.p, ws->views.p, n, ws->g.n, ws->ikey[0].p,
+                                     ws->ival[0].p, ws->capacity, st, &ws->launches));
+    }
+    {
+        ProfScope ps(ws, ST_TILE, st);
+        VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, total,
+                                      bits_for(ws->n_tiles), ws->hist.p, ws->scan_tmp.p, &ws->inst_key,
+                                      &ws->inst_item, st, &ws->launches));
+    }
     VG_TRY(ensure(ws, ws->ranges, (size_t)ws->n_tiles, "tile ranges"));
-    VG_CUDA(ws, launch_ranges(ws->inst_key, total, ws->ranges.p, ws->n_tiles, st, &ws->launches));
+    {
+        ProfScope ps(ws, ST_RANGES, st);
+        VG_CUDA(ws, launch_ranges(ws->inst_key, total, ws->ranges.p, ws->n_tiles, st, &ws->launches));
+    }
     ws->stage = 2;
     return VG_OK;
 }
@@ -381,8 +447,12 @@ vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stre
         pc = ws->counters.p + 1;
         VG_CUDA(ws, cudaMemsetAsync(pc, 0, sizeof(unsigned long long), st));
     }
-    VG_CUDA(ws, launch_render_fwd(ws->views.p, ws->tile_view.p, ws->n_tiles, ws->ranges.p, ws->inst_item, ws->rec.p,
-                                  ws->bp, rgb, T_final, ws->T_fin.p, ws->S_fin.p, ws->nlast.p, pc, st, &ws->launches));
+    {
+        ProfScope ps(ws, ST_FWD, st);
+        VG_CUDA(ws, launch_render_fwd(ws->views.p, ws->tile_view.p, ws->n_tiles, ws->ranges.p, ws->inst_item,
+                                      ws->rec.p, ws->bp, rgb, T_final, ws->T_fin.p, ws->S_fin.p, ws->nlast.p, pc, st,
+                                      &ws->launches));
+    }
     ws->stage = 3;
     return VG_OK;
 }
@@ -395,12 +465,31 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
         return fail(ws, VG_ERR_INVALID_ARG, "a gradient pointer is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     VG_TRY(ensure(ws, ws->grad, (size_t)ws->n_items * kGradN, "gradient accumulators"));
+    if ((ws->opts.flags & VG_FLAG_GRAD_ZERO) && ws->g.n > 0) {
+        const size_t n = (size_t)ws->g.n;
+        VG_CUDA(ws, cudaMemsetAsync(dmu, 0, n * 3 * sizeof(float), st));
+        VG_CUDA(ws, cudaMemsetAsync(dscale, 0, n * 3 * sizeof(float), st));
+        VG_CUDA(ws, cudaMemsetAsync(dquat, 0, n * 4 * sizeof(float), st));
+        VG_CUDA(ws, cudaMemsetAsync(dkappa, 0, n * sizeof(float), st));
+        if (dsh)
+            VG_CUDA(ws, cudaMemsetAsync(dsh, 0, n * 3 * (size_t)((ws->g.sh_degree + 1) * (ws->g.sh_degree + 1)) *
+                                                    sizeof(float), st));
+    }
     if (ws->n_items > 0)
         VG_CUDA(ws, cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st));
-    VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, ws->n_tiles, ws->ranges.p, ws->inst_item, ws->rec.p,
-                                  ws->bp, ws->T_fin.p, ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, ws->grad.p, st,
-                                  &ws->launches));
+    unsigned long long *pc = nullptr;
+    if (ws->opts.flags & VG_FLAG_COUNT_PAIRS) {
+        pc = ws->counters.p + 2;
+        VG_CUDA(ws, cudaMemsetAsync(pc, 0, sizeof(unsigned long long), st));
+    }
+    {
+        ProfScope ps(ws, ST_BWD, st);
+        VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, ws->n_tiles, ws->ranges.p, ws->inst_item,
+                                      ws->rec.p, ws->bp, ws->T_fin.p, ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT,
+                                      ws->grad.p, pc, st, &ws->launches));
+    }
     if (ws->n_items > 0) {
+        ProfScope ps(ws, ST_CHAIN, st);
         GaussIn g = ws->g;
         VG_CUDA(ws, launch_chain(g, ws->views.p, ws->n_views, ws->grad.p, dmu, dscale, dquat, dkappa, dsh, st,
                                  &ws->launches));
@@ -429,6 +518,7 @@ vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n
                      float *grad, void *stream) {
     if (!ws) return VG_ERR_INVALID_ARG;
     if (n < 0 || !loss || (n > 0 && (!x || !y || !grad))) return fail(ws, VG_ERR_INVALID_ARG, "invalid loss arguments");
+    ProfScope ps(ws, ST_LOSS, (cudaStream_t)stream);
     VG_CUDA(ws, launch_l2_loss(x, y, n, scale, loss, grad, (cudaStream_t)stream, &ws->launches));
     return VG_OK;
 }
@@ -436,7 +526,7 @@ vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n
 vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream) {
     if (!ws || !out) return VG_ERR_INVALID_ARG;
     VG_CUDA(ws, cudaStreamSynchronize((cudaStream_t)stream));
-    unsigned long long c[2] = {0, 0};
+    unsigned long long c[3] = {0, 0, 0};
     VG_CUDA(ws, cudaMemcpy(c, ws->counters.p, sizeof(c), cudaMemcpyDeviceToHost));
     memset(out, 0, sizeof(*out));
     out->n_items = ws->n_items;
@@ -446,6 +536,7 @@ vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream) {
     out->n_pixels = ws->n_pixels;
     out->instance_capacity = ws->capacity;
     out->n_pairs = (int64_t)c[1];
+    out->n_pairs_bwd = (int64_t)c[2];
     out->launches = ws->launches;
     size_t bytes = ws->views.n * sizeof(ViewInfo) + ws->tile_view.n * 4 + ws->rec.n * 16 + ws->depth.n * 4 +
                    ws->count.n * 4 + ws->offsets.n * 4 + ws->rect.n * 8 + ws->ranges.n * 8 + ws->S_fin.n * 4 +
@@ -453,6 +544,46 @@ vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream) {
     for (int k = 0; k < 2; ++k)
         bytes += (ws->skey[k].n + ws->sval[k].n + ws->ikey[k].n + ws->ival[k].n) * 4;
     out->device_bytes = (int64_t)bytes;
+    return VG_OK;
+}
+
+vg_status vg_profile_enable(vg_workspace *ws, int32_t enable) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    for (auto &r : ws->prof) {
+        ws->prof_pool.push_back(r.a);
+        ws->prof_pool.push_back(r.b);
+    }
+    ws->prof.clear();
+    ws->prof_on = enable != 0;
+    return VG_OK;
+}
+
+vg_status vg_profile_read(vg_workspace *ws, vg_stage_time *out, int32_t capacity, int32_t *n_out) {
+    if (!ws || !n_out || (capacity > 0 && !out)) return VG_ERR_INVALID_ARG;
+    double tot[ST_COUNT] = {0};
+    long long calls[ST_COUNT] = {0};
+    for (auto &r : ws->prof) {
+        VG_CUDA(ws, cudaEventSynchronize(r.b));
+        float ms = 0.0f;
+        VG_CUDA(ws, cudaEventElapsedTime(&ms, r.a, r.b));
+        tot[r.stage] += ms;
+        calls[r.stage] += 1;
+        ws->prof_pool.push_back(r.a);
+        ws->prof_pool.push_back(r.b);
+    }
+    ws->prof.clear();
+    int n = 0;
+    for (int k = 0; k < ST_COUNT; ++k) {
+        if (!calls[k]) continue;
+        if (n < capacity) {
+            memset(out[n].name, 0, sizeof(out[n].name));
+            strncpy(out[n].name, kStageName[k], sizeof(out[n].name) - 1);
+            out[n].calls = calls[k];
+            out[n].total_ms = tot[k];
+        }
+        ++n;
+    }
+    *n_out = n < capacity ? n : capacity;
     return VG_OK;
 }
 

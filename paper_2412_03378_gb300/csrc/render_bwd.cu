@@ -15,11 +15,13 @@ namespace vg {
 
 constexpr int kGradUsed = 22;
 
+template <bool COUNT>
 __global__ void __launch_bounds__(kTilePix)
 k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const uint2 *__restrict__ ranges,
              const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, BlendParams bp,
              const float *__restrict__ T_fin, const float *__restrict__ S_fin, const uint32_t *__restrict__ nlast,
-             const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT, float *__restrict__ grad_acc) {
+             const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT, float *__restrict__ grad_acc,
+             unsigned long long *__restrict__ pair_count) {
     __shared__ float4 srec[kTilePix * kRecF4];
     __shared__ float sacc[kTilePix * kGradUsed];
     __shared__ uint32_t sitem[kTilePix];
@@ -56,6 +58,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     float Tafter = ex2_approx(__fmul_rn(-kLog2eF, S));
     float R0 = Tend * bp.bg[0], R1 = Tend * bp.bg[1], R2 = Tend * bp.bg[2];
     const float gTterm = -gT * Tend;
+    unsigned long long pairs = 0;
 
     for (uint32_t end = tile_last; end > rg.x;) {
         const uint32_t start = (end - rg.x > (uint32_t)kTilePix) ? end - kTilePix : rg.x;
@@ -75,6 +78,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
 #pragma unroll
             for (int k = 0; k < kGradUsed; ++k) gv[k] = 0.0f;
             bool on = inside && idx < my_last;
+            if (COUNT && on) ++pairs;
             if (on) {
                 const float4 *r = &srec[j * kRecF4];
                 const float4 r5 = r[5];
@@ -140,15 +144,26 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
         __syncthreads();
         end = start;
     }
+    if (COUNT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        if (lane == 0 && pairs) atomicAdd(pair_count, pairs);
+    }
 }
 
 cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, long long n_tiles, const uint2 *ranges,
                               const uint32_t *sorted_item, const float4 *rec, const BlendParams &bp, const float *T_fin,
                               const float *S_fin, const uint32_t *nlast, const float *dL_drgb, const float *dL_dT,
-                              float *grad_acc, cudaStream_t st, long long *launches) {
+                              float *grad_acc, unsigned long long *pair_count, cudaStream_t st, long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
-    k_render_bwd<<<(unsigned)n_tiles, kTilePix, 0, st>>>(views_d, tile_view, ranges, sorted_item, rec, bp, T_fin, S_fin,
-                                                         nlast, dL_drgb, dL_dT, grad_acc);
+    if (pair_count)
+        k_render_bwd<true><<<(unsigned)n_tiles, kTilePix, 0, st>>>(views_d, tile_view, ranges, sorted_item, rec, bp,
+                                                                  T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc,
+                                                                  pair_count);
+    else
+        k_render_bwd<false><<<(unsigned)n_tiles, kTilePix, 0, st>>>(views_d, tile_view, ranges, sorted_item, rec, bp,
+                                                                   T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc,
+                                                                   nullptr);
     *launches += 1;
     return cudaGetLastError();
 }

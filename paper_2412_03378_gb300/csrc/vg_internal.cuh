@@ -110,7 +110,7 @@ cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, lon
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
                               const BlendParams &bp, const float *T_fin, const float *S_fin,
                               const uint32_t *nlast, const float *dL_drgb, const float *dL_dT, float *grad_acc,
-                              cudaStream_t st, long long *launches);
+                              unsigned long long *pair_count, cudaStream_t st, long long *launches);
 
 cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc,
                          float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st,
