@@ -179,6 +179,34 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
                         float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh,
                         void *stream);
 
+/* Backward that allocates no device memory.  The paper has no counterpart: this is a
+ * library-usage variant of vg_render_bwd with the same arguments and results.
+ *
+ * vg_render_bwd keeps its per-(view, Gaussian) gradient accumulator (96 bytes per item) in
+ * the workspace and grows it with cudaMalloc when a larger scene arrives; cudaFree and
+ * cudaMalloc can also synchronise the whole device.  Some callers cannot allow that at
+ * backward time: a process whose device memory belongs to another allocator (a framework's
+ * caching allocator) or to a budget fixed in advance, or a latency-critical loop that must
+ * not stall on a device-wide synchronisation.  This entry point serves them: it calls no
+ * cudaMalloc, cudaFree or allocating library routine, and keeps the accumulator in a
+ * fixed array inside the library instead.
+ *
+ *  - Limit: views x Gaussians of the last vg_preprocess must be <= VG_NOALLOC_MAX_ITEMS;
+ *    larger requests return VG_ERR_INVALID_ARG and launch nothing.
+ *  - The array (VG_NOALLOC_MAX_ITEMS x 96 bytes = 6 MiB) is a static device allocation of
+ *    the library: every GPU that loads the library holds it until the process exits.
+ *  - The first call on a device looks up the array's device address with that device
+ *    current; make that first call before any stream capture.
+ *  - Every call shares the one array.  Each call clears the part it uses before
+ *    accumulating, but calls whose work overlaps on the GPU (different streams or
+ *    workspaces in flight at once) race on it: serialise them.
+ *  - The workspace's forward state must exist (vg_render_fwd ran on it); nothing in the
+ *    workspace is resized. */
+#define VG_NOALLOC_MAX_ITEMS 65536
+vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const float *dL_dT,
+                                float *dmu, float *dscale, float *dquat, float *dkappa,
+                                float *dsh, void *stream);
+
 /* Tomography (Sec. 6.2, Eq. 21): for every angle and detector pixel,
  *   proj[a][j][i] = exp(-sum_g tau_g(ray)),  float32 device buffer [n_angles][det_h][det_w].
  * If dL_dproj is not NULL it also runs the backward and accumulates dmu, dscale, dquat,

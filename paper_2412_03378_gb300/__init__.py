@@ -82,6 +82,7 @@ _SIGS = {
     "vg_bin_sort": [ctypes.c_void_p, ctypes.c_void_p],
     "vg_render_fwd": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_render_bwd": [ctypes.c_void_p] + [ctypes.c_void_p] * 7 + [ctypes.c_void_p],
+    "vg_render_bwd_noalloc": [ctypes.c_void_p] + [ctypes.c_void_p] * 7 + [ctypes.c_void_p],
     "vg_project_tomo": [ctypes.c_void_p] * 11,
     "vg_l2_loss": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
@@ -250,6 +251,11 @@ class Workspace:
     def render_bwd(self, dL_drgb, dL_dT, dmu, dscale, dquat, dkappa, dsh, stream=None):
         self._chk(self._L.vg_render_bwd(self.h, _ptr(dL_drgb), _ptr(dL_dT), _ptr(dmu), _ptr(dscale), _ptr(dquat),
                                         _ptr(dkappa), _ptr(dsh), _stream(stream)))
+
+    def render_bwd_noalloc(self, dL_drgb, dL_dT, dmu, dscale, dquat, dkappa, dsh, stream=None):
+        """vg_render_bwd_noalloc: the backward without any device allocation (see vg.h)."""
+        self._chk(self._L.vg_render_bwd_noalloc(self.h, _ptr(dL_drgb), _ptr(dL_dT), _ptr(dmu), _ptr(dscale),
+                                                _ptr(dquat), _ptr(dkappa), _ptr(dsh), _stream(stream)))
 
     def project_tomo(self, g: Gaussians, beam, opts: Opts, proj, dL_dproj=None, dmu=None, dscale=None, dquat=None,
                      dkappa=None, stream=None):

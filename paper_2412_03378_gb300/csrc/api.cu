@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -494,6 +495,69 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
         VG_CUDA(ws, launch_chain(g, ws->views.p, ws->n_views, ws->grad.p, dmu, dscale, dquat, dkappa, dsh, st,
                                  &ws->launches));
     }
+    return VG_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free backward
+// The per-item gradient accumulator of vg_render_bwd_noalloc: a fixed array that the
+// library's module brings onto every device it is loaded on.  Host code must not pass the
+// symbol itself to a kernel (in host code it names a host-side stand-in); the device
+// address comes from cudaGetSymbolAddress, looked up once per device.
+static __device__ __align__(256) float g_noalloc_acc[(size_t)VG_NOALLOC_MAX_ITEMS * kGradN];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kNoallocMaxDevices = 64;
+float *g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+vg_status noalloc_scratch(vg_workspace *ws, float **out) {
+    int dev = -1;
+    VG_CUDA(ws, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(ws, VG_ERR_UNSUPPORTED, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_acc);
+        if (e != cudaSuccess || !p)
+            return fail(ws, VG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = (float *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return VG_OK;
+}
+}  // namespace
+
+vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const float *dL_dT, float *dmu,
+                                float *dscale, float *dquat, float *dkappa, float *dsh, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (ws->stage < 3) return fail(ws, VG_ERR_STATE, "vg_render_bwd_noalloc before vg_render_fwd");
+    if ((!dL_drgb && ws->n_pixels > 0) || (ws->g.n > 0 && (!dmu || !dscale || !dquat || !dkappa)))
+        return fail(ws, VG_ERR_INVALID_ARG, "a gradient pointer is NULL");
+    if (ws->n_items > (long long)VG_NOALLOC_MAX_ITEMS)
+        return fail(ws, VG_ERR_INVALID_ARG,
+                    "views x Gaussians = " + std::to_string(ws->n_items) + " exceeds VG_NOALLOC_MAX_ITEMS = " +
+                        std::to_string((long long)VG_NOALLOC_MAX_ITEMS) + " of the allocation-free backward");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *acc = nullptr;
+    VG_TRY(noalloc_scratch(ws, &acc));
+    if ((ws->opts.flags & VG_FLAG_GRAD_ZERO) && ws->g.n > 0) {
+        const size_t n = (size_t)ws->g.n;
+        VG_CUDA(ws, cudaMemsetAsync(dmu, 0, n * 3 * sizeof(float), st));
+        VG_CUDA(ws, cudaMemsetAsync(dscale, 0, n * 3 * sizeof(float), st));
+        VG_CUDA(ws, cudaMemsetAsync(dquat, 0, n * 4 * sizeof(float), st));
+        VG_CUDA(ws, cudaMemsetAsync(dkappa, 0, n * sizeof(float), st));
+        if (dsh)
+            VG_CUDA(ws, cudaMemsetAsync(dsh, 0, n * 3 * (size_t)((ws->g.sh_degree + 1) * (ws->g.sh_degree + 1)) *
+                                                    sizeof(float), st));
+    }
+    // the array keeps the previous call's sums: clear the part this call accumulates into
+    if (ws->n_items > 0) VG_CUDA(ws, cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st));
+    VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, ws->n_tiles, ws->ranges.p, ws->inst_item, ws->rec.p,
+                                  ws->bp, ws->T_fin.p, ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, acc, nullptr, st,
+                                  &ws->launches));
+    if (ws->n_items > 0)
+        VG_CUDA(ws, launch_chain(ws->g, ws->views.p, ws->n_views, acc, dmu, dscale, dquat, dkappa, dsh, st,
+                                 &ws->launches));
     return VG_OK;
 }
 
