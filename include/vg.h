@@ -94,12 +94,18 @@ typedef struct {
  *   tau_max    tau is clamped to tau_max, i.e. alpha <= 1 - exp(-tau_max) (INFINITY: none);
  *   T_stop     a pixel stops once its transmittance falls below T_stop (0: never);
  *   bg         background colour added with the final transmittance;
- *   z_near     Gaussians whose mean has camera z <= z_near are culled. */
+ *   z_near     Gaussians whose mean has camera z <= z_near are culled.
+ * The paper states none of these values; the two presets used by the tests are "exact"
+ * (alpha_min 0, tau_max inf, T_stop 0) and the 3DGS conventions (alpha_min 1/255,
+ * tau_max ln 100, T_stop 1e-4). */
 typedef struct {
     float alpha_min, tau_cut, tau_max, T_stop;
     float bg[3];
     float z_near;
     uint32_t flags;      /* VG_FLAG_* */
+    int32_t pixels_per_thread;  /* blend kernels: pixels owned by one thread, 1, 2 or 4;
+                                   0 = the library default.  Results are identical; only
+                                   speed differs (see vg_autotune). */
 } vg_opts;
 
 #define VG_FLAG_FIXED_CAPACITY 1u  /* never synchronise to read the instance count; fail with

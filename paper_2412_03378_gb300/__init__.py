@@ -56,7 +56,7 @@ class _Beam(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("alpha_min", ctypes.c_float), ("tau_cut", ctypes.c_float), ("tau_max", ctypes.c_float),
                 ("T_stop", ctypes.c_float), ("bg", ctypes.c_float * 3), ("z_near", ctypes.c_float),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("pixels_per_thread", ctypes.c_int32)]
 
 
 class _StageTime(ctypes.Structure):
@@ -135,6 +135,7 @@ class Opts:
     bg: tuple = (0.0, 0.0, 0.0)
     z_near: float = 0.2
     flags: int = 0
+    pixels_per_thread: int = 0
 
     @staticmethod
     def exact(**kw):
@@ -153,7 +154,7 @@ class Opts:
         o.alpha_min, o.tau_cut, o.tau_max, o.T_stop = self.alpha_min, self.tau_cut, self.tau_max, self.T_stop
         for k in range(3):
             o.bg[k] = self.bg[k]
-        o.z_near, o.flags = self.z_near, self.flags
+        o.z_near, o.flags, o.pixels_per_thread = self.z_near, self.flags, self.pixels_per_thread
         return o
 
 

@@ -320,6 +320,34 @@ cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, uint2 *r
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------- tile order
+// Longest-first scheduling of the blend kernels: tiles sorted by descending instance count
+// (a stable 16-bit radix sort of 0xFFFF - min(count, 0xFFFF)).
+__global__ void k_tile_keys(const uint2 *__restrict__ ranges, long long n, uint32_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t c = r.y - r.x;
+        keys[t] = 0xFFFFu - (c < 0xFFFFu ? c : 0xFFFFu);
+        vals[t] = (uint32_t)t;
+    }
+}
+
+cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *keys, uint32_t *vals,
+                              uint32_t *keys_tmp, uint32_t *vals_tmp, uint32_t *hist, uint32_t *scan_tmp,
+                              uint32_t **order, cudaStream_t st, long long *launches) {
+    if (n_tiles <= 0) {
+        *order = vals;
+        return cudaSuccess;
+    }
+    long long b = (n_tiles + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    k_tile_keys<<<(unsigned)b, 256, 0, st>>>(ranges, n_tiles, keys, vals);
+    *launches += 1;
+    uint32_t *ko = nullptr;
+    return launch_radix_sort(keys, vals, keys_tmp, vals_tmp, n_tiles, 16, hist, scan_tmp, &ko, order, st, launches);
+}
+
 // ---------------------------------------------------------------------------- L2 loss
 __global__ void k_l2_loss(const float *__restrict__ x, const float *__restrict__ y, long long n, float scale,
                           float *__restrict__ loss, float *__restrict__ grad) {

@@ -54,4 +54,95 @@ __device__ __forceinline__ void eval_pair(const float4 &r0, const float4 &r1, co
     e.tau = __fmul_rn(ex2_approx(fmaf(e.m2, -kHalfLog2e, __fadd_rn(r5.x, p.Lp))), e.rs);
 }
 
+// A thread owns P pixels of a 16x16 tile (P = 1, 2 or 4); 256 / P threads per tile.
+//   P = 1: pixel (t % 16, t / 16)
+//   P = 2: pixels (t % 16, 2 (t / 16) + k), k = 0, 1            (a warp covers 16 x 4 pixels)
+//   P = 4: pixels (2 (t % 8) + (k & 1), 2 (t / 8) + (k >> 1))    (a warp covers 16 x 8 pixels)
+// d' and o' x d' are affine in the pixel offset, so a thread's other pixels follow from its
+// first by one add per component.  Forward and backward both use pair_eval_at(), so they
+// compute the same bits and take the same skip decisions.
+template <int P>
+struct PixLayout {
+    static constexpr int kThreads = kTilePix / P;
+    __device__ static void origin(int t, int &x, int &y) {
+        if (P == 1) {
+            x = t & 15;
+            y = t >> 4;
+        } else if (P == 2) {
+            x = t & 15;
+            y = 2 * (t >> 4);
+        } else {
+            x = 2 * (t & 7);
+            y = 2 * (t >> 3);
+        }
+    }
+    __host__ __device__ static constexpr int ox(int k) { return P == 4 ? (k & 1) : 0; }
+    __host__ __device__ static constexpr int oy(int k) { return P == 4 ? (k >> 1) : (P == 2 ? k : 0); }
+};
+
+struct QuadBase {
+    float dx, dy;          // offset of the thread's first pixel from the reference pixel
+    float dp[3], cr[3];    // d' and o' x d' there
+};
+
+__device__ __forceinline__ void quad_base(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
+                                          const float4 &r4, float x0, float y0, QuadBase &b) {
+    b.dx = __fsub_rn(x0, r4.z);
+    b.dy = __fsub_rn(y0, r4.w);
+    b.dp[0] = fmaf(r0.x, b.dx, fmaf(r0.w, b.dy, r1.z));
+    b.dp[1] = fmaf(r0.y, b.dx, fmaf(r1.x, b.dy, r1.w));
+    b.dp[2] = fmaf(r0.z, b.dx, fmaf(r1.y, b.dy, r2.x));
+    b.cr[0] = fmaf(r2.y, b.dx, fmaf(r3.x, b.dy, r3.w));
+    b.cr[1] = fmaf(r2.z, b.dx, fmaf(r3.y, b.dy, r4.x));
+    b.cr[2] = fmaf(r2.w, b.dx, fmaf(r3.z, b.dy, r4.y));
+}
+
+// d', o' x d', (dx, dy) of the pixel at offset (sx, sy) from the thread's first pixel, and
+// its tau (unclamped).
+__device__ __forceinline__ void pair_eval_at(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
+                                             const float4 &r5, const QuadBase &b, bool sx, bool sy, float Lp,
+                                             PairEval &e) {
+    const float A0[3] = {r0.x, r0.y, r0.z}, A1[3] = {r0.w, r1.x, r1.y};
+    const float C0[3] = {r2.y, r2.z, r2.w}, C1[3] = {r3.x, r3.y, r3.z};
+    e.dx = sx ? __fadd_rn(b.dx, 1.0f) : b.dx;
+    e.dy = sy ? __fadd_rn(b.dy, 1.0f) : b.dy;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float dpc = b.dp[c], crc = b.cr[c];
+        if (sx) {
+            dpc = __fadd_rn(dpc, A0[c]);
+            crc = __fadd_rn(crc, C0[c]);
+        }
+        if (sy) {
+            dpc = __fadd_rn(dpc, A1[c]);
+            crc = __fadd_rn(crc, C1[c]);
+        }
+        e.dp[c] = dpc;
+        e.cr[c] = crc;
+    }
+    const float a = fmaf(e.dp[0], e.dp[0], fmaf(e.dp[1], e.dp[1], __fmul_rn(e.dp[2], e.dp[2])));
+    const float q = fmaf(e.cr[0], e.cr[0], fmaf(e.cr[1], e.cr[1], __fmul_rn(e.cr[2], e.cr[2])));
+    e.rs = rsqrt_approx(a);
+    e.m2 = __fmul_rn(q, __fmul_rn(e.rs, e.rs));
+    e.tau = __fmul_rn(ex2_approx(fmaf(e.m2, -kHalfLog2e, __fadd_rn(r5.x, Lp))), e.rs);
+}
+
+// Warp reduce-scatter of NV <= 32 per-lane values: afterwards lane k (k < NV) holds the sum
+// over the warp of value k.  Five exchange steps of halving width: 16+8+4+2+1 shuffles.
+template <int NV>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[32], int lane) {
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool hi = (lane & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            if (i >= NV && i + w >= NV) continue;   // both halves are structurally zero
+            const float keep = hi ? v[i + w] : v[i];
+            const float send = hi ? v[i] : v[i + w];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return v[0];
+}
+
 }  // namespace vg

@@ -15,53 +15,77 @@ namespace vg {
 
 constexpr int kGradUsed = 22;
 
-template <bool COUNT>
-__global__ void __launch_bounds__(kTilePix)
-k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const uint2 *__restrict__ ranges,
-             const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, BlendParams bp,
-             const float *__restrict__ T_fin, const float *__restrict__ S_fin, const uint32_t *__restrict__ nlast,
-             const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT, float *__restrict__ grad_acc,
-             unsigned long long *__restrict__ pair_count) {
-    __shared__ float4 srec[kTilePix * kRecF4];
-    __shared__ float sacc[kTilePix * kGradUsed];
-    __shared__ uint32_t sitem[kTilePix];
+template <int P> struct BwdBounds;
+template <> struct BwdBounds<1> { static constexpr int kMinBlocks = 2; };
+template <> struct BwdBounds<2> { static constexpr int kMinBlocks = 4; };
+template <> struct BwdBounds<4> { static constexpr int kMinBlocks = 8; };
+
+// One CTA per tile (longest list first), 256/P threads owning P pixels each.  Per record the
+// 22 partials are summed over the thread's pixels in registers, then over the warp by a
+// reduce-scatter (lane k ends with partial k), over the CTA in shared memory, and finally
+// added to the item's accumulator with one set of global atomics per (tile, Gaussian).
+template <int P, bool COUNT>
+__global__ void __launch_bounds__(PixLayout<P>::kThreads, BwdBounds<P>::kMinBlocks)
+k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
+             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
+             BlendParams bp, const float *__restrict__ T_fin, const float *__restrict__ S_fin,
+             const uint32_t *__restrict__ nlast, const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT,
+             float *__restrict__ grad_acc, unsigned long long *__restrict__ pair_count) {
+    using L = PixLayout<P>;
+    constexpr int kThreads = L::kThreads;
+    constexpr int kChunk = kThreads;
+    __shared__ float4 srec[kChunk * kRecF4];
+    __shared__ float sacc[kChunk * kGradUsed];
+    __shared__ uint32_t sitem[kChunk];
     __shared__ uint32_t s_last;
 
-    const int tile = blockIdx.x;
+    const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
     const ViewInfo &V = views[tile_view[tile]];
     const int local = tile - V.tile_base;
     const int tyi = local / V.tiles_x, txi = local - tyi * V.tiles_x;
-    const int x = txi * kTile + (threadIdx.x & (kTile - 1)), y = tyi * kTile + (threadIdx.x / kTile);
-    const bool inside = x < V.W && y < V.H;
-    const PixelRay pr = pixel_ray(V, x, y);
+    int ix, iy;
+    L::origin(threadIdx.x, ix, iy);
+    const int x0 = txi * kTile + ix, y0 = tyi * kTile + iy;
     const uint2 rg = ranges[tile];
     const int lane = threadIdx.x & 31;
 
-    uint32_t my_last = rg.x;
-    float S = 0.0f, Tend = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, gT = 0.0f;
-    if (inside) {
-        const long long pix = V.pix_base + (long long)y * V.W + x;
-        my_last = nlast[pix];
-        S = S_fin[pix];
-        Tend = T_fin[pix];
-        g0 = dL_drgb[3 * pix];
-        g1 = dL_drgb[3 * pix + 1];
-        g2 = dL_drgb[3 * pix + 2];
-        gT = dL_dT ? dL_dT[pix] : 0.0f;
+    float Lp[P], S[P], Tafter[P], R0[P], R1[P], R2[P], g0[P], g1[P], g2[P], gTterm[P];
+    uint32_t my_last[P];
+    uint32_t thr_last = rg.x;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const int x = x0 + L::ox(k), y = y0 + L::oy(k);
+        Lp[k] = pixel_ray(V, x, y).Lp;
+        my_last[k] = rg.x;
+        S[k] = 0.0f;
+        float Tend = 1.0f;
+        g0[k] = g1[k] = g2[k] = gTterm[k] = 0.0f;
+        if (x < V.W && y < V.H) {
+            const long long pix = V.pix_base + (long long)y * V.W + x;
+            my_last[k] = nlast[pix];
+            S[k] = S_fin[pix];
+            Tend = T_fin[pix];
+            g0[k] = dL_drgb[3 * pix];
+            g1[k] = dL_drgb[3 * pix + 1];
+            g2[k] = dL_drgb[3 * pix + 2];
+            gTterm[k] = dL_dT ? -dL_dT[pix] * Tend : 0.0f;
+        }
+        Tafter[k] = ex2_approx(__fmul_rn(-kLog2eF, S[k]));
+        R0[k] = Tend * bp.bg[0];
+        R1[k] = Tend * bp.bg[1];
+        R2[k] = Tend * bp.bg[2];
+        thr_last = max(thr_last, my_last[k]);
     }
     if (threadIdx.x == 0) s_last = rg.x;
     __syncthreads();
-    if (my_last > rg.x) atomicMax(&s_last, my_last);
+    if (thr_last > rg.x) atomicMax(&s_last, thr_last);
     __syncthreads();
     const uint32_t tile_last = s_last;
-
-    float Tafter = ex2_approx(__fmul_rn(-kLog2eF, S));
-    float R0 = Tend * bp.bg[0], R1 = Tend * bp.bg[1], R2 = Tend * bp.bg[2];
-    const float gTterm = -gT * Tend;
+    const float xf = (float)x0, yf = (float)y0;
     unsigned long long pairs = 0;
 
     for (uint32_t end = tile_last; end > rg.x;) {
-        const uint32_t start = (end - rg.x > (uint32_t)kTilePix) ? end - kTilePix : rg.x;
+        const uint32_t start = (end - rg.x > (uint32_t)kChunk) ? end - kChunk : rg.x;
         const uint32_t n = end - start;
         if (threadIdx.x < n) {
             const uint32_t item = sorted_item[start + threadIdx.x];
@@ -70,73 +94,70 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
 #pragma unroll
             for (int k = 0; k < kRecF4; ++k) srec[threadIdx.x * kRecF4 + k] = __ldg(src + k);
         }
-        for (int k = threadIdx.x; k < kTilePix * kGradUsed; k += kTilePix) sacc[k] = 0.0f;
+        for (int k = threadIdx.x; k < kChunk * kGradUsed; k += kThreads) sacc[k] = 0.0f;
         __syncthreads();
         for (int j = (int)n - 1; j >= 0; --j) {
             const uint32_t idx = start + (uint32_t)j;
-            float gv[kGradUsed];
+            float gv[32];
 #pragma unroll
-            for (int k = 0; k < kGradUsed; ++k) gv[k] = 0.0f;
-            bool on = inside && idx < my_last;
-            if (COUNT && on) ++pairs;
-            if (on) {
+            for (int k = 0; k < 32; ++k) gv[k] = 0.0f;
+            bool any = false;
+            if (idx < thr_last) {
                 const float4 *r = &srec[j * kRecF4];
-                const float4 r5 = r[5];
-                PairEval e;
-                eval_pair(r[0], r[1], r[2], r[3], r[4], r5, pr, e);
-                const bool clamped = e.tau > bp.tau_max;
-                const float tau = fminf(e.tau, bp.tau_max);
-                if (tau < bp.tau_skip) {
-                    on = false;
-                } else {
+                const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
+                QuadBase qb;
+                quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    if (idx >= my_last[k]) continue;
+                    PairEval e;
+                    pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
+                    if (COUNT) ++pairs;
+                    const bool clamped = e.tau > bp.tau_max;
+                    const float tau = fminf(e.tau, bp.tau_max);
+                    if (tau < bp.tau_skip) continue;
+                    any = true;
                     const float e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
                     const float alpha = __fsub_rn(1.0f, e2);
-                    const float Sb = S - tau;
+                    const float Sb = S[k] - tau;
                     const float Tb = ex2_approx(-kLog2eF * Sb);
                     const float aT = alpha * Tb;
-                    gv[19] = g0 * aT;
-                    gv[20] = g1 * aT;
-                    gv[21] = g2 * aT;
-                    const float dtau = g0 * (r5.y * Tafter - R0) + g1 * (r5.z * Tafter - R1) +
-                                       g2 * (r5.w * Tafter - R2) + gTterm;
-                    R0 = fmaf(r5.y, aT, R0);
-                    R1 = fmaf(r5.z, aT, R1);
-                    R2 = fmaf(r5.w, aT, R2);
-                    S = Sb;
-                    Tafter = Tb;
+                    gv[19] = fmaf(g0[k], aT, gv[19]);
+                    gv[20] = fmaf(g1[k], aT, gv[20]);
+                    gv[21] = fmaf(g2[k], aT, gv[21]);
+                    const float dtau = g0[k] * (r5.y * Tafter[k] - R0[k]) + g1[k] * (r5.z * Tafter[k] - R1[k]) +
+                                       g2[k] * (r5.w * Tafter[k] - R2[k]) + gTterm[k];
+                    R0[k] = fmaf(r5.y, aT, R0[k]);
+                    R1[k] = fmaf(r5.z, aT, R1[k]);
+                    R2[k] = fmaf(r5.w, aT, R2[k]);
+                    S[k] = Sb;
+                    Tafter[k] = Tb;
                     if (!clamped) {
-                        const float G = dtau * tau;               // dL / d ln(tau)
-                        const float r2 = e.rs * e.rs;
-                        const float gda = G * r2 * (e.m2 - 1.0f);   // 2 dL/da
-                        const float gdq = -G * r2;                  // 2 dL/dq
+                        const float G = dtau * tau;                // dL / d ln(tau)
+                        const float r2s = e.rs * e.rs;
+                        const float gda = G * r2s * (e.m2 - 1.0f);   // 2 dL/da
+                        const float gdq = -G * r2s;                  // 2 dL/dq
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
                             const float a_ = gda * e.dp[c], q_ = gdq * e.cr[c];
-                            gv[c] = a_ * e.dx;
-                            gv[3 + c] = a_ * e.dy;
-                            gv[6 + c] = a_;
-                            gv[9 + c] = q_ * e.dx;
-                            gv[12 + c] = q_ * e.dy;
-                            gv[15 + c] = q_;
+                            gv[c] = fmaf(a_, e.dx, gv[c]);
+                            gv[3 + c] = fmaf(a_, e.dy, gv[3 + c]);
+                            gv[6 + c] += a_;
+                            gv[9 + c] = fmaf(q_, e.dx, gv[9 + c]);
+                            gv[12 + c] = fmaf(q_, e.dy, gv[12 + c]);
+                            gv[15 + c] += q_;
                         }
-                        gv[18] = G;
+                        gv[18] += G;
                     }
                 }
             }
-            if (__any_sync(0xffffffffu, on)) {
-#pragma unroll
-                for (int k = 0; k < kGradUsed; ++k) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) gv[k] += __shfl_xor_sync(0xffffffffu, gv[k], o);
-                }
-                float mine = 0.0f;
-#pragma unroll
-                for (int k = 0; k < kGradUsed; ++k) mine = (lane == k) ? gv[k] : mine;
-                if (lane < kGradUsed) atomicAdd(&sacc[j * kGradUsed + lane], mine);
+            if (__any_sync(0xffffffffu, any)) {
+                const float mine = warp_reduce_scatter<kGradUsed>(gv, lane);
+                if (lane < kGradUsed && mine != 0.0f) atomicAdd(&sacc[j * kGradUsed + lane], mine);
             }
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < (int)n * kGradUsed; k += kTilePix) {
+        for (int k = threadIdx.x; k < (int)n * kGradUsed; k += kThreads) {
             const int jj = k / kGradUsed, c = k - jj * kGradUsed;
             const float v = sacc[k];
             if (v != 0.0f) atomicAdd(&grad_acc[(size_t)sitem[jj] * kGradN + c], v);
@@ -151,19 +172,37 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
 }
 
-cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, long long n_tiles, const uint2 *ranges,
-                              const uint32_t *sorted_item, const float4 *rec, const BlendParams &bp, const float *T_fin,
-                              const float *S_fin, const uint32_t *nlast, const float *dL_drgb, const float *dL_dT,
-                              float *grad_acc, unsigned long long *pair_count, cudaStream_t st, long long *launches) {
-    if (n_tiles <= 0) return cudaSuccess;
+template <int P>
+static void launch_bwd_p(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                         const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const BlendParams &bp,
+                         const float *T_fin, const float *S_fin, const uint32_t *nlast, const float *dL_drgb,
+                         const float *dL_dT, float *grad_acc, unsigned long long *pair_count, cudaStream_t st) {
+    const unsigned threads = PixLayout<P>::kThreads;
     if (pair_count)
-        k_render_bwd<true><<<(unsigned)n_tiles, kTilePix, 0, st>>>(views_d, tile_view, ranges, sorted_item, rec, bp,
-                                                                  T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc,
-                                                                  pair_count);
+        k_render_bwd<P, true><<<(unsigned)n_tiles, threads, 0, st>>>(views_d, tile_view, tile_order, ranges,
+                                                                    sorted_item, rec, bp, T_fin, S_fin, nlast, dL_drgb,
+                                                                    dL_dT, grad_acc, pair_count);
     else
-        k_render_bwd<false><<<(unsigned)n_tiles, kTilePix, 0, st>>>(views_d, tile_view, ranges, sorted_item, rec, bp,
-                                                                   T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc,
-                                                                   nullptr);
+        k_render_bwd<P, false><<<(unsigned)n_tiles, threads, 0, st>>>(views_d, tile_view, tile_order, ranges,
+                                                                     sorted_item, rec, bp, T_fin, S_fin, nlast, dL_drgb,
+                                                                     dL_dT, grad_acc, nullptr);
+}
+
+cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
+                              const BlendParams &bp, int ppt, const float *T_fin, const float *S_fin,
+                              const uint32_t *nlast, const float *dL_drgb, const float *dL_dT, float *grad_acc,
+                              unsigned long long *pair_count, cudaStream_t st, long long *launches) {
+    if (n_tiles <= 0) return cudaSuccess;
+    if (ppt == 1)
+        launch_bwd_p<1>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, T_fin, S_fin, nlast,
+                        dL_drgb, dL_dT, grad_acc, pair_count, st);
+    else if (ppt == 4)
+        launch_bwd_p<4>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, T_fin, S_fin, nlast,
+                        dL_drgb, dL_dT, grad_acc, pair_count, st);
+    else
+        launch_bwd_p<2>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, T_fin, S_fin, nlast,
+                        dL_drgb, dL_dT, grad_acc, pair_count, st);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -1,75 +1,98 @@
 // Front-to-back blend of the depth-sorted per-tile lists (Eq. 14 with the Eq. 19 alpha).
 //
-// One CTA per 16x16 tile, one thread per pixel.  Records of the tile's Gaussians are staged
-// through shared memory in chunks of 256 in depth order; every pixel evaluates the closed
-// form in FP32 (FMA pipe + 3 MUFU ops per pair) and the CTA leaves as soon as all of its
-// pixels have reached T < T_stop.  No tensor cores: the work is not a dense contraction.
+// One CTA per 16x16 tile, tiles taken longest list first; each of the 256/P threads owns P
+// pixels (P = 1, 2, 4).  Records of the tile's Gaussians are staged through shared memory in
+// depth-ordered chunks (one record per thread); every record is read once per thread and
+// serves its P pixels, whose d' and o' x d' follow from the first pixel's by one add per
+// component.  The closed form is evaluated in FP32 (FMA pipe + 3 MUFU ops per pair); the CTA
+// leaves once all of its pixels have reached T < T_stop.  No tensor cores: the work is not a
+// dense contraction.
 #include "blend.cuh"
 
 namespace vg {
 
-template <bool COUNT>
-__global__ void __launch_bounds__(kTilePix)
-k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const uint2 *__restrict__ ranges,
-             const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, BlendParams bp,
-             float *__restrict__ rgb, float *__restrict__ T_user, float *__restrict__ T_ws, float *__restrict__ S_out,
-             uint32_t *__restrict__ nlast_out, unsigned long long *__restrict__ pair_count) {
-    __shared__ float4 srec[kTilePix * kRecF4];
-    const int tile = blockIdx.x;
+template <int P> struct FwdBounds;
+template <> struct FwdBounds<1> { static constexpr int kMinBlocks = 3; };
+template <> struct FwdBounds<2> { static constexpr int kMinBlocks = 6; };
+template <> struct FwdBounds<4> { static constexpr int kMinBlocks = 12; };
+
+template <int P, bool COUNT>
+__global__ void __launch_bounds__(PixLayout<P>::kThreads, FwdBounds<P>::kMinBlocks)
+k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
+             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
+             BlendParams bp, float *__restrict__ rgb, float *__restrict__ T_user, float *__restrict__ T_ws,
+             float *__restrict__ S_out, uint32_t *__restrict__ nlast_out, unsigned long long *__restrict__ pair_count) {
+    using L = PixLayout<P>;
+    constexpr int kChunk = L::kThreads;
+    __shared__ float4 srec[kChunk * kRecF4];
+    const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
     const ViewInfo &V = views[tile_view[tile]];
     const int local = tile - V.tile_base;
     const int tyi = local / V.tiles_x, txi = local - tyi * V.tiles_x;
-    const int x = txi * kTile + (threadIdx.x & (kTile - 1)), y = tyi * kTile + (threadIdx.x / kTile);
-    const bool inside = x < V.W && y < V.H;
-    const PixelRay pr = pixel_ray(V, x, y);
+    int ix, iy;
+    L::origin(threadIdx.x, ix, iy);
+    const int x0 = txi * kTile + ix, y0 = tyi * kTile + iy;
+    float Lp[P], T[P], S[P], c0[P], c1[P], c2[P];
+    uint32_t last[P];
     const uint2 rg = ranges[tile];
-
-    float T = 1.0f, S = 0.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
-    uint32_t last = rg.x;
-    bool done = !inside;
+    unsigned live = 0;   // bit k: pixel k is inside the image and not finished
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const int x = x0 + L::ox(k), y = y0 + L::oy(k);
+        Lp[k] = pixel_ray(V, x, y).Lp;
+        T[k] = 1.0f;
+        S[k] = c0[k] = c1[k] = c2[k] = 0.0f;
+        last[k] = rg.x;
+        if (x < V.W && y < V.H) live |= 1u << k;
+    }
+    const float xf = (float)x0, yf = (float)y0;
     unsigned long long pairs = 0;
-    for (uint32_t base = rg.x; base < rg.y; base += kTilePix) {
-        const uint32_t n = min((uint32_t)kTilePix, rg.y - base);
+    for (uint32_t base = rg.x; base < rg.y; base += kChunk) {
+        const uint32_t n = min((uint32_t)kChunk, rg.y - base);
         if (threadIdx.x < n) {
             const float4 *src = rec + (size_t)sorted_item[base + threadIdx.x] * kRecF4;
 #pragma unroll
             for (int k = 0; k < kRecF4; ++k) srec[threadIdx.x * kRecF4 + k] = __ldg(src + k);
         }
         __syncthreads();
-        if (!done) {
-            for (uint32_t j = 0; j < n; ++j) {
-                const float4 *r = &srec[j * kRecF4];
-                const float4 r5 = r[5];
+        for (uint32_t j = 0; j < n && live; ++j) {
+            const float4 *r = &srec[j * kRecF4];
+            const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
+            QuadBase qb;
+            quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                if (!(live & (1u << k))) continue;
                 PairEval e;
-                eval_pair(r[0], r[1], r[2], r[3], r[4], r5, pr, e);
+                pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
                 if (COUNT) ++pairs;
                 const float tau = fminf(e.tau, bp.tau_max);
                 if (tau < bp.tau_skip) continue;
                 const float e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
-                const float w = __fmul_rn(__fsub_rn(1.0f, e2), T);
-                c0 = fmaf(r5.y, w, c0);
-                c1 = fmaf(r5.z, w, c1);
-                c2 = fmaf(r5.w, w, c2);
-                T = __fmul_rn(T, e2);
-                S = __fadd_rn(S, tau);
-                last = base + j + 1;
-                if (T < bp.T_stop) {
-                    done = true;
-                    break;
-                }
+                const float w = __fmul_rn(__fsub_rn(1.0f, e2), T[k]);
+                c0[k] = fmaf(r5.y, w, c0[k]);
+                c1[k] = fmaf(r5.z, w, c1[k]);
+                c2[k] = fmaf(r5.w, w, c2[k]);
+                T[k] = __fmul_rn(T[k], e2);
+                S[k] = __fadd_rn(S[k], tau);
+                last[k] = base + j + 1;
+                if (T[k] < bp.T_stop) live &= ~(1u << k);
             }
         }
-        if (__syncthreads_count(!done) == 0) break;
+        if (__syncthreads_count(live != 0) == 0) break;
     }
-    if (inside) {
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const int x = x0 + L::ox(k), y = y0 + L::oy(k);
+        if (x >= V.W || y >= V.H) continue;
         const long long pix = V.pix_base + (long long)y * V.W + x;
-        rgb[3 * pix + 0] = fmaf(T, bp.bg[0], c0);
-        rgb[3 * pix + 1] = fmaf(T, bp.bg[1], c1);
-        rgb[3 * pix + 2] = fmaf(T, bp.bg[2], c2);
-        T_ws[pix] = T;
-        if (T_user) T_user[pix] = T;
-        S_out[pix] = S;
-        nlast_out[pix] = last;
+        rgb[3 * pix + 0] = fmaf(T[k], bp.bg[0], c0[k]);
+        rgb[3 * pix + 1] = fmaf(T[k], bp.bg[1], c1[k]);
+        rgb[3 * pix + 2] = fmaf(T[k], bp.bg[2], c2[k]);
+        T_ws[pix] = T[k];
+        if (T_user) T_user[pix] = T[k];
+        S_out[pix] = S[k];
+        nlast_out[pix] = last[k];
     }
     if (COUNT) {
 #pragma unroll
@@ -78,17 +101,37 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
 }
 
-cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, long long n_tiles, const uint2 *ranges,
-                              const uint32_t *sorted_item, const float4 *rec, const BlendParams &bp, float *rgb,
-                              float *T_user, float *T_ws, float *S_out, uint32_t *nlast_out,
-                              unsigned long long *pair_count, cudaStream_t st, long long *launches) {
-    if (n_tiles <= 0) return cudaSuccess;
+template <int P>
+static void launch_fwd_p(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                         const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const BlendParams &bp,
+                         float *rgb, float *T_user, float *T_ws, float *S_out, uint32_t *nlast_out,
+                         unsigned long long *pair_count, cudaStream_t st) {
+    const unsigned threads = PixLayout<P>::kThreads;
     if (pair_count)
-        k_render_fwd<true><<<(unsigned)n_tiles, kTilePix, 0, st>>>(views_d, tile_view, ranges, sorted_item, rec, bp,
-                                                                  rgb, T_user, T_ws, S_out, nlast_out, pair_count);
+        k_render_fwd<P, true><<<(unsigned)n_tiles, threads, 0, st>>>(views_d, tile_view, tile_order, ranges,
+                                                                    sorted_item, rec, bp, rgb, T_user, T_ws, S_out,
+                                                                    nlast_out, pair_count);
     else
-        k_render_fwd<false><<<(unsigned)n_tiles, kTilePix, 0, st>>>(views_d, tile_view, ranges, sorted_item, rec, bp,
-                                                                   rgb, T_user, T_ws, S_out, nlast_out, nullptr);
+        k_render_fwd<P, false><<<(unsigned)n_tiles, threads, 0, st>>>(views_d, tile_view, tile_order, ranges,
+                                                                     sorted_item, rec, bp, rgb, T_user, T_ws, S_out,
+                                                                     nlast_out, nullptr);
+}
+
+cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
+                              const BlendParams &bp, int ppt, float *rgb, float *T_user, float *T_ws, float *S_out,
+                              uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st,
+                              long long *launches) {
+    if (n_tiles <= 0) return cudaSuccess;
+    if (ppt == 1)
+        launch_fwd_p<1>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, rgb, T_user, T_ws, S_out,
+                        nlast_out, pair_count, st);
+    else if (ppt == 4)
+        launch_fwd_p<4>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, rgb, T_user, T_ws, S_out,
+                        nlast_out, pair_count, st);
+    else
+        launch_fwd_p<2>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, rgb, T_user, T_ws, S_out,
+                        nlast_out, pair_count, st);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -100,17 +100,22 @@ cudaError_t launch_duplicate(const uint32_t *perm, const uint32_t *offsets, cons
 cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, uint2 *ranges, long long n_tiles,
                           cudaStream_t st, long long *launches);
 
-cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, long long n_tiles,
+cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
-                              const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
+                              const BlendParams &bp, int ppt, float *rgb, float *T_user, float *T_ws, float *S_out,
                               uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st,
                               long long *launches);
 
-cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, long long n_tiles,
+cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
-                              const BlendParams &bp, const float *T_fin, const float *S_fin,
+                              const BlendParams &bp, int ppt, const float *T_fin, const float *S_fin,
                               const uint32_t *nlast, const float *dL_drgb, const float *dL_dT, float *grad_acc,
                               unsigned long long *pair_count, cudaStream_t st, long long *launches);
+
+// Longest-first tile order: order[i] = tile with the i-th largest instance count.
+cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *keys, uint32_t *vals,
+                              uint32_t *keys_tmp, uint32_t *vals_tmp, uint32_t *hist, uint32_t *scan_tmp,
+                              uint32_t **order, cudaStream_t st, long long *launches);
 
 cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc,
                          float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st,

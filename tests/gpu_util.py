@@ -12,18 +12,18 @@ def dev_scene(vg, scene, rec_dtype=torch.float32, sh_dtype=torch.float32):
                         t(scene.kappa, rec_dtype), t(scene.sh, sh_dtype), scene.sh_degree)
 
 
-def vg_opts(vg, o, flags=0):
+def vg_opts(vg, o, flags=0, ppt=0):
     return vg.Opts(alpha_min=o["alpha_min"], tau_cut=o["tau_cut"], tau_max=o["tau_max"], T_stop=o["T_stop"],
-                   bg=tuple(o["bg"]), z_near=o["z_near"], flags=flags)
+                   bg=tuple(o["bg"]), z_near=o["z_near"], flags=flags, pixels_per_thread=ppt)
 
 
-def run_forward(vg, scene, cams, o, ws=None, flags=0, g=None):
+def run_forward(vg, scene, cams, o, ws=None, flags=0, g=None, ppt=0):
     ws = ws or vg.Workspace()
     g = g or dev_scene(vg, scene)
     P = sum(c.width * c.height for c in cams)
     rgb = torch.full((P, 3), float("nan"), device="cuda:0")
     T = torch.full((P,), float("nan"), device="cuda:0")
-    ws.preprocess(g, cams, vg_opts(vg, o, flags))
+    ws.preprocess(g, cams, vg_opts(vg, o, flags, ppt))
     ws.bin_sort()
     ws.render_fwd(rgb, T)
     torch.cuda.synchronize()
@@ -52,5 +52,29 @@ def grad_rel_err(g_gpu, g_ref):
     return float(np.max(np.abs(g_gpu - g_ref) / np.maximum(np.abs(g_ref), floor)))
 
 
-def oracle_lists_from_gpu_order(L):
-    return L
+def grad_block_err(g_gpu, g_ref, n):
+    """Per-Gaussian relative error of one parameter block (vector norm over its components),
+    floored at 1e-3 of the largest block norm of that parameter type."""
+    g = np.asarray(g_gpu, np.float64).reshape(n, -1)
+    r = np.asarray(g_ref, np.float64).reshape(n, -1)
+    nr = np.linalg.norm(r, axis=1)
+    floor = 1e-3 * max(float(nr.max()), 1e-30)
+    return np.linalg.norm(g - r, axis=1) / np.maximum(nr, floor)
+
+
+FLAT_ANISO = 20.0     # Gaussians with s_max / s_min above this count as flattened
+FLAT_TOL = 5e-3       # FP32 conditioning of thin Gaussians: error ~ eps * distance / s_min
+
+
+def check_grads(gg, ref, scene, tol, keys=("mu", "scale", "quat", "kappa", "sh")):
+    """Non-flattened Gaussians within tol, flattened ones within FLAT_TOL; returns the worst."""
+    aniso = scene.scale.max(1) / scene.scale.min(1)
+    flat_ = aniso > FLAT_ANISO
+    worst = {}
+    for k in keys:
+        e = grad_block_err(gg[k], ref[k], scene.n)
+        assert np.max(np.abs(ref[k])) > 0, k
+        worst[k] = (float(e[~flat_].max()) if (~flat_).any() else 0.0, float(e[flat_].max()) if flat_.any() else 0.0)
+        assert worst[k][0] < tol, (k, worst[k])
+        assert worst[k][1] < FLAT_TOL, (k, worst[k])
+    return worst
