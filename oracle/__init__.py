@@ -57,9 +57,9 @@ def lib():
         P = ctypes.c_void_p
         i32, i64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
         L.orc_keys.restype = i64
-        L.orc_keys.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, f32, f32, P, P]
+        L.orc_keys.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, f32, f32, P, P, P]
         L.orc_tomo_keys.restype = i64
-        L.orc_tomo_keys.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, f32, P]
+        L.orc_tomo_keys.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, f32, P, P]
         L.orc_bin.restype = i64
         L.orc_bin.argtypes = [i32, i32, P, P, P, P, i64, i64, P, P]
         L.orc_sh_basis.restype = None
@@ -69,12 +69,12 @@ def lib():
         L.orc_render.restype = None
         L.orc_render.argtypes = [i32, P, P, P, P, P, i32, i32, P, P, i32, i32, P, P, P, P, i32, P, P, P, P, P, P, P]
         L.orc_render_grad.restype = None
-        L.orc_render_grad.argtypes = [i32, P, P, P, P, P, i32, i32, P, P, i32, i32, P, P, P, P, P, P, P, P,
+        L.orc_render_grad.argtypes = [i32, P, P, P, P, P, i32, i32, P, P, i32, i32, P, P, P, P, P, P, P, P, P,
                                       P, P, P, P, P]
         L.orc_tomo.restype = None
-        L.orc_tomo.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, P, P, i32, P, P, P]
+        L.orc_tomo.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, P, P, P, i32, P, P, P]
         L.orc_tomo_grad.restype = None
-        L.orc_tomo_grad.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, P, P, P, P,
+        L.orc_tomo_grad.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, P, P, P, P, P,
                                     P, P, P, P]
         L.orc_num_threads.restype = i32
         _LIB = L
@@ -135,18 +135,20 @@ def _opts_arr(opts):
 
 
 # ------------------------------------------------------------------------------------------
-def keys(scene, cams, opts=None, tile=(16, 16)):
-    """FP32 key function: depth key bits [V, N] (0xFFFFFFFF = invalid or behind z_near) and
-    tile rectangles [V, N, 4] = (tx0, ty0, tx1, ty1) inclusive, -1 when culled."""
+def keys(scene, cams, opts=None, tile=(16, 16), with_pixels=False):
+    """FP32 key function: depth key bits [V, N] (0xFFFFFFFF = invalid or behind z_near),
+    tile rectangles [V, N, 4] = (tx0, ty0, tx1, ty1) inclusive, -1 when culled, and (with
+    with_pixels) the pixel footprint rectangles [V, N, 4] = (x0, y0, x1, y1) inclusive."""
     _, o = _opts_arr(opts)
     mu, sc, q, k, _sh = _scene_arrays(scene)
     cf, wh = cam_arrays(cams)
     V, N = len(cams), scene.n
     depth = np.zeros((V, N), np.uint32)
     rect = np.zeros((V, N, 4), np.int32)
+    prect = np.zeros((V, N, 4), np.int32)
     lib().orc_keys(N, _p(mu), _p(sc), _p(q), _p(k), V, _p(cf), _p(wh), tile[0], tile[1],
-                   np.float32(o["z_near"]), np.float32(o["tau_cut"]), _p(depth), _p(rect))
-    return depth, rect
+                   np.float32(o["z_near"]), np.float32(o["tau_cut"]), _p(depth), _p(rect), _p(prect))
+    return (depth, rect, prect) if with_pixels else (depth, rect)
 
 
 def bin(scene_n, n_views, depth, rect, tiles_x, tile_base, n_tiles):
@@ -167,11 +169,11 @@ def bin(scene_n, n_views, depth, rect, tiles_x, tile_base, n_tiles):
 
 
 def lists(scene, cams, opts=None, tile=(16, 16)):
-    depth, rect = keys(scene, cams, opts, tile)
+    depth, rect, prect = keys(scene, cams, opts, tile, with_pixels=True)
     tx, ty, base, nt = tile_layout(cams, tile)
     ts, sg = bin(scene.n, len(cams), depth, rect, tx, base, nt)
-    return dict(depth=depth, rect=rect, tile_start=ts, sorted_g=sg, tiles_x=tx, tiles_y=ty, tile_base=base,
-                n_tiles=nt, tile=tile)
+    return dict(depth=depth, rect=rect, prect=prect, tile_start=ts, sorted_g=sg, tiles_x=tx, tiles_y=ty,
+                tile_base=base, n_tiles=nt, tile=tile)
 
 
 def render(scene, cams, opts=None, L=None, brute=False, mask=None, tile=(16, 16)):
@@ -190,7 +192,7 @@ def render(scene, cams, opts=None, L=None, brute=False, mask=None, tile=(16, 16)
     lib().orc_render(scene.n, _p(mu), _p(sc), _p(q), _p(k), _p(sh), scene.sh_degree, len(cams), _p(cf), _p(wh),
                      L["tile"][0], L["tile"][1], _p(oa), _p(L["tile_start"]), _p(L["sorted_g"]),
                      _p(_c(L["tile_base"], np.int32)), int(brute), _p(_c(L["depth"], np.uint32)),
-                     _p(_c(L["rect"], np.int32)), _p(pb), _p(m), _p(rgb), _p(T), _p(nb))
+                     _p(_c(L["prect"], np.int32)), _p(pb), _p(m), _p(rgb), _p(T), _p(nb))
     out_rgb, out_T, out_n = [], [], []
     for v, c in enumerate(cams):
         s = slice(pb[v], pb[v] + c.width * c.height)
@@ -219,7 +221,8 @@ def render_grad(scene, cams, opts, L, dL_drgb, dL_dT=None, mask=None):
     m = None if mask is None else _c(mask, np.int32)
     lib().orc_render_grad(N, _p(mu), _p(sc), _p(q), _p(k), _p(sh), scene.sh_degree, len(cams), _p(cf), _p(wh),
                           L["tile"][0], L["tile"][1], _p(oa), _p(L["tile_start"]), _p(L["sorted_g"]),
-                          _p(_c(L["tile_base"], np.int32)), _p(pb), _p(g_rgb), _p(g_T), _p(m),
+                          _p(_c(L["tile_base"], np.int32)), _p(_c(L["prect"], np.int32)), _p(pb), _p(g_rgb),
+                          _p(g_T), _p(m),
                           _p(out["mu"]), _p(out["scale"]), _p(out["quat"]), _p(out["kappa"]), _p(out["sh"]))
     return out
 
@@ -243,25 +246,27 @@ def sh_basis(degree, direction):
 
 
 # ------------------------------------------------------------------------------ tomography
-def tomo_keys(scene, beam, tau_cut=1e-6, tile=(16, 16)):
+def tomo_keys(scene, beam, tau_cut=1e-6, tile=(16, 16), with_pixels=False):
     mu, sc, q, k, _ = _scene_arrays(scene)
     A, N = len(beam.angles), scene.n
     rect = np.zeros((A, N, 4), np.int32)
+    prect = np.zeros((A, N, 4), np.int32)
     lib().orc_tomo_keys(N, _p(mu), _p(sc), _p(q), _p(k), A, _p(_c(beam.angles, np.float32)), beam.det_w,
                         beam.det_h, beam.pitch_u, beam.pitch_v, beam.u0, beam.v0, tile[0], tile[1],
-                        np.float32(tau_cut), _p(rect))
-    return rect
+                        np.float32(tau_cut), _p(rect), _p(prect))
+    return (rect, prect) if with_pixels else rect
 
 
 def tomo_lists(scene, beam, tau_cut=1e-6, tile=(16, 16)):
-    rect = tomo_keys(scene, beam, tau_cut, tile)
+    rect, prect = tomo_keys(scene, beam, tau_cut, tile, with_pixels=True)
     A = len(beam.angles)
     tx = (beam.det_w + tile[0] - 1) // tile[0]
     ty = (beam.det_h + tile[1] - 1) // tile[1]
     txs = np.full(A, tx, np.int32)
     base = (np.arange(A) * tx * ty).astype(np.int32)
     ts, sg = bin(scene.n, A, None, rect, txs, base, A * tx * ty)
-    return dict(rect=rect, tile_start=ts, sorted_g=sg, tiles_x=tx, tiles_y=ty, n_tiles=A * tx * ty, tile=tile)
+    return dict(rect=rect, prect=prect, tile_start=ts, sorted_g=sg, tiles_x=tx, tiles_y=ty, n_tiles=A * tx * ty,
+                tile=tile)
 
 
 def tomo(scene, beam, L=None, brute=False, mask=None, tau_cut=1e-6, tile=(16, 16)):
@@ -271,15 +276,16 @@ def tomo(scene, beam, L=None, brute=False, mask=None, tau_cut=1e-6, tile=(16, 16
     mu, sc, q, k, _ = _scene_arrays(scene, np.float64)
     A = len(beam.angles)
     ls = np.zeros((A, beam.det_h, beam.det_w))
-    pr = np.zeros((A, beam.det_h, beam.det_w))
+    proj_out = np.zeros((A, beam.det_h, beam.det_w))
     ts = L["tile_start"] if L is not None else np.zeros(1, np.int64)
     sg = L["sorted_g"] if L is not None else np.zeros(1, np.int32)
+    pr = _c(L["prect"], np.int32) if L is not None else None
     tl = L["tile"] if L is not None else tile
     m = None if mask is None else _c(mask, np.int32)
     lib().orc_tomo(scene.n, _p(mu), _p(sc), _p(q), _p(k), A, _p(_c(beam.angles, np.float32)), beam.det_w,
                    beam.det_h, beam.pitch_u, beam.pitch_v, beam.u0, beam.v0, tl[0], tl[1], _p(ts), _p(sg),
-                   int(brute), _p(m), _p(ls), _p(pr))
-    return ls, pr
+                   _p(pr), int(brute), _p(m), _p(ls), _p(proj_out))
+    return ls, proj_out
 
 
 def tomo_grad(scene, beam, L, dL_dproj, mask=None):
@@ -289,6 +295,7 @@ def tomo_grad(scene, beam, L, dL_dproj, mask=None):
     m = None if mask is None else _c(mask, np.int32)
     lib().orc_tomo_grad(N, _p(mu), _p(sc), _p(q), _p(k), A, _p(_c(beam.angles, np.float32)), beam.det_w,
                         beam.det_h, beam.pitch_u, beam.pitch_v, beam.u0, beam.v0, L["tile"][0], L["tile"][1],
-                        _p(L["tile_start"]), _p(L["sorted_g"]), _p(_c(dL_dproj, np.float64)), _p(m),
+                        _p(L["tile_start"]), _p(L["sorted_g"]), _p(_c(L["prect"], np.int32)),
+                        _p(_c(dL_dproj, np.float64)), _p(m),
                         _p(out["mu"]), _p(out["scale"]), _p(out["quat"]), _p(out["kappa"]))
     return out

@@ -109,9 +109,10 @@ static void pixel_span(float lo, float hi, int n, int *ilo, int *ihi)
 
 static int key_persp(const float *mu, const float *s, const float *q, float kap, const float *cf,
                      int W, int H, int tw, int th, float z_near, float tau_cut, uint32_t *depth,
-                     int32_t rect[4])
+                     int32_t rect[4], int32_t prect[4])
 {
     rect[0] = rect[1] = rect[2] = rect[3] = -1;
+    prect[0] = prect[1] = prect[2] = prect[3] = -1;
     *depth = 0xFFFFFFFFu;
     float Sig[9], smax;
     if (!cov_fp32(mu, s, q, kap, Sig, &smax)) return 0;
@@ -141,6 +142,10 @@ static int key_persp(const float *mu, const float *s, const float *q, float kap,
         rect[1] = 0;
         rect[2] = tiles_x - 1;
         rect[3] = tiles_y - 1;
+        prect[0] = 0;
+        prect[1] = 0;
+        prect[2] = W - 1;
+        prect[3] = H - 1;
         return 1;
     }
     float k22 = k2 * k2;
@@ -167,12 +172,16 @@ static int key_persp(const float *mu, const float *s, const float *q, float kap,
     rect[1] = iy0 / th;
     rect[2] = ix1 / tw;
     rect[3] = iy1 / th;
+    prect[0] = ix0;
+    prect[1] = iy0;
+    prect[2] = ix1;
+    prect[3] = iy1;
     return 1;
 }
 
 int64_t orc_keys(int n, const float *mu, const float *scale, const float *quat, const float *kappa,
                  int n_views, const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
-                 float z_near, float tau_cut, uint32_t *depth_bits, int32_t *rect)
+                 float z_near, float tau_cut, uint32_t *depth_bits, int32_t *rect, int32_t *prect)
 {
     int64_t total = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -181,7 +190,7 @@ int64_t orc_keys(int n, const float *mu, const float *scale, const float *quat, 
             int32_t *r = rect + 4 * it;
             if (key_persp(mu + 3 * g, scale + 3 * g, quat + 4 * g, kappa[g], cam_f + 16 * v,
                           cam_wh[2 * v], cam_wh[2 * v + 1], tile_w, tile_h, z_near, tau_cut,
-                          depth_bits + it, r))
+                          depth_bits + it, r, prect + 4 * it))
                 total += (int64_t)(r[2] - r[0] + 1) * (r[3] - r[1] + 1);
         }
     }
@@ -191,7 +200,7 @@ int64_t orc_keys(int n, const float *mu, const float *scale, const float *quat, 
 int64_t orc_tomo_keys(int n, const float *mu, const float *scale, const float *quat,
                       const float *kappa, int n_angles, const float *angles, int det_w, int det_h,
                       float pitch_u, float pitch_v, float u0, float v0, int tile_w, int tile_h,
-                      float tau_cut, int32_t *rect)
+                      float tau_cut, int32_t *rect, int32_t *prect)
 {
     int64_t total = 0;
     for (int a = 0; a < n_angles; ++a) {
@@ -199,7 +208,9 @@ int64_t orc_tomo_keys(int n, const float *mu, const float *scale, const float *q
         float st = (float)sin((double)angles[a]);
         for (int g = 0; g < n; ++g) {
             int32_t *r = rect + 4 * ((int64_t)a * n + g);
+            int32_t *pr = prect + 4 * ((int64_t)a * n + g);
             r[0] = r[1] = r[2] = r[3] = -1;
+            pr[0] = pr[1] = pr[2] = pr[3] = -1;
             float Sig[9], smax, k2;
             const float *m = mu + 3 * g;
             if (!cov_fp32(m, scale + 3 * g, quat + 4 * g, kappa[g], Sig, &smax)) continue;
@@ -220,6 +231,10 @@ int64_t orc_tomo_keys(int n, const float *mu, const float *scale, const float *q
             r[1] = iy0 / tile_h;
             r[2] = ix1 / tile_w;
             r[3] = iy1 / tile_h;
+            pr[0] = ix0;
+            pr[1] = iy0;
+            pr[2] = ix1;
+            pr[3] = iy1;
             total += (int64_t)(r[2] - r[0] + 1) * (r[3] - r[1] + 1);
         }
     }
@@ -509,17 +524,25 @@ static double tau_skip_of(double alpha_min)
     return -log1p(-alpha_min);
 }
 
+/* A Gaussian contributes to the pixels of its footprint rectangle (inclusive pixel
+ * bounds from the key function); tile lists are the coarse version of the same set. */
+static int outside(const int32_t *prect, int64_t item, int x, int y)
+{
+    if (!prect) return 0;
+    const int32_t *r = prect + 4 * item;
+    return x < r[0] || x > r[2] || y < r[1] || y > r[3];
+}
+
 /* ================================ forward render ================================ */
 
 void orc_render(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
                 const double *sh, int sh_degree, int n_views, const float *cam_f,
                 const int32_t *cam_wh, int tile_w, int tile_h, const double *opts,
                 const int64_t *tile_start, const int32_t *sorted_g, const int32_t *view_tile_base,
-                int brute, const uint32_t *depth_bits, const int32_t *rect,
+                int brute, const uint32_t *depth_bits, const int32_t *prect,
                 const int64_t *pix_base, const int32_t *pix_mask, double *rgb, double *T_final,
                 int32_t *n_blend)
 {
-    (void)rect;
     const double tau_skip = tau_skip_of(opts[0]);
     const double tau_max = opts[2], T_stop = opts[3];
     const double bg[3] = {opts[4], opts[5], opts[6]};
@@ -567,6 +590,7 @@ void orc_render(int n, const double *mu, const double *scale, const double *quat
             int nb = 0;
             for (int64_t k = lo; k < hi; ++k) {
                 int64_t g = brute ? ord[k].g : sorted_g[k];
+                if (!brute && outside(prect, (int64_t)v * n + g, x, y)) continue;
                 double a, b, c, p[3];
                 double tau = tau64(&G[g], cam.o, d, &a, &b, &c, p);
                 if (tau > tau_max) tau = tau_max;
@@ -665,7 +689,7 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
                      const double *kappa, const double *sh, int sh_degree, int n_views,
                      const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
                      const double *opts, const int64_t *tile_start, const int32_t *sorted_g,
-                     const int32_t *view_tile_base, const int64_t *pix_base,
+                     const int32_t *view_tile_base, const int32_t *prect, const int64_t *pix_base,
                      const double *dL_drgb, const double *dL_dT, const int32_t *pix_mask,
                      double *dmu, double *dscale, double *dquat, double *dkappa, double *dsh)
 {
@@ -707,6 +731,7 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
                 int nr = 0;
                 for (int64_t k = lo; k < hi; ++k) {
                     int64_t g = sorted_g[k];
+                    if (outside(prect, (int64_t)v * n + g, x, y)) continue;
                     double a, b, c, p[3];
                     double tau = tau64(&G[g], cam.o, d, &a, &b, &c, p);
                     int clamped = 0;
@@ -791,7 +816,7 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
 void orc_tomo(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
               int n_angles, const float *angles, int det_w, int det_h, float pitch_u,
               float pitch_v, float u0, float v0, int tile_w, int tile_h,
-              const int64_t *tile_start, const int32_t *sorted_g, int brute,
+              const int64_t *tile_start, const int32_t *sorted_g, const int32_t *prect, int brute,
               const int32_t *pix_mask, double *line_sum, double *proj)
 {
     gauss64 *G = (gauss64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(gauss64));
@@ -822,6 +847,7 @@ void orc_tomo(int n, const double *mu, const double *scale, const double *quat, 
             } else {
                 int64_t tile = (int64_t)an * tiles_x * tiles_y + (int64_t)(j / tile_h) * tiles_x + i / tile_w;
                 for (int64_t k = tile_start[tile]; k < tile_start[tile + 1]; ++k) {
+                    if (outside(prect, (int64_t)an * n + sorted_g[k], i, j)) continue;
                     double a, b, c, p[3];
                     sum += tau64(&G[sorted_g[k]], o, d, &a, &b, &c, p);
                 }
@@ -837,8 +863,9 @@ void orc_tomo(int n, const double *mu, const double *scale, const double *quat, 
 void orc_tomo_grad(int n, const double *mu, const double *scale, const double *quat,
                    const double *kappa, int n_angles, const float *angles, int det_w, int det_h,
                    float pitch_u, float pitch_v, float u0, float v0, int tile_w, int tile_h,
-                   const int64_t *tile_start, const int32_t *sorted_g, const double *dL_dproj,
-                   const int32_t *pix_mask, double *dmu, double *dscale, double *dquat, double *dkappa)
+                   const int64_t *tile_start, const int32_t *sorted_g, const int32_t *prect,
+                   const double *dL_dproj, const int32_t *pix_mask, double *dmu, double *dscale,
+                   double *dquat, double *dkappa)
 {
     gauss64 *G = (gauss64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(gauss64));
     double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * ACC_N, sizeof(double));
@@ -860,6 +887,7 @@ void orc_tomo_grad(int n, const double *mu, const double *scale, const double *q
             int64_t tile = (int64_t)an * tiles_x * tiles_y + (int64_t)(j / tile_h) * tiles_x + i / tile_w;
             double sum = 0;
             for (int64_t k = tile_start[tile]; k < tile_start[tile + 1]; ++k) {
+                if (outside(prect, (int64_t)an * n + sorted_g[k], i, j)) continue;
                 double a, b, c, p[3];
                 sum += tau64(&G[sorted_g[k]], o, d, &a, &b, &c, p);
             }
@@ -867,6 +895,7 @@ void orc_tomo_grad(int n, const double *mu, const double *scale, const double *q
             double dLdtau = -exp(-sum) * dL_dproj[gp];
             for (int64_t k = tile_start[tile]; k < tile_start[tile + 1]; ++k) {
                 int64_t g = sorted_g[k];
+                if (outside(prect, (int64_t)an * n + g, i, j)) continue;
                 double a, b, c, p[3];
                 double tau = tau64(&G[g], o, d, &a, &b, &c, p);
                 acc_tau(&acc[ACC_N * g], &G[g], dLdtau, tau, a, b, d, p);

@@ -21,14 +21,16 @@
 extern "C" {
 #endif
 
-/* Key function (tile rectangle and depth key) in FP32 with a fixed operation order. */
+/* Key function (depth key, tile rectangle and pixel footprint rectangle) in FP32 with a
+ * fixed operation order.  Tiled evaluation restricts each Gaussian to the pixels of its
+ * footprint rectangle (prect, inclusive); brute-force evaluation does not. */
 int64_t orc_keys(int n, const float *mu, const float *scale, const float *quat, const float *kappa,
                  int n_views, const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
-                 float z_near, float tau_cut, uint32_t *depth_bits, int32_t *rect);
+                 float z_near, float tau_cut, uint32_t *depth_bits, int32_t *rect, int32_t *prect);
 int64_t orc_tomo_keys(int n, const float *mu, const float *scale, const float *quat,
                       const float *kappa, int n_angles, const float *angles, int det_w, int det_h,
                       float pitch_u, float pitch_v, float u0, float v0, int tile_w, int tile_h,
-                      float tau_cut, int32_t *rect);
+                      float tau_cut, int32_t *rect, int32_t *prect);
 /* Stable sort of (tile, depth, Gaussian) instances; fills tile_start[n_tiles+1], sorted_g. */
 int64_t orc_bin(int n, int n_views, const uint32_t *depth_bits, const int32_t *rect,
                 const int32_t *view_tiles_x, const int32_t *view_tile_base, int64_t n_tiles_total,
@@ -42,7 +44,7 @@ void orc_render(int n, const double *mu, const double *scale, const double *quat
                 const double *kappa, const double *sh, int sh_degree, int n_views, const float *cam_f,
                 const int32_t *cam_wh, int tile_w, int tile_h, const double *opts,
                 const int64_t *tile_start, const int32_t *sorted_g, const int32_t *view_tile_base,
-                int brute, const uint32_t *depth_bits, const int32_t *rect,
+                int brute, const uint32_t *depth_bits, const int32_t *prect,
                 const int64_t *pix_base, const int32_t *pix_mask, double *rgb, double *T_final,
                 int32_t *n_blend);
 
@@ -50,21 +52,21 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
                      const double *kappa, const double *sh, int sh_degree, int n_views,
                      const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
                      const double *opts, const int64_t *tile_start, const int32_t *sorted_g,
-                     const int32_t *view_tile_base, const int64_t *pix_base,
+                     const int32_t *view_tile_base, const int32_t *prect, const int64_t *pix_base,
                      const double *dL_drgb, const double *dL_dT, const int32_t *pix_mask,
                      double *dmu, double *dscale, double *dquat, double *dkappa, double *dsh);
 
 void orc_tomo(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
               int n_angles, const float *angles, int det_w, int det_h, float pitch_u,
               float pitch_v, float u0, float v0, int tile_w, int tile_h,
-              const int64_t *tile_start, const int32_t *sorted_g, int brute,
+              const int64_t *tile_start, const int32_t *sorted_g, const int32_t *prect, int brute,
               const int32_t *pix_mask, double *line_sum, double *proj);
 
 void orc_tomo_grad(int n, const double *mu, const double *scale, const double *quat,
                    const double *kappa, int n_angles, const float *angles, int det_w, int det_h,
                    float pitch_u, float pitch_v, float u0, float v0, int tile_w, int tile_h,
-                   const int64_t *tile_start, const int32_t *sorted_g, const double *dL_dproj,
-                   const int32_t *pix_mask, double *dmu, double *dscale, double *dquat, double *dkappa);
+                   const int64_t *tile_start, const int32_t *sorted_g, const int32_t *prect,
+                   const double *dL_dproj, const int32_t *pix_mask, double *dmu, double *dscale, double *dquat, double *dkappa);
 
 int orc_num_threads(void);
 

@@ -41,7 +41,7 @@ struct vg_workspace {
     DBuf<int> tile_view;
     DBuf<float4> rec;
     DBuf<uint32_t> depth, count, offsets;
-    DBuf<short4> rect;
+    DBuf<short4> rect, prect;
     DBuf<uint32_t> skey[2], sval[2];
     DBuf<uint32_t> ikey[2], ival[2];
     uint32_t *perm = nullptr;          // items in depth order (points into sval)
@@ -71,10 +71,10 @@ struct vg_workspace {
 
 namespace {
 
-// Measured on the 1M-Gaussian 1280x832 workload (GB300): forward 0.57 / 0.53 / 0.77 ms and
-// backward 1.21 / 1.26 / 1.30 ms for 1 / 2 / 4 pixels per thread.
+// Measured on the 1M-Gaussian 1280x832 workload (GB300, footprint culling on): forward
+// 0.53 / 0.49 / 0.74 ms and backward 1.32 / 1.16 / 1.19 ms for 1 / 2 / 4 pixels per thread.
 constexpr int kDefaultPixelsFwd = 2;
-constexpr int kDefaultPixelsBwd = 1;
+constexpr int kDefaultPixelsBwd = 2;
 
 enum Stage { ST_PRE, ST_DEPTH, ST_SCAN, ST_DUP, ST_TILE, ST_RANGES, ST_FWD, ST_BWD, ST_CHAIN, ST_LOSS, ST_TFWD,
              ST_TBWD, ST_COUNT };
@@ -234,6 +234,7 @@ vg_status vg_workspace_destroy(vg_workspace *ws) {
     release(ws->count);
     release(ws->offsets);
     release(ws->rect);
+    release(ws->prect);
     for (int k = 0; k < 2; ++k) {
         release(ws->skey[k]);
         release(ws->sval[k]);
@@ -268,6 +269,7 @@ static vg_status reserve_items(vg_workspace *ws, long long n_items) {
     VG_TRY(ensure(ws, ws->depth, (size_t)n_items, "depth keys"));
     VG_TRY(ensure(ws, ws->count, (size_t)n_items, "tile counts"));
     VG_TRY(ensure(ws, ws->rect, (size_t)n_items, "tile rectangles"));
+    VG_TRY(ensure(ws, ws->prect, (size_t)n_items, "pixel rectangles"));
     VG_TRY(ensure(ws, ws->offsets, (size_t)n_items + 1, "offsets"));
     for (int k = 0; k < 2; ++k) {
         VG_TRY(ensure(ws, ws->skey[k], (size_t)n_items, "sort keys"));
@@ -357,7 +359,7 @@ vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera
         V.H = c.height;
         V.tiles_x = (c.width + kTile - 1) / kTile;
         V.tiles_y = (c.height + kTile - 1) / kTile;
-        if (V.tiles_x > 32767 || V.tiles_y > 32767) return fail(ws, VG_ERR_INVALID_ARG, "image too large");
+        if (c.width > 32767 || c.height > 32767) return fail(ws, VG_ERR_INVALID_ARG, "image wider or taller than 32767");
         V.tile_base = (int)tile_base;
         V.pix_base = pix_base;
         for (int t = 0; t < V.tiles_x * V.tiles_y; ++t) tv.push_back(v);
@@ -392,11 +394,12 @@ vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera
     ws->ppt_bwd = opts->pixels_per_thread ? opts->pixels_per_thread : kDefaultPixelsBwd;
     ws->bp.T_stop = opts->T_stop;
     for (int c = 0; c < 3; ++c) ws->bp.bg[c] = opts->bg[c];
+    ws->bp.pixel_test = ws->bp.tau_skip < opts->tau_cut ? 1 : 0;
     VG_CUDA(ws, cudaMemsetAsync(ws->counters.p, 0, sizeof(unsigned long long), st));
     if (n_items > 0) {
         ProfScope ps(ws, ST_PRE, st);
         VG_CUDA(ws, launch_preprocess(ws->g, ws->views.p, n_views, opts->z_near, opts->tau_cut, ws->rec.p, ws->depth.p,
-                                      ws->count.p, ws->rect.p, ws->counters.p, st, &ws->launches));
+                                      ws->count.p, ws->rect.p, ws->prect.p, ws->counters.p, st, &ws->launches));
     }
     ws->stage = 1;
     return VG_OK;
@@ -481,7 +484,7 @@ vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stre
     {
         ProfScope ps(ws, ST_FWD, st);
         VG_CUDA(ws, launch_render_fwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
-                                      ws->ranges.p, ws->inst_item, ws->rec.p, ws->bp, ws->ppt_fwd, rgb, T_final,
+                                      ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_fwd, rgb, T_final,
                                       ws->T_fin.p, ws->S_fin.p, ws->nlast.p, pc, st, &ws->launches));
     }
     ws->stage = 3;
@@ -516,7 +519,8 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
     {
         ProfScope ps(ws, ST_BWD, st);
         VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
-                                      ws->ranges.p, ws->inst_item, ws->rec.p, ws->bp, ws->ppt_bwd, ws->T_fin.p,
+                                      ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_bwd,
+                                      ws->T_fin.p,
                                       ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, ws->grad.p, pc, st,
                                       &ws->launches));
     }
@@ -584,7 +588,8 @@ vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const fl
     // the array keeps the previous call's sums: clear the part this call accumulates into
     if (ws->n_items > 0) VG_CUDA(ws, cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st));
     VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
-                                  ws->ranges.p, ws->inst_item, ws->rec.p, ws->bp, ws->ppt_bwd, ws->T_fin.p, ws->S_fin.p,
+                                  ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_bwd, ws->T_fin.p,
+                                  ws->S_fin.p,
                                   ws->nlast.p, dL_drgb, dL_dT, acc, nullptr, st, &ws->launches));
     if (ws->n_items > 0)
         VG_CUDA(ws, launch_chain(ws->g, ws->views.p, ws->n_views, acc, dmu, dscale, dquat, dkappa, dsh, st,
@@ -657,7 +662,7 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
             VG_CUDA(ws, cudaMemsetAsync(ws->depth.p, 0xFF, sizeof(uint32_t) * (size_t)items, st));
             VG_CUDA(ws, launch_tomo_preprocess(ws->g, ws->tomo_cs.p + 2 * (size_t)a0, nb, beam->det_w, beam->det_h,
                                                beam->pitch_u, beam->pitch_v, beam->u0, beam->v0, opts->tau_cut,
-                                               ws->rec.p, ws->count.p, ws->rect.p, st, &ws->launches));
+                                               ws->rec.p, ws->count.p, ws->rect.p, ws->prect.p, st, &ws->launches));
         }
         {
             ProfScope ps(ws, ST_SCAN, st);
@@ -687,15 +692,15 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
         {
             ProfScope ps(ws, ST_TFWD, st);
             VG_CUDA(ws, launch_tomo_fwd(ws->ranges.p, n_tiles, tiles_x, (int)tpv, beam->det_w, beam->det_h,
-                                        ws->inst_item, ws->rec.p, proj_b, st, &ws->launches));
+                                        ws->inst_item, ws->rec.p, ws->prect.p, proj_b, st, &ws->launches));
         }
         if (dL_dproj && items > 0) {
             VG_TRY(ensure(ws, ws->grad, (size_t)items * 8, "gradient accumulators"));
             VG_CUDA(ws, cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)items * 8, st));
             ProfScope ps(ws, ST_TBWD, st);
             VG_CUDA(ws, launch_tomo_bwd(ws->ranges.p, n_tiles, tiles_x, (int)tpv, beam->det_w, beam->det_h,
-                                        ws->inst_item, ws->rec.p, proj_b, dL_dproj + (size_t)a0 * det_px, ws->grad.p,
-                                        st, &ws->launches));
+                                        ws->inst_item, ws->rec.p, ws->prect.p, proj_b, dL_dproj + (size_t)a0 * det_px,
+                                        ws->grad.p, st, &ws->launches));
             VG_CUDA(ws, launch_tomo_chain(ws->g, ws->tomo_cs.p, A, (long long)a0 * N, items, beam->pitch_u,
                                           beam->pitch_v, beam->u0, beam->v0, ws->grad.p, dmu, dscale, dquat, dkappa,
                                           st, &ws->launches));

@@ -80,6 +80,39 @@ struct PixLayout {
     __host__ __device__ static constexpr int oy(int k) { return P == 4 ? (k >> 1) : (P == 2 ? k : 0); }
 };
 
+// Bounds of the pixels a warp owns, for the warp-uniform footprint test of each record.
+struct WarpBox {
+    int x0, y0, x1, y1;
+};
+
+template <int P>
+__device__ __forceinline__ WarpBox warp_box(int x0, int y0) {
+    int xmin = x0, xmax = x0, ymin = y0, ymax = y0;
+#pragma unroll
+    for (int k = 1; k < P; ++k) {
+        xmax = max(xmax, x0 + PixLayout<P>::ox(k));
+        ymax = max(ymax, y0 + PixLayout<P>::oy(k));
+    }
+    WarpBox b;
+    b.x0 = __reduce_min_sync(0xffffffffu, xmin);
+    b.y0 = __reduce_min_sync(0xffffffffu, ymin);
+    b.x1 = __reduce_max_sync(0xffffffffu, xmax);
+    b.y1 = __reduce_max_sync(0xffffffffu, ymax);
+    return b;
+}
+
+__device__ __forceinline__ bool box_misses(const WarpBox &b, const short4 &r) {
+    return r.z < b.x0 || r.x > b.x1 || r.w < b.y0 || r.y > b.y1;
+}
+
+__device__ __forceinline__ bool box_inside(const WarpBox &b, const short4 &r) {
+    return r.x <= b.x0 && r.z >= b.x1 && r.y <= b.y0 && r.w >= b.y1;
+}
+
+__device__ __forceinline__ bool pixel_outside(int x, int y, const short4 &r) {
+    return x < r.x || x > r.z || y < r.y || y > r.w;
+}
+
 struct QuadBase {
     float dx, dy;          // offset of the thread's first pixel from the reference pixel
     float dp[3], cr[3];    // d' and o' x d' there

@@ -99,12 +99,13 @@ __device__ __forceinline__ void pixel_span(float lo, float hi, int n, int &ilo, 
     ihi = (hi >= (float)(n - 1)) ? n - 1 : (int)floorf(hi);
 }
 
-// Key function of one (view, Gaussian): camera depth of the mean (FP32 bits) and the
-// conservative tile rectangle of the Mahalanobis-k ellipsoid's screen bounding box.
+// Key function of one (view, Gaussian): camera depth of the mean (FP32 bits), the
+// conservative pixel rectangle of the Mahalanobis-k ellipsoid's screen bounding box (a
+// Gaussian contributes only to these pixels) and the tile rectangle covering it.
 // Returns 0 = invalid/behind z_near, 1 = valid but no footprint, 2 = visible.
 __device__ __forceinline__ int key_persp(const ViewInfo &V, const float mu[3], const float Sig[9], float smax,
                                          float kap, float z_near, float tau_cut, uint32_t &depth, short4 &rect,
-                                         float &Zf) {
+                                         short4 &prect, float &Zf) {
     const float *C = V.R;
     float X = VG_ADD(VG_ADD(VG_ADD(VG_MUL(C[0], mu[0]), VG_MUL(C[1], mu[1])), VG_MUL(C[2], mu[2])), V.t[0]);
     float Y = VG_ADD(VG_ADD(VG_ADD(VG_MUL(C[3], mu[0]), VG_MUL(C[4], mu[1])), VG_MUL(C[5], mu[2])), V.t[1]);
@@ -130,6 +131,7 @@ __device__ __forceinline__ int key_persp(const ViewInfo &V, const float mu[3], c
     float a2 = VG_SUB(ZZ, VG_MUL(k2, szz));
     if (!(a2 > 0.0f)) {   // the cutoff ellipsoid reaches the camera plane: the whole view
         rect = make_short4(0, 0, (short)(V.tiles_x - 1), (short)(V.tiles_y - 1));
+        prect = make_short4(0, 0, (short)(V.W - 1), (short)(V.H - 1));
         return 2;
     }
     float k22 = VG_MUL(k2, k2);
@@ -153,6 +155,7 @@ __device__ __forceinline__ int key_persp(const ViewInfo &V, const float mu[3], c
     pixel_span(ylo, yhi, V.H, iy0, iy1);
     if (ix0 > ix1 || iy0 > iy1) return 1;
     rect = make_short4((short)(ix0 / kTile), (short)(iy0 / kTile), (short)(ix1 / kTile), (short)(iy1 / kTile));
+    prect = make_short4((short)ix0, (short)iy0, (short)ix1, (short)iy1);
     return 2;
 }
 

@@ -24,19 +24,20 @@ template <> struct BwdBounds<4> { static constexpr int kMinBlocks = 8; };
 // 22 partials are summed over the thread's pixels in registers, then over the warp by a
 // reduce-scatter (lane k ends with partial k), over the CTA in shared memory, and finally
 // added to the item's accumulator with one set of global atomics per (tile, Gaussian).
-template <int P, bool COUNT>
+template <int P, bool COUNT, bool PIXTEST>
 __global__ void __launch_bounds__(PixLayout<P>::kThreads, BwdBounds<P>::kMinBlocks)
 k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
-             BlendParams bp, const float *__restrict__ T_fin, const float *__restrict__ S_fin,
+             const short4 *__restrict__ prect, BlendParams bp, const float *__restrict__ T_fin, const float *__restrict__ S_fin,
              const uint32_t *__restrict__ nlast, const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT,
              float *__restrict__ grad_acc, unsigned long long *__restrict__ pair_count) {
     using L = PixLayout<P>;
     constexpr int kThreads = L::kThreads;
-    constexpr int kChunk = kThreads;
+    constexpr int kChunk = kThreads < 128 ? kThreads : 128;   // records per shared-memory chunk
     __shared__ float4 srec[kChunk * kRecF4];
     __shared__ float sacc[kChunk * kGradUsed];
     __shared__ uint32_t sitem[kChunk];
+    __shared__ short4 srect[kChunk];
     __shared__ uint32_t s_last;
 
     const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
@@ -81,6 +82,8 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     if (thr_last > rg.x) atomicMax(&s_last, thr_last);
     __syncthreads();
     const uint32_t tile_last = s_last;
+    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, thr_last);
+    const WarpBox wb = warp_box<P>(x0, y0);
     const float xf = (float)x0, yf = (float)y0;
     unsigned long long pairs = 0;
 
@@ -93,11 +96,15 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             const float4 *src = rec + (size_t)item * kRecF4;
 #pragma unroll
             for (int k = 0; k < kRecF4; ++k) srec[threadIdx.x * kRecF4 + k] = __ldg(src + k);
+            srect[threadIdx.x] = prect[item];
         }
         for (int k = threadIdx.x; k < kChunk * kGradUsed; k += kThreads) sacc[k] = 0.0f;
         __syncthreads();
         for (int j = (int)n - 1; j >= 0; --j) {
             const uint32_t idx = start + (uint32_t)j;
+            const short4 pr = srect[j];
+            // warp-uniform: nothing of this warp reached the record, or its footprint misses the warp
+            if (idx >= warp_last || box_misses(wb, pr)) continue;
             float gv[32];
 #pragma unroll
             for (int k = 0; k < 32; ++k) gv[k] = 0.0f;
@@ -110,6 +117,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
 #pragma unroll
                 for (int k = 0; k < P; ++k) {
                     if (idx >= my_last[k]) continue;
+                    if (PIXTEST && pixel_outside(x0 + L::ox(k), y0 + L::oy(k), pr)) continue;
                     PairEval e;
                     pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
                     if (COUNT) ++pairs;
@@ -172,36 +180,51 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
 }
 
-template <int P>
-static void launch_bwd_p(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
-                         const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const BlendParams &bp,
-                         const float *T_fin, const float *S_fin, const uint32_t *nlast, const float *dL_drgb,
-                         const float *dL_dT, float *grad_acc, unsigned long long *pair_count, cudaStream_t st) {
+template <int P, bool PIXTEST>
+static void launch_bwd_pt(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                          const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                          const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
+                          const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
+                          cudaStream_t st) {
     const unsigned threads = PixLayout<P>::kThreads;
     if (pair_count)
-        k_render_bwd<P, true><<<(unsigned)n_tiles, threads, 0, st>>>(views_d, tile_view, tile_order, ranges,
-                                                                    sorted_item, rec, bp, T_fin, S_fin, nlast, dL_drgb,
-                                                                    dL_dT, grad_acc, pair_count);
+        k_render_bwd<P, true, PIXTEST><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
+            grad_acc, pair_count);
     else
-        k_render_bwd<P, false><<<(unsigned)n_tiles, threads, 0, st>>>(views_d, tile_view, tile_order, ranges,
-                                                                     sorted_item, rec, bp, T_fin, S_fin, nlast, dL_drgb,
-                                                                     dL_dT, grad_acc, nullptr);
+        k_render_bwd<P, false, PIXTEST><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
+            grad_acc, nullptr);
+}
+
+template <int P>
+static void launch_bwd_p(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                         const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                         const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
+                         const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
+                         cudaStream_t st) {
+    if (bp.pixel_test)
+        launch_bwd_pt<P, true>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, T_fin,
+                               S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
+    else
+        launch_bwd_pt<P, false>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, T_fin,
+                                S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
 }
 
 cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
-                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
+                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                               const BlendParams &bp, int ppt, const float *T_fin, const float *S_fin,
                               const uint32_t *nlast, const float *dL_drgb, const float *dL_dT, float *grad_acc,
                               unsigned long long *pair_count, cudaStream_t st, long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
     if (ppt == 1)
-        launch_bwd_p<1>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, T_fin, S_fin, nlast,
+        launch_bwd_p<1>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast,
                         dL_drgb, dL_dT, grad_acc, pair_count, st);
     else if (ppt == 4)
-        launch_bwd_p<4>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, T_fin, S_fin, nlast,
+        launch_bwd_p<4>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast,
                         dL_drgb, dL_dT, grad_acc, pair_count, st);
     else
-        launch_bwd_p<2>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, T_fin, S_fin, nlast,
+        launch_bwd_p<2>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast,
                         dL_drgb, dL_dT, grad_acc, pair_count, st);
     *launches += 1;
     return cudaGetLastError();

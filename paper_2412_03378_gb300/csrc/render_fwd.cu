@@ -16,15 +16,16 @@ template <> struct FwdBounds<1> { static constexpr int kMinBlocks = 3; };
 template <> struct FwdBounds<2> { static constexpr int kMinBlocks = 6; };
 template <> struct FwdBounds<4> { static constexpr int kMinBlocks = 12; };
 
-template <int P, bool COUNT>
+template <int P, bool COUNT, bool PIXTEST>
 __global__ void __launch_bounds__(PixLayout<P>::kThreads, FwdBounds<P>::kMinBlocks)
 k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
-             BlendParams bp, float *__restrict__ rgb, float *__restrict__ T_user, float *__restrict__ T_ws,
+             const short4 *__restrict__ prect, BlendParams bp, float *__restrict__ rgb, float *__restrict__ T_user, float *__restrict__ T_ws,
              float *__restrict__ S_out, uint32_t *__restrict__ nlast_out, unsigned long long *__restrict__ pair_count) {
     using L = PixLayout<P>;
     constexpr int kChunk = L::kThreads;
     __shared__ float4 srec[kChunk * kRecF4];
+    __shared__ short4 srect[kChunk];
     const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
     const ViewInfo &V = views[tile_view[tile]];
     const int local = tile - V.tile_base;
@@ -46,16 +47,21 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
         if (x < V.W && y < V.H) live |= 1u << k;
     }
     const float xf = (float)x0, yf = (float)y0;
+    const WarpBox wb = warp_box<P>(x0, y0);
     unsigned long long pairs = 0;
     for (uint32_t base = rg.x; base < rg.y; base += kChunk) {
         const uint32_t n = min((uint32_t)kChunk, rg.y - base);
         if (threadIdx.x < n) {
-            const float4 *src = rec + (size_t)sorted_item[base + threadIdx.x] * kRecF4;
+            const uint32_t item = sorted_item[base + threadIdx.x];
+            const float4 *src = rec + (size_t)item * kRecF4;
 #pragma unroll
             for (int k = 0; k < kRecF4; ++k) srec[threadIdx.x * kRecF4 + k] = __ldg(src + k);
+            srect[threadIdx.x] = prect[item];
         }
         __syncthreads();
         for (uint32_t j = 0; j < n && live; ++j) {
+            const short4 pr = srect[j];
+            if (box_misses(wb, pr)) continue;   // no pixel of this warp is in the footprint
             const float4 *r = &srec[j * kRecF4];
             const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
             QuadBase qb;
@@ -63,6 +69,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
 #pragma unroll
             for (int k = 0; k < P; ++k) {
                 if (!(live & (1u << k))) continue;
+                if (PIXTEST && pixel_outside(x0 + L::ox(k), y0 + L::oy(k), pr)) continue;
                 PairEval e;
                 pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
                 if (COUNT) ++pairs;
@@ -101,36 +108,49 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
 }
 
-template <int P>
-static void launch_fwd_p(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
-                         const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const BlendParams &bp,
-                         float *rgb, float *T_user, float *T_ws, float *S_out, uint32_t *nlast_out,
-                         unsigned long long *pair_count, cudaStream_t st) {
+template <int P, bool PIXTEST>
+static void launch_fwd_pt(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                          const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                          const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
+                          uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
     const unsigned threads = PixLayout<P>::kThreads;
     if (pair_count)
-        k_render_fwd<P, true><<<(unsigned)n_tiles, threads, 0, st>>>(views_d, tile_view, tile_order, ranges,
-                                                                    sorted_item, rec, bp, rgb, T_user, T_ws, S_out,
-                                                                    nlast_out, pair_count);
+        k_render_fwd<P, true, PIXTEST><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
+            pair_count);
     else
-        k_render_fwd<P, false><<<(unsigned)n_tiles, threads, 0, st>>>(views_d, tile_view, tile_order, ranges,
-                                                                     sorted_item, rec, bp, rgb, T_user, T_ws, S_out,
-                                                                     nlast_out, nullptr);
+        k_render_fwd<P, false, PIXTEST><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
+            nullptr);
+}
+
+template <int P>
+static void launch_fwd_p(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                         const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                         const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
+                         uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
+    if (bp.pixel_test)
+        launch_fwd_pt<P, true>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb,
+                               T_user, T_ws, S_out, nlast_out, pair_count, st);
+    else
+        launch_fwd_pt<P, false>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb,
+                                T_user, T_ws, S_out, nlast_out, pair_count, st);
 }
 
 cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
-                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
+                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                               const BlendParams &bp, int ppt, float *rgb, float *T_user, float *T_ws, float *S_out,
                               uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st,
                               long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
     if (ppt == 1)
-        launch_fwd_p<1>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, rgb, T_user, T_ws, S_out,
+        launch_fwd_p<1>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out,
                         nlast_out, pair_count, st);
     else if (ppt == 4)
-        launch_fwd_p<4>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, rgb, T_user, T_ws, S_out,
+        launch_fwd_p<4>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out,
                         nlast_out, pair_count, st);
     else
-        launch_fwd_p<2>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, bp, rgb, T_user, T_ws, S_out,
+        launch_fwd_p<2>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out,
                         nlast_out, pair_count, st);
     *launches += 1;
     return cudaGetLastError();

@@ -77,7 +77,7 @@ template <typename RT>
 __global__ void __launch_bounds__(256)
 k_tomo_preprocess(GaussIn g, const float *__restrict__ cs, int n_angles, int det_w, int det_h, float pu, float pv,
                   float u0, float v0, float tau_cut, float4 *__restrict__ rec, uint32_t *__restrict__ count,
-                  short4 *__restrict__ rect) {
+                  short4 *__restrict__ rect, short4 *__restrict__ prect) {
     const long long n_items = (long long)g.n * n_angles;
     const int tiles_x = (det_w + kTile - 1) / kTile;
     (void)tiles_x;
@@ -88,7 +88,7 @@ k_tomo_preprocess(GaussIn g, const float *__restrict__ cs, int n_angles, int det
         const float ct = cs[2 * a], st = cs[2 * a + 1];
         float mu[3], s[3], q[4], kap, Sig[9], Rq[9], qn[4], smax, k2;
         load_gauss<RT>(g, gi, mu, s, q, kap);
-        short4 rc = make_short4(-1, -1, -1, -1);
+        short4 rc = make_short4(-1, -1, -1, -1), prc = rc;
         uint32_t cnt = 0;
         if (key_cov(mu, s, q, kap, Sig, Rq, qn, smax) && key_k2(kap, smax, tau_cut, k2)) {
             // key function: orthographic bounding box of the Mahalanobis-k ellipsoid (FP32, fixed order)
@@ -108,6 +108,7 @@ k_tomo_preprocess(GaussIn g, const float *__restrict__ cs, int n_angles, int det
             pixel_span(ylo, yhi, det_h, iy0, iy1);
             if (ix0 <= ix1 && iy0 <= iy1) {
                 rc = make_short4((short)(ix0 / kTile), (short)(iy0 / kTile), (short)(ix1 / kTile), (short)(iy1 / kTile));
+                prc = make_short4((short)ix0, (short)iy0, (short)ix1, (short)iy1);
                 cnt = (uint32_t)(rc.z - rc.x + 1) * (uint32_t)(rc.w - rc.y + 1);
                 TomoGeom G;
                 tomo_geom(mu, s, Rq, ct, st, pu, pv, u0, v0, G);
@@ -118,12 +119,14 @@ k_tomo_preprocess(GaussIn g, const float *__restrict__ cs, int n_angles, int det
         }
         count[it] = cnt;
         rect[it] = rc;
+        prect[it] = prc;
     }
 }
 
 cudaError_t launch_tomo_preprocess(const GaussIn &g, const float *cs_d, int n_angles, int det_w, int det_h,
                                    float pitch_u, float pitch_v, float u0, float v0, float tau_cut, float4 *rec,
-                                   uint32_t *count, short4 *rect, cudaStream_t st, long long *launches) {
+                                   uint32_t *count, short4 *rect, short4 *prect, cudaStream_t st,
+                                   long long *launches) {
     const long long n_items = (long long)g.n * n_angles;
     long long b = (n_items + 255) / 256;
     if (b > 152 * 32) b = 152 * 32;
@@ -131,13 +134,13 @@ cudaError_t launch_tomo_preprocess(const GaussIn &g, const float *cs_d, int n_an
     *launches += 1;
     if (g.rec_dtype == VG_BF16)
         k_tomo_preprocess<__nv_bfloat16><<<(unsigned)b, 256, 0, st>>>(g, cs_d, n_angles, det_w, det_h, pitch_u, pitch_v,
-                                                                      u0, v0, tau_cut, rec, count, rect);
+                                                                      u0, v0, tau_cut, rec, count, rect, prect);
     else if (g.rec_dtype == VG_F16)
         k_tomo_preprocess<__half><<<(unsigned)b, 256, 0, st>>>(g, cs_d, n_angles, det_w, det_h, pitch_u, pitch_v, u0,
-                                                               v0, tau_cut, rec, count, rect);
+                                                               v0, tau_cut, rec, count, rect, prect);
     else
         k_tomo_preprocess<float><<<(unsigned)b, 256, 0, st>>>(g, cs_d, n_angles, det_w, det_h, pitch_u, pitch_v, u0,
-                                                              v0, tau_cut, rec, count, rect);
+                                                              v0, tau_cut, rec, count, rect, prect);
     return cudaGetLastError();
 }
 
@@ -149,35 +152,55 @@ constexpr int kTomoChunk = kQuadThreads;
 
 __global__ void __launch_bounds__(kQuadThreads, 12)
 k_tomo_fwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, int det_w, int det_h,
-           const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, float *__restrict__ proj) {
+           const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, const short4 *__restrict__ prect,
+           float *__restrict__ proj) {
     __shared__ float4 srec[kTomoChunk * 2];
+    __shared__ short4 srect[kTomoChunk];
     const int tile = blockIdx.x;
     const int view = tile / tiles_per_view, local = tile - view * tiles_per_view;
     const int ty = local / tiles_x, tx = local - ty * tiles_x;
     const int x0 = tx * kTile + 2 * (threadIdx.x & 7), y0 = ty * kTile + 2 * (threadIdx.x >> 3);
     const float xf = (float)x0, yf = (float)y0;
+    const WarpBox wb = warp_box<4>(x0, y0);
     const uint2 rg = ranges[tile];
     float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (uint32_t base = rg.x; base < rg.y; base += kTomoChunk) {
         const uint32_t n = min((uint32_t)kTomoChunk, rg.y - base);
         __syncthreads();
         if (threadIdx.x < n) {
-            const float4 *src = rec + 2 * (size_t)sorted_item[base + threadIdx.x];
+            const uint32_t item = sorted_item[base + threadIdx.x];
+            const float4 *src = rec + 2 * (size_t)item;
             srec[2 * threadIdx.x] = __ldg(src);
             srec[2 * threadIdx.x + 1] = __ldg(src + 1);
+            srect[threadIdx.x] = prect[item];
         }
         __syncthreads();
         for (uint32_t j = 0; j < n; ++j) {
+            const short4 pr = srect[j];
+            if (box_misses(wb, pr)) continue;   // the footprint misses every pixel of this warp
             const float4 r0 = srec[2 * j], r1 = srec[2 * j + 1];
             const float dx = xf - r0.x, dy = yf - r0.y;
             const float ya0 = fmaf(r0.z, dx, r1.x * dy), ya1 = fmaf(r0.w, dx, r1.y * dy);   // pixel (0,0)
             const float yb0 = ya0 + r0.z, yb1 = ya1 + r0.w;                                   // (1,0)
             const float yc0 = ya0 + r1.x, yc1 = ya1 + r1.y;                                   // (0,1)
             const float yd0 = yb0 + r1.x, yd1 = yb1 + r1.y;                                   // (1,1)
-            sum[0] += ex2_approx(fmaf(fmaf(ya0, ya0, ya1 * ya1), -kHalfLog2e, r1.z));
-            sum[1] += ex2_approx(fmaf(fmaf(yb0, yb0, yb1 * yb1), -kHalfLog2e, r1.z));
-            sum[2] += ex2_approx(fmaf(fmaf(yc0, yc0, yc1 * yc1), -kHalfLog2e, r1.z));
-            sum[3] += ex2_approx(fmaf(fmaf(yd0, yd0, yd1 * yd1), -kHalfLog2e, r1.z));
+            const float ta = ex2_approx(fmaf(fmaf(ya0, ya0, ya1 * ya1), -kHalfLog2e, r1.z));
+            const float tb = ex2_approx(fmaf(fmaf(yb0, yb0, yb1 * yb1), -kHalfLog2e, r1.z));
+            const float tc = ex2_approx(fmaf(fmaf(yc0, yc0, yc1 * yc1), -kHalfLog2e, r1.z));
+            const float td = ex2_approx(fmaf(fmaf(yd0, yd0, yd1 * yd1), -kHalfLog2e, r1.z));
+            if (box_inside(wb, pr)) {            // warp-uniform fast path: every pixel is inside
+                sum[0] += ta;
+                sum[1] += tb;
+                sum[2] += tc;
+                sum[3] += td;
+            } else {                             // footprint rectangle, separable in x and y
+                const bool xa = x0 >= pr.x && x0 <= pr.z, xb = x0 + 1 >= pr.x && x0 + 1 <= pr.z;
+                const bool ya = y0 >= pr.y && y0 <= pr.w, yb = y0 + 1 >= pr.y && y0 + 1 <= pr.w;
+                sum[0] += (xa && ya) ? ta : 0.0f;
+                sum[1] += (xb && ya) ? tb : 0.0f;
+                sum[2] += (xa && yb) ? tc : 0.0f;
+                sum[3] += (xb && yb) ? td : 0.0f;
+            }
         }
     }
 #pragma unroll
@@ -188,11 +211,11 @@ k_tomo_fwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
 }
 
 cudaError_t launch_tomo_fwd(const uint2 *ranges, long long n_tiles, int tiles_x, int tiles_per_view, int det_w,
-                            int det_h, const uint32_t *sorted_item, const float4 *rec, float *proj, cudaStream_t st,
-                            long long *launches) {
+                            int det_h, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                            float *proj, cudaStream_t st, long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
     k_tomo_fwd<<<(unsigned)n_tiles, kQuadThreads, 0, st>>>(ranges, tiles_x, tiles_per_view, det_w, det_h,
-                                                           sorted_item, rec, proj);
+                                                           sorted_item, rec, prect, proj);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -203,10 +226,11 @@ cudaError_t launch_tomo_fwd(const uint2 *ranges, long long n_tiles, int tiles_x,
 // are summed over the quad, reduce-scattered over the warp and summed over the CTA.
 __global__ void __launch_bounds__(kQuadThreads, 12)
 k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, int det_w, int det_h,
-           const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, const float *__restrict__ proj,
-           const float *__restrict__ dL_dproj, float *__restrict__ grad_acc) {
+           const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, const short4 *__restrict__ prect,
+           const float *__restrict__ proj, const float *__restrict__ dL_dproj, float *__restrict__ grad_acc) {
     constexpr int NV = 7;
     __shared__ float4 srec[kTomoChunk * 2];
+    __shared__ short4 srect[kTomoChunk];
     __shared__ float sacc[kTomoChunk * NV];
     __shared__ uint32_t sitem[kTomoChunk];
     const int tile = blockIdx.x;
@@ -225,6 +249,7 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
             gtau[k] = -proj[pix] * dL_dproj[pix];
         }
     }
+    const WarpBox wb = warp_box<4>(x0, y0);
     const uint2 rg = ranges[tile];
     for (uint32_t base = rg.x; base < rg.y; base += kTomoChunk) {
         const uint32_t n = min((uint32_t)kTomoChunk, rg.y - base);
@@ -233,22 +258,33 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
             sitem[threadIdx.x] = item;
             srec[2 * threadIdx.x] = __ldg(rec + 2 * (size_t)item);
             srec[2 * threadIdx.x + 1] = __ldg(rec + 2 * (size_t)item + 1);
+            srect[threadIdx.x] = prect[item];
         }
         for (int k = threadIdx.x; k < kTomoChunk * NV; k += kQuadThreads) sacc[k] = 0.0f;
         __syncthreads();
         for (uint32_t j = 0; j < n; ++j) {
+            const short4 pr = srect[j];
+            if (box_misses(wb, pr)) continue;
             const float4 r0 = srec[2 * j], r1 = srec[2 * j + 1];
             float v[32];
 #pragma unroll
             for (int k = 0; k < 32; ++k) v[k] = 0.0f;
             const float dx0 = xf - r0.x, dy0 = yf - r0.y;
+            const float ya0 = fmaf(r0.z, dx0, r1.x * dy0), ya1 = fmaf(r0.w, dx0, r1.y * dy0);
+            const float yb0 = ya0 + r0.z, yb1 = ya1 + r0.w;
+            const float q0[4] = {ya0, yb0, ya0 + r1.x, yb0 + r1.x}, q1[4] = {ya1, yb1, ya1 + r1.y, yb1 + r1.y};
+            // footprint rectangle, separable in x and y; all-true when the warp lies inside it
+            const bool full = box_inside(wb, pr);
+            const bool xa = full || (x0 >= pr.x && x0 <= pr.z), xb = full || (x0 + 1 >= pr.x && x0 + 1 <= pr.z);
+            const bool ya = full || (y0 >= pr.y && y0 <= pr.w), yb = full || (y0 + 1 >= pr.y && y0 + 1 <= pr.w);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float dx = (k & 1) ? dx0 + 1.0f : dx0, dy = (k & 2) ? dy0 + 1.0f : dy0;
-                const float y0v = fmaf(r0.z, dx, r1.x * dy), y1v = fmaf(r0.w, dx, r1.y * dy);
+                const float y0v = q0[k], y1v = q1[k];
                 const float m2 = fmaf(y0v, y0v, y1v * y1v);
                 const float tau = ex2_approx(fmaf(m2, -kHalfLog2e, r1.z));
-                const float G = gtau[k] * tau;                  // dL / d ln(tau)
+                const bool in = ((k & 1) ? xb : xa) && ((k & 2) ? yb : ya);
+                const float G = in ? gtau[k] * tau : 0.0f;      // dL / d ln(tau)
                 const float gy0 = -G * y0v, gy1 = -G * y1v;
                 v[0] = fmaf(gy0, dx, v[0]);
                 v[1] = fmaf(gy1, dx, v[1]);
@@ -272,11 +308,12 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
 }
 
 cudaError_t launch_tomo_bwd(const uint2 *ranges, long long n_tiles, int tiles_x, int tiles_per_view, int det_w,
-                            int det_h, const uint32_t *sorted_item, const float4 *rec, const float *proj,
-                            const float *dL_dproj, float *grad_acc, cudaStream_t st, long long *launches) {
+                            int det_h, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                            const float *proj, const float *dL_dproj, float *grad_acc, cudaStream_t st,
+                            long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
     k_tomo_bwd<<<(unsigned)n_tiles, kQuadThreads, 0, st>>>(ranges, tiles_x, tiles_per_view, det_w, det_h,
-                                                           sorted_item, rec, proj, dL_dproj, grad_acc);
+                                                           sorted_item, rec, prect, proj, dL_dproj, grad_acc);
     *launches += 1;
     return cudaGetLastError();
 }

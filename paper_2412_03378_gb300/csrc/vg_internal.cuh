@@ -39,6 +39,8 @@ struct BlendParams {
     float tau_max;
     float T_stop;
     float bg[3];
+    int pixel_test;       // test every pixel against the Gaussian's footprint rectangle
+                          // (needed when tau_skip < tau_cut; otherwise implied by the skip)
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -65,11 +67,11 @@ template <> __device__ __forceinline__ float ld_f<__half>(const __half *p, long 
 // kernels they launched to *launches.
 cudaError_t launch_preprocess(const GaussIn &g, const ViewInfo *views_d, int n_views, float z_near,
                               float tau_cut, float4 *rec, uint32_t *depth, uint32_t *count, short4 *rect,
-                              unsigned long long *n_visible, cudaStream_t st, long long *launches);
+                              short4 *prect, unsigned long long *n_visible, cudaStream_t st, long long *launches);
 
 cudaError_t launch_tomo_preprocess(const GaussIn &g, const float *cs_d /* [A][2] cos, sin */, int n_angles,
                                    int det_w, int det_h, float pitch_u, float pitch_v, float u0, float v0,
-                                   float tau_cut, float4 *rec, uint32_t *count, short4 *rect,
+                                   float tau_cut, float4 *rec, uint32_t *count, short4 *rect, short4 *prect,
                                    cudaStream_t st, long long *launches);
 
 // Exclusive scan of n uint32 values into out (out[n] = total).  tmp must hold
@@ -101,13 +103,13 @@ cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, uint2 *r
                           cudaStream_t st, long long *launches);
 
 cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
-                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
+                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                               const BlendParams &bp, int ppt, float *rgb, float *T_user, float *T_ws, float *S_out,
                               uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st,
                               long long *launches);
 
 cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
-                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
+                              const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                               const BlendParams &bp, int ppt, const float *T_fin, const float *S_fin,
                               const uint32_t *nlast, const float *dL_drgb, const float *dL_dT, float *grad_acc,
                               unsigned long long *pair_count, cudaStream_t st, long long *launches);
@@ -122,12 +124,13 @@ cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views,
                          long long *launches);
 
 cudaError_t launch_tomo_fwd(const uint2 *ranges, long long n_tiles, int tiles_x, int tiles_per_view, int det_w,
-                            int det_h, const uint32_t *sorted_item, const float4 *rec, float *proj,
-                            cudaStream_t st, long long *launches);
+                            int det_h, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                            float *proj, cudaStream_t st, long long *launches);
 
 cudaError_t launch_tomo_bwd(const uint2 *ranges, long long n_tiles, int tiles_x, int tiles_per_view, int det_w,
-                            int det_h, const uint32_t *sorted_item, const float4 *rec, const float *proj,
-                            const float *dL_dproj, float *grad_acc, cudaStream_t st, long long *launches);
+                            int det_h, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                            const float *proj, const float *dL_dproj, float *grad_acc, cudaStream_t st,
+                            long long *launches);
 
 cudaError_t launch_tomo_chain(const GaussIn &g, const float *cs_d, int n_angles, long long item0, long long n_items,
                               float pitch_u, float pitch_v, float u0, float v0, const float *grad_acc, float *dmu,

@@ -196,6 +196,13 @@ def test_footprint_is_conservative(mode):
     assert g_idx.size > 1000
     missing = ~member[g_idx, tile[py, px]]
     assert missing.sum() == 0
+    # ... and inside the Gaussian's pixel footprint rectangle
+    pr = L["prect"][0]
+    inside = (px >= pr[g_idx, 0]) & (px <= pr[g_idx, 2]) & (py >= pr[g_idx, 1]) & (py <= pr[g_idx, 3])
+    assert inside.all()
+    # the rectangle lies within the tile rectangle
+    ok = L["rect"][0, :, 0] >= 0
+    assert np.all(pr[ok, 0] // 16 == L["rect"][0, ok, 0]) and np.all(pr[ok, 3] // 16 == L["rect"][0, ok, 3])
     # and the blend over tile lists equals the blend over all Gaussians up to truncation
     rgb, T, _ = oracle.render(scene, cams, opts, L)
     rgbb, Tb, _ = oracle.render(scene, cams, opts, L, brute=True)
