@@ -109,11 +109,21 @@ def make_workload(frac):
     return scene, cams, target
 
 
+TRAFFIC_SOURCES = ("render_bwd.cu", "blend.cuh", "geometry.cuh", "vg_internal.cuh")
+
+
+def kernel_source_sha1():
+    """sha1 over the sources the backward blend kernel is compiled from, in a fixed order."""
+    h = hashlib.sha1()
+    for name in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2412_03378_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record():
     """DRAM bytes per launch of the backward blend kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged (null otherwise)."""
+    valid only while the kernel's sources are unchanged (null otherwise)."""
     p = os.path.join(ROOT, "profiles", "render_bwd_cfg2_traffic.txt")
-    src = os.path.join(ROOT, "paper_2412_03378_gb300", "csrc", "render_bwd.cu")
     if not os.path.exists(p):
         return None
     kv = {}
@@ -121,8 +131,7 @@ def traffic_record():
         if ":" in line:
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    if kv.get("source_sha1") != sha:
+    if kv.get("source_sha1") != kernel_source_sha1():
         return None
     try:
         return float(kv["dram_bytes_per_launch"])

@@ -199,7 +199,7 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
  *
  *  - Limit: views x Gaussians of the last vg_preprocess must be <= VG_NOALLOC_MAX_ITEMS;
  *    larger requests return VG_ERR_INVALID_ARG and launch nothing.
- *  - The array (VG_NOALLOC_MAX_ITEMS x 96 bytes = 6 MiB) is a static device allocation of
+ *  - The array (VG_NOALLOC_MAX_ITEMS x 64 bytes = 4 MiB) is a static device allocation of
  *    the library: every GPU that loads the library holds it until the process exits.
  *  - The first call on a device looks up the array's device address with that device
  *    current; make that first call before any stream capture.

@@ -499,16 +499,6 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
         return fail(ws, VG_ERR_INVALID_ARG, "a gradient pointer is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     VG_TRY(ensure(ws, ws->grad, (size_t)ws->n_items * kGradN, "gradient accumulators"));
-    if ((ws->opts.flags & VG_FLAG_GRAD_ZERO) && ws->g.n > 0) {
-        const size_t n = (size_t)ws->g.n;
-        VG_CUDA(ws, cudaMemsetAsync(dmu, 0, n * 3 * sizeof(float), st));
-        VG_CUDA(ws, cudaMemsetAsync(dscale, 0, n * 3 * sizeof(float), st));
-        VG_CUDA(ws, cudaMemsetAsync(dquat, 0, n * 4 * sizeof(float), st));
-        VG_CUDA(ws, cudaMemsetAsync(dkappa, 0, n * sizeof(float), st));
-        if (dsh)
-            VG_CUDA(ws, cudaMemsetAsync(dsh, 0, n * 3 * (size_t)((ws->g.sh_degree + 1) * (ws->g.sh_degree + 1)) *
-                                                    sizeof(float), st));
-    }
     if (ws->n_items > 0)
         VG_CUDA(ws, cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st));
     unsigned long long *pc = nullptr;
@@ -524,11 +514,11 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
                                       ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, ws->grad.p, pc, st,
                                       &ws->launches));
     }
-    if (ws->n_items > 0) {
+    {
+        // the chain writes every Gaussian's gradient: overwriting with VG_FLAG_GRAD_ZERO, else adding
         ProfScope ps(ws, ST_CHAIN, st);
-        GaussIn g = ws->g;
-        VG_CUDA(ws, launch_chain(g, ws->views.p, ws->n_views, ws->grad.p, dmu, dscale, dquat, dkappa, dsh, st,
-                                 &ws->launches));
+        VG_CUDA(ws, launch_chain(ws->g, ws->views.p, ws->n_views, ws->grad.p, (ws->opts.flags & VG_FLAG_GRAD_ZERO) ? 1 : 0,
+                                 dmu, dscale, dquat, dkappa, dsh, st, &ws->launches));
     }
     return VG_OK;
 }
@@ -575,25 +565,14 @@ vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const fl
     cudaStream_t st = (cudaStream_t)stream;
     float *acc = nullptr;
     VG_TRY(noalloc_scratch(ws, &acc));
-    if ((ws->opts.flags & VG_FLAG_GRAD_ZERO) && ws->g.n > 0) {
-        const size_t n = (size_t)ws->g.n;
-        VG_CUDA(ws, cudaMemsetAsync(dmu, 0, n * 3 * sizeof(float), st));
-        VG_CUDA(ws, cudaMemsetAsync(dscale, 0, n * 3 * sizeof(float), st));
-        VG_CUDA(ws, cudaMemsetAsync(dquat, 0, n * 4 * sizeof(float), st));
-        VG_CUDA(ws, cudaMemsetAsync(dkappa, 0, n * sizeof(float), st));
-        if (dsh)
-            VG_CUDA(ws, cudaMemsetAsync(dsh, 0, n * 3 * (size_t)((ws->g.sh_degree + 1) * (ws->g.sh_degree + 1)) *
-                                                    sizeof(float), st));
-    }
     // the array keeps the previous call's sums: clear the part this call accumulates into
     if (ws->n_items > 0) VG_CUDA(ws, cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st));
     VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
                                   ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_bwd, ws->T_fin.p,
                                   ws->S_fin.p,
                                   ws->nlast.p, dL_drgb, dL_dT, acc, nullptr, st, &ws->launches));
-    if (ws->n_items > 0)
-        VG_CUDA(ws, launch_chain(ws->g, ws->views.p, ws->n_views, acc, dmu, dscale, dquat, dkappa, dsh, st,
-                                 &ws->launches));
+    VG_CUDA(ws, launch_chain(ws->g, ws->views.p, ws->n_views, acc, (ws->opts.flags & VG_FLAG_GRAD_ZERO) ? 1 : 0, dmu,
+                             dscale, dquat, dkappa, dsh, st, &ws->launches));
     return VG_OK;
 }
 

@@ -160,22 +160,49 @@ __device__ __forceinline__ void pair_eval_at(const float4 &r0, const float4 &r1,
     e.tau = __fmul_rn(ex2_approx(fmaf(e.m2, -kHalfLog2e, __fadd_rn(r5.x, Lp))), e.rs);
 }
 
-// Warp reduce-scatter of NV <= 32 per-lane values: afterwards lane k (k < NV) holds the sum
-// over the warp of value k.  Five exchange steps of halving width: 16+8+4+2+1 shuffles.
-template <int NV>
-__device__ __forceinline__ float warp_reduce_scatter(float (&v)[32], int lane) {
+// Warp reduce-scatter of NP per-lane values (NP a power of two, 2..32).  Each exchange step
+// with partner lane^w keeps half of the lane's values and sends the other half while more than
+// one value is left (NP/2 + NP/4 + ... shuffles), then plain butterfly adds finish the sum.
+// Afterwards lane l holds the warp sum of value scatter_index<NP>(l); the 32/NP lanes that
+// differ only in their low log2(32/NP) bits hold the same value.
+template <int NP>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NP], int lane) {
+    static_assert(NP >= 2 && NP <= 32 && (NP & (NP - 1)) == 0, "NP must be a power of two");
 #pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
-        const bool hi = (lane & w) != 0;
+    for (int s = 0; s < 5; ++s) {
+        const int w = 16 >> s;
+        const int c = NP >> s;   // values the lane still holds
+        if (c > 1) {
+            const int h = c / 2;
+            const bool hi = (lane & w) != 0;
 #pragma unroll
-        for (int i = 0; i < w; ++i) {
-            if (i >= NV && i + w >= NV) continue;   // both halves are structurally zero
-            const float keep = hi ? v[i + w] : v[i];
-            const float send = hi ? v[i] : v[i + w];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+            for (int i = 0; i < h; ++i) {
+                const float keep = hi ? v[i + h] : v[i];
+                const float send = hi ? v[i] : v[i + h];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+            }
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], w);
         }
     }
     return v[0];
+}
+
+template <int NP>
+__device__ __forceinline__ int scatter_index(int lane) {
+    int idx = 0;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int c = NP >> s;
+        if (c > 1 && (lane & (16 >> s))) idx += c / 2;
+    }
+    return idx;
+}
+
+// True for the one lane of each group that holds the same reduce-scatter result.
+template <int NP>
+__device__ __forceinline__ bool scatter_writer(int lane) {
+    return (lane & (32 / NP - 1)) == 0;
 }
 
 }  // namespace vg

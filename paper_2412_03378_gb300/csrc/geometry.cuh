@@ -159,17 +159,70 @@ __device__ __forceinline__ int key_persp(const ViewInfo &V, const float mu[3], c
     return 2;
 }
 
+// ------------------------------------------------------------------ double-float arithmetic
+// Error-free transformations in FP32: two_sum (Knuth) gives s + e == a + b exactly, two_prod
+// (via FMA) gives p + e == a * b exactly.  Sums of products accumulated with them as in the
+// Dot2 algorithm (Ogita, Rump, Oishi: "Accurate Sum and Dot Product", SIAM J. Sci. Comput. 2005)
+// are as accurate as if computed in twice the working precision, i.e. ~48 significant bits,
+// on the FP32 pipe (GB300's FP64 rate is a small fraction of its FP32 rate).
+struct DF {
+    float hi, lo;   // unevaluated sum hi + lo
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return DF{s, e};
+}
+
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return DF{p, fmaf(a, b, -p)};
+}
+
+// acc + a * b with the product and the leading sum error-free (one Dot2 step)
+__device__ __forceinline__ DF df_fma(DF acc, float a, float b) {
+    const DF p = two_prod(a, b);
+    const DF s = two_sum(acc.hi, p.hi);
+    return DF{s.hi, __fadd_rn(acc.lo, __fadd_rn(s.lo, p.lo))};
+}
+
+// acc + a * (b.hi + b.lo)
+__device__ __forceinline__ DF df_fma(DF acc, float a, DF b) {
+    DF r = df_fma(acc, a, b.hi);
+    r.lo = fmaf(a, b.lo, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ DF df_add(DF acc, DF b) {
+    const DF s = two_sum(acc.hi, b.hi);
+    return DF{s.hi, __fadd_rn(acc.lo, __fadd_rn(s.lo, b.lo))};
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ float df_float(DF a) { return __fadd_rn(a.hi, a.lo); }
+
+// renormalised so that |lo| <= ulp(hi) / 2
+__device__ __forceinline__ DF df_norm(DF a) {
+    const float s = __fadd_rn(a.hi, a.lo);
+    return DF{s, __fsub_rn(a.lo, __fsub_rn(s, a.hi))};
+}
+
+// ------------------------------------------------------------------ record geometry
 // Blend-record geometry of one (view, Gaussian).  With B = Rc Rq and M = S^-1 B^T the
 // whitening in camera coordinates, a pixel ray d_c = (u, v, 1) maps to d' = M d_c and the
 // camera centre to o' = -M mu_c.  Pixels are addressed relative to the projected mean
 // (px0, py0), so that d' = A0 dx + A1 dy + A2 and o' x d' = C0 dx + C1 dy + C2 with
 // C2 ~ 0: the cancellation-prone cross product is formed per Gaussian in extra precision
-// instead of per pixel.
+// (double-float) instead of per pixel.
 struct ItemGeom {
     float M[9];        // row-major
-    double muc[3];     // camera-space mean, FP64
-    float op[3];       // o'
-    float px0, py0;    // reference pixel (projected mean, rounded)
+    DF muc[3];         // camera-space mean, double-float
+    DF opx[3];         // o' = -M mu_c, double-float
+    float op[3];       // o' rounded to FP32
+    float px0, py0;    // reference pixel: the projected mean in FP32
     float dc0[3];      // camera ray through the reference pixel
     float Dx, Dy;      // reference pixel minus the exact projection, in pixels
     float A[9];        // A0, A1, A2 (rows of 3)
@@ -197,23 +250,41 @@ __device__ __forceinline__ void item_geom(const ViewInfo &V, const float mu[3], 
 #pragma unroll
         for (int j = 0; j < 3; ++j) G.M[3 * i + j] = B[3 * j + i] * is;
     }
+    // mu_c = Rc mu + t and o' = -M mu_c, both to ~48 bits
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-        G.muc[k] = fma((double)Rc[3 * k], (double)mu[0],
-                       fma((double)Rc[3 * k + 1], (double)mu[1], fma((double)Rc[3 * k + 2], (double)mu[2], (double)V.t[k])));
+    for (int k = 0; k < 3; ++k) {
+        DF acc = DF{V.t[k], 0.0f};
+        acc = df_fma(acc, Rc[3 * k], mu[0]);
+        acc = df_fma(acc, Rc[3 * k + 1], mu[1]);
+        acc = df_fma(acc, Rc[3 * k + 2], mu[2]);
+        G.muc[k] = df_norm(acc);
+    }
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-        G.op[i] = (float)(-fma((double)G.M[3 * i], G.muc[0],
-                               fma((double)G.M[3 * i + 1], G.muc[1], (double)G.M[3 * i + 2] * G.muc[2])));
-    float Xf = (float)G.muc[0], Yf = (float)G.muc[1], Zf = (float)G.muc[2];
-    float izf = 1.0f / Zf;
+    for (int i = 0; i < 3; ++i) {
+        DF acc = DF{0.0f, 0.0f};
+        acc = df_fma(acc, -G.M[3 * i], G.muc[0]);
+        acc = df_fma(acc, -G.M[3 * i + 1], G.muc[1]);
+        acc = df_fma(acc, -G.M[3 * i + 2], G.muc[2]);
+        G.opx[i] = df_norm(acc);
+        G.op[i] = G.opx[i].hi;
+    }
+    const float Xf = G.muc[0].hi, Yf = G.muc[1].hi, Zf = G.muc[2].hi;
+    const float izf = 1.0f / Zf;
     G.px0 = fmaf(V.fx, Xf * izf, V.cx - 0.5f);
     G.py0 = fmaf(V.fy, Yf * izf, V.cy - 0.5f);
-    double ex = ((double)G.px0 + 0.5 - (double)V.cx), ey = ((double)G.py0 + 0.5 - (double)V.cy);
-    G.Dx = (float)fma(ex, G.muc[2], -(double)V.fx * G.muc[0]) * izf;
-    G.Dy = (float)fma(ey, G.muc[2], -(double)V.fy * G.muc[1]) * izf;
-    G.dc0[0] = (float)ex / V.fx;
-    G.dc0[1] = (float)ey / V.fy;
+    // (px0 + 0.5 - cx) exactly as a double-float; then D = (e Z - f X) / Z to ~48 bits before rounding
+    const DF ex = df_add(two_sum(G.px0, 0.5f), DF{-V.cx, 0.0f});
+    const DF ey = df_add(two_sum(G.py0, 0.5f), DF{-V.cy, 0.0f});
+    DF nx = df_fma(DF{0.0f, 0.0f}, ex.hi, G.muc[2]);
+    nx.lo = fmaf(ex.lo, G.muc[2].hi, nx.lo);
+    nx = df_fma(nx, -V.fx, G.muc[0]);
+    DF ny = df_fma(DF{0.0f, 0.0f}, ey.hi, G.muc[2]);
+    ny.lo = fmaf(ey.lo, G.muc[2].hi, ny.lo);
+    ny = df_fma(ny, -V.fy, G.muc[1]);
+    G.Dx = df_float(nx) * izf;
+    G.Dy = df_float(ny) * izf;
+    G.dc0[0] = df_float(ex) / V.fx;
+    G.dc0[1] = df_float(ey) / V.fy;
     G.dc0[2] = 1.0f;
     float ifx = 1.0f / V.fx, ify = 1.0f / V.fy;
 #pragma unroll
@@ -289,9 +360,60 @@ __device__ __forceinline__ void eval_colour(const GaussIn &g, long long gi, cons
     const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
     const ST *sh = (const ST *)g.sh + (long long)gi * K * 3;
     float acc[3] = {0.5f, 0.5f, 0.5f};
-    for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {   // unrolled so that Y stays in registers
+        if (k >= K) break;
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[c] = fmaf(ld_f<ST>(sh, 3 * k + c), Y[k], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        raw[c] = acc[c];
+        rgb[c] = fmaxf(acc[c], 0.0f);
+    }
+}
+
+// ------------------------------------------------------------------ warp staging of per-Gaussian rows
+// Per-Gaussian rows (SH coefficients, blend records) are contiguous in global memory, one row per
+// Gaussian.  A warp that owns 32 consecutive Gaussians moves their rows through shared memory so
+// that every global load and store instruction covers consecutive addresses; each lane then
+// works on its own row, padded to an odd stride (conflict-free across lanes).
+constexpr int kRowStride = 49;   // >= 48 SH floats (degree 3) and >= 24 record floats; odd
+
+// floor(e / w) as (e * row_inv(w)) >> 20, exact for e < 2^20 / w (here e < 32 * 48)
+__host__ __device__ __forceinline__ uint32_t row_inv(int w) { return ((1u << 20) + (uint32_t)w - 1u) / (uint32_t)w; }
+
+template <typename T>
+__device__ __forceinline__ void warp_load_rows(const T *src, int rows, int w, float *buf, int lane) {
+    const uint32_t inv = row_inv(w), total = (uint32_t)(rows * w);
+#pragma unroll 4
+    for (uint32_t e = lane; e < total; e += 32) {
+        const uint32_t r = (e * inv) >> 20, c = e - r * (uint32_t)w;
+        buf[r * kRowStride + c] = ld_f<T>(src, e);
+    }
+}
+
+__device__ __forceinline__ void warp_store_rows(float *dst, int rows, int w, const float *buf, int lane) {
+    const uint32_t inv = row_inv(w), total = (uint32_t)(rows * w);
+    for (uint32_t e = lane; e < total; e += 32) {
+        const uint32_t r = (e * inv) >> 20, c = e - r * (uint32_t)w;
+        dst[e] = buf[r * kRowStride + c];
+    }
+}
+
+// view-dependent colour from a staged SH row (same operation order as eval_colour)
+__device__ __forceinline__ void eval_colour_row(int deg, const float *row, const float dir[3], float rgb[3],
+                                                float raw[3]) {
+    float Y[16];
+    sh_basis(deg, dir[0], dir[1], dir[2], Y);
+    const int K = (deg + 1) * (deg + 1);
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k >= K) break;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = fmaf(row[3 * k + c], Y[k], acc[c]);
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         raw[c] = acc[c];

@@ -4,26 +4,32 @@
 // log-transmittance S = sum tau (no per-pair state is kept by the forward):
 //   T_i = exp(-(S_after - tau_i)),  dL/dc_i = g alpha_i T_i,
 //   dL/dtau_i = g . (c_i T_{i+1} - R_i) - gT T_end,  R_i = sum_{j>i} c_j alpha_j T_j + T_end bg,
-// then differentiates tau with respect to the record (A0..A2, C0..C2, ln kappa).  Per
-// Gaussian the 22 partials are summed over the warp with shuffles, over the CTA in shared
-// memory, and added to the per-item accumulator with one set of global atomics per
-// (tile, Gaussian).  k_chain maps the accumulators to dmu, dscale, dquat, dkappa, dsh.
+// then differentiates tau with respect to the record.  d' = A u and o' x d' = C u are linear in
+// u = (dx, dy, 1), so with ga = 2 dL/da and gq = 2 dL/dq per pixel (a = |d'|^2, q = |o' x d'|^2)
+//   dL/dA = A sum_p ga u u^T,   dL/dC = C sum_p gq u u^T:
+// per Gaussian only the two symmetric 3x3 moment matrices (6 + 6 values), sum dL/dln(kappa) and
+// the three colour partials are summed -- 16 values.  They are reduce-scattered over the warp
+// with shuffles, summed over the CTA in shared memory, and added to the per-item accumulator
+// with one set of global atomics per (tile, Gaussian).  k_chain multiplies by A and C and maps
+// the result to dmu, dscale, dquat, dkappa, dsh.
 #include "blend.cuh"
 #include "geometry.cuh"
 
 namespace vg {
 
-constexpr int kGradUsed = 22;
+// Accumulator layout per item: [0..5] sum ga (xx, xy, x, yy, y, 1), [6..11] the same for gq,
+// [12] sum dL/dln(kappa), [13..15] dL/dcolour.
+constexpr int kGradUsed = 16;
+static_assert(kGradUsed <= kGradN, "accumulator too small");
 
 template <int P> struct BwdBounds;
 template <> struct BwdBounds<1> { static constexpr int kMinBlocks = 2; };
 template <> struct BwdBounds<2> { static constexpr int kMinBlocks = 4; };
 template <> struct BwdBounds<4> { static constexpr int kMinBlocks = 8; };
 
-// One CTA per tile (longest list first), 256/P threads owning P pixels each.  Per record the
-// 22 partials are summed over the thread's pixels in registers, then over the warp by a
-// reduce-scatter (lane k ends with partial k), over the CTA in shared memory, and finally
-// added to the item's accumulator with one set of global atomics per (tile, Gaussian).
+// One CTA per tile (longest list first), 256/P threads owning P pixels each.  Each warp first
+// ballots which records of the staged chunk it needs (some pixel of the warp reached the record
+// and the record's footprint touches the warp's pixels), then visits only those, back to front.
 template <int P, bool COUNT, bool PIXTEST>
 __global__ void __launch_bounds__(PixLayout<P>::kThreads, BwdBounds<P>::kMinBlocks)
 k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
@@ -49,6 +55,8 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     const int x0 = txi * kTile + ix, y0 = tyi * kTile + iy;
     const uint2 rg = ranges[tile];
     const int lane = threadIdx.x & 31;
+    const int sidx = scatter_index<kGradUsed>(lane);
+    const bool swrite = scatter_writer<kGradUsed>(lane);
 
     float Lp[P], S[P], Tafter[P], R0[P], R1[P], R2[P], g0[P], g1[P], g2[P], gTterm[P];
     uint32_t my_last[P];
@@ -89,8 +97,8 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
 
     for (uint32_t end = tile_last; end > rg.x;) {
         const uint32_t start = (end - rg.x > (uint32_t)kChunk) ? end - kChunk : rg.x;
-        const uint32_t n = end - start;
-        if (threadIdx.x < n) {
+        const int n = (int)(end - start);
+        if ((int)threadIdx.x < n) {
             const uint32_t item = sorted_item[start + threadIdx.x];
             sitem[threadIdx.x] = item;
             const float4 *src = rec + (size_t)item * kRecF4;
@@ -100,72 +108,82 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
         }
         for (int k = threadIdx.x; k < kChunk * kGradUsed; k += kThreads) sacc[k] = 0.0f;
         __syncthreads();
-        for (int j = (int)n - 1; j >= 0; --j) {
-            const uint32_t idx = start + (uint32_t)j;
-            const short4 pr = srect[j];
-            // warp-uniform: nothing of this warp reached the record, or its footprint misses the warp
-            if (idx >= warp_last || box_misses(wb, pr)) continue;
-            float gv[32];
+        for (int w0 = (n - 1) & ~31; w0 >= 0; w0 -= 32) {
+            const int jl = w0 + lane;
+            const bool need = jl < n && start + (uint32_t)jl < warp_last && !box_misses(wb, srect[jl]);
+            unsigned m = __ballot_sync(0xffffffffu, need);
+            while (m) {
+                const int b = 31 - __clz(m);
+                m ^= 1u << b;
+                const int j = w0 + b;
+                const uint32_t idx = start + (uint32_t)j;
+                float gv[kGradUsed];
 #pragma unroll
-            for (int k = 0; k < 32; ++k) gv[k] = 0.0f;
-            bool any = false;
-            if (idx < thr_last) {
-                const float4 *r = &srec[j * kRecF4];
-                const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
-                QuadBase qb;
-                quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
+                for (int k = 0; k < kGradUsed; ++k) gv[k] = 0.0f;
+                bool any = false;
+                if (idx < thr_last) {
+                    const float4 *r = &srec[j * kRecF4];
+                    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
+                    short4 pr;
+                    if (PIXTEST) pr = srect[j];
+                    QuadBase qb;
+                    quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
 #pragma unroll
-                for (int k = 0; k < P; ++k) {
-                    if (idx >= my_last[k]) continue;
-                    if (PIXTEST && pixel_outside(x0 + L::ox(k), y0 + L::oy(k), pr)) continue;
-                    PairEval e;
-                    pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
-                    if (COUNT) ++pairs;
-                    const bool clamped = e.tau > bp.tau_max;
-                    const float tau = fminf(e.tau, bp.tau_max);
-                    if (tau < bp.tau_skip) continue;
-                    any = true;
-                    const float e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
-                    const float alpha = __fsub_rn(1.0f, e2);
-                    const float Sb = S[k] - tau;
-                    const float Tb = ex2_approx(-kLog2eF * Sb);
-                    const float aT = alpha * Tb;
-                    gv[19] = fmaf(g0[k], aT, gv[19]);
-                    gv[20] = fmaf(g1[k], aT, gv[20]);
-                    gv[21] = fmaf(g2[k], aT, gv[21]);
-                    const float dtau = g0[k] * (r5.y * Tafter[k] - R0[k]) + g1[k] * (r5.z * Tafter[k] - R1[k]) +
-                                       g2[k] * (r5.w * Tafter[k] - R2[k]) + gTterm[k];
-                    R0[k] = fmaf(r5.y, aT, R0[k]);
-                    R1[k] = fmaf(r5.z, aT, R1[k]);
-                    R2[k] = fmaf(r5.w, aT, R2[k]);
-                    S[k] = Sb;
-                    Tafter[k] = Tb;
-                    if (!clamped) {
-                        const float G = dtau * tau;                // dL / d ln(tau)
-                        const float r2s = e.rs * e.rs;
-                        const float gda = G * r2s * (e.m2 - 1.0f);   // 2 dL/da
-                        const float gdq = -G * r2s;                  // 2 dL/dq
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const float a_ = gda * e.dp[c], q_ = gdq * e.cr[c];
-                            gv[c] = fmaf(a_, e.dx, gv[c]);
-                            gv[3 + c] = fmaf(a_, e.dy, gv[3 + c]);
-                            gv[6 + c] += a_;
-                            gv[9 + c] = fmaf(q_, e.dx, gv[9 + c]);
-                            gv[12 + c] = fmaf(q_, e.dy, gv[12 + c]);
-                            gv[15 + c] += q_;
+                    for (int k = 0; k < P; ++k) {
+                        if (idx >= my_last[k]) continue;
+                        if (PIXTEST && pixel_outside(x0 + L::ox(k), y0 + L::oy(k), pr)) continue;
+                        PairEval e;
+                        pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
+                        if (COUNT) ++pairs;
+                        const bool clamped = e.tau > bp.tau_max;
+                        const float tau = fminf(e.tau, bp.tau_max);
+                        if (tau < bp.tau_skip) continue;
+                        any = true;
+                        const float e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
+                        const float alpha = __fsub_rn(1.0f, e2);
+                        const float Sb = S[k] - tau;
+                        const float Tb = ex2_approx(-kLog2eF * Sb);
+                        const float aT = alpha * Tb;
+                        gv[13] = fmaf(g0[k], aT, gv[13]);
+                        gv[14] = fmaf(g1[k], aT, gv[14]);
+                        gv[15] = fmaf(g2[k], aT, gv[15]);
+                        const float dtau = g0[k] * (r5.y * Tafter[k] - R0[k]) + g1[k] * (r5.z * Tafter[k] - R1[k]) +
+                                           g2[k] * (r5.w * Tafter[k] - R2[k]) + gTterm[k];
+                        R0[k] = fmaf(r5.y, aT, R0[k]);
+                        R1[k] = fmaf(r5.z, aT, R1[k]);
+                        R2[k] = fmaf(r5.w, aT, R2[k]);
+                        S[k] = Sb;
+                        Tafter[k] = Tb;
+                        if (!clamped) {
+                            const float G = dtau * tau;                  // dL / d ln(tau)
+                            const float r2s = e.rs * e.rs;
+                            const float ga = G * r2s * (e.m2 - 1.0f);    // 2 dL/da
+                            const float gq = -G * r2s;                   // 2 dL/dq
+                            const float xx = e.dx * e.dx, xy = e.dx * e.dy, yy = e.dy * e.dy;
+                            gv[0] = fmaf(ga, xx, gv[0]);
+                            gv[1] = fmaf(ga, xy, gv[1]);
+                            gv[2] = fmaf(ga, e.dx, gv[2]);
+                            gv[3] = fmaf(ga, yy, gv[3]);
+                            gv[4] = fmaf(ga, e.dy, gv[4]);
+                            gv[5] += ga;
+                            gv[6] = fmaf(gq, xx, gv[6]);
+                            gv[7] = fmaf(gq, xy, gv[7]);
+                            gv[8] = fmaf(gq, e.dx, gv[8]);
+                            gv[9] = fmaf(gq, yy, gv[9]);
+                            gv[10] = fmaf(gq, e.dy, gv[10]);
+                            gv[11] += gq;
+                            gv[12] += G;
                         }
-                        gv[18] += G;
                     }
                 }
-            }
-            if (__any_sync(0xffffffffu, any)) {
-                const float mine = warp_reduce_scatter<kGradUsed>(gv, lane);
-                if (lane < kGradUsed && mine != 0.0f) atomicAdd(&sacc[j * kGradUsed + lane], mine);
+                if (__any_sync(0xffffffffu, any)) {
+                    const float mine = warp_reduce_scatter<kGradUsed>(gv, lane);
+                    if (swrite && mine != 0.0f) atomicAdd(&sacc[j * kGradUsed + sidx], mine);
+                }
             }
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < (int)n * kGradUsed; k += kThreads) {
+        for (int k = threadIdx.x; k < n * kGradUsed; k += kThreads) {
             const int jj = k / kGradUsed, c = k - jj * kGradUsed;
             const float v = sacc[k];
             if (v != 0.0f) atomicAdd(&grad_acc[(size_t)sitem[jj] * kGradN + c], v);
@@ -237,14 +255,43 @@ __device__ __forceinline__ void cross_add(const float a[3], const float b[3], fl
     c[2] += a[0] * b[1] - a[1] * b[0];
 }
 
+// One thread per Gaussian: it visits the Gaussian's item in every view, sums the parameter
+// gradients in registers and writes them once (overwriting when `zero`, else adding), so no
+// atomics are needed.  A warp owns 32 consecutive Gaussians: their SH rows are read, and their
+// SH-gradient rows accumulated and written, through shared memory with coalesced instructions.
+constexpr int kChainWarps = 2;
+
 template <typename RT, typename ST>
-__global__ void __launch_bounds__(128)
-k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float *__restrict__ grad_acc,
+__global__ void __launch_bounds__(32 * kChainWarps, 6)
+k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float *__restrict__ grad_acc, int zero,
         float *__restrict__ dmu, float *__restrict__ dscale, float *__restrict__ dquat, float *__restrict__ dkappa,
         float *__restrict__ dsh) {
-    const long long n_items = (long long)g.n * n_views;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < n_items;
-         it += (long long)gridDim.x * blockDim.x) {
+    __shared__ float ssh[kChainWarps][32 * kRowStride];    // SH coefficients, as float
+    __shared__ float sdsh[kChainWarps][32 * kRowStride];   // SH gradient being accumulated
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1), K3 = 3 * K;
+    float *shrow = ssh[wi] + lane * kRowStride, *dshrow = sdsh[wi] + lane * kRowStride;
+    const long long n_chunks = ((long long)g.n + 31) / 32;
+    for (long long ch = (long long)blockIdx.x * kChainWarps + wi; ch < n_chunks; ch += (long long)gridDim.x * kChainWarps) {
+        const long long gbase = ch * 32;
+        const int nloc = (int)min(32LL, (long long)g.n - gbase);
+        const long long gi = gbase + lane;
+        if (g.sh != nullptr) warp_load_rows<ST>((const ST *)g.sh + gbase * K3, nloc, K3, ssh[wi], lane);
+        if (dsh != nullptr) {
+            if (zero) {
+                for (int k = 0; k < K3; ++k) dshrow[k] = 0.0f;
+            } else {
+                warp_load_rows<float>(dsh + gbase * K3, nloc, K3, sdsh[wi], lane);
+            }
+        }
+        __syncwarp();
+        if (lane < nloc) {
+        float mu[3], s[3], q[4], kap, Sig[9], Rq[9], qn[4], smax;
+        load_gauss<RT>(g, gi, mu, s, q, kap);
+        const bool valid = key_cov(mu, s, q, kap, Sig, Rq, qn, smax);
+        float am[3] = {0.0f, 0.0f, 0.0f}, asc[3] = {0.0f, 0.0f, 0.0f}, aq[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ak = 0.0f;
+        for (int v = 0; valid && v < n_views; ++v) {
+        const long long it = (long long)v * g.n + gi;
         const float4 *ga4 = (const float4 *)(grad_acc + it * kGradN);
         float ga[kGradN];
         bool any = false;
@@ -258,20 +305,22 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
             any |= (t.x != 0.0f) | (t.y != 0.0f) | (t.z != 0.0f) | (t.w != 0.0f);
         }
         if (!any) continue;
-        const int v = (int)(it / g.n);
-        const long long gi = it - (long long)v * g.n;
         const ViewInfo &V = views[v];
-        float mu[3], s[3], q[4], kap, Sig[9], Rq[9], qn[4], smax;
-        load_gauss<RT>(g, gi, mu, s, q, kap);
-        if (!key_cov(mu, s, q, kap, Sig, Rq, qn, smax)) continue;
         ItemGeom G;
         item_geom(V, mu, s, Rq, G);
-
+        // dA_j = sum_k A_k Ma[k][j], dC_j = sum_k C_k Mq[k][j] with the symmetric moments
+        // Ma = sum ga u u^T over u = (dx, dy, 1), stored as (xx, xy, x, yy, y, 1).
         float dA[9], dC[9];
+        {
+            const float Ma[9] = {ga[0], ga[1], ga[2], ga[1], ga[3], ga[4], ga[2], ga[4], ga[5]};
+            const float Mq[9] = {ga[6], ga[7], ga[8], ga[7], ga[9], ga[10], ga[8], ga[10], ga[11]};
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            dA[k] = ga[k];
-            dC[k] = ga[9 + k];
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    dA[3 * j + c] = G.A[c] * Ma[j] + G.A[3 + c] * Ma[3 + j] + G.A[6 + c] * Ma[6 + j];
+                    dC[3 * j + c] = G.Cc[c] * Mq[j] + G.Cc[3 + c] * Mq[3 + j] + G.Cc[6 + c] * Mq[6 + j];
+                }
         }
         // The record's C_k = o' x A_k with o' = -M mu_c.  Writing mu_c = t0 dc0 - v0 and
         // o' = Q2 - t0 A2 (t0 = camera depth of the mean, v0 and Q2 small), the two largest
@@ -280,13 +329,12 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
         //   dL/dM = sum_k (dA_k + dC_k x Q2) (x) b_k - t0 [(dC0 x A2) (x) b_0 + (dC1 x A2) (x) b_1]
         //           - t0 (A0 x dC0 + A1 x dC1) (x) dc0 + dop (x) v0,   b = (e0/fx, e1/fy, dc0),
         //   dL/dmu_c = -M^T dop,  dop = sum_k A_k x dC_k.
-        const float t0 = (float)G.muc[2];
+        const float t0 = G.muc[2].hi;
         float Q2[3], v0[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const double opd = -(G.M[3 * i] * G.muc[0] + G.M[3 * i + 1] * G.muc[1] + G.M[3 * i + 2] * G.muc[2]);
-            Q2[i] = (float)(opd + (double)t0 * (double)G.A[6 + i]);
-            v0[i] = (float)((double)t0 * (double)G.dc0[i] - G.muc[i]);
+            Q2[i] = df_float(df_fma(G.opx[i], t0, G.A[6 + i]));
+            v0[i] = df_float(df_fma(df_neg(G.muc[i]), t0, G.dc0[i]));
         }
         float dop[3] = {0.0f, 0.0f, 0.0f}, H[3] = {0.0f, 0.0f, 0.0f}, E[9] = {0.0f}, F[6] = {0.0f};
 #pragma unroll
@@ -343,25 +391,26 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
         const float dot = qn[0] * dqn[0] + qn[1] * dqn[1] + qn[2] * dqn[2] + qn[3] * dqn[3];
 
         // colour: rgb = max(sh . Y(dir) + 0.5, 0), dir = (mu - o)/|mu - o|
-        if (g.sh != nullptr && (ga[19] != 0.0f || ga[20] != 0.0f || ga[21] != 0.0f)) {
+        if (g.sh != nullptr && (ga[13] != 0.0f || ga[14] != 0.0f || ga[15] != 0.0f)) {
             float dir[3], len, rgb[3], raw[3];
             view_dir(V, mu, dir, len);
-            eval_colour<ST>(g, gi, dir, rgb, raw);
+            eval_colour_row(g.sh_degree, shrow, dir, rgb, raw);
             float Y[16], dY[16][3];
             sh_basis(g.sh_degree, dir[0], dir[1], dir[2], Y);
             sh_basis_grad(g.sh_degree, dir[0], dir[1], dir[2], dY);
-            const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
-            const ST *sh = (const ST *)g.sh + gi * K * 3;
-            float gd[3] = {0.0f, 0.0f, 0.0f};
-            for (int c = 0; c < 3; ++c) {
-                if (!(raw[c] > 0.0f)) continue;
-                const float gc = ga[19 + c];
-                for (int k = 0; k < K; ++k) {
-                    if (dsh) atomicAdd(&dsh[(gi * K + k) * 3 + c], gc * Y[k]);
-                    const float sc = gc * ld_f<ST>(sh, 3 * k + c);
+            float gc[3], gd[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gc[c] = raw[c] > 0.0f ? ga[13 + c] : 0.0f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if (k >= K) break;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float sc = gc[c] * shrow[3 * k + c];
                     gd[0] = fmaf(sc, dY[k][0], gd[0]);
                     gd[1] = fmaf(sc, dY[k][1], gd[1]);
                     gd[2] = fmaf(sc, dY[k][2], gd[2]);
+                    if (dsh != nullptr) dshrow[3 * k + c] += gc[c] * Y[k];
                 }
             }
             const float dd = gd[0] * dir[0] + gd[1] * dir[1] + gd[2] * dir[2];
@@ -371,51 +420,69 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            atomicAdd(&dmu[3 * gi + c], dm[c]);
-            atomicAdd(&dscale[3 * gi + c], dsc[c]);
+            am[c] += dm[c];
+            asc[c] += dsc[c];
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) atomicAdd(&dquat[4 * gi + c], (dqn[c] - qn[c] * dot) / qnorm);
-        atomicAdd(&dkappa[gi], ga[18] / kap);
+        for (int c = 0; c < 4; ++c) aq[c] += (dqn[c] - qn[c] * dot) / qnorm;
+        ak += ga[12] / kap;
+        }
+        if (zero) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dmu[3 * gi + c] = am[c];
+                dscale[3 * gi + c] = asc[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dquat[4 * gi + c] = aq[c];
+            dkappa[gi] = ak;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dmu[3 * gi + c] += am[c];
+                dscale[3 * gi + c] += asc[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dquat[4 * gi + c] += aq[c];
+            dkappa[gi] += ak;
+        }
+        }
+        __syncwarp();
+        if (dsh != nullptr) warp_store_rows(dsh + gbase * K3, nloc, K3, sdsh[wi], lane);
+        __syncwarp();   // the buffers are reused by the next chunk
     }
 }
 
 template <typename RT, typename ST>
-static cudaError_t launch_chain_t(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc,
+static cudaError_t launch_chain_t(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc, int zero,
                                   float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st) {
-    const long long n_items = (long long)g.n * n_views;
-    long long b = (n_items + 127) / 128;
-    if (b > 152 * 32) b = 152 * 32;
+    long long b = ((long long)g.n + 32 * kChainWarps - 1) / (32 * kChainWarps);
+    if (b > 152 * 64) b = 152 * 64;
     if (b < 1) b = 1;
-    k_chain<RT, ST><<<(unsigned)b, 128, 0, st>>>(g, views_d, n_views, grad_acc, dmu, dscale, dquat, dkappa, dsh);
+    k_chain<RT, ST><<<(unsigned)b, 32 * kChainWarps, 0, st>>>(g, views_d, n_views, grad_acc, zero, dmu, dscale, dquat, dkappa, dsh);
     return cudaGetLastError();
 }
 
-cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc, float *dmu,
-                         float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st, long long *launches) {
+cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc, int zero,
+                         float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st,
+                         long long *launches) {
+    if (g.n <= 0) return cudaSuccess;
     *launches += 1;
+#define VG_CHAIN(RT, ST) launch_chain_t<RT, ST>(g, views_d, n_views, grad_acc, zero, dmu, dscale, dquat, dkappa, dsh, st)
     if (g.rec_dtype == VG_F32) {
-        if (g.sh_dtype == VG_F16)
-            return launch_chain_t<float, __half>(g, views_d, n_views, grad_acc, dmu, dscale, dquat, dkappa, dsh, st);
-        if (g.sh_dtype == VG_BF16)
-            return launch_chain_t<float, __nv_bfloat16>(g, views_d, n_views, grad_acc, dmu, dscale, dquat, dkappa, dsh, st);
-        return launch_chain_t<float, float>(g, views_d, n_views, grad_acc, dmu, dscale, dquat, dkappa, dsh, st);
+        if (g.sh_dtype == VG_F16) return VG_CHAIN(float, __half);
+        if (g.sh_dtype == VG_BF16) return VG_CHAIN(float, __nv_bfloat16);
+        return VG_CHAIN(float, float);
     }
     if (g.rec_dtype == VG_BF16) {
-        if (g.sh_dtype == VG_F16)
-            return launch_chain_t<__nv_bfloat16, __half>(g, views_d, n_views, grad_acc, dmu, dscale, dquat, dkappa, dsh,
-                                                         st);
-        if (g.sh_dtype == VG_F32)
-            return launch_chain_t<__nv_bfloat16, float>(g, views_d, n_views, grad_acc, dmu, dscale, dquat, dkappa, dsh,
-                                                        st);
-        return launch_chain_t<__nv_bfloat16, __nv_bfloat16>(g, views_d, n_views, grad_acc, dmu, dscale, dquat, dkappa,
-                                                            dsh, st);
+        if (g.sh_dtype == VG_F16) return VG_CHAIN(__nv_bfloat16, __half);
+        if (g.sh_dtype == VG_F32) return VG_CHAIN(__nv_bfloat16, float);
+        return VG_CHAIN(__nv_bfloat16, __nv_bfloat16);
     }
-    if (g.sh_dtype == VG_F32)
-        return launch_chain_t<__half, float>(g, views_d, n_views, grad_acc, dmu, dscale, dquat, dkappa, dsh, st);
-    if (g.sh_dtype == VG_BF16)
-        return launch_chain_t<__half, __nv_bfloat16>(g, views_d, n_views, grad_acc, dmu, dscale, dquat, dkappa, dsh, st);
-    return launch_chain_t<__half, __half>(g, views_d, n_views, grad_acc, dmu, dscale, dquat, dkappa, dsh, st);
+    if (g.sh_dtype == VG_F32) return VG_CHAIN(__half, float);
+    if (g.sh_dtype == VG_BF16) return VG_CHAIN(__half, __nv_bfloat16);
+    return VG_CHAIN(__half, __half);
+#undef VG_CHAIN
 }
 
 }  // namespace vg

@@ -48,6 +48,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
     const float xf = (float)x0, yf = (float)y0;
     const WarpBox wb = warp_box<P>(x0, y0);
+    const int lane = threadIdx.x & 31;
     unsigned long long pairs = 0;
     for (uint32_t base = rg.x; base < rg.y; base += kChunk) {
         const uint32_t n = min((uint32_t)kChunk, rg.y - base);
@@ -59,31 +60,40 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             srect[threadIdx.x] = prect[item];
         }
         __syncthreads();
-        for (uint32_t j = 0; j < n && live; ++j) {
-            const short4 pr = srect[j];
-            if (box_misses(wb, pr)) continue;   // no pixel of this warp is in the footprint
-            const float4 *r = &srec[j * kRecF4];
-            const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
-            QuadBase qb;
-            quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
+        // the warp ballots the records whose footprint touches its pixels and visits only those
+        for (int w0 = 0; w0 < (int)n; w0 += 32) {
+            if (!__any_sync(0xffffffffu, live != 0)) break;
+            const int jl = w0 + lane;
+            unsigned m = __ballot_sync(0xffffffffu, jl < (int)n && !box_misses(wb, srect[jl]));
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int j = w0 + b;
+                const float4 *r = &srec[j * kRecF4];
+                const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
+                short4 pr;
+                if (PIXTEST) pr = srect[j];
+                QuadBase qb;
+                quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
 #pragma unroll
-            for (int k = 0; k < P; ++k) {
-                if (!(live & (1u << k))) continue;
-                if (PIXTEST && pixel_outside(x0 + L::ox(k), y0 + L::oy(k), pr)) continue;
-                PairEval e;
-                pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
-                if (COUNT) ++pairs;
-                const float tau = fminf(e.tau, bp.tau_max);
-                if (tau < bp.tau_skip) continue;
-                const float e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
-                const float w = __fmul_rn(__fsub_rn(1.0f, e2), T[k]);
-                c0[k] = fmaf(r5.y, w, c0[k]);
-                c1[k] = fmaf(r5.z, w, c1[k]);
-                c2[k] = fmaf(r5.w, w, c2[k]);
-                T[k] = __fmul_rn(T[k], e2);
-                S[k] = __fadd_rn(S[k], tau);
-                last[k] = base + j + 1;
-                if (T[k] < bp.T_stop) live &= ~(1u << k);
+                for (int k = 0; k < P; ++k) {
+                    if (!(live & (1u << k))) continue;
+                    if (PIXTEST && pixel_outside(x0 + L::ox(k), y0 + L::oy(k), pr)) continue;
+                    PairEval e;
+                    pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
+                    if (COUNT) ++pairs;
+                    const float tau = fminf(e.tau, bp.tau_max);
+                    if (tau < bp.tau_skip) continue;
+                    const float e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
+                    const float w = __fmul_rn(__fsub_rn(1.0f, e2), T[k]);
+                    c0[k] = fmaf(r5.y, w, c0[k]);
+                    c1[k] = fmaf(r5.z, w, c1[k]);
+                    c2[k] = fmaf(r5.w, w, c2[k]);
+                    T[k] = __fmul_rn(T[k], e2);
+                    S[k] = __fadd_rn(S[k], tau);
+                    last[k] = base + j + 1;
+                    if (T[k] < bp.T_stop) live &= ~(1u << k);
+                }
             }
         }
         if (__syncthreads_count(live != 0) == 0) break;
@@ -104,7 +114,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-        if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(pair_count, pairs);
+        if (lane == 0 && pairs) atomicAdd(pair_count, pairs);
     }
 }
 

@@ -162,6 +162,7 @@ k_tomo_fwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
     const int x0 = tx * kTile + 2 * (threadIdx.x & 7), y0 = ty * kTile + 2 * (threadIdx.x >> 3);
     const float xf = (float)x0, yf = (float)y0;
     const WarpBox wb = warp_box<4>(x0, y0);
+    const int lane = threadIdx.x & 31;
     const uint2 rg = ranges[tile];
     float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (uint32_t base = rg.x; base < rg.y; base += kTomoChunk) {
@@ -175,31 +176,46 @@ k_tomo_fwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
             srect[threadIdx.x] = prect[item];
         }
         __syncthreads();
-        for (uint32_t j = 0; j < n; ++j) {
-            const short4 pr = srect[j];
-            if (box_misses(wb, pr)) continue;   // the footprint misses every pixel of this warp
-            const float4 r0 = srec[2 * j], r1 = srec[2 * j + 1];
-            const float dx = xf - r0.x, dy = yf - r0.y;
-            const float ya0 = fmaf(r0.z, dx, r1.x * dy), ya1 = fmaf(r0.w, dx, r1.y * dy);   // pixel (0,0)
-            const float yb0 = ya0 + r0.z, yb1 = ya1 + r0.w;                                   // (1,0)
-            const float yc0 = ya0 + r1.x, yc1 = ya1 + r1.y;                                   // (0,1)
-            const float yd0 = yb0 + r1.x, yd1 = yb1 + r1.y;                                   // (1,1)
-            const float ta = ex2_approx(fmaf(fmaf(ya0, ya0, ya1 * ya1), -kHalfLog2e, r1.z));
-            const float tb = ex2_approx(fmaf(fmaf(yb0, yb0, yb1 * yb1), -kHalfLog2e, r1.z));
-            const float tc = ex2_approx(fmaf(fmaf(yc0, yc0, yc1 * yc1), -kHalfLog2e, r1.z));
-            const float td = ex2_approx(fmaf(fmaf(yd0, yd0, yd1 * yd1), -kHalfLog2e, r1.z));
-            if (box_inside(wb, pr)) {            // warp-uniform fast path: every pixel is inside
-                sum[0] += ta;
-                sum[1] += tb;
-                sum[2] += tc;
-                sum[3] += td;
-            } else {                             // footprint rectangle, separable in x and y
-                const bool xa = x0 >= pr.x && x0 <= pr.z, xb = x0 + 1 >= pr.x && x0 + 1 <= pr.z;
-                const bool ya = y0 >= pr.y && y0 <= pr.w, yb = y0 + 1 >= pr.y && y0 + 1 <= pr.w;
-                sum[0] += (xa && ya) ? ta : 0.0f;
-                sum[1] += (xb && ya) ? tb : 0.0f;
-                sum[2] += (xa && yb) ? tc : 0.0f;
-                sum[3] += (xb && yb) ? td : 0.0f;
+        // the warp ballots the records whose footprint touches its pixels and whether it lies
+        // inside the footprint; it visits only those records
+        for (int w0 = 0; w0 < (int)n; w0 += 32) {
+            const int jl = w0 + lane;
+            bool need = false, full = false;
+            if (jl < (int)n) {
+                const short4 pr = srect[jl];
+                need = !box_misses(wb, pr);
+                full = box_inside(wb, pr);
+            }
+            unsigned m = __ballot_sync(0xffffffffu, need);
+            const unsigned mf = __ballot_sync(0xffffffffu, full);
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int j = w0 + b;
+                const float4 r0 = srec[2 * j], r1 = srec[2 * j + 1];
+                const float dx = xf - r0.x, dy = yf - r0.y;
+                const float ya0 = fmaf(r0.z, dx, r1.x * dy), ya1 = fmaf(r0.w, dx, r1.y * dy);   // pixel (0,0)
+                const float yb0 = ya0 + r0.z, yb1 = ya1 + r0.w;                                   // (1,0)
+                const float yc0 = ya0 + r1.x, yc1 = ya1 + r1.y;                                   // (0,1)
+                const float yd0 = yb0 + r1.x, yd1 = yb1 + r1.y;                                   // (1,1)
+                const float ta = ex2_approx(fmaf(fmaf(ya0, ya0, ya1 * ya1), -kHalfLog2e, r1.z));
+                const float tb = ex2_approx(fmaf(fmaf(yb0, yb0, yb1 * yb1), -kHalfLog2e, r1.z));
+                const float tc = ex2_approx(fmaf(fmaf(yc0, yc0, yc1 * yc1), -kHalfLog2e, r1.z));
+                const float td = ex2_approx(fmaf(fmaf(yd0, yd0, yd1 * yd1), -kHalfLog2e, r1.z));
+                if ((mf >> b) & 1u) {                // every pixel of the warp is inside
+                    sum[0] += ta;
+                    sum[1] += tb;
+                    sum[2] += tc;
+                    sum[3] += td;
+                } else {                             // footprint rectangle, separable in x and y
+                    const short4 pr = srect[j];
+                    const bool xa = x0 >= pr.x && x0 <= pr.z, xb = x0 + 1 >= pr.x && x0 + 1 <= pr.z;
+                    const bool ya = y0 >= pr.y && y0 <= pr.w, yb = y0 + 1 >= pr.y && y0 + 1 <= pr.w;
+                    sum[0] += (xa && ya) ? ta : 0.0f;
+                    sum[1] += (xb && ya) ? tb : 0.0f;
+                    sum[2] += (xa && yb) ? tc : 0.0f;
+                    sum[3] += (xb && yb) ? td : 0.0f;
+                }
             }
         }
     }
@@ -228,7 +244,7 @@ __global__ void __launch_bounds__(kQuadThreads, 12)
 k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, int det_w, int det_h,
            const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, const short4 *__restrict__ prect,
            const float *__restrict__ proj, const float *__restrict__ dL_dproj, float *__restrict__ grad_acc) {
-    constexpr int NV = 7;
+    constexpr int NV = 7, NP = 8;   // partials used, and padded to a power of two
     __shared__ float4 srec[kTomoChunk * 2];
     __shared__ short4 srect[kTomoChunk];
     __shared__ float sacc[kTomoChunk * NV];
@@ -239,6 +255,8 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
     const int x0 = tx * kTile + 2 * (threadIdx.x & 7), y0 = ty * kTile + 2 * (threadIdx.x >> 3);
     const float xf = (float)x0, yf = (float)y0;
     const int lane = threadIdx.x & 31;
+    const int sidx = scatter_index<NP>(lane);
+    const bool swrite = scatter_writer<NP>(lane);
     float gtau[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -262,40 +280,47 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
         }
         for (int k = threadIdx.x; k < kTomoChunk * NV; k += kQuadThreads) sacc[k] = 0.0f;
         __syncthreads();
-        for (uint32_t j = 0; j < n; ++j) {
-            const short4 pr = srect[j];
-            if (box_misses(wb, pr)) continue;
-            const float4 r0 = srec[2 * j], r1 = srec[2 * j + 1];
-            float v[32];
+        for (int w0 = 0; w0 < (int)n; w0 += 32) {
+            const int jl = w0 + lane;
+            const bool need = jl < (int)n && !box_misses(wb, srect[jl]);
+            unsigned m = __ballot_sync(0xffffffffu, need);
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int j = w0 + b;
+                const short4 pr = srect[j];
+                const float4 r0 = srec[2 * j], r1 = srec[2 * j + 1];
+                float v[NP];
 #pragma unroll
-            for (int k = 0; k < 32; ++k) v[k] = 0.0f;
-            const float dx0 = xf - r0.x, dy0 = yf - r0.y;
-            const float ya0 = fmaf(r0.z, dx0, r1.x * dy0), ya1 = fmaf(r0.w, dx0, r1.y * dy0);
-            const float yb0 = ya0 + r0.z, yb1 = ya1 + r0.w;
-            const float q0[4] = {ya0, yb0, ya0 + r1.x, yb0 + r1.x}, q1[4] = {ya1, yb1, ya1 + r1.y, yb1 + r1.y};
-            // footprint rectangle, separable in x and y; all-true when the warp lies inside it
-            const bool full = box_inside(wb, pr);
-            const bool xa = full || (x0 >= pr.x && x0 <= pr.z), xb = full || (x0 + 1 >= pr.x && x0 + 1 <= pr.z);
-            const bool ya = full || (y0 >= pr.y && y0 <= pr.w), yb = full || (y0 + 1 >= pr.y && y0 + 1 <= pr.w);
+                for (int k = 0; k < NP; ++k) v[k] = 0.0f;
+                const float dx0 = xf - r0.x, dy0 = yf - r0.y;
+                const float ya0 = fmaf(r0.z, dx0, r1.x * dy0), ya1 = fmaf(r0.w, dx0, r1.y * dy0);
+                const float yb0 = ya0 + r0.z, yb1 = ya1 + r0.w;
+                const float q0[4] = {ya0, yb0, ya0 + r1.x, yb0 + r1.x}, q1[4] = {ya1, yb1, ya1 + r1.y, yb1 + r1.y};
+                // footprint rectangle, separable in x and y; all-true when the warp lies inside it
+                const bool full = box_inside(wb, pr);
+                const bool xa = full || (x0 >= pr.x && x0 <= pr.z), xb = full || (x0 + 1 >= pr.x && x0 + 1 <= pr.z);
+                const bool ya = full || (y0 >= pr.y && y0 <= pr.w), yb = full || (y0 + 1 >= pr.y && y0 + 1 <= pr.w);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float dx = (k & 1) ? dx0 + 1.0f : dx0, dy = (k & 2) ? dy0 + 1.0f : dy0;
-                const float y0v = q0[k], y1v = q1[k];
-                const float m2 = fmaf(y0v, y0v, y1v * y1v);
-                const float tau = ex2_approx(fmaf(m2, -kHalfLog2e, r1.z));
-                const bool in = ((k & 1) ? xb : xa) && ((k & 2) ? yb : ya);
-                const float G = in ? gtau[k] * tau : 0.0f;      // dL / d ln(tau)
-                const float gy0 = -G * y0v, gy1 = -G * y1v;
-                v[0] = fmaf(gy0, dx, v[0]);
-                v[1] = fmaf(gy1, dx, v[1]);
-                v[2] = fmaf(gy0, dy, v[2]);
-                v[3] = fmaf(gy1, dy, v[3]);
-                v[4] += gy0;
-                v[5] += gy1;
-                v[6] += G;
+                for (int k = 0; k < 4; ++k) {
+                    const float dx = (k & 1) ? dx0 + 1.0f : dx0, dy = (k & 2) ? dy0 + 1.0f : dy0;
+                    const float y0v = q0[k], y1v = q1[k];
+                    const float m2 = fmaf(y0v, y0v, y1v * y1v);
+                    const float tau = ex2_approx(fmaf(m2, -kHalfLog2e, r1.z));
+                    const bool in = ((k & 1) ? xb : xa) && ((k & 2) ? yb : ya);
+                    const float G = in ? gtau[k] * tau : 0.0f;      // dL / d ln(tau)
+                    const float gy0 = -G * y0v, gy1 = -G * y1v;
+                    v[0] = fmaf(gy0, dx, v[0]);
+                    v[1] = fmaf(gy1, dx, v[1]);
+                    v[2] = fmaf(gy0, dy, v[2]);
+                    v[3] = fmaf(gy1, dy, v[3]);
+                    v[4] += gy0;
+                    v[5] += gy1;
+                    v[6] += G;
+                }
+                const float mine = warp_reduce_scatter<NP>(v, lane);
+                if (swrite && sidx < NV && mine != 0.0f) atomicAdd(&sacc[j * NV + sidx], mine);
             }
-            const float mine = warp_reduce_scatter<NV>(v, lane);
-            if (lane < NV && mine != 0.0f) atomicAdd(&sacc[j * NV + lane], mine);
         }
         __syncthreads();
         for (int k = threadIdx.x; k < (int)n * NV; k += kQuadThreads) {

@@ -14,7 +14,7 @@ namespace vg {
 constexpr int kTile = 16;                 // square pixel tiles
 constexpr int kTilePix = kTile * kTile;   // one thread per pixel in the blend kernels
 constexpr int kRecF4 = 6;                 // blend record: 6 x float4 = 96 bytes
-constexpr int kGradN = 24;                // per-item gradient accumulator (22 used)
+constexpr int kGradN = 16;                // per-item gradient accumulator (moments, dln kappa, colour)
 constexpr int kTomoRecF4 = 2;             // tomography record: 2 x float4
 
 // Per-view constants, device side.
@@ -119,7 +119,7 @@ cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *
                               uint32_t *keys_tmp, uint32_t *vals_tmp, uint32_t *hist, uint32_t *scan_tmp,
                               uint32_t **order, cudaStream_t st, long long *launches);
 
-cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc,
+cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc, int zero,
                          float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st,
                          long long *launches);
 

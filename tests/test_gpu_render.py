@@ -162,3 +162,90 @@ def test_backward_random_weights(gpu_lib, seed):
     gg = run_backward(vg, ws, g, wr, wT)
     ref = oracle.render_grad(scene, cams, o, oracle.lists(scene, cams, o), wr, wT)
     check_grads(gg, ref, scene, GRAD_TOL)
+
+
+def _grads_like(g, fill):
+    import torch
+    dev = torch.device("cuda:0")
+    return dict(mu=torch.full((g.n, 3), fill, device=dev), scale=torch.full((g.n, 3), fill, device=dev),
+                quat=torch.full((g.n, 4), fill, device=dev), kappa=torch.full((g.n,), fill, device=dev),
+                sh=torch.full(tuple(g.sh.shape), fill, device=dev))
+
+
+def _bwd_into(ws, rgb, wr, wT, grads):
+    import torch
+    dev = torch.device("cuda:0")
+    gr = torch.as_tensor(np.ascontiguousarray(wr, dtype=np.float32)).to(dev)
+    gt = torch.as_tensor(np.ascontiguousarray(wT, dtype=np.float32)).to(dev)
+    ws.render_bwd(gr, gt, grads["mu"], grads["scale"], grads["quat"], grads["kappa"], grads["sh"])
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
+
+
+def test_backward_grad_zero_overwrites_and_plain_accumulates(gpu_lib):
+    """VG_FLAG_GRAD_ZERO overwrites NaN-filled outputs; without it a second backward adds."""
+    vg = gpu_lib
+    scene = synth.uniform_scene(237, 515, log_scale=(-3.5, -2.2), sh_degree=2, sh_std=0.25, flatten_frac=0.1,
+                                extent=0.9)
+    cams = synth.small_views(2, 0, [(40, 24), (37, 29)])
+    o = dict(oracle.EXACT, bg=(0.2, 0.4, 0.1))
+    rng = np.random.default_rng(11)
+    ws, g, rgb, T = run_forward(vg, scene, cams, o, flags=vg.FLAG_GRAD_ZERO)
+    wr = rng.normal(size=(rgb.shape[0], 3))
+    wT = rng.normal(size=rgb.shape[0])
+    ref = oracle.render_grad(scene, cams, o, oracle.lists(scene, cams, o), wr, wT)
+    gg = _bwd_into(ws, rgb, wr, wT, _grads_like(g, float("nan")))
+    assert all(np.isfinite(v).all() for v in gg.values())
+    check_grads(gg, ref, scene, GRAD_TOL)
+    ws2, g2, rgb2, _ = run_forward(vg, scene, cams, o, flags=0)
+    grads = _grads_like(g2, 0.0)
+    _bwd_into(ws2, rgb2, wr, wT, grads)
+    twice = _bwd_into(ws2, rgb2, wr, wT, grads)
+    check_grads({k: v / 2.0 for k, v in twice.items()}, ref, scene, GRAD_TOL)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_sh_degrees(gpu_lib, deg):
+    """Forward and backward for SH degrees 0-2 (row widths 3, 12, 27) on a Gaussian count
+    that leaves a partial warp of rows."""
+    vg = gpu_lib
+    scene = synth.uniform_scene(301, 600 + deg, log_scale=(-3.5, -2.2), sh_degree=deg, sh_std=0.3,
+                                flatten_frac=0.1, extent=0.9)
+    cams = synth.small_views(2, 1, [(48, 32), (31, 45)])
+    o = dict(oracle.EXACT, bg=(0.3, 0.2, 0.1))
+    ws, g, rgb, T = run_forward(vg, scene, cams, o)
+    ref_rgb, ref_T, _ = oracle.render(scene, cams, o)
+    assert np.max(np.abs(rgb - flat(ref_rgb))) < IMG_TOL
+    rng = np.random.default_rng(deg)
+    wr = rng.normal(size=(rgb.shape[0], 3))
+    wT = rng.normal(size=rgb.shape[0])
+    gg = run_backward(vg, ws, g, wr, wT)
+    ref = oracle.render_grad(scene, cams, o, oracle.lists(scene, cams, o), wr, wT)
+    check_grads(gg, ref, scene, GRAD_TOL)
+
+
+@pytest.mark.parametrize("rec_dtype,sh_dtype", [("bf16", "bf16"), ("f16", "f16"), ("f32", "bf16"), ("bf16", "f32")])
+def test_reduced_precision_storage(gpu_lib, rec_dtype, sh_dtype):
+    """Parameters stored as bf16 / f16 are widened to FP32 on load: the result equals the
+    oracle's on the same (rounded) parameter values."""
+    import torch
+    vg = gpu_lib
+    dts = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+    scene, cams = _multi_view_scene()
+    rnd = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(dts[dt]).float().numpy()
+    sq = synth.Scene(rnd(scene.mu, rec_dtype), rnd(scene.scale, rec_dtype), rnd(scene.quat, rec_dtype),
+                     rnd(scene.kappa, rec_dtype), rnd(scene.sh, sh_dtype), scene.sh_degree)
+    g = dev_scene(vg, sq, rec_dtype=dts[rec_dtype], sh_dtype=dts[sh_dtype])
+    o = dict(oracle.EXACT, bg=(0.3, 0.2, 0.1))
+    ws, g, rgb, T = run_forward(vg, sq, cams, o, g=g)
+    ref_rgb, _, _ = oracle.render(sq, cams, o)
+    assert np.max(np.abs(rgb - flat(ref_rgb))) < IMG_TOL
+    depth, rect = ws.read_keys()
+    od, orc = oracle.keys(sq, cams, o)
+    assert np.array_equal(depth, od.reshape(-1)) and np.array_equal(rect, orc.reshape(-1, 4))
+    rng = np.random.default_rng(5)
+    wr = rng.normal(size=(rgb.shape[0], 3))
+    wT = rng.normal(size=rgb.shape[0])
+    gg = run_backward(vg, ws, g, wr, wT)
+    ref = oracle.render_grad(sq, cams, o, oracle.lists(sq, cams, o), wr, wT)
+    check_grads(gg, ref, sq, GRAD_TOL)
