@@ -127,6 +127,8 @@ typedef struct {
     int64_t launches;         /* kernels launched by this workspace since creation          */
     int64_t device_bytes;     /* device memory held by the workspace                        */
     int64_t n_pairs_bwd;      /* pairs replayed by the last counted render_bwd              */
+    int64_t n_blend;          /* pairs of the last counted render_fwd with tau >= tau_skip   */
+    int64_t n_blend_bwd;      /* pairs of the last counted render_bwd with tau >= tau_skip   */
 } vg_stats;
 
 /* Per-stage device time recorded with CUDA events on the launching stream while

@@ -66,7 +66,7 @@ class _StageTime(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("n_items", "n_visible", "n_culled", "n_instances", "n_tiles",
                                               "n_pixels", "instance_capacity", "n_pairs", "launches",
-                                              "device_bytes", "n_pairs_bwd")]
+                                              "device_bytes", "n_pairs_bwd", "n_blend", "n_blend_bwd")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

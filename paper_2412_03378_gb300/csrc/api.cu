@@ -52,12 +52,13 @@ struct vg_workspace {
     DBuf<uint32_t> nlast;
     DBuf<float> grad;
     DBuf<uint32_t> hist, scan_tmp;
-    DBuf<unsigned long long> counters;   // [0] visible items, [1] evaluated pairs
+    DBuf<unsigned long long> counters;   // [0] visible items; fwd [1] evaluated, [2] blended pairs; bwd [3], [4];
+                                         // [6] instance total of the last scan, [7] look-back timeout flag
     DBuf<float> tomo_cs;
-    DBuf<uint32_t> tord_k[2], tord_v[2];  // tile-order sort buffers
+    DBuf<uint32_t> tord;                  // tile order buffer
     uint32_t *tile_order = nullptr;       // longest-first tile order of the last bin_sort
     int ppt_fwd = 2, ppt_bwd = 1;         // pixels per thread of the blend kernels
-    uint32_t *h_total = nullptr;         // pinned
+    uint32_t *h_total = nullptr;         // pinned: [0..1] instance total (u64), [2] look-back timeout flag
 
     // per-stage event timing (vg_profile_enable)
     bool prof_on = false;
@@ -74,7 +75,7 @@ namespace {
 // Measured on the 1M-Gaussian 1280x832 workload (GB300, footprint culling on): forward
 // 0.53 / 0.49 / 0.74 ms and backward 1.32 / 1.16 / 1.19 ms for 1 / 2 / 4 pixels per thread.
 constexpr int kDefaultPixelsFwd = 2;
-constexpr int kDefaultPixelsBwd = 2;
+constexpr int kDefaultPixelsBwd = 1;
 
 enum Stage { ST_PRE, ST_DEPTH, ST_SCAN, ST_DUP, ST_TILE, ST_RANGES, ST_FWD, ST_BWD, ST_CHAIN, ST_LOSS, ST_TFWD,
              ST_TBWD, ST_COUNT };
@@ -250,10 +251,7 @@ vg_status vg_workspace_destroy(vg_workspace *ws) {
     release(ws->scan_tmp);
     release(ws->counters);
     release(ws->tomo_cs);
-    for (int k = 0; k < 2; ++k) {
-        release(ws->tord_k[k]);
-        release(ws->tord_v[k]);
-    }
+    release(ws->tord);
     if (ws->h_total) cudaFreeHost(ws->h_total);
     for (auto &r : ws->prof) {
         cudaEventDestroy(r.a);
@@ -279,9 +277,24 @@ static vg_status reserve_items(vg_workspace *ws, long long n_items) {
 }
 
 static vg_status reserve_sort_scratch(vg_workspace *ws, long long n) {
-    VG_TRY(ensure(ws, ws->hist, radix_hist_words(n), "radix histogram"));
-    const long long scan_n = std::max<long long>(n, (long long)radix_hist_words(n));
-    VG_TRY(ensure(ws, ws->scan_tmp, scan_tmp_words(scan_n), "scan scratch"));
+    VG_TRY(ensure(ws, ws->hist, radix_scratch_words(n, 32), "radix sort scratch"));
+    VG_TRY(ensure(ws, ws->scan_tmp, scan_tmp_words(n), "scan scratch"));
+    return VG_OK;
+}
+
+static unsigned long long *total64_ptr(vg_workspace *ws) { return ws->counters.p + 6; }
+static uint32_t *lookback_err_ptr(vg_workspace *ws) { return (uint32_t *)(ws->counters.p + 7); }
+
+// Reads the instance total of the last scan and the look-back timeout flag (synchronises st).
+static vg_status read_total(vg_workspace *ws, cudaStream_t st, long long *total) {
+    VG_CUDA(ws, cudaMemcpyAsync(ws->h_total, ws->counters.p + 6, 2 * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, st));
+    VG_CUDA(ws, cudaStreamSynchronize(st));
+    if (ws->h_total[2] != 0) {
+        cudaMemsetAsync(lookback_err_ptr(ws), 0, sizeof(uint32_t), st);
+        return fail(ws, VG_ERR_CUDA, "a look-back wait of the scan or sort timed out");
+    }
+    *total = (long long)(((unsigned long long)ws->h_total[1] << 32) | ws->h_total[0]);
     return VG_OK;
 }
 
@@ -414,25 +427,24 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
     // 1. items by depth key (stable: ties keep index order)
     {
         ProfScope ps(ws, ST_DEPTH, st);
-        VG_CUDA(ws, cudaMemcpyAsync(ws->skey[0].p, ws->depth.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice,
-                                    st));
-        VG_CUDA(ws, launch_iota(ws->sval[0].p, n, st, &ws->launches));
         uint32_t *ksorted = nullptr;
-        VG_CUDA(ws, launch_radix_sort(ws->skey[0].p, ws->sval[0].p, ws->skey[1].p, ws->sval[1].p, n, 32, ws->hist.p,
-                                      ws->scan_tmp.p, &ksorted, &ws->perm, st, &ws->launches));
+        VG_CUDA(ws, launch_radix_sort(ws->depth.p, nullptr, ws->skey[0].p, ws->sval[0].p, ws->skey[1].p,
+                                      ws->sval[1].p, n, 32, ws->hist.p, lookback_err_ptr(ws), &ksorted, &ws->perm, st,
+                                      &ws->launches));
     }
     // 2. instance offsets in depth order
     {
         ProfScope ps(ws, ST_SCAN, st);
-        VG_CUDA(ws, launch_scan_gather(ws->count.p, ws->perm, ws->offsets.p, n, ws->scan_tmp.p, st, &ws->launches));
+        VG_CUDA(ws, launch_scan_gather(ws->count.p, ws->perm, ws->offsets.p, n, ws->scan_tmp.p, total64_ptr(ws),
+                                       lookback_err_ptr(ws), st, &ws->launches));
     }
     long long total;
     if (ws->opts.flags & VG_FLAG_FIXED_CAPACITY) {
         return fail(ws, VG_ERR_UNSUPPORTED, "fixed-capacity binning is not implemented in this build");
     } else {
-        VG_CUDA(ws, cudaMemcpyAsync(ws->h_total, ws->offsets.p + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        VG_CUDA(ws, cudaStreamSynchronize(st));
-        total = (long long)ws->h_total[0];
+        VG_TRY(read_total(ws, st, &total));
+        if (total > (long long)(1u << 30) - 1)
+            return fail(ws, VG_ERR_INVALID_ARG, "more than 2^30 - 1 (tile, Gaussian) instances");
         VG_TRY(reserve_instances(ws, total));
     }
     ws->n_inst = total;
@@ -444,25 +456,17 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
     }
     {
         ProfScope ps(ws, ST_TILE, st);
-        VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, total,
-                                      bits_for(ws->n_tiles), ws->hist.p, ws->scan_tmp.p, &ws->inst_key,
-                                      &ws->inst_item, st, &ws->launches));
+        VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, ws->ikey[0].p,
+                                      ws->ival[0].p, total, bits_for(ws->n_tiles), ws->hist.p, lookback_err_ptr(ws),
+                                      &ws->inst_key, &ws->inst_item, st, &ws->launches));
     }
     VG_TRY(ensure(ws, ws->ranges, (size_t)ws->n_tiles, "tile ranges"));
+    VG_TRY(ensure(ws, ws->tord, (size_t)ws->n_tiles, "tile order"));
     {
         ProfScope ps(ws, ST_RANGES, st);
         VG_CUDA(ws, launch_ranges(ws->inst_key, total, ws->ranges.p, ws->n_tiles, st, &ws->launches));
-    }
-    VG_TRY(reserve_sort_scratch(ws, ws->n_tiles));
-    for (int k = 0; k < 2; ++k) {
-        VG_TRY(ensure(ws, ws->tord_k[k], (size_t)ws->n_tiles, "tile order"));
-        VG_TRY(ensure(ws, ws->tord_v[k], (size_t)ws->n_tiles, "tile order"));
-    }
-    {
-        ProfScope ps(ws, ST_RANGES, st);
-        VG_CUDA(ws, launch_tile_order(ws->ranges.p, ws->n_tiles, ws->tord_k[0].p, ws->tord_v[0].p, ws->tord_k[1].p,
-                                      ws->tord_v[1].p, ws->hist.p, ws->scan_tmp.p, &ws->tile_order, st,
-                                      &ws->launches));
+        VG_CUDA(ws, launch_tile_order(ws->ranges.p, ws->n_tiles, ws->tord.p, st, &ws->launches));
+        ws->tile_order = ws->tord.p;
     }
     ws->stage = 2;
     return VG_OK;
@@ -479,7 +483,7 @@ vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stre
     unsigned long long *pc = nullptr;
     if (ws->opts.flags & VG_FLAG_COUNT_PAIRS) {
         pc = ws->counters.p + 1;
-        VG_CUDA(ws, cudaMemsetAsync(pc, 0, sizeof(unsigned long long), st));
+        VG_CUDA(ws, cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), st));
     }
     {
         ProfScope ps(ws, ST_FWD, st);
@@ -503,8 +507,8 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
         VG_CUDA(ws, cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st));
     unsigned long long *pc = nullptr;
     if (ws->opts.flags & VG_FLAG_COUNT_PAIRS) {
-        pc = ws->counters.p + 2;
-        VG_CUDA(ws, cudaMemsetAsync(pc, 0, sizeof(unsigned long long), st));
+        pc = ws->counters.p + 3;
+        VG_CUDA(ws, cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), st));
     }
     {
         ProfScope ps(ws, ST_BWD, st);
@@ -645,11 +649,13 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
         }
         {
             ProfScope ps(ws, ST_SCAN, st);
-            VG_CUDA(ws, launch_scan(ws->count.p, ws->offsets.p, items, ws->scan_tmp.p, st, &ws->launches));
+            VG_CUDA(ws, launch_scan_gather(ws->count.p, nullptr, ws->offsets.p, items, ws->scan_tmp.p,
+                                           total64_ptr(ws), lookback_err_ptr(ws), st, &ws->launches));
         }
-        VG_CUDA(ws, cudaMemcpyAsync(ws->h_total, ws->offsets.p + items, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        VG_CUDA(ws, cudaStreamSynchronize(st));
-        const long long total = (long long)ws->h_total[0];
+        long long total = 0;
+        VG_TRY(read_total(ws, st, &total));
+        if (total > (long long)(1u << 30) - 1)
+            return fail(ws, VG_ERR_INVALID_ARG, "more than 2^30 - 1 (tile, Gaussian) instances in an angle batch");
         VG_TRY(reserve_instances(ws, total));
         {
             ProfScope ps(ws, ST_DUP, st);
@@ -658,9 +664,9 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
         }
         {
             ProfScope ps(ws, ST_TILE, st);
-            VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, total,
-                                          bits_for(n_tiles), ws->hist.p, ws->scan_tmp.p, &ws->inst_key,
-                                          &ws->inst_item, st, &ws->launches));
+            VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, ws->ikey[0].p,
+                                          ws->ival[0].p, total, bits_for(n_tiles), ws->hist.p, lookback_err_ptr(ws),
+                                          &ws->inst_key, &ws->inst_item, st, &ws->launches));
         }
         VG_TRY(ensure(ws, ws->ranges, (size_t)n_tiles, "tile ranges"));
         {
@@ -707,7 +713,7 @@ vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n
 vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream) {
     if (!ws || !out) return VG_ERR_INVALID_ARG;
     VG_CUDA(ws, cudaStreamSynchronize((cudaStream_t)stream));
-    unsigned long long c[3] = {0, 0, 0};
+    unsigned long long c[5] = {0, 0, 0, 0, 0};
     VG_CUDA(ws, cudaMemcpy(c, ws->counters.p, sizeof(c), cudaMemcpyDeviceToHost));
     memset(out, 0, sizeof(*out));
     out->n_items = ws->n_items;
@@ -717,7 +723,9 @@ vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream) {
     out->n_pixels = ws->n_pixels;
     out->instance_capacity = ws->capacity;
     out->n_pairs = (int64_t)c[1];
-    out->n_pairs_bwd = (int64_t)c[2];
+    out->n_blend = (int64_t)c[2];
+    out->n_pairs_bwd = (int64_t)c[3];
+    out->n_blend_bwd = (int64_t)c[4];
     out->launches = ws->launches;
     size_t bytes = ws->views.n * sizeof(ViewInfo) + ws->tile_view.n * 4 + ws->rec.n * 16 + ws->depth.n * 4 +
                    ws->count.n * 4 + ws->offsets.n * 4 + ws->rect.n * 8 + ws->ranges.n * 8 + ws->S_fin.n * 4 +

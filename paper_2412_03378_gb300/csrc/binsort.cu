@@ -1,5 +1,5 @@
-// Tile binning and sorting: device-wide exclusive scan, a stable LSD radix sort of
-// (uint32 key, uint32 value) pairs, instance duplication and per-tile ranges.
+// Tile binning and sorting: single-pass exclusive scan, a stable single-pass-per-digit LSD
+// radix sort of (uint32 key, uint32 value) pairs, instance duplication and per-tile ranges.
 //
 // The per-tile front-to-back order (tile, depth, Gaussian index) is built in two stable
 // steps: items are sorted by depth key (ties keep index order), their instances are
@@ -9,257 +9,352 @@
 
 namespace vg {
 
+// ---------------------------------------------------------------------------- look-back
+// Single-pass prefix sums with decoupled look-back (Merrill, Garland: "Single-pass Parallel
+// Prefix Scan with Decoupled Look-back", NVIDIA TR 2016): a CTA takes the next tile index
+// from an atomic counter, publishes its tile's aggregate, then walks back over the tiles before
+// it, adding aggregates until it meets an inclusive prefix, and publishes its own.  A CTA only
+// ever waits for tiles handed out before its own, which belong to CTAs already running, so the
+// walk always ends; the spin on each status word is bounded anyway and a timeout sets a sticky
+// error flag that the host reads at its next synchronisation.
+constexpr int kSpinLimit = 1 << 21;
+
+// 32-bit status: 2 flag bits + 30-bit count (radix sort, counts < 2^30)
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kCountMask = (1u << 30) - 1u;
+// 64-bit status: 2 flag bits + 62-bit sum (scan)
+constexpr unsigned long long kFlagAgg64 = 1ull << 62, kFlagPre64 = 2ull << 62, kSumMask64 = (1ull << 62) - 1ull;
+
+// The walk reads kLookWin status words at a time (all loads in flight together) and then
+// consumes them nearest first; tile 0 always holds an inclusive prefix, so the walk ends there
+// at the latest.
+#ifndef VG_LOOK_WIN
+#define VG_LOOK_WIN 8
+#endif
+constexpr int kLookWin = VG_LOOK_WIN;
+
+__device__ __forceinline__ uint32_t lookback32(const uint32_t *status, long long tile, int stride, int col,
+                                               uint32_t *err) {
+    uint32_t prefix = 0;
+    for (long long t = tile - 1; t >= 0; t -= kLookWin) {
+        uint32_t s[kLookWin];
+#pragma unroll
+        for (int k = 0; k < kLookWin; ++k) s[k] = (t - k >= 0) ? __ldcv(status + (t - k) * stride + col) : kFlagPre;
+#pragma unroll
+        for (int k = 0; k < kLookWin; ++k) {
+            for (int spins = 0; (s[k] >> 30) == 0; ++spins) {
+                if (spins >= kSpinLimit) {
+                    atomicExch(err, 1u);
+                    return prefix;
+                }
+                s[k] = __ldcv(status + (t - k) * stride + col);
+            }
+            prefix += s[k] & kCountMask;
+            if ((s[k] & ~kCountMask) == kFlagPre) return prefix;
+        }
+    }
+    return prefix;
+}
+
+// Warp-cooperative walk (all 32 lanes call it): lane l reads the status of tile t - l, so one
+// round trip covers 32 predecessors; the walk stops at the nearest inclusive prefix once every
+// tile up to it has published.
+__device__ __forceinline__ unsigned long long warp_lookback64(const unsigned long long *status, long long tile,
+                                                              uint32_t *err) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long prefix = 0;
+    for (long long t = tile - 1; t >= 0; t -= 32) {
+        const long long my = t - lane;
+        unsigned long long s = my >= 0 ? __ldcv(status + my) : kFlagPre64;
+        unsigned need = 0xffffffffu, pre = 0;
+        for (int spins = 0;; ++spins) {
+            pre = __ballot_sync(0xffffffffu, (s & ~kSumMask64) == kFlagPre64);
+            need = pre ? ((pre & (0u - pre)) << 1) - 1u : 0xffffffffu;   // lanes up to the nearest prefix
+            const unsigned waiting = __ballot_sync(0xffffffffu, (s >> 62) == 0) & need;
+            if (waiting == 0) break;
+            if (spins >= kSpinLimit) {
+                if (lane == 0) atomicExch(err, 1u);
+                break;
+            }
+            if ((s >> 62) == 0) s = __ldcv(status + my);
+        }
+        unsigned long long v = ((need >> lane) & 1u) ? (s & kSumMask64) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        prefix += v;
+        if (pre) break;
+    }
+    return prefix;
+}
+
+// Exclusive scan over the threads of a CTA of NT threads (NT/32 warps); returns the exclusive
+// prefix of x and the CTA total.  ws must hold NT/32 words; the CTA is synchronised on return.
+template <int NT>
+__device__ __forceinline__ unsigned long long cta_excl_scan(unsigned long long x, unsigned long long *ws,
+                                                            unsigned long long &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    unsigned long long before = 0, all = 0;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) {
+        const unsigned long long v = ws[k];
+        before += (k < w) ? v : 0ull;
+        all += v;
+    }
+    __syncthreads();
+    total = all;
+    return before + incl - x;
+}
+
 // ---------------------------------------------------------------------------- scan
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-size_t scan_tmp_words(long long n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1024; }
-
-__device__ __forceinline__ uint32_t load_count(const uint32_t *in, const uint32_t *perm, long long i) {
-    return perm ? in[perm[i]] : in[i];
+size_t scan_tmp_words(long long n) {
+    const long long tiles = (n + kScanTile - 1) / kScanTile;
+    return (size_t)(2 * tiles + 4);   // u64 status per tile, tile counter
 }
 
+// Exclusive scan of count[perm[i]] (perm may be NULL); out[n] = total (low 32 bits) and
+// total64 = the full sum.  tmp: tile counter in tmp[0], u64 status from tmp + 2.
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_reduce(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm, long long n,
-              uint32_t *__restrict__ block_sums) {
-    __shared__ uint32_t warp_sums[kScanThreads / 32];
-    const long long base = (long long)blockIdx.x * kScanTile;
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        long long i = base + k * kScanThreads + threadIdx.x;
-        if (i < n) s += load_count(in, perm, i);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = s;
+k_scan_onepass(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm, long long n, uint32_t *__restrict__ out,
+               uint32_t *tmp, unsigned long long *total64, uint32_t *err) {
+    __shared__ unsigned long long ws[kScanThreads / 32];
+    __shared__ unsigned long long s_prefix;
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tmp, 1u);
     __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t t = threadIdx.x < kScanThreads / 32 ? warp_sums[threadIdx.x] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) block_sums[blockIdx.x] = t;
-    }
-}
-
-// Exclusive scan of the block sums by one block; writes the grand total to *total.
-__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *__restrict__ sums, int nb, uint32_t *__restrict__ total) {
-    __shared__ uint32_t warp_tot[32];
-    __shared__ uint32_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < nb; base += 1024) {
-        int i = base + threadIdx.x;
-        uint32_t v = i < nb ? sums[i] : 0;
-        uint32_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if ((threadIdx.x & 31) >= o) x += y;
-        }
-        if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = x;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            uint32_t w = warp_tot[threadIdx.x];
-            uint32_t xw = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, xw, o);
-                if (threadIdx.x >= o) xw += y;
-            }
-            warp_tot[threadIdx.x] = xw - w;   // exclusive
-        }
-        __syncthreads();
-        uint32_t excl = carry + warp_tot[threadIdx.x >> 5] + x - v;
-        if (i < nb) sums[i] = excl;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + v;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *total = carry;
-}
-
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_down(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm, long long n,
-            const uint32_t *__restrict__ block_off, uint32_t *__restrict__ out) {
-    __shared__ uint32_t warp_tot[kScanThreads / 32];
-    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    const long long tile = s_tile;
+    unsigned long long *status = (unsigned long long *)(tmp + 2);
+    const long long i0 = tile * kScanTile + (long long)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
-    uint32_t s = 0;
+    unsigned long long sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        long long i = base + k;
-        v[k] = i < n ? load_count(in, perm, i) : 0;
-        s += v[k];
+        const long long i = i0 + k;
+        v[k] = i < n ? (perm ? in[perm[i]] : in[i]) : 0u;
+        sum += v[k];
     }
-    uint32_t x = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) >= o) x += y;
-    }
-    if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = x;
-    __syncthreads();
+    unsigned long long agg;
+    const unsigned long long excl = cta_excl_scan<kScanThreads>(sum, ws, agg);
     if (threadIdx.x < 32) {
-        uint32_t w = threadIdx.x < kScanThreads / 32 ? warp_tot[threadIdx.x] : 0;
-        uint32_t xw = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, xw, o);
-            if (threadIdx.x >= o) xw += y;
+        unsigned long long prefix = 0;
+        if (tile == 0) {
+            if (threadIdx.x == 0) atomicExch(status, kFlagPre64 | agg);
+        } else {
+            if (threadIdx.x == 0) atomicExch(status + tile, kFlagAgg64 | agg);
+            prefix = warp_lookback64(status, tile, err);
+            if (threadIdx.x == 0) atomicExch(status + tile, kFlagPre64 | (prefix + agg));
         }
-        if (threadIdx.x < kScanThreads / 32) warp_tot[threadIdx.x] = xw - w;
+        if (threadIdx.x == 0) {
+            s_prefix = prefix;
+            if ((tile + 1) * kScanTile >= n) {   // the last tile writes the total
+                out[n] = (uint32_t)(prefix + agg);
+                *total64 = prefix + agg;
+            }
+        }
     }
     __syncthreads();
-    uint32_t run = block_off[blockIdx.x] + warp_tot[threadIdx.x >> 5] + x - s;
+    unsigned long long run = s_prefix + excl;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        long long i = base + k;
-        if (i < n) out[i] = run;
+        const long long i = i0 + k;
+        if (i < n) out[i] = (uint32_t)run;
         run += v[k];
     }
 }
 
-__global__ void k_write_total(const uint32_t *total, uint32_t *out, long long n) { out[n] = *total; }
-
 cudaError_t launch_scan_gather(const uint32_t *count, const uint32_t *perm, uint32_t *out, long long n, uint32_t *tmp,
-                               cudaStream_t st, long long *launches) {
-    const long long nb = (n + kScanTile - 1) / kScanTile;
-    uint32_t *sums = tmp, *total = tmp + nb;
-    if (nb > 0) {
-        k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(count, perm, n, sums);
-        *launches += 1;
+                               unsigned long long *total64, uint32_t *err, cudaStream_t st, long long *launches) {
+    const long long tiles = (n + kScanTile - 1) / kScanTile;
+    cudaError_t e = cudaMemsetAsync(tmp, 0, scan_tmp_words(n) * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    if (tiles == 0) {
+        e = cudaMemsetAsync(out, 0, sizeof(uint32_t), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(total64, 0, sizeof(unsigned long long), st);
+        return e;
     }
-    k_scan_top<<<1, 1024, 0, st>>>(sums, (int)nb, total);
-    *launches += 1;
-    if (nb > 0) {
-        k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(count, perm, n, sums, out);
-        *launches += 1;
-    }
-    k_write_total<<<1, 1, 0, st>>>(total, out, n);
+    k_scan_onepass<<<(unsigned)tiles, kScanThreads, 0, st>>>(count, perm, n, out, tmp, total64, err);
     *launches += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const uint32_t *in, uint32_t *out, long long n, uint32_t *tmp, cudaStream_t st,
-                        long long *launches) {
-    return launch_scan_gather(in, nullptr, out, n, tmp, st, launches);
-}
-
 // ---------------------------------------------------------------------------- radix sort
+// Stable LSD radix sort, one kernel per 8-bit digit (Adinets, Merrill: "Onesweep: A Faster
+// Least Significant Digit Radix Sort for GPUs", 2022): the digit totals of every pass come
+// from one histogram kernel up front; per pass a CTA ranks its 2048-key tile stably in shared
+// memory, finds each digit's offset from the tiles before it by decoupled look-back, and
+// writes the tile digit by digit, so that stores land in consecutive runs.
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 8;                         // per thread
-constexpr int kRsTile = kRsThreads * kRsItems;      // 2048 keys per block
+#ifndef VG_RS_ITEMS
+#define VG_RS_ITEMS 8
+#endif
+constexpr int kRsItems = VG_RS_ITEMS;                // keys per thread
+constexpr int kRsTile = kRsThreads * kRsItems;      // keys per CTA tile
 constexpr int kRsBins = 256;
+#ifndef VG_HIST_AGG
+#define VG_HIST_AGG 0   // 1: aggregate equal digits over a warp (match_any) before the shared-memory atomic
+#endif
 
-size_t radix_hist_words(long long n) { return (size_t)kRsBins * (size_t)((n + kRsTile - 1) / kRsTile + 1); }
+static int rs_passes(int bits) { return (bits + 7) / 8; }
 
-__global__ void __launch_bounds__(kRsThreads)
-k_radix_hist(const uint32_t *__restrict__ keys, long long n, int shift, uint32_t mask, uint32_t *__restrict__ hist,
-             int n_blocks) {
-    __shared__ uint32_t cnt[kRsBins];
-    cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const long long base = (long long)blockIdx.x * kRsTile;
-#pragma unroll
-    for (int k = 0; k < kRsItems; ++k) {
-        long long i = base + k * kRsThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & mask], 1u);
-    }
-    __syncthreads();
-    hist[(long long)threadIdx.x * n_blocks + blockIdx.x] = cnt[threadIdx.x];
+size_t radix_scratch_words(long long n, int bits) {
+    const long long tiles = (n + kRsTile - 1) / kRsTile;
+    const int p = rs_passes(bits);
+    return (size_t)p * kRsBins + (size_t)p + 8 + (size_t)p * (size_t)tiles * kRsBins;
 }
 
-// Stable scatter: warp w owns keys [w*256, (w+1)*256) of the block tile and ranks them in
-// order, 32 at a time, with __match_any_sync; per-digit warp counts are then scanned
-// across warps so every key gets its rank in the tile's original order.
+// digit totals of all passes: ghist[p * 256 + d]
 __global__ void __launch_bounds__(kRsThreads)
-k_radix_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, uint32_t *__restrict__ ko,
-                uint32_t *__restrict__ vo, long long n, int shift, uint32_t mask, const uint32_t *__restrict__ hist,
-                int n_blocks) {
-    __shared__ uint32_t warp_cnt[kRsWarps][kRsBins];
-    __shared__ uint32_t digit_base[kRsBins];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kRsWarps * kRsBins; i += kRsThreads) (&warp_cnt[0][0])[i] = 0;
-    digit_base[threadIdx.x] = hist[(long long)threadIdx.x * n_blocks + blockIdx.x];
+k_digit_hist(const uint32_t *__restrict__ keys, long long n, int bits, uint32_t *__restrict__ ghist) {
+    __shared__ uint32_t h[4][kRsBins];
+    const int passes = (bits + 7) / 8;
+    for (int i = threadIdx.x; i < 4 * kRsBins; i += kRsThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    const long long base = (long long)blockIdx.x * kRsTile + w * (kRsItems * 32);
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // the loop condition is the same for every lane of a warp (its first index), so that the
+    // per-digit counts can be aggregated over the warp before the shared-memory atomics
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i - lane < n; i += stride) {
+        const bool valid = i < n;
+        const uint32_t k = valid ? keys[i] : 0u;
+        for (int p = 0; p < passes; ++p) {
+            const int nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
+#if VG_HIST_AGG
+            const uint32_t dg = valid ? ((k >> (8 * p)) & ((1u << nb) - 1u)) : 0xFFFFFFFFu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&h[p][dg], (uint32_t)__popc(peers));
+#else
+            if (valid) atomicAdd(&h[p][(k >> (8 * p)) & ((1u << nb) - 1u)], 1u);
+#endif
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRsBins; i += kRsThreads) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&ghist[i], c);
+    }
+}
+
+__global__ void __launch_bounds__(kRsThreads)
+k_onesweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, uint32_t *__restrict__ ko,
+           uint32_t *__restrict__ vo, long long n, int shift, uint32_t mask, const uint32_t *__restrict__ ghist,
+           uint32_t *status, uint32_t *tile_ctr, uint32_t *err) {
+    __shared__ uint32_t wcnt[kRsWarps][kRsBins];    // per-warp digit counts, then exclusive over warps
+    __shared__ uint32_t dig_local[kRsBins];          // first slot of each digit in the ranked tile
+    __shared__ uint32_t dig_global[kRsBins];         // first output position of each digit's run
+    __shared__ uint32_t sk[kRsTile], sv[kRsTile];
+    __shared__ unsigned long long wsum[kRsWarps];
+    __shared__ uint32_t s_tile;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, d = threadIdx.x;
+    for (int i = threadIdx.x; i < kRsWarps * kRsBins; i += kRsThreads) (&wcnt[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    __syncthreads();
+    const long long tile = s_tile;
+    // 1. stable rank inside the tile: warp w ranks keys [w*256, (w+1)*256) of the tile in order,
+    //    32 at a time, with __match_any_sync
+    const long long base = tile * kRsTile + w * (kRsItems * 32);
     uint32_t k[kRsItems], v[kRsItems], r[kRsItems];
 #pragma unroll
     for (int it = 0; it < kRsItems; ++it) {
         const long long i = base + it * 32 + lane;
         const bool valid = i < n;
         k[it] = valid ? keys[i] : 0u;
-        v[it] = valid ? vals[i] : 0u;
-        const uint32_t d = valid ? ((k[it] >> shift) & mask) : 0xFFFFFFFFu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        v[it] = valid ? (vals ? vals[i] : (uint32_t)i) : 0u;
+        const uint32_t dg = valid ? ((k[it] >> shift) & mask) : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
         const uint32_t lower = peers & ((1u << lane) - 1u);
-        const uint32_t prev = valid ? warp_cnt[w][d] : 0u;
+        const uint32_t prev = valid ? wcnt[w][dg] : 0u;
         __syncwarp();
-        if (valid && lower == 0u) warp_cnt[w][d] = prev + __popc(peers);
+        if (valid && lower == 0u) wcnt[w][dg] = prev + __popc(peers);
         __syncwarp();
         r[it] = prev + __popc(lower);
     }
     __syncthreads();
-    {
-        uint32_t run = 0;
+    // 2. per digit (thread d): exclusive offsets over warps and the tile's count
+    uint32_t cnt = 0;
 #pragma unroll
-        for (int ww = 0; ww < kRsWarps; ++ww) {
-            uint32_t c = warp_cnt[ww][threadIdx.x];
-            warp_cnt[ww][threadIdx.x] = run;
-            run += c;
-        }
+    for (int ww = 0; ww < kRsWarps; ++ww) {
+        const uint32_t c = wcnt[ww][d];
+        wcnt[ww][d] = cnt;
+        cnt += c;
     }
+    if (tile == 0)
+        atomicExch(status + d, kFlagPre | cnt);
+    else
+        atomicExch(status + tile * kRsBins + d, kFlagAgg | cnt);
+    unsigned long long tot;
+    const uint32_t local = (uint32_t)cta_excl_scan<kRsThreads>(cnt, wsum, tot);
+    const uint32_t gbase = (uint32_t)cta_excl_scan<kRsThreads>(ghist[d], wsum, tot);
+    uint32_t prefix = 0;
+    if (tile > 0) {
+        prefix = lookback32(status, tile, kRsBins, d, err);
+        atomicExch(status + tile * kRsBins + d, kFlagPre | (prefix + cnt));
+    }
+    dig_local[d] = local;
+    dig_global[d] = gbase + prefix;
     __syncthreads();
+    // 3. place the keys in digit order in shared memory, then write each digit's run
 #pragma unroll
     for (int it = 0; it < kRsItems; ++it) {
         const long long i = base + it * 32 + lane;
         if (i < n) {
-            const uint32_t d = (k[it] >> shift) & mask;
-            const uint32_t pos = digit_base[d] + warp_cnt[w][d] + r[it];
-            ko[pos] = k[it];
-            vo[pos] = v[it];
+            const uint32_t dg = (k[it] >> shift) & mask;
+            const uint32_t p = dig_local[dg] + wcnt[w][dg] + r[it];
+            sk[p] = k[it];
+            sv[p] = v[it];
         }
+    }
+    __syncthreads();
+    const long long rem = n - tile * kRsTile;
+    const int tn = rem < kRsTile ? (int)rem : kRsTile;
+    for (int i = threadIdx.x; i < tn; i += kRsThreads) {
+        const uint32_t key = sk[i];
+        const uint32_t dg = (key >> shift) & mask;
+        const uint32_t pos = dig_global[dg] + (uint32_t)i - dig_local[dg];
+        ko[pos] = key;
+        vo[pos] = sv[i];
     }
 }
 
-cudaError_t launch_radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp, uint32_t *vals_tmp, long long n,
-                              int bits, uint32_t *hist, uint32_t *scan_tmp, uint32_t **keys_out, uint32_t **vals_out,
-                              cudaStream_t st, long long *launches) {
-    uint32_t *ka = keys, *va = vals, *kb = keys_tmp, *vb = vals_tmp;
-    const int n_blocks = (int)((n + kRsTile - 1) / kRsTile);
-    if (n > 0) {
-        for (int shift = 0; shift < bits; shift += 8) {
-            const int nbits = bits - shift < 8 ? bits - shift : 8;
-            const uint32_t mask = (1u << nbits) - 1u;
-            k_radix_hist<<<n_blocks, kRsThreads, 0, st>>>(ka, n, shift, mask, hist, n_blocks);
-            *launches += 1;
-            cudaError_t e = launch_scan(hist, hist, (long long)kRsBins * n_blocks, scan_tmp, st, launches);
-            if (e != cudaSuccess) return e;
-            k_radix_scatter<<<n_blocks, kRsThreads, 0, st>>>(ka, va, kb, vb, n, shift, mask, hist, n_blocks);
-            *launches += 1;
-            uint32_t *t = ka; ka = kb; kb = t;
-            t = va; va = vb; vb = t;
-        }
-    }
-    *keys_out = ka;
-    *vals_out = va;
-    return cudaGetLastError();
-}
-
-__global__ void k_iota(uint32_t *v, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        v[i] = (uint32_t)i;
-}
-
-cudaError_t launch_iota(uint32_t *v, long long n, cudaStream_t st, long long *launches) {
-    long long b = (n + 255) / 256;
-    if (b > 152 * 32) b = 152 * 32;
-    if (b < 1) b = 1;
-    k_iota<<<(unsigned)b, 256, 0, st>>>(v, n);
+cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *ka, uint32_t *va,
+                              uint32_t *kb, uint32_t *vb, long long n, int bits, uint32_t *scratch, uint32_t *err,
+                              uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st, long long *launches) {
+    const int passes = rs_passes(bits);
+    *keys_out = const_cast<uint32_t *>(keys_in);
+    *vals_out = const_cast<uint32_t *>(vals_in);
+    if (n <= 0 || passes == 0) return cudaSuccess;
+    if (n > (long long)kCountMask) return cudaErrorInvalidValue;
+    const long long tiles = (n + kRsTile - 1) / kRsTile;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, radix_scratch_words(n, bits) * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    uint32_t *ghist = scratch, *ctr = scratch + passes * kRsBins, *status = ctr + passes + 8;
+    long long hb = (n + kRsThreads - 1) / kRsThreads;
+    if (hb > 152 * 8) hb = 152 * 8;
+    k_digit_hist<<<(unsigned)hb, kRsThreads, 0, st>>>(keys_in, n, bits, ghist);
     *launches += 1;
+    const uint32_t *ki = keys_in, *vi = vals_in;
+    for (int p = 0; p < passes; ++p) {
+        uint32_t *kout = (p & 1) ? kb : ka, *vout = (p & 1) ? vb : va;
+        const int nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
+        k_onesweep<<<(unsigned)tiles, kRsThreads, 0, st>>>(ki, vi, kout, vout, n, 8 * p, (1u << nb) - 1u,
+                                                           ghist + p * kRsBins, status + (size_t)p * tiles * kRsBins,
+                                                           ctr + p, err);
+        *launches += 1;
+        ki = kout;
+        vi = vout;
+    }
+    *keys_out = const_cast<uint32_t *>(ki);
+    *vals_out = const_cast<uint32_t *>(vi);
     return cudaGetLastError();
 }
 
@@ -321,31 +416,47 @@ cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, uint2 *r
 }
 
 // ---------------------------------------------------------------------------- tile order
-// Longest-first scheduling of the blend kernels: tiles sorted by descending instance count
-// (a stable 16-bit radix sort of 0xFFFF - min(count, 0xFFFF)).
-__global__ void k_tile_keys(const uint2 *__restrict__ ranges, long long n, uint32_t *__restrict__ keys,
-                            uint32_t *__restrict__ vals) {
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+// Longest-first scheduling of the blend kernels: tiles in descending order of their instance
+// count, bucketed at a third of an octave (64 buckets) by one CTA.  The order only decides
+// which tile a CTA of the blend kernels takes; every order gives the same results.
+constexpr int kOrderBuckets = 64;
+
+__device__ __forceinline__ int order_bucket(uint32_t c) {
+    if (c == 0) return 0;
+    const int b = 1 + (int)(3.0f * __log2f((float)c));
+    return b < kOrderBuckets - 1 ? b : kOrderBuckets - 1;
+}
+
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, long long n, uint32_t *__restrict__ order) {
+    __shared__ uint32_t cnt[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long t = threadIdx.x; t < n; t += blockDim.x) {
         const uint2 r = ranges[t];
-        const uint32_t c = r.y - r.x;
-        keys[t] = 0xFFFFu - (c < 0xFFFFu ? c : 0xFFFFu);
-        vals[t] = (uint32_t)t;
+        atomicAdd(&cnt[order_bucket(r.y - r.x)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // descending: largest bucket first
+        uint32_t run = 0;
+        for (int b = kOrderBuckets - 1; b >= 0; --b) {
+            const uint32_t c = cnt[b];
+            cnt[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (long long t = threadIdx.x; t < n; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        order[atomicAdd(&cnt[order_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
     }
 }
 
-cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *keys, uint32_t *vals,
-                              uint32_t *keys_tmp, uint32_t *vals_tmp, uint32_t *hist, uint32_t *scan_tmp,
-                              uint32_t **order, cudaStream_t st, long long *launches) {
-    if (n_tiles <= 0) {
-        *order = vals;
-        return cudaSuccess;
-    }
-    long long b = (n_tiles + 255) / 256;
-    if (b > 152 * 8) b = 152 * 8;
-    k_tile_keys<<<(unsigned)b, 256, 0, st>>>(ranges, n_tiles, keys, vals);
+cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *order, cudaStream_t st,
+                              long long *launches) {
+    if (n_tiles <= 0) return cudaSuccess;
+    k_tile_order<<<1, 1024, 0, st>>>(ranges, n_tiles, order);
     *launches += 1;
-    uint32_t *ko = nullptr;
-    return launch_radix_sort(keys, vals, keys_tmp, vals_tmp, n_tiles, 16, hist, scan_tmp, &ko, order, st, launches);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------- L2 loss

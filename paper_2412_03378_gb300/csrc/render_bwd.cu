@@ -93,7 +93,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     const uint32_t warp_last = __reduce_max_sync(0xffffffffu, thr_last);
     const WarpBox wb = warp_box<P>(x0, y0);
     const float xf = (float)x0, yf = (float)y0;
-    unsigned long long pairs = 0;
+    unsigned long long pairs = 0, blended = 0;   // evaluated / blended pairs (COUNT only)
 
     for (uint32_t end = tile_last; end > rg.x;) {
         const uint32_t start = (end - rg.x > (uint32_t)kChunk) ? end - kChunk : rg.x;
@@ -138,6 +138,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                         const bool clamped = e.tau > bp.tau_max;
                         const float tau = fminf(e.tau, bp.tau_max);
                         if (tau < bp.tau_skip) continue;
+                        if (COUNT) ++blended;
                         any = true;
                         const float e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
                         const float alpha = __fsub_rn(1.0f, e2);
@@ -193,8 +194,12 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
     if (COUNT) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+            blended += __shfl_xor_sync(0xffffffffu, blended, o);
+        }
         if (lane == 0 && pairs) atomicAdd(pair_count, pairs);
+        if (lane == 0 && blended) atomicAdd(pair_count + 1, blended);
     }
 }
 

@@ -49,7 +49,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     const float xf = (float)x0, yf = (float)y0;
     const WarpBox wb = warp_box<P>(x0, y0);
     const int lane = threadIdx.x & 31;
-    unsigned long long pairs = 0;
+    unsigned long long pairs = 0, blended = 0;   // evaluated / blended pairs (COUNT only)
     for (uint32_t base = rg.x; base < rg.y; base += kChunk) {
         const uint32_t n = min((uint32_t)kChunk, rg.y - base);
         if (threadIdx.x < n) {
@@ -84,6 +84,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                     if (COUNT) ++pairs;
                     const float tau = fminf(e.tau, bp.tau_max);
                     if (tau < bp.tau_skip) continue;
+                    if (COUNT) ++blended;
                     const float e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
                     const float w = __fmul_rn(__fsub_rn(1.0f, e2), T[k]);
                     c0[k] = fmaf(r5.y, w, c0[k]);
@@ -113,8 +114,12 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
     if (COUNT) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+            blended += __shfl_xor_sync(0xffffffffu, blended, o);
+        }
         if (lane == 0 && pairs) atomicAdd(pair_count, pairs);
+        if (lane == 0 && blended) atomicAdd(pair_count + 1, blended);
     }
 }
 

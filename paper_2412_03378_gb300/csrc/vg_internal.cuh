@@ -74,24 +74,22 @@ cudaError_t launch_tomo_preprocess(const GaussIn &g, const float *cs_d /* [A][2]
                                    float tau_cut, float4 *rec, uint32_t *count, short4 *rect, short4 *prect,
                                    cudaStream_t st, long long *launches);
 
-// Exclusive scan of n uint32 values into out (out[n] = total).  tmp must hold
-// scan_tmp_words(n) uint32.
+// Single-pass exclusive scan of count[perm[i]] (perm may be NULL) into out[0..n); out[n] and
+// *total64 receive the total.  tmp must hold scan_tmp_words(n) uint32; *err is set if a
+// look-back wait timed out.
 size_t scan_tmp_words(long long n);
-cudaError_t launch_scan(const uint32_t *in, uint32_t *out, long long n, uint32_t *tmp, cudaStream_t st,
-                        long long *launches);
-// Scan of count[perm[i]] (gathered through a permutation); perm may be NULL.
 cudaError_t launch_scan_gather(const uint32_t *count, const uint32_t *perm, uint32_t *out, long long n,
-                               uint32_t *tmp, cudaStream_t st, long long *launches);
+                               uint32_t *tmp, unsigned long long *total64, uint32_t *err, cudaStream_t st,
+                               long long *launches);
 
-// Stable LSD radix sort of (key, value) pairs over key bits [0, bits).  Result ends in
-// keys_out/vals_out; the *_tmp buffers are clobbered.  hist must hold
-// radix_hist_words(n) uint32.
-size_t radix_hist_words(long long n);
-cudaError_t launch_radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp, uint32_t *vals_tmp, long long n,
-                              int bits, uint32_t *hist, uint32_t *scan_tmp, uint32_t **keys_out,
-                              uint32_t **vals_out, cudaStream_t st, long long *launches);
-
-cudaError_t launch_iota(uint32_t *v, long long n, cudaStream_t st, long long *launches);
+// Stable LSD radix sort of (key, value) pairs over key bits [0, bits) (n < 2^30), one kernel
+// per 8-bit digit.  Reads keys_in / vals_in (vals_in NULL: values are the input positions);
+// pass p writes (ka, va) for even p and (kb, vb) for odd p; the result pointers are returned
+// in keys_out / vals_out.  scratch must hold radix_scratch_words(n, bits) uint32.
+size_t radix_scratch_words(long long n, int bits);
+cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *ka, uint32_t *va,
+                              uint32_t *kb, uint32_t *vb, long long n, int bits, uint32_t *scratch, uint32_t *err,
+                              uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st, long long *launches);
 
 // Duplicate items into (tile key, item) instances, in the order given by perm (NULL = item
 // order).  offsets[i] is the first instance slot of the i-th item in that order.
@@ -114,10 +112,9 @@ cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, con
                               const uint32_t *nlast, const float *dL_drgb, const float *dL_dT, float *grad_acc,
                               unsigned long long *pair_count, cudaStream_t st, long long *launches);
 
-// Longest-first tile order: order[i] = tile with the i-th largest instance count.
-cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *keys, uint32_t *vals,
-                              uint32_t *keys_tmp, uint32_t *vals_tmp, uint32_t *hist, uint32_t *scan_tmp,
-                              uint32_t **order, cudaStream_t st, long long *launches);
+// Longest-first tile order: order[] lists the tiles by descending instance count (bucketed).
+cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *order, cudaStream_t st,
+                              long long *launches);
 
 cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc, int zero,
                          float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st,

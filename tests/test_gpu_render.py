@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import check_grads, dev_scene, flat, grad_rel_err, run_backward, run_forward
+from gpu_util import check_grads, dev_scene, flat, grad_rel_err, run_backward, run_forward, vg_opts
 
 pytestmark = pytest.mark.gpu
 
@@ -249,3 +249,25 @@ def test_reduced_precision_storage(gpu_lib, rec_dtype, sh_dtype):
     gg = run_backward(vg, ws, g, wr, wT)
     ref = oracle.render_grad(sq, cams, o, oracle.lists(sq, cams, o), wr, wT)
     check_grads(gg, ref, sq, GRAD_TOL)
+
+
+@pytest.mark.parametrize("mode", ["exact", "compat"])
+def test_bins_many_sort_tiles(gpu_lib, mode):
+    """50,000 Gaussians at 1280x832: the depth sort, the instance scan and the tile sort span
+    dozens of look-back tiles; keys, per-tile ranges and lists stay bit-exact."""
+    vg = gpu_lib
+    scene, cams, _ = synth.config2(0.05)
+    o = oracle.EXACT if mode == "exact" else oracle.COMPAT
+    g = dev_scene(vg, scene)
+    ws = vg.Workspace()
+    ws.preprocess(g, cams, vg_opts(vg, o))
+    ws.bin_sort()
+    depth, rect = ws.read_keys()
+    od, orc = oracle.keys(scene, cams, o)
+    assert np.array_equal(depth, od.reshape(-1))
+    assert np.array_equal(rect, orc.reshape(-1, 4))
+    ts, items = ws.read_bins()
+    L = oracle.lists(scene, cams, o)
+    assert len(items) > 20 * 2048
+    assert np.array_equal(ts, L["tile_start"])
+    assert np.array_equal(items, L["sorted_g"])
