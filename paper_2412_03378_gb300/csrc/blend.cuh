@@ -54,10 +54,11 @@ __device__ __forceinline__ void eval_pair(const float4 &r0, const float4 &r1, co
     e.tau = __fmul_rn(ex2_approx(fmaf(e.m2, -kHalfLog2e, __fadd_rn(r5.x, p.Lp))), e.rs);
 }
 
-// A thread owns P pixels of a 16x16 tile (P = 1, 2 or 4); 256 / P threads per tile.
-//   P = 1: pixel (t % 16, t / 16)
-//   P = 2: pixels (t % 16, 2 (t / 16) + k), k = 0, 1            (a warp covers 16 x 4 pixels)
-//   P = 4: pixels (2 (t % 8) + (k & 1), 2 (t / 8) + (k >> 1))    (a warp covers 16 x 8 pixels)
+// A thread owns P pixels of a 16x16 tile (P = 1, 2 or 4); 256 / P threads per tile.  Warps own
+// near-square pixel boxes, which the footprint tests below cull best.  With w = t / 32, l = t % 32:
+//   P = 1: pixel (8 (w % 2) + l % 8, 4 (w / 2) + l / 8)               (a warp covers 8 x 4 pixels)
+//   P = 2: pixels (8 (w % 2) + l % 8, 8 (w / 2) + 2 (l / 8) + k)      (8 x 8)
+//   P = 4: pixels (2 (t % 8) + (k & 1), 2 (t / 8) + (k >> 1))         (16 x 8)
 // d' and o' x d' are affine in the pixel offset, so a thread's other pixels follow from its
 // first by one add per component.  Forward and backward both use pair_eval_at(), so they
 // compute the same bits and take the same skip decisions.
@@ -65,12 +66,13 @@ template <int P>
 struct PixLayout {
     static constexpr int kThreads = kTilePix / P;
     __device__ static void origin(int t, int &x, int &y) {
+        const int w = t >> 5, l = t & 31;
         if (P == 1) {
-            x = t & 15;
-            y = t >> 4;
+            x = 8 * (w & 1) + (l & 7);
+            y = 4 * (w >> 1) + (l >> 3);
         } else if (P == 2) {
-            x = t & 15;
-            y = 2 * (t >> 4);
+            x = 8 * (w & 1) + (l & 7);
+            y = 8 * (w >> 1) + 2 * (l >> 3);
         } else {
             x = 2 * (t & 7);
             y = 2 * (t >> 3);
@@ -111,6 +113,79 @@ __device__ __forceinline__ bool box_inside(const WarpBox &b, const short4 &r) {
 
 __device__ __forceinline__ bool pixel_outside(int x, int y, const short4 &r) {
     return x < r.x || x > r.z || y < r.y || y > r.w;
+}
+
+// Conservative opacity test of one record against a warp's pixel box, for blending with
+// tau_skip >= tau_cut (pairs with tau < tau_skip are skipped by the blend itself).  With
+// u = (dx, dy, 1) in the record's pixel offsets, tau = K |d_c| / |A u| exp(-m^2 / 2) and
+// m^2 = |C u|^2 / |A u|^2.  Over the box, |A u| >= |A u_c| - |A0| hx - |A1| hy (u_c the box
+// centre, hx, hy its half-widths) and |d_c| <= its largest corner value, which bounds the
+// amplitude by Amax; tau >= tau_skip then needs m^2 <= r^2 = 2 ln(Amax / tau_skip), i.e.
+// Q(u) = |C u|^2 - r^2 |A u|^2 <= 0 somewhere in the box.  The box minimum of the quadratic
+// Q is found exactly (interior stationary point, else the four edges); r^2 is inflated by a
+// relative 1e-3 plus 1e-2 so that FP32 rounding never turns a blended pair into a culled one.
+// Returns false only when every pixel of the box has tau < tau_skip.
+struct BoxCull {
+    float x0, y0, x1, y1;   // pixel box (inclusive pixel indices)
+    float l2dmax;           // log2 of the largest |d_c| over the box
+    float l2tskip;          // log2(tau_skip)
+};
+
+__device__ __forceinline__ BoxCull box_cull(const ViewInfo &V, const WarpBox &b, float tau_skip) {
+    BoxCull c;
+    c.x0 = (float)b.x0;
+    c.y0 = (float)b.y0;
+    c.x1 = (float)b.x1;
+    c.y1 = (float)b.y1;
+    float m = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // |d_c|^2 is convex in the pixel position: largest at a corner
+        const float u = ((k & 1 ? c.x1 : c.x0) + 0.5f - V.cx) / V.fx;
+        const float v = ((k & 2 ? c.y1 : c.y0) + 0.5f - V.cy) / V.fy;
+        m = fmaxf(m, fmaf(u, u, fmaf(v, v, 1.0f)));
+    }
+    c.l2dmax = 0.5f * __log2f(m) + 1e-4f;
+    c.l2tskip = __log2f(tau_skip);
+    return c;
+}
+
+__device__ __forceinline__ float quad_edge_min(float h, float hc, float c0, float lo, float hi) {
+    // min over s in [lo, hi] of h s^2 + 2 hc s + c0 (h > 0)
+    const float s = fminf(fmaxf(-hc / h, lo), hi);
+    return fmaf(fmaf(h, s, 2.0f * hc), s, c0);
+}
+
+__device__ __forceinline__ bool box_may_blend(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
+                                              const float4 &r4, const float4 &r5, const BoxCull &bc) {
+    const float A0[3] = {r0.x, r0.y, r0.z}, A1[3] = {r0.w, r1.x, r1.y}, A2[3] = {r1.z, r1.w, r2.x};
+    const float C0[3] = {r2.y, r2.z, r2.w}, C1[3] = {r3.x, r3.y, r3.z}, C2[3] = {r3.w, r4.x, r4.y};
+    const float ex0 = bc.x0 - r4.z, ex1 = bc.x1 - r4.z, ey0 = bc.y0 - r4.w, ey1 = bc.y1 - r4.w;
+    const float cx = 0.5f * (ex0 + ex1), cy = 0.5f * (ey0 + ey1), hx = 0.5f * (ex1 - ex0), hy = 0.5f * (ey1 - ey0);
+    float au[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) au[i] = fmaf(A0[i], cx, fmaf(A1[i], cy, A2[i]));
+    const float nA0 = sqrtf(A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2]);
+    const float nA1 = sqrtf(A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2]);
+    const float low = sqrtf(au[0] * au[0] + au[1] * au[1] + au[2] * au[2]) * 0.9999f - nA0 * hx - nA1 * hy;
+    if (!(low > 0.0f)) return true;                      // no useful amplitude bound: keep
+    const float t = r5.x + bc.l2dmax - __log2f(low) - bc.l2tskip;   // log2(Amax / tau_skip)
+    if (!(t > -1e-3f)) return false;                     // Amax < tau_skip: no pixel blends
+    const float r2s = fmaf(1.3862944f * 1.001f, fmaxf(t, 0.0f), 1e-2f);   // 2 ln 2 t, inflated
+    auto dot = [](const float *a, const float *b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); };
+    const float h00 = fmaf(-r2s, dot(A0, A0), dot(C0, C0)), h01 = fmaf(-r2s, dot(A0, A1), dot(C0, C1));
+    const float h11 = fmaf(-r2s, dot(A1, A1), dot(C1, C1)), b0 = fmaf(-r2s, dot(A0, A2), dot(C0, C2));
+    const float b1 = fmaf(-r2s, dot(A1, A2), dot(C1, C2)), c0 = fmaf(-r2s, dot(A2, A2), dot(C2, C2));
+    const float det = fmaf(h00, h11, -h01 * h01);
+    if (!(h00 > 0.0f) || !(h11 > 0.0f) || !(det > 0.0f)) return true;   // not an ellipse: keep
+    // interior stationary point
+    const float xs = (h01 * b1 - h11 * b0) / det, ys = (h01 * b0 - h00 * b1) / det;
+    if (xs >= ex0 && xs <= ex1 && ys >= ey0 && ys <= ey1) return true;  // the ellipse centre is in the box
+    // the minimum lies on an edge: y = ey0 / ey1 (quadratic in x), x = ex0 / ex1 (quadratic in y)
+    float q = quad_edge_min(h00, fmaf(h01, ey0, b0), fmaf(fmaf(h11, ey0, 2.0f * b1), ey0, c0), ex0, ex1);
+    q = fminf(q, quad_edge_min(h00, fmaf(h01, ey1, b0), fmaf(fmaf(h11, ey1, 2.0f * b1), ey1, c0), ex0, ex1));
+    q = fminf(q, quad_edge_min(h11, fmaf(h01, ex0, b1), fmaf(fmaf(h00, ex0, 2.0f * b0), ex0, c0), ey0, ey1));
+    q = fminf(q, quad_edge_min(h11, fmaf(h01, ex1, b1), fmaf(fmaf(h00, ex1, 2.0f * b0), ex1, c0), ey0, ey1));
+    return q <= 0.0f;
 }
 
 struct QuadBase {

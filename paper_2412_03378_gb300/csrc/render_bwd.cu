@@ -23,13 +23,14 @@ constexpr int kGradUsed = 16;
 static_assert(kGradUsed <= kGradN, "accumulator too small");
 
 template <int P> struct BwdBounds;
-template <> struct BwdBounds<1> { static constexpr int kMinBlocks = 2; };
+template <> struct BwdBounds<1> { static constexpr int kMinBlocks = 3; };
 template <> struct BwdBounds<2> { static constexpr int kMinBlocks = 4; };
 template <> struct BwdBounds<4> { static constexpr int kMinBlocks = 8; };
 
 // One CTA per tile (longest list first), 256/P threads owning P pixels each.  Each warp first
-// ballots which records of the staged chunk it needs (some pixel of the warp reached the record
-// and the record's footprint touches the warp's pixels), then visits only those, back to front.
+// ballots which records of the staged chunk it needs (some pixel of the warp reached the record,
+// the record's footprint touches the warp's pixels and, when pairs below tau_skip are skipped,
+// its opacity can reach tau_skip there), then visits only those, back to front.
 template <int P, bool COUNT, bool PIXTEST>
 __global__ void __launch_bounds__(PixLayout<P>::kThreads, BwdBounds<P>::kMinBlocks)
 k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
@@ -92,6 +93,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     const uint32_t tile_last = s_last;
     const uint32_t warp_last = __reduce_max_sync(0xffffffffu, thr_last);
     const WarpBox wb = warp_box<P>(x0, y0);
+    const BoxCull bc = box_cull(V, wb, bp.tau_skip);
     const float xf = (float)x0, yf = (float)y0;
     unsigned long long pairs = 0, blended = 0;   // evaluated / blended pairs (COUNT only)
 
@@ -110,7 +112,11 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
         __syncthreads();
         for (int w0 = (n - 1) & ~31; w0 >= 0; w0 -= 32) {
             const int jl = w0 + lane;
-            const bool need = jl < n && start + (uint32_t)jl < warp_last && !box_misses(wb, srect[jl]);
+            bool need = jl < n && start + (uint32_t)jl < warp_last && !box_misses(wb, srect[jl]);
+            if (!PIXTEST && need) {   // skip records whose opacity stays below tau_skip on this warp
+                const float4 *q = &srec[jl * kRecF4];
+                need = box_may_blend(q[0], q[1], q[2], q[3], q[4], q[5], bc);
+            }
             unsigned m = __ballot_sync(0xffffffffu, need);
             while (m) {
                 const int b = 31 - __clz(m);

@@ -13,7 +13,7 @@ namespace vg {
 
 template <int P> struct FwdBounds;
 template <> struct FwdBounds<1> { static constexpr int kMinBlocks = 3; };
-template <> struct FwdBounds<2> { static constexpr int kMinBlocks = 6; };
+template <> struct FwdBounds<2> { static constexpr int kMinBlocks = 7; };
 template <> struct FwdBounds<4> { static constexpr int kMinBlocks = 12; };
 
 template <int P, bool COUNT, bool PIXTEST>
@@ -48,6 +48,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
     const float xf = (float)x0, yf = (float)y0;
     const WarpBox wb = warp_box<P>(x0, y0);
+    const BoxCull bc = box_cull(V, wb, bp.tau_skip);
     const int lane = threadIdx.x & 31;
     unsigned long long pairs = 0, blended = 0;   // evaluated / blended pairs (COUNT only)
     for (uint32_t base = rg.x; base < rg.y; base += kChunk) {
@@ -60,11 +61,17 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             srect[threadIdx.x] = prect[item];
         }
         __syncthreads();
-        // the warp ballots the records whose footprint touches its pixels and visits only those
+        // the warp ballots the records whose footprint touches its pixels (and, when pairs below
+        // tau_skip are skipped, whose opacity can reach tau_skip there) and visits only those
         for (int w0 = 0; w0 < (int)n; w0 += 32) {
             if (!__any_sync(0xffffffffu, live != 0)) break;
             const int jl = w0 + lane;
-            unsigned m = __ballot_sync(0xffffffffu, jl < (int)n && !box_misses(wb, srect[jl]));
+            bool need = jl < (int)n && !box_misses(wb, srect[jl]);
+            if (!PIXTEST && need) {   // skip records whose opacity stays below tau_skip on this warp
+                const float4 *q = &srec[jl * kRecF4];
+                need = box_may_blend(q[0], q[1], q[2], q[3], q[4], q[5], bc);
+            }
+            unsigned m = __ballot_sync(0xffffffffu, need);
             while (m) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
