@@ -393,6 +393,23 @@ __device__ __forceinline__ void warp_load_rows(const T *src, int rows, int w, fl
     }
 }
 
+// FP32 rows: asynchronous 4-byte global-to-shared copies (cp.async), so that all of the warp's
+// loads are in flight at once without passing through registers.  The caller waits with
+// rows_wait() before __syncwarp().
+template <>
+__device__ __forceinline__ void warp_load_rows<float>(const float *src, int rows, int w, float *buf, int lane) {
+    const uint32_t inv = row_inv(w), total = (uint32_t)(rows * w);
+    for (uint32_t e = lane; e < total; e += 32) {
+        const uint32_t r = (e * inv) >> 20, c = e - r * (uint32_t)w;
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(buf + r * kRowStride + c);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + e) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// completes this thread's outstanding row copies
+__device__ __forceinline__ void rows_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ __forceinline__ void warp_store_rows(float *dst, int rows, int w, const float *buf, int lane) {
     const uint32_t inv = row_inv(w), total = (uint32_t)(rows * w);
     for (uint32_t e = lane; e < total; e += 32) {

@@ -9,7 +9,7 @@ namespace vg {
 constexpr int kPreWarps = 4;   // warps per CTA; each owns 32 consecutive Gaussians of one view at a time
 
 template <typename RT, typename ST>
-__global__ void __launch_bounds__(32 * kPreWarps, 5)
+__global__ void __launch_bounds__(32 * kPreWarps)
 k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z_near, float tau_cut,
              float4 *__restrict__ rec, uint32_t *__restrict__ depth, uint32_t *__restrict__ count,
              short4 *__restrict__ rect, short4 *__restrict__ prect, unsigned long long *__restrict__ n_visible) {
@@ -29,6 +29,7 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
         const long long it = (long long)v * g.n + gi;
         // the SH rows of the warp's Gaussians, coalesced, before (and independent of) the key
         warp_load_rows<ST>((const ST *)g.sh + gbase * K3, nloc, K3, buf, lane);
+        rows_wait();
         __syncwarp();
         const ViewInfo &V = views[v];
         int state = 0;

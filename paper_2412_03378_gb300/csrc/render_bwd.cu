@@ -20,10 +20,13 @@ namespace vg {
 // Accumulator layout per item: [0..5] sum ga (xx, xy, x, yy, y, 1), [6..11] the same for gq,
 // [12] sum dL/dln(kappa), [13..15] dL/dcolour.
 constexpr int kGradUsed = 16;
+#ifndef VG_BWD_CHUNK
+#define VG_BWD_CHUNK 256
+#endif
 static_assert(kGradUsed <= kGradN, "accumulator too small");
 
 template <int P> struct BwdBounds;
-template <> struct BwdBounds<1> { static constexpr int kMinBlocks = 3; };
+template <> struct BwdBounds<1> { static constexpr int kMinBlocks = 4; };
 template <> struct BwdBounds<2> { static constexpr int kMinBlocks = 4; };
 template <> struct BwdBounds<4> { static constexpr int kMinBlocks = 8; };
 
@@ -40,7 +43,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
              float *__restrict__ grad_acc, unsigned long long *__restrict__ pair_count) {
     using L = PixLayout<P>;
     constexpr int kThreads = L::kThreads;
-    constexpr int kChunk = kThreads < 128 ? kThreads : 128;   // records per shared-memory chunk
+    constexpr int kChunk = VG_BWD_CHUNK;   // records per shared-memory chunk
     __shared__ float4 srec[kChunk * kRecF4];
     __shared__ float sacc[kChunk * kGradUsed];
     __shared__ uint32_t sitem[kChunk];
@@ -100,13 +103,13 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     for (uint32_t end = tile_last; end > rg.x;) {
         const uint32_t start = (end - rg.x > (uint32_t)kChunk) ? end - kChunk : rg.x;
         const int n = (int)(end - start);
-        if ((int)threadIdx.x < n) {
-            const uint32_t item = sorted_item[start + threadIdx.x];
-            sitem[threadIdx.x] = item;
+        for (int r = threadIdx.x; r < n; r += kThreads) {
+            const uint32_t item = sorted_item[start + r];
+            sitem[r] = item;
             const float4 *src = rec + (size_t)item * kRecF4;
 #pragma unroll
-            for (int k = 0; k < kRecF4; ++k) srec[threadIdx.x * kRecF4 + k] = __ldg(src + k);
-            srect[threadIdx.x] = prect[item];
+            for (int k = 0; k < kRecF4; ++k) srec[r * kRecF4 + k] = __ldg(src + k);
+            srect[r] = prect[item];
         }
         for (int k = threadIdx.x; k < kChunk * kGradUsed; k += kThreads) sacc[k] = 0.0f;
         __syncthreads();
@@ -295,6 +298,7 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
                 warp_load_rows<float>(dsh + gbase * K3, nloc, K3, sdsh[wi], lane);
             }
         }
+        rows_wait();
         __syncwarp();
         if (lane < nloc) {
         float mu[3], s[3], q[4], kap, Sig[9], Rq[9], qn[4], smax;

@@ -11,6 +11,10 @@
 
 namespace vg {
 
+#ifndef VG_FWD_CHUNK
+#define VG_FWD_CHUNK 128
+#endif
+
 template <int P> struct FwdBounds;
 template <> struct FwdBounds<1> { static constexpr int kMinBlocks = 3; };
 template <> struct FwdBounds<2> { static constexpr int kMinBlocks = 7; };
@@ -23,7 +27,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
              const short4 *__restrict__ prect, BlendParams bp, float *__restrict__ rgb, float *__restrict__ T_user, float *__restrict__ T_ws,
              float *__restrict__ S_out, uint32_t *__restrict__ nlast_out, unsigned long long *__restrict__ pair_count) {
     using L = PixLayout<P>;
-    constexpr int kChunk = L::kThreads;
+    constexpr int kChunk = VG_FWD_CHUNK > L::kThreads ? VG_FWD_CHUNK : L::kThreads;   // records per barrier
     __shared__ float4 srec[kChunk * kRecF4];
     __shared__ short4 srect[kChunk];
     const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
@@ -53,12 +57,12 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     unsigned long long pairs = 0, blended = 0;   // evaluated / blended pairs (COUNT only)
     for (uint32_t base = rg.x; base < rg.y; base += kChunk) {
         const uint32_t n = min((uint32_t)kChunk, rg.y - base);
-        if (threadIdx.x < n) {
-            const uint32_t item = sorted_item[base + threadIdx.x];
+        for (uint32_t r = threadIdx.x; r < n; r += L::kThreads) {
+            const uint32_t item = sorted_item[base + r];
             const float4 *src = rec + (size_t)item * kRecF4;
 #pragma unroll
-            for (int k = 0; k < kRecF4; ++k) srec[threadIdx.x * kRecF4 + k] = __ldg(src + k);
-            srect[threadIdx.x] = prect[item];
+            for (int k = 0; k < kRecF4; ++k) srec[r * kRecF4 + k] = __ldg(src + k);
+            srect[r] = prect[item];
         }
         __syncthreads();
         // the warp ballots the records whose footprint touches its pixels (and, when pairs below
