@@ -352,6 +352,32 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
     dY[15][0] = -3.0f * e * (xx - yy); dY[15][1] = 6.0f * e * x * y;  dY[15][2] = 0.0f;
 }
 
+// g = sum_k w_k grad Y_k(x, y, z): the basis gradients of sh_basis_grad, weighted and summed
+// term by term without materialising them.
+__device__ __forceinline__ void sh_grad_dot(int deg, float x, float y, float z, const float w[16], float g[3]) {
+    g[0] = g[1] = g[2] = 0.0f;
+    if (deg < 1) return;
+    const float c1 = 0.48860251190291992f;
+    g[0] = -c1 * w[3];
+    g[1] = -c1 * w[1];
+    g[2] = c1 * w[2];
+    if (deg < 2) return;
+    const float a = 1.0925484305920792f, b = 0.31539156525252005f, c = 0.54627421529603959f;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    g[0] += a * y * w[4] - 2.0f * b * x * w[6] - a * z * w[7] + 2.0f * c * x * w[8];
+    g[1] += a * x * w[4] - a * z * w[5] - 2.0f * b * y * w[6] - 2.0f * c * y * w[8];
+    g[2] += -a * y * w[5] + 4.0f * b * z * w[6] - a * x * w[7];
+    if (deg < 3) return;
+    const float e = 0.59004358992664352f, f = 2.8906114426405538f, gg = 0.45704579946446572f,
+                h = 0.37317633259011540f, i = 1.4453057213202769f;
+    g[0] += -6.0f * e * x * y * w[9] + f * y * z * w[10] + 2.0f * gg * x * y * w[11] - 6.0f * h * x * z * w[12] -
+            gg * (4.0f * zz - 3.0f * xx - yy) * w[13] + 2.0f * i * x * z * w[14] - 3.0f * e * (xx - yy) * w[15];
+    g[1] += -3.0f * e * (xx - yy) * w[9] + f * x * z * w[10] - gg * (4.0f * zz - xx - 3.0f * yy) * w[11] -
+            6.0f * h * y * z * w[12] + 2.0f * gg * x * y * w[13] - 2.0f * i * y * z * w[14] + 6.0f * e * x * y * w[15];
+    g[2] += f * x * y * w[10] - 8.0f * gg * y * z * w[11] + h * (6.0f * zz - 3.0f * xx - 3.0f * yy) * w[12] -
+            8.0f * gg * x * z * w[13] + i * (xx - yy) * w[14];
+}
+
 template <typename ST>
 __device__ __forceinline__ void eval_colour(const GaussIn &g, long long gi, const float dir[3], float rgb[3],
                                             float raw[3]) {
@@ -410,11 +436,12 @@ __device__ __forceinline__ void warp_load_rows<float>(const float *src, int rows
 // completes this thread's outstanding row copies
 __device__ __forceinline__ void rows_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-__device__ __forceinline__ void warp_store_rows(float *dst, int rows, int w, const float *buf, int lane) {
+__device__ __forceinline__ void warp_store_rows(float *dst, int rows, int w, const float *buf, int lane,
+                                                int stride = kRowStride) {
     const uint32_t inv = row_inv(w), total = (uint32_t)(rows * w);
     for (uint32_t e = lane; e < total; e += 32) {
         const uint32_t r = (e * inv) >> 20, c = e - r * (uint32_t)w;
-        dst[e] = buf[r * kRowStride + c];
+        dst[e] = buf[r * (uint32_t)stride + c];
     }
 }
 

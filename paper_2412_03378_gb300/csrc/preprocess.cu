@@ -9,14 +9,16 @@ namespace vg {
 constexpr int kPreWarps = 4;   // warps per CTA; each owns 32 consecutive Gaussians of one view at a time
 
 template <typename RT, typename ST>
-__global__ void __launch_bounds__(32 * kPreWarps)
+__global__ void __launch_bounds__(32 * kPreWarps, 5)
 k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z_near, float tau_cut,
              float4 *__restrict__ rec, uint32_t *__restrict__ depth, uint32_t *__restrict__ count,
              short4 *__restrict__ rect, short4 *__restrict__ prect, unsigned long long *__restrict__ n_visible) {
-    __shared__ float sbuf[kPreWarps][32 * kRowStride];
+    constexpr int kRecStride = 4 * kRecF4 + 1;   // 24 record floats, odd stride
+    __shared__ float sbuf[kPreWarps][32 * kRowStride];   // SH rows
+    __shared__ float srow[kPreWarps][32 * kRecStride];   // record rows
     const int lane = threadIdx.x & 31;
-    float *buf = sbuf[threadIdx.x >> 5];
-    float *row = buf + lane * kRowStride;
+    float *buf = sbuf[threadIdx.x >> 5], *rbuf = srow[threadIdx.x >> 5];
+    float *row = buf + lane * kRowStride, *rrow = rbuf + lane * kRecStride;
     const int K3 = 3 * (g.sh_degree + 1) * (g.sh_degree + 1);
     const long long per_view = ((long long)g.n + 31) / 32;
     const long long n_chunks = per_view * n_views;
@@ -35,7 +37,6 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
         int state = 0;
         uint32_t cnt = 0, dk = 0xFFFFFFFFu;
         short4 rc = make_short4(-1, -1, -1, -1), prc = rc;
-        float rr[24];
         if (lane < nloc) {
             float mu[3], s[3], q[4], kap;
             load_gauss<RT>(g, gi, mu, s, q, kap);
@@ -51,15 +52,15 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
                 eval_colour_row(g.sh_degree, row, dir, rgb, raw);
 #pragma unroll
                 for (int k = 0; k < 9; ++k) {
-                    rr[k] = G.A[k];
-                    rr[9 + k] = G.Cc[k];
+                    rrow[k] = G.A[k];
+                    rrow[9 + k] = G.Cc[k];
                 }
-                rr[18] = G.px0;
-                rr[19] = G.py0;
-                rr[20] = log2f(kap) + kLog2Sqrt2Pi;
-                rr[21] = rgb[0];
-                rr[22] = rgb[1];
-                rr[23] = rgb[2];
+                rrow[18] = G.px0;
+                rrow[19] = G.py0;
+                rrow[20] = log2f(kap) + kLog2Sqrt2Pi;
+                rrow[21] = rgb[0];
+                rrow[22] = rgb[1];
+                rrow[23] = rgb[2];
             } else {
                 rc = make_short4(-1, -1, -1, -1);
                 prc = rc;
@@ -69,15 +70,11 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
             rect[it] = rc;
             prect[it] = prc;
         }
-        __syncwarp();   // every lane has read its SH row
-        if (state == 2) {
-#pragma unroll
-            for (int k = 0; k < 24; ++k) row[k] = rr[k];
-        }
         __syncwarp();
         // records of the warp's items are contiguous: write them coalesced (rows of invisible
         // items carry stale values that no tile list references)
-        warp_store_rows((float *)(rec + ((long long)v * g.n + gbase) * kRecF4), nloc, 4 * kRecF4, buf, lane);
+        warp_store_rows((float *)(rec + ((long long)v * g.n + gbase) * kRecF4), nloc, 4 * kRecF4, rbuf, lane,
+                        kRecStride);
         const unsigned vis = __ballot_sync(0xffffffffu, state == 2);
         if (lane == 0 && vis) atomicAdd(n_visible, (unsigned long long)__popc(vis));
         __syncwarp();   // the buffer is reused by the next chunk

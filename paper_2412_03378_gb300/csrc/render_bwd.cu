@@ -276,7 +276,7 @@ __device__ __forceinline__ void cross_add(const float a[3], const float b[3], fl
 constexpr int kChainWarps = 2;
 
 template <typename RT, typename ST>
-__global__ void __launch_bounds__(32 * kChainWarps, 6)
+__global__ void __launch_bounds__(32 * kChainWarps, 8)
 k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float *__restrict__ grad_acc, int zero,
         float *__restrict__ dmu, float *__restrict__ dscale, float *__restrict__ dquat, float *__restrict__ dkappa,
         float *__restrict__ dsh) {
@@ -407,27 +407,31 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
 
         // colour: rgb = max(sh . Y(dir) + 0.5, 0), dir = (mu - o)/|mu - o|
         if (g.sh != nullptr && (ga[13] != 0.0f || ga[14] != 0.0f || ga[15] != 0.0f)) {
-            float dir[3], len, rgb[3], raw[3];
+            float dir[3], len;
             view_dir(V, mu, dir, len);
-            eval_colour_row(g.sh_degree, shrow, dir, rgb, raw);
-            float Y[16], dY[16][3];
+            float Y[16];
             sh_basis(g.sh_degree, dir[0], dir[1], dir[2], Y);
-            sh_basis_grad(g.sh_degree, dir[0], dir[1], dir[2], dY);
-            float gc[3], gd[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int c = 0; c < 3; ++c) gc[c] = raw[c] > 0.0f ? ga[13 + c] : 0.0f;
+            float raw[3] = {0.5f, 0.5f, 0.5f};   // colour before the clamp (same order as eval_colour_row)
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 if (k >= K) break;
 #pragma unroll
+                for (int c = 0; c < 3; ++c) raw[c] = fmaf(shrow[3 * k + c], Y[k], raw[c]);
+            }
+            float gc[3], w[16], gd[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gc[c] = raw[c] > 0.0f ? ga[13 + c] : 0.0f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                w[k] = 0.0f;
+                if (k >= K) continue;
+#pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float sc = gc[c] * shrow[3 * k + c];
-                    gd[0] = fmaf(sc, dY[k][0], gd[0]);
-                    gd[1] = fmaf(sc, dY[k][1], gd[1]);
-                    gd[2] = fmaf(sc, dY[k][2], gd[2]);
+                    w[k] = fmaf(gc[c], shrow[3 * k + c], w[k]);
                     if (dsh != nullptr) dshrow[3 * k + c] += gc[c] * Y[k];
                 }
             }
+            sh_grad_dot(g.sh_degree, dir[0], dir[1], dir[2], w, gd);
             const float dd = gd[0] * dir[0] + gd[1] * dir[1] + gd[2] * dir[2];
             const float il = 1.0f / len;
 #pragma unroll
