@@ -122,9 +122,10 @@ __device__ __forceinline__ bool pixel_outside(int x, int y, const short4 &r) {
 // centre, hx, hy its half-widths) and |d_c| <= its largest corner value, which bounds the
 // amplitude by Amax; tau >= tau_skip then needs m^2 <= r^2 = 2 ln(Amax / tau_skip), i.e.
 // Q(u) = |C u|^2 - r^2 |A u|^2 <= 0 somewhere in the box.  The box minimum of the quadratic
-// Q is found exactly (interior stationary point, else the four edges); r^2 is inflated by a
-// relative 1e-3 plus 1e-2 so that FP32 rounding never turns a blended pair into a culled one.
-// Returns false only when every pixel of the box has tau < tau_skip.
+// Q is found from the interior stationary point (kept when it lies within a pixel of the box)
+// or the four edges; r^2 is inflated by a relative 1e-3 plus 1e-2 so that FP32 rounding never
+// turns a blended pair into a culled one.  Returns false only when every pixel of the box has
+// tau < tau_skip.
 struct BoxCull {
     float x0, y0, x1, y1;   // pixel box (inclusive pixel indices)
     float l2dmax;           // log2 of the largest |d_c| over the box
@@ -149,42 +150,55 @@ __device__ __forceinline__ BoxCull box_cull(const ViewInfo &V, const WarpBox &b,
     return c;
 }
 
-__device__ __forceinline__ float quad_edge_min(float h, float hc, float c0, float lo, float hi) {
-    // min over s in [lo, hi] of h s^2 + 2 hc s + c0 (h > 0)
-    const float s = fminf(fmaxf(-hc / h, lo), hi);
+__device__ __forceinline__ float quad_edge_min(float h, float rh, float hc, float c0, float lo, float hi) {
+    // min over s in [lo, hi] of h s^2 + 2 hc s + c0 (h > 0, rh ~ 1/h): a misplaced vertex only
+    // raises the value by h ds^2, far inside the margins of box_may_blend
+    const float s = fminf(fmaxf(-hc * rh, lo), hi);
     return fmaf(fmaf(h, s, 2.0f * hc), s, c0);
 }
 
-__device__ __forceinline__ bool box_may_blend(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
-                                              const float4 &r4, const float4 &r5, const BoxCull &bc) {
+// Per record, the Gram matrices the test needs: G = A^T A and K = C^T C over the columns
+// (A0, A1, A2), (C0, C1, C2), packed as (g00 g01 g02 g11) (g12 g22 k00 k01) (k02 k11 k12 k22).
+constexpr int kCullF4 = 3;
+
+__device__ __forceinline__ void cull_row(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
+                                         const float4 &r4, float4 out[kCullF4]) {
     const float A0[3] = {r0.x, r0.y, r0.z}, A1[3] = {r0.w, r1.x, r1.y}, A2[3] = {r1.z, r1.w, r2.x};
     const float C0[3] = {r2.y, r2.z, r2.w}, C1[3] = {r3.x, r3.y, r3.z}, C2[3] = {r3.w, r4.x, r4.y};
-    const float ex0 = bc.x0 - r4.z, ex1 = bc.x1 - r4.z, ey0 = bc.y0 - r4.w, ey1 = bc.y1 - r4.w;
+    auto dot = [](const float *a, const float *b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); };
+    out[0] = make_float4(dot(A0, A0), dot(A0, A1), dot(A0, A2), dot(A1, A1));
+    out[1] = make_float4(dot(A1, A2), dot(A2, A2), dot(C0, C0), dot(C0, C1));
+    out[2] = make_float4(dot(C0, C2), dot(C1, C1), dot(C1, C2), dot(C2, C2));
+}
+
+// The test of the record (px0, py0, log2 K from the record; Gram matrices from cull_row).
+__device__ __forceinline__ bool box_may_blend(const float4 &ga, const float4 &gb, const float4 &gc, float px0,
+                                              float py0, float l2K, const BoxCull &bc) {
+    const float g00 = ga.x, g01 = ga.y, g02 = ga.z, g11 = ga.w, g12 = gb.x, g22 = gb.y;
+    const float k00 = gb.z, k01 = gb.w, k02 = gc.x, k11 = gc.y, k12 = gc.z, k22 = gc.w;
+    const float ex0 = bc.x0 - px0, ex1 = bc.x1 - px0, ey0 = bc.y0 - py0, ey1 = bc.y1 - py0;
     const float cx = 0.5f * (ex0 + ex1), cy = 0.5f * (ey0 + ey1), hx = 0.5f * (ex1 - ex0), hy = 0.5f * (ey1 - ey0);
-    float au[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) au[i] = fmaf(A0[i], cx, fmaf(A1[i], cy, A2[i]));
-    const float nA0 = sqrtf(A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2]);
-    const float nA1 = sqrtf(A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2]);
-    const float low = sqrtf(au[0] * au[0] + au[1] * au[1] + au[2] * au[2]) * 0.9999f - nA0 * hx - nA1 * hy;
+    // |A u_c|^2 = u_c^T G u_c with u_c = (cx, cy, 1)
+    const float au2 = fmaf(cx, fmaf(g00, cx, 2.0f * fmaf(g01, cy, g02)), fmaf(cy, fmaf(g11, cy, 2.0f * g12), g22));
+    const float low = sqrtf(fmaxf(au2, 0.0f)) * 0.9999f - sqrtf(g00) * hx - sqrtf(g11) * hy;
     if (!(low > 0.0f)) return true;                      // no useful amplitude bound: keep
-    const float t = r5.x + bc.l2dmax - __log2f(low) - bc.l2tskip;   // log2(Amax / tau_skip)
+    const float t = l2K + bc.l2dmax - __log2f(low) - bc.l2tskip;   // log2(Amax / tau_skip)
     if (!(t > -1e-3f)) return false;                     // Amax < tau_skip: no pixel blends
     const float r2s = fmaf(1.3862944f * 1.001f, fmaxf(t, 0.0f), 1e-2f);   // 2 ln 2 t, inflated
-    auto dot = [](const float *a, const float *b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); };
-    const float h00 = fmaf(-r2s, dot(A0, A0), dot(C0, C0)), h01 = fmaf(-r2s, dot(A0, A1), dot(C0, C1));
-    const float h11 = fmaf(-r2s, dot(A1, A1), dot(C1, C1)), b0 = fmaf(-r2s, dot(A0, A2), dot(C0, C2));
-    const float b1 = fmaf(-r2s, dot(A1, A2), dot(C1, C2)), c0 = fmaf(-r2s, dot(A2, A2), dot(C2, C2));
+    const float h00 = fmaf(-r2s, g00, k00), h01 = fmaf(-r2s, g01, k01), h11 = fmaf(-r2s, g11, k11);
+    const float b0 = fmaf(-r2s, g02, k02), b1 = fmaf(-r2s, g12, k12), c0 = fmaf(-r2s, g22, k22);
     const float det = fmaf(h00, h11, -h01 * h01);
     if (!(h00 > 0.0f) || !(h11 > 0.0f) || !(det > 0.0f)) return true;   // not an ellipse: keep
-    // interior stationary point
-    const float xs = (h01 * b1 - h11 * b0) / det, ys = (h01 * b0 - h00 * b1) / det;
-    if (xs >= ex0 && xs <= ex1 && ys >= ey0 && ys <= ey1) return true;  // the ellipse centre is in the box
-    // the minimum lies on an edge: y = ey0 / ey1 (quadratic in x), x = ex0 / ex1 (quadratic in y)
-    float q = quad_edge_min(h00, fmaf(h01, ey0, b0), fmaf(fmaf(h11, ey0, 2.0f * b1), ey0, c0), ex0, ex1);
-    q = fminf(q, quad_edge_min(h00, fmaf(h01, ey1, b0), fmaf(fmaf(h11, ey1, 2.0f * b1), ey1, c0), ex0, ex1));
-    q = fminf(q, quad_edge_min(h11, fmaf(h01, ex0, b1), fmaf(fmaf(h00, ex0, 2.0f * b0), ex0, c0), ey0, ey1));
-    q = fminf(q, quad_edge_min(h11, fmaf(h01, ex1, b1), fmaf(fmaf(h00, ex1, 2.0f * b0), ex1, c0), ey0, ey1));
+    const float rdet = rcp_approx(det);
+    const float xs = (h01 * b1 - h11 * b0) * rdet, ys = (h01 * b0 - h00 * b1) * rdet;
+    // the ellipse centre within a pixel of the box: keep (its neighbourhood is the minimum)
+    if (xs >= ex0 - 1.0f && xs <= ex1 + 1.0f && ys >= ey0 - 1.0f && ys <= ey1 + 1.0f) return true;
+    // otherwise the minimum lies on an edge: y = ey0 / ey1 (quadratic in x), x = ex0 / ex1 (in y)
+    const float rh00 = rcp_approx(h00), rh11 = rcp_approx(h11);
+    float q = quad_edge_min(h00, rh00, fmaf(h01, ey0, b0), fmaf(fmaf(h11, ey0, 2.0f * b1), ey0, c0), ex0, ex1);
+    q = fminf(q, quad_edge_min(h00, rh00, fmaf(h01, ey1, b0), fmaf(fmaf(h11, ey1, 2.0f * b1), ey1, c0), ex0, ex1));
+    q = fminf(q, quad_edge_min(h11, rh11, fmaf(h01, ex0, b1), fmaf(fmaf(h00, ex0, 2.0f * b0), ex0, c0), ey0, ey1));
+    q = fminf(q, quad_edge_min(h11, rh11, fmaf(h01, ex1, b1), fmaf(fmaf(h00, ex1, 2.0f * b0), ex1, c0), ey0, ey1));
     return q <= 0.0f;
 }
 

@@ -21,7 +21,7 @@ namespace vg {
 // [12] sum dL/dln(kappa), [13..15] dL/dcolour.
 constexpr int kGradUsed = 16;
 #ifndef VG_BWD_CHUNK
-#define VG_BWD_CHUNK 256
+#define VG_BWD_CHUNK 192
 #endif
 static_assert(kGradUsed <= kGradN, "accumulator too small");
 
@@ -48,6 +48,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     __shared__ float sacc[kChunk * kGradUsed];
     __shared__ uint32_t sitem[kChunk];
     __shared__ short4 srect[kChunk];
+    __shared__ float4 scull[PIXTEST ? 1 : kChunk * kCullF4];   // Gram matrices for the opacity test
     __shared__ uint32_t s_last;
 
     const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
@@ -107,9 +108,14 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             const uint32_t item = sorted_item[start + r];
             sitem[r] = item;
             const float4 *src = rec + (size_t)item * kRecF4;
+            float4 q[kRecF4];
 #pragma unroll
-            for (int k = 0; k < kRecF4; ++k) srec[r * kRecF4 + k] = __ldg(src + k);
+            for (int k = 0; k < kRecF4; ++k) {
+                q[k] = __ldg(src + k);
+                srec[r * kRecF4 + k] = q[k];
+            }
             srect[r] = prect[item];
+            if (!PIXTEST) cull_row(q[0], q[1], q[2], q[3], q[4], &scull[r * kCullF4]);
         }
         for (int k = threadIdx.x; k < kChunk * kGradUsed; k += kThreads) sacc[k] = 0.0f;
         __syncthreads();
@@ -117,8 +123,9 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             const int jl = w0 + lane;
             bool need = jl < n && start + (uint32_t)jl < warp_last && !box_misses(wb, srect[jl]);
             if (!PIXTEST && need) {   // skip records whose opacity stays below tau_skip on this warp
-                const float4 *q = &srec[jl * kRecF4];
-                need = box_may_blend(q[0], q[1], q[2], q[3], q[4], q[5], bc);
+                const float4 *q = &scull[jl * kCullF4];
+                const float4 r4 = srec[jl * kRecF4 + 4];
+                need = box_may_blend(q[0], q[1], q[2], r4.z, r4.w, srec[jl * kRecF4 + 5].x, bc);
             }
             unsigned m = __ballot_sync(0xffffffffu, need);
             while (m) {

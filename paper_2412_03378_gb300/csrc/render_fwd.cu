@@ -30,6 +30,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     constexpr int kChunk = VG_FWD_CHUNK > L::kThreads ? VG_FWD_CHUNK : L::kThreads;   // records per barrier
     __shared__ float4 srec[kChunk * kRecF4];
     __shared__ short4 srect[kChunk];
+    __shared__ float4 scull[PIXTEST ? 1 : kChunk * kCullF4];   // Gram matrices for the opacity test
     const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
     const ViewInfo &V = views[tile_view[tile]];
     const int local = tile - V.tile_base;
@@ -60,9 +61,14 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
         for (uint32_t r = threadIdx.x; r < n; r += L::kThreads) {
             const uint32_t item = sorted_item[base + r];
             const float4 *src = rec + (size_t)item * kRecF4;
+            float4 q[kRecF4];
 #pragma unroll
-            for (int k = 0; k < kRecF4; ++k) srec[r * kRecF4 + k] = __ldg(src + k);
+            for (int k = 0; k < kRecF4; ++k) {
+                q[k] = __ldg(src + k);
+                srec[r * kRecF4 + k] = q[k];
+            }
             srect[r] = prect[item];
+            if (!PIXTEST) cull_row(q[0], q[1], q[2], q[3], q[4], &scull[r * kCullF4]);
         }
         __syncthreads();
         // the warp ballots the records whose footprint touches its pixels (and, when pairs below
@@ -72,8 +78,9 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             const int jl = w0 + lane;
             bool need = jl < (int)n && !box_misses(wb, srect[jl]);
             if (!PIXTEST && need) {   // skip records whose opacity stays below tau_skip on this warp
-                const float4 *q = &srec[jl * kRecF4];
-                need = box_may_blend(q[0], q[1], q[2], q[3], q[4], q[5], bc);
+                const float4 *q = &scull[jl * kCullF4];
+                const float4 r4 = srec[jl * kRecF4 + 4];
+                need = box_may_blend(q[0], q[1], q[2], r4.z, r4.w, srec[jl * kRecF4 + 5].x, bc);
             }
             unsigned m = __ballot_sync(0xffffffffu, need);
             while (m) {

@@ -54,6 +54,11 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 template <typename T> __device__ __forceinline__ float ld_f(const T *p, long long i);
 template <> __device__ __forceinline__ float ld_f<float>(const float *p, long long i) { return __ldg(p + i); }
