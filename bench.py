@@ -150,6 +150,74 @@ def peaks():
         return {}
 
 
+# ----------------------------------------------------------------------------- batched graph path
+def batched_graph(vg, scene, cam0, rgb_view0, n_views, steps, warmup, dev):
+    """The same scene with BF16 parameters and FP16 SH, n_views views at the same resolution
+    (the single-view camera first), fixed-capacity binning and the whole step (preprocess,
+    bin/sort, forward, L2 loss, backward) replayed as one CUDA graph."""
+    import torch
+
+    import synth
+
+    cams = [cam0] + synth.fibonacci_cameras(n_views - 1, 4.0, [(cam0.width, cam0.height)] * (n_views - 1))
+    cv = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev).to(dt).contiguous()
+    bf = torch.bfloat16
+    g = vg.Gaussians(cv(scene.mu, bf), cv(scene.scale, bf), cv(scene.quat, bf), cv(scene.kappa, bf),
+                     cv(scene.sh, torch.float16), scene.sh_degree)
+    P = sum(c.width * c.height for c in cams)
+    tiles = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in cams)
+    tgt = torch.as_tensor(synth.random_image(2102, (P, 3))).to(dev)
+    ws = vg.Workspace()
+    # size the instance capacity from one eager pass (25% headroom)
+    ws.preprocess(g, cams, vg.Opts.compat())
+    ws.bin_sort()
+    n_inst = ws.query()["n_instances"]
+    ws.reserve(g.n * n_views, int(n_inst * 1.25) + 4096, P, tiles)
+    opts = vg.Opts.compat(flags=vg.FLAG_GRAD_ZERO | vg.FLAG_FIXED_CAPACITY)
+    rgb, T, dl = torch.empty(P, 3, device=dev), torch.empty(P, device=dev), torch.empty(P, 3, device=dev)
+    loss = torch.zeros(1, device=dev)
+    grads = [torch.empty(g.n, 3, device=dev), torch.empty(g.n, 3, device=dev), torch.empty(g.n, 4, device=dev),
+             torch.empty(g.n, device=dev), torch.empty(tuple(g.sh.shape), device=dev)]
+    scale = 1.0 / float(rgb.numel())
+
+    def step():
+        ws.preprocess(g, cams, opts)
+        ws.bin_sort()
+        ws.render_fwd(rgb, T)
+        ws.l2_loss(rgb, tgt, scale, loss, dl)
+        ws.render_bwd(dl, None, *grads)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(max(1, warmup)):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(max(1, warmup)):
+        graph.replay()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    q = ws.query()   # raises if the fixed capacity overflowed during the run
+    P0 = cam0.width * cam0.height
+    err = (rgb[:P0] - rgb_view0).abs()
+    return {"views": n_views, "width": cam0.width, "height": cam0.height,
+            "storage": "bf16 mu/scale/quat/kappa, f16 SH; FP32 records and arithmetic",
+            "launch": "fixed-capacity binning, whole step replayed as one CUDA graph",
+            "steps_per_s": steps / t, "views_per_s": steps * n_views / t, "ms_per_step": t * 1e3 / steps,
+            "instances": q["n_instances"], "instance_capacity": q["instance_capacity"],
+            "view0_vs_fp32_max_abs": float(err.max()), "view0_vs_fp32_mean_abs": float(err.mean())}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_ours(args):
     import torch
@@ -336,6 +404,10 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if args.batch_views > 1:
+        bg_ = batched_graph(vg, scene, cams[0], rgb.detach().clone(), args.batch_views, args.steps, args.warmup, dev)
+        bg_["ratio_vs_plain_views_per_s"] = bg_["views_per_s"] / value * world
+        out["batched_graph"] = bg_
     if world == 1 and not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = cpu_baseline(scene, cams, target)
@@ -434,6 +506,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frac", type=float, default=1.0, help="scale the Gaussian count (parity/smoke use only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-views", type=int, default=4,
+                    help="views of the BF16 / graph-replayed batched measurement (0: skip it)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("note: fewer than 3 warm-up steps")

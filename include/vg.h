@@ -104,12 +104,19 @@ typedef struct {
     float z_near;
     uint32_t flags;      /* VG_FLAG_* */
     int32_t pixels_per_thread;  /* blend kernels: pixels owned by one thread, 1, 2 or 4;
-                                   0 = the library default.  Results are identical; only
-                                   speed differs (see vg_autotune). */
+                                   0 = the library defaults (forward 2, backward 1, the
+                                   fastest measured).  Results are identical; only speed
+                                   differs. */
 } vg_opts;
 
-#define VG_FLAG_FIXED_CAPACITY 1u  /* never synchronise to read the instance count; fail with
-                                      VG_ERR_CAPACITY beyond the reserved capacity        */
+#define VG_FLAG_FIXED_CAPACITY 1u  /* vg_bin_sort never synchronises: the instance count stays
+                                      on the device and the kernels cover the capacity reserved
+                                      with vg_workspace_reserve.  More instances than that are
+                                      dropped and latched: the next vg_query returns
+                                      VG_ERR_CAPACITY.  With every buffer reserved (and the views
+                                      uploaded by an earlier call with the same cameras), a
+                                      step issues no allocation, copy from pageable memory or
+                                      synchronisation, so it can be captured in a CUDA graph. */
 #define VG_FLAG_GRAD_ZERO 4u       /* render_bwd / project_tomo zero their gradient outputs
                                       before accumulating into them                        */
 #define VG_FLAG_COUNT_PAIRS 2u     /* render_fwd / render_bwd also count evaluated (pixel,
@@ -150,7 +157,9 @@ vg_status vg_workspace_create(vg_workspace **ws);
 vg_status vg_workspace_destroy(vg_workspace *ws);
 
 /* Pre-size the workspace (synchronous): n_items = views x Gaussians, n_instances = tile
- * instances, n_pixels and n_tiles over all views.  Needed before fixed-capacity use. */
+ * instances, n_pixels and n_tiles over all views.  Needed before fixed-capacity use; it
+ * reserves every buffer a step uses except the per-view camera table, which the first
+ * vg_preprocess with those cameras allocates and uploads. */
 vg_status vg_workspace_reserve(vg_workspace *ws, int64_t n_items, int64_t n_instances,
                                int64_t n_pixels, int64_t n_tiles);
 
@@ -167,7 +176,9 @@ vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera
 /* Tile binning and depth sort (Sec. 7: per-tile sorting of primitives front to back).
  * Emits one instance per (tile, item) the footprint covers and sorts instances by
  * (tile, depth key, Gaussian index) with a stable on-device radix sort.  Synchronises once
- * to read the instance count unless VG_FLAG_FIXED_CAPACITY is set. */
+ * to read the instance count unless VG_FLAG_FIXED_CAPACITY is set.  Device-side errors (a
+ * bounded look-back wait that gave up, a capacity overflow) are latched and returned by this
+ * call's synchronisation, or by the next vg_query. */
 vg_status vg_bin_sort(vg_workspace *ws, void *stream);
 
 /* Front-to-back blend (Sec. 4.1, Eq. 14 with the Eq. 19 alpha).  Outputs, device memory:
@@ -190,7 +201,7 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
 /* Backward that allocates no device memory.  The paper has no counterpart: this is a
  * library-usage variant of vg_render_bwd with the same arguments and results.
  *
- * vg_render_bwd keeps its per-(view, Gaussian) gradient accumulator (96 bytes per item) in
+ * vg_render_bwd keeps its per-(view, Gaussian) gradient accumulator (64 bytes per item) in
  * the workspace and grows it with cudaMalloc when a larger scene arrives; cudaFree and
  * cudaMalloc can also synchronise the whole device.  Some callers cannot allow that at
  * backward time: a process whose device memory belongs to another allocator (a framework's
@@ -229,7 +240,10 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
 vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n, float scale,
                      float *loss, float *grad, void *stream);
 
-/* Statistics of the last calls (synchronises the stream). */
+/* Statistics of the last calls (synchronises the stream).  *out is filled in every case; the
+ * status is the first device-side error latched since the last report (VG_ERR_CAPACITY when
+ * a fixed-capacity bin_sort had more instances than reserved, VG_ERR_TIMEOUT when a bounded
+ * device wait gave up), which this call clears, else VG_OK. */
 vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream);
 
 /* Enable (1) or disable (0) per-stage event timing; enabling clears earlier records. */

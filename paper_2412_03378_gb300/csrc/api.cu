@@ -285,15 +285,23 @@ static vg_status reserve_sort_scratch(vg_workspace *ws, long long n) {
 static unsigned long long *total64_ptr(vg_workspace *ws) { return ws->counters.p + 6; }
 static uint32_t *lookback_err_ptr(vg_workspace *ws) { return (uint32_t *)(ws->counters.p + 7); }
 
-// Reads the instance total of the last scan and the look-back timeout flag (synchronises st).
+// Reports (and clears) error bits latched on the device: a look-back timeout, a capacity
+// overflow.  Reads h_total[2] as filled by the last copy of counters[6..7].
+static vg_status latched_status(vg_workspace *ws, cudaStream_t st) {
+    const uint32_t e = ws->h_total[2];
+    if (e == 0) return VG_OK;
+    ws->h_total[2] = 0;
+    cudaMemsetAsync(lookback_err_ptr(ws), 0, sizeof(uint32_t), st);
+    if (e & kDevErrTimeout) return fail(ws, VG_ERR_TIMEOUT, "a look-back wait of the scan or sort timed out");
+    return fail(ws, VG_ERR_CAPACITY, "more (tile, Gaussian) instances than the fixed capacity");
+}
+
+// Reads the instance total of the last scan and the latched error bits (synchronises st).
 static vg_status read_total(vg_workspace *ws, cudaStream_t st, long long *total) {
     VG_CUDA(ws, cudaMemcpyAsync(ws->h_total, ws->counters.p + 6, 2 * sizeof(unsigned long long),
                                 cudaMemcpyDeviceToHost, st));
     VG_CUDA(ws, cudaStreamSynchronize(st));
-    if (ws->h_total[2] != 0) {
-        cudaMemsetAsync(lookback_err_ptr(ws), 0, sizeof(uint32_t), st);
-        return fail(ws, VG_ERR_CUDA, "a look-back wait of the scan or sort timed out");
-    }
+    VG_TRY(latched_status(ws, st));
     *total = (long long)(((unsigned long long)ws->h_total[1] << 32) | ws->h_total[0]);
     return VG_OK;
 }
@@ -323,6 +331,7 @@ vg_status vg_workspace_reserve(vg_workspace *ws, int64_t n_items, int64_t n_inst
     if (s == VG_OK) s = ensure(ws, ws->ranges, (size_t)n_tiles, "tile ranges");
     if (s == VG_OK) s = ensure(ws, ws->tile_view, (size_t)n_tiles, "tile views");
     if (s == VG_OK) s = ensure(ws, ws->grad, (size_t)n_items * kGradN, "gradient accumulators");
+    if (s == VG_OK) s = ensure(ws, ws->tord, (size_t)n_tiles, "tile order");
     ws->opts.flags = flags;
     return s;
 }
@@ -429,25 +438,34 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
         ProfScope ps(ws, ST_DEPTH, st);
         uint32_t *ksorted = nullptr;
         VG_CUDA(ws, launch_radix_sort(ws->depth.p, nullptr, ws->skey[0].p, ws->sval[0].p, ws->skey[1].p,
-                                      ws->sval[1].p, n, 32, ws->hist.p, lookback_err_ptr(ws), &ksorted, &ws->perm, st,
-                                      &ws->launches));
+                                      ws->sval[1].p, n, nullptr, 32, ws->hist.p, lookback_err_ptr(ws), &ksorted,
+                                      &ws->perm, st, &ws->launches));
     }
     // 2. instance offsets in depth order
+    const bool fixed = (ws->opts.flags & VG_FLAG_FIXED_CAPACITY) != 0;
     {
         ProfScope ps(ws, ST_SCAN, st);
         VG_CUDA(ws, launch_scan_gather(ws->count.p, ws->perm, ws->offsets.p, n, ws->scan_tmp.p, total64_ptr(ws),
-                                       lookback_err_ptr(ws), st, &ws->launches));
+                                       fixed ? (unsigned long long)ws->capacity : ~0ull, lookback_err_ptr(ws), st,
+                                       &ws->launches));
     }
+    // The instance count: read back (one synchronisation), or, with a fixed capacity, left on
+    // the device; the kernels below then cover the capacity and read the count themselves.
     long long total;
-    if (ws->opts.flags & VG_FLAG_FIXED_CAPACITY) {
-        return fail(ws, VG_ERR_UNSUPPORTED, "fixed-capacity binning is not implemented in this build");
+    const unsigned long long *total_dev = nullptr;
+    if (fixed) {
+        if (ws->capacity <= 0 || !ws->ikey[1].p)
+            return fail(ws, VG_ERR_CAPACITY, "fixed capacity: reserve instances with vg_workspace_reserve first");
+        total = ws->capacity;
+        total_dev = total64_ptr(ws);
+        ws->n_inst = -1;   // known on the device only
     } else {
         VG_TRY(read_total(ws, st, &total));
         if (total > (long long)(1u << 30) - 1)
             return fail(ws, VG_ERR_INVALID_ARG, "more than 2^30 - 1 (tile, Gaussian) instances");
         VG_TRY(reserve_instances(ws, total));
+        ws->n_inst = total;
     }
-    ws->n_inst = total;
     // 3. duplicate in depth order, 4. stable sort by tile id, 5. per-tile ranges
     {
         ProfScope ps(ws, ST_DUP, st);
@@ -457,14 +475,14 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
     {
         ProfScope ps(ws, ST_TILE, st);
         VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, ws->ikey[0].p,
-                                      ws->ival[0].p, total, bits_for(ws->n_tiles), ws->hist.p, lookback_err_ptr(ws),
-                                      &ws->inst_key, &ws->inst_item, st, &ws->launches));
+                                      ws->ival[0].p, total, total_dev, bits_for(ws->n_tiles), ws->hist.p,
+                                      lookback_err_ptr(ws), &ws->inst_key, &ws->inst_item, st, &ws->launches));
     }
     VG_TRY(ensure(ws, ws->ranges, (size_t)ws->n_tiles, "tile ranges"));
     VG_TRY(ensure(ws, ws->tord, (size_t)ws->n_tiles, "tile order"));
     {
         ProfScope ps(ws, ST_RANGES, st);
-        VG_CUDA(ws, launch_ranges(ws->inst_key, total, ws->ranges.p, ws->n_tiles, st, &ws->launches));
+        VG_CUDA(ws, launch_ranges(ws->inst_key, total, total_dev, ws->ranges.p, ws->n_tiles, st, &ws->launches));
         VG_CUDA(ws, launch_tile_order(ws->ranges.p, ws->n_tiles, ws->tord.p, st, &ws->launches));
         ws->tile_order = ws->tord.p;
     }
@@ -650,7 +668,7 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
         {
             ProfScope ps(ws, ST_SCAN, st);
             VG_CUDA(ws, launch_scan_gather(ws->count.p, nullptr, ws->offsets.p, items, ws->scan_tmp.p,
-                                           total64_ptr(ws), lookback_err_ptr(ws), st, &ws->launches));
+                                           total64_ptr(ws), ~0ull, lookback_err_ptr(ws), st, &ws->launches));
         }
         long long total = 0;
         VG_TRY(read_total(ws, st, &total));
@@ -665,13 +683,13 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
         {
             ProfScope ps(ws, ST_TILE, st);
             VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, ws->ikey[0].p,
-                                          ws->ival[0].p, total, bits_for(n_tiles), ws->hist.p, lookback_err_ptr(ws),
-                                          &ws->inst_key, &ws->inst_item, st, &ws->launches));
+                                          ws->ival[0].p, total, nullptr, bits_for(n_tiles), ws->hist.p,
+                                          lookback_err_ptr(ws), &ws->inst_key, &ws->inst_item, st, &ws->launches));
         }
         VG_TRY(ensure(ws, ws->ranges, (size_t)n_tiles, "tile ranges"));
         {
             ProfScope ps(ws, ST_RANGES, st);
-            VG_CUDA(ws, launch_ranges(ws->inst_key, total, ws->ranges.p, n_tiles, st, &ws->launches));
+            VG_CUDA(ws, launch_ranges(ws->inst_key, total, nullptr, ws->ranges.p, n_tiles, st, &ws->launches));
         }
         float *proj_b = proj + (size_t)a0 * det_px;
         {
@@ -713,12 +731,13 @@ vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n
 vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream) {
     if (!ws || !out) return VG_ERR_INVALID_ARG;
     VG_CUDA(ws, cudaStreamSynchronize((cudaStream_t)stream));
-    unsigned long long c[5] = {0, 0, 0, 0, 0};
+    unsigned long long c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     VG_CUDA(ws, cudaMemcpy(c, ws->counters.p, sizeof(c), cudaMemcpyDeviceToHost));
     memset(out, 0, sizeof(*out));
     out->n_items = ws->n_items;
     out->n_visible = (int64_t)c[0];
-    out->n_instances = ws->n_inst;
+    // with a fixed capacity the instance count lives on the device (c[6]); an overflow is latched
+    out->n_instances = ws->n_inst >= 0 ? ws->n_inst : (int64_t)std::min<unsigned long long>(c[6], (unsigned long long)ws->capacity);
     out->n_tiles = ws->n_tiles;
     out->n_pixels = ws->n_pixels;
     out->instance_capacity = ws->capacity;
@@ -733,7 +752,8 @@ vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream) {
     for (int k = 0; k < 2; ++k)
         bytes += (ws->skey[k].n + ws->sval[k].n + ws->ikey[k].n + ws->ival[k].n) * 4;
     out->device_bytes = (int64_t)bytes;
-    return VG_OK;
+    ws->h_total[2] = (uint32_t)c[7];
+    return latched_status(ws, (cudaStream_t)stream);
 }
 
 vg_status vg_profile_enable(vg_workspace *ws, int32_t enable) {
@@ -795,16 +815,23 @@ vg_status vg_read_keys(vg_workspace *ws, uint32_t *depth_bits, int32_t *rect) {
 }
 
 vg_status vg_read_bins(vg_workspace *ws, int64_t *tile_start, int32_t *sorted_item) {
-    if (!ws || !tile_start || (!sorted_item && ws->n_inst > 0)) return VG_ERR_INVALID_ARG;
+    if (!ws || !tile_start) return VG_ERR_INVALID_ARG;
     if (ws->stage < 2 && !ws->tomo_read) return fail(ws, VG_ERR_STATE, "no bin_sort to read");
     VG_CUDA(ws, cudaDeviceSynchronize());
+    long long n_inst = ws->n_inst;
+    if (n_inst < 0) {   // fixed capacity: the count is on the device
+        unsigned long long t = 0;
+        VG_CUDA(ws, cudaMemcpy(&t, total64_ptr(ws), sizeof(t), cudaMemcpyDeviceToHost));
+        n_inst = (long long)std::min<unsigned long long>(t, (unsigned long long)ws->capacity);
+    }
+    if (!sorted_item && n_inst > 0) return VG_ERR_INVALID_ARG;
     std::vector<uint2> rg((size_t)ws->n_tiles);
     if (ws->n_tiles > 0)
         VG_CUDA(ws, cudaMemcpy(rg.data(), ws->ranges.p, rg.size() * sizeof(uint2), cudaMemcpyDeviceToHost));
     tile_start[0] = 0;
     for (long long t = 0; t < ws->n_tiles; ++t) tile_start[t + 1] = tile_start[t] + (int64_t)(rg[t].y - rg[t].x);
-    if (ws->n_inst > 0)
-        VG_CUDA(ws, cudaMemcpy(sorted_item, ws->inst_item, (size_t)ws->n_inst * 4, cudaMemcpyDeviceToHost));
+    if (n_inst > 0)
+        VG_CUDA(ws, cudaMemcpy(sorted_item, ws->inst_item, (size_t)n_inst * 4, cudaMemcpyDeviceToHost));
     return VG_OK;
 }
 

@@ -16,8 +16,10 @@ namespace vg {
 // it, adding aggregates until it meets an inclusive prefix, and publishes its own.  A CTA only
 // ever waits for tiles handed out before its own, which belong to CTAs already running, so the
 // walk always ends; the spin on each status word is bounded anyway and a timeout sets a sticky
-// error flag that the host reads at its next synchronisation.
+// error flag that the host reads at its next synchronisation.  Flag bits: kErrTimeout (a
+// look-back wait gave up), kErrCapacity (more instances than the fixed capacity).
 constexpr int kSpinLimit = 1 << 21;
+constexpr uint32_t kErrTimeout = kDevErrTimeout, kErrCapacity = kDevErrCapacity;
 
 // 32-bit status: 2 flag bits + 30-bit count (radix sort, counts < 2^30)
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kCountMask = (1u << 30) - 1u;
@@ -43,7 +45,7 @@ __device__ __forceinline__ uint32_t lookback32(const uint32_t *status, long long
         for (int k = 0; k < kLookWin; ++k) {
             for (int spins = 0; (s[k] >> 30) == 0; ++spins) {
                 if (spins >= kSpinLimit) {
-                    atomicExch(err, 1u);
+                    atomicOr(err, kErrTimeout);
                     return prefix;
                 }
                 s[k] = __ldcv(status + (t - k) * stride + col);
@@ -72,7 +74,7 @@ __device__ __forceinline__ unsigned long long warp_lookback64(const unsigned lon
             const unsigned waiting = __ballot_sync(0xffffffffu, (s >> 62) == 0) & need;
             if (waiting == 0) break;
             if (spins >= kSpinLimit) {
-                if (lane == 0) atomicExch(err, 1u);
+                if (lane == 0) atomicOr(err, kErrTimeout);
                 break;
             }
             if ((s >> 62) == 0) s = __ldcv(status + my);
@@ -126,7 +128,7 @@ size_t scan_tmp_words(long long n) {
 // total64 = the full sum.  tmp: tile counter in tmp[0], u64 status from tmp + 2.
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_onepass(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm, long long n, uint32_t *__restrict__ out,
-               uint32_t *tmp, unsigned long long *total64, uint32_t *err) {
+               uint32_t *tmp, unsigned long long *total64, unsigned long long cap, uint32_t *err) {
     __shared__ unsigned long long ws[kScanThreads / 32];
     __shared__ unsigned long long s_prefix;
     __shared__ uint32_t s_tile;
@@ -159,6 +161,7 @@ k_scan_onepass(const uint32_t *__restrict__ in, const uint32_t *__restrict__ per
             if ((tile + 1) * kScanTile >= n) {   // the last tile writes the total
                 out[n] = (uint32_t)(prefix + agg);
                 *total64 = prefix + agg;
+                if (prefix + agg > cap) atomicOr(err, kErrCapacity);
             }
         }
     }
@@ -173,7 +176,8 @@ k_scan_onepass(const uint32_t *__restrict__ in, const uint32_t *__restrict__ per
 }
 
 cudaError_t launch_scan_gather(const uint32_t *count, const uint32_t *perm, uint32_t *out, long long n, uint32_t *tmp,
-                               unsigned long long *total64, uint32_t *err, cudaStream_t st, long long *launches) {
+                               unsigned long long *total64, unsigned long long cap, uint32_t *err, cudaStream_t st,
+                               long long *launches) {
     const long long tiles = (n + kScanTile - 1) / kScanTile;
     cudaError_t e = cudaMemsetAsync(tmp, 0, scan_tmp_words(n) * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
@@ -182,7 +186,7 @@ cudaError_t launch_scan_gather(const uint32_t *count, const uint32_t *perm, uint
         if (e == cudaSuccess) e = cudaMemsetAsync(total64, 0, sizeof(unsigned long long), st);
         return e;
     }
-    k_scan_onepass<<<(unsigned)tiles, kScanThreads, 0, st>>>(count, perm, n, out, tmp, total64, err);
+    k_scan_onepass<<<(unsigned)tiles, kScanThreads, 0, st>>>(count, perm, n, out, tmp, total64, cap, err);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -215,7 +219,9 @@ size_t radix_scratch_words(long long n, int bits) {
 
 // digit totals of all passes: ghist[p * 256 + d]
 __global__ void __launch_bounds__(kRsThreads)
-k_digit_hist(const uint32_t *__restrict__ keys, long long n, int bits, uint32_t *__restrict__ ghist) {
+k_digit_hist(const uint32_t *__restrict__ keys, long long n, const unsigned long long *__restrict__ n_dev, int bits,
+             uint32_t *__restrict__ ghist) {
+    if (n_dev && (long long)*n_dev < n) n = (long long)*n_dev;
     __shared__ uint32_t h[4][kRsBins];
     const int passes = (bits + 7) / 8;
     for (int i = threadIdx.x; i < 4 * kRsBins; i += kRsThreads) (&h[0][0])[i] = 0;
@@ -247,8 +253,8 @@ k_digit_hist(const uint32_t *__restrict__ keys, long long n, int bits, uint32_t 
 
 __global__ void __launch_bounds__(kRsThreads)
 k_onesweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, uint32_t *__restrict__ ko,
-           uint32_t *__restrict__ vo, long long n, int shift, uint32_t mask, const uint32_t *__restrict__ ghist,
-           uint32_t *status, uint32_t *tile_ctr, uint32_t *err) {
+           uint32_t *__restrict__ vo, long long n, const unsigned long long *__restrict__ n_dev, int shift,
+           uint32_t mask, const uint32_t *__restrict__ ghist, uint32_t *status, uint32_t *tile_ctr, uint32_t *err) {
     __shared__ uint32_t wcnt[kRsWarps][kRsBins];    // per-warp digit counts, then exclusive over warps
     __shared__ uint32_t dig_local[kRsBins];          // first slot of each digit in the ranked tile
     __shared__ uint32_t dig_global[kRsBins];         // first output position of each digit's run
@@ -260,6 +266,8 @@ k_onesweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
     if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
     __syncthreads();
     const long long tile = s_tile;
+    if (n_dev && (long long)*n_dev < n) n = (long long)*n_dev;   // the count is known on the device only
+    if (tile * kRsTile >= n) return;                             // the grid covers a larger capacity
     // 1. stable rank inside the tile: warp w ranks keys [w*256, (w+1)*256) of the tile in order,
     //    32 at a time, with __match_any_sync
     const long long base = tile * kRsTile + w * (kRsItems * 32);
@@ -327,8 +335,9 @@ k_onesweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
 }
 
 cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *ka, uint32_t *va,
-                              uint32_t *kb, uint32_t *vb, long long n, int bits, uint32_t *scratch, uint32_t *err,
-                              uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st, long long *launches) {
+                              uint32_t *kb, uint32_t *vb, long long n, const unsigned long long *n_dev, int bits,
+                              uint32_t *scratch, uint32_t *err, uint32_t **keys_out, uint32_t **vals_out,
+                              cudaStream_t st, long long *launches) {
     const int passes = rs_passes(bits);
     *keys_out = const_cast<uint32_t *>(keys_in);
     *vals_out = const_cast<uint32_t *>(vals_in);
@@ -340,13 +349,13 @@ cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, 
     uint32_t *ghist = scratch, *ctr = scratch + passes * kRsBins, *status = ctr + passes + 8;
     long long hb = (n + kRsThreads - 1) / kRsThreads;
     if (hb > 152 * 8) hb = 152 * 8;
-    k_digit_hist<<<(unsigned)hb, kRsThreads, 0, st>>>(keys_in, n, bits, ghist);
+    k_digit_hist<<<(unsigned)hb, kRsThreads, 0, st>>>(keys_in, n, n_dev, bits, ghist);
     *launches += 1;
     const uint32_t *ki = keys_in, *vi = vals_in;
     for (int p = 0; p < passes; ++p) {
         uint32_t *kout = (p & 1) ? kb : ka, *vout = (p & 1) ? vb : va;
         const int nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
-        k_onesweep<<<(unsigned)tiles, kRsThreads, 0, st>>>(ki, vi, kout, vout, n, 8 * p, (1u << nb) - 1u,
+        k_onesweep<<<(unsigned)tiles, kRsThreads, 0, st>>>(ki, vi, kout, vout, n, n_dev, 8 * p, (1u << nb) - 1u,
                                                            ghist + p * kRsBins, status + (size_t)p * tiles * kRsBins,
                                                            ctr + p, err);
         *launches += 1;
@@ -394,7 +403,9 @@ cudaError_t launch_duplicate(const uint32_t *perm, const uint32_t *offsets, cons
 }
 
 // ---------------------------------------------------------------------------- ranges
-__global__ void k_ranges(const uint32_t *__restrict__ key, long long n, uint2 *__restrict__ ranges) {
+__global__ void k_ranges(const uint32_t *__restrict__ key, long long n, const unsigned long long *__restrict__ n_dev,
+                         uint2 *__restrict__ ranges) {
+    if (n_dev && (long long)*n_dev < n) n = (long long)*n_dev;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const uint32_t t = key[i];
         if (i == 0 || key[i - 1] != t) ranges[t].x = (uint32_t)i;
@@ -402,14 +413,14 @@ __global__ void k_ranges(const uint32_t *__restrict__ key, long long n, uint2 *_
     }
 }
 
-cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, uint2 *ranges, long long n_tiles,
-                          cudaStream_t st, long long *launches) {
+cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, const unsigned long long *n_dev, uint2 *ranges,
+                          long long n_tiles, cudaStream_t st, long long *launches) {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, st);
     if (e != cudaSuccess) return e;
     if (n_inst > 0) {
         long long b = (n_inst + 255) / 256;
         if (b > 152 * 64) b = 152 * 64;
-        k_ranges<<<(unsigned)b, 256, 0, st>>>(sorted_key, n_inst, ranges);
+        k_ranges<<<(unsigned)b, 256, 0, st>>>(sorted_key, n_inst, n_dev, ranges);
         *launches += 1;
     }
     return cudaGetLastError();

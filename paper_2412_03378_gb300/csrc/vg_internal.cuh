@@ -79,22 +79,28 @@ cudaError_t launch_tomo_preprocess(const GaussIn &g, const float *cs_d /* [A][2]
                                    float tau_cut, float4 *rec, uint32_t *count, short4 *rect, short4 *prect,
                                    cudaStream_t st, long long *launches);
 
+// Error bits latched in the workspace's device flag word.
+constexpr uint32_t kDevErrTimeout = 1u, kDevErrCapacity = 2u;
+
 // Single-pass exclusive scan of count[perm[i]] (perm may be NULL) into out[0..n); out[n] and
-// *total64 receive the total.  tmp must hold scan_tmp_words(n) uint32; *err is set if a
-// look-back wait timed out.
+// *total64 receive the total.  tmp must hold scan_tmp_words(n) uint32; *err gets
+// kDevErrTimeout if a look-back wait timed out and kDevErrCapacity if the total exceeds cap.
 size_t scan_tmp_words(long long n);
 cudaError_t launch_scan_gather(const uint32_t *count, const uint32_t *perm, uint32_t *out, long long n,
-                               uint32_t *tmp, unsigned long long *total64, uint32_t *err, cudaStream_t st,
-                               long long *launches);
+                               uint32_t *tmp, unsigned long long *total64, unsigned long long cap, uint32_t *err,
+                               cudaStream_t st, long long *launches);
 
 // Stable LSD radix sort of (key, value) pairs over key bits [0, bits) (n < 2^30), one kernel
 // per 8-bit digit.  Reads keys_in / vals_in (vals_in NULL: values are the input positions);
 // pass p writes (ka, va) for even p and (kb, vb) for odd p; the result pointers are returned
-// in keys_out / vals_out.  scratch must hold radix_scratch_words(n, bits) uint32.
+// in keys_out / vals_out.  scratch must hold radix_scratch_words(n, bits) uint32.  With n_dev
+// non-NULL the kernels sort min(n, *n_dev) keys (a count known on the device only; n is then
+// the capacity the launch covers).
 size_t radix_scratch_words(long long n, int bits);
 cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *ka, uint32_t *va,
-                              uint32_t *kb, uint32_t *vb, long long n, int bits, uint32_t *scratch, uint32_t *err,
-                              uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st, long long *launches);
+                              uint32_t *kb, uint32_t *vb, long long n, const unsigned long long *n_dev, int bits,
+                              uint32_t *scratch, uint32_t *err, uint32_t **keys_out, uint32_t **vals_out,
+                              cudaStream_t st, long long *launches);
 
 // Duplicate items into (tile key, item) instances, in the order given by perm (NULL = item
 // order).  offsets[i] is the first instance slot of the i-th item in that order.
@@ -102,8 +108,8 @@ cudaError_t launch_duplicate(const uint32_t *perm, const uint32_t *offsets, cons
                              const ViewInfo *views, long long n_items, int n_per_view, uint32_t *inst_key,
                              uint32_t *inst_val, long long capacity, cudaStream_t st, long long *launches);
 
-cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, uint2 *ranges, long long n_tiles,
-                          cudaStream_t st, long long *launches);
+cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, const unsigned long long *n_dev, uint2 *ranges,
+                          long long n_tiles, cudaStream_t st, long long *launches);
 
 cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
