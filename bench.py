@@ -498,6 +498,59 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------- tomography
+def run_tomo(args):
+    """Tomography (config 4: 200,000 Gaussians, 256 parallel-beam angles, 512^2 detector; --frac
+    scales the Gaussian count): one step = projection, L2 loss against the projection of the
+    50,000 ground-truth Gaussians, and the backward.  Prints one JSON line."""
+    import torch
+
+    import paper_2412_03378_gb300 as vg
+    import synth
+
+    vg.load()
+    dev = torch.device("cuda:0")
+    scene, beam, gt = synth.config4(args.frac)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev).contiguous()
+    g = vg.Gaussians(t(scene.mu), t(scene.scale), t(scene.quat), t(scene.kappa), t(scene.sh), 0)
+    gg = vg.Gaussians(t(gt.mu), t(gt.scale), t(gt.quat), t(gt.kappa), t(gt.sh), 0)
+    A = len(beam.angles)
+    ws = vg.Workspace()
+    tgt = torch.empty(A, beam.det_h, beam.det_w, device=dev)
+    ws.project_tomo(gg, beam, vg.Opts(tau_cut=1e-6), tgt)
+    proj, dl = torch.empty_like(tgt), torch.empty_like(tgt)
+    loss = torch.zeros(1, device=dev)
+    grads = [torch.zeros(g.n, 3, device=dev), torch.zeros(g.n, 3, device=dev), torch.zeros(g.n, 4, device=dev),
+             torch.zeros(g.n, device=dev)]
+    o = vg.Opts(tau_cut=1e-6, flags=vg.FLAG_GRAD_ZERO)
+
+    def step():
+        ws.project_tomo(g, beam, o, proj)
+        ws.l2_loss(proj, tgt, 1.0 / proj.numel(), loss, dl)
+        ws.project_tomo(g, beam, o, proj, dl, *grads)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ws.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    stages = ws.profile_read()
+    t_s = e0.elapsed_time(e1) / 1e3
+    out = {"metric": "tomography fwd+bwd steps/s", "value": args.steps / t_s, "unit": "steps/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_s * 1e3 / args.steps,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"tomography, {g.n} Gaussians, {A} parallel-beam angles, "
+                                  f"{beam.det_w}x{beam.det_h} detector", "frac": args.frac},
+           "stages_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in stages.items()},
+           "loss": float(loss.item())}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -508,11 +561,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-views", type=int, default=4,
                     help="views of the BF16 / graph-replayed batched measurement (0: skip it)")
+    ap.add_argument("--workload", choices=["render", "tomo"], default="render",
+                    help="render: the headline training step; tomo: the tomography step (config 4)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("note: fewer than 3 warm-up steps")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "tomo":
+        run_tomo(args)
     else:
         run_ours(args)
 
