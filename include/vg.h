@@ -240,6 +240,14 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
 vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n, float scale,
                      float *loss, float *grad, void *stream);
 
+/* Autotuner (synchronous; allocates scratch): after vg_bin_sort, times the forward and the
+ * backward blend with 1, 2 and 4 pixels per thread (which also sets each warp's pixel box:
+ * 8x4, 8x8 or 16x8 pixels) on the binned workload, `reps` timed runs each after one warm-up,
+ * and keeps the fastest of each as this workspace's default for vg_opts.pixels_per_thread = 0.
+ * The chosen values are written to *ppt_fwd / *ppt_bwd (either may be NULL).  Results of the
+ * blend do not depend on the choice.  Call vg_render_fwd again before vg_render_bwd. */
+vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t *ppt_bwd, void *stream);
+
 /* Statistics of the last calls (synchronises the stream).  *out is filled in every case; the
  * status is the first device-side error latched since the last report (VG_ERR_CAPACITY when
  * a fixed-capacity bin_sort had more instances than reserved, VG_ERR_TIMEOUT when a bounded
@@ -260,6 +268,11 @@ vg_status vg_profile_read(vg_workspace *ws, vg_stage_time *out, int32_t capacity
  *   sorted_item [n_instances] int32 (item = view * n + Gaussian). */
 vg_status vg_read_keys(vg_workspace *ws, uint32_t *depth_bits, int32_t *rect);
 vg_status vg_read_bins(vg_workspace *ws, int64_t *tile_start, int32_t *sorted_item);
+/* The lists of tiles [tile0, tile1) only: counts [tile1 - tile0] int64 and their items,
+ * concatenated in tile order, into sorted_item (capacity `cap` entries; *n_out receives the
+ * number written, VG_ERR_INVALID_ARG when cap is too small). */
+vg_status vg_read_bins_range(vg_workspace *ws, int64_t tile0, int64_t tile1, int64_t *counts,
+                             int32_t *sorted_item, int64_t cap, int64_t *n_out);
 
 /* Message of the last failure on this workspace ("" if none).  ws may be NULL for
  * failures of vg_workspace_create. */

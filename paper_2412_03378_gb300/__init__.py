@@ -77,6 +77,7 @@ _SIGS = {
     "vg_workspace_create": [ctypes.c_void_p],
     "vg_workspace_destroy": [ctypes.c_void_p],
     "vg_workspace_reserve": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64],
+    "vg_autotune": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_preprocess": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                       ctypes.c_void_p],
     "vg_bin_sort": [ctypes.c_void_p, ctypes.c_void_p],
@@ -91,6 +92,8 @@ _SIGS = {
     "vg_profile_enable": [ctypes.c_void_p, ctypes.c_int32],
     "vg_profile_read": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "vg_read_bins": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "vg_read_bins_range": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_int64, ctypes.c_void_p],
 }
 
 
@@ -237,6 +240,12 @@ class Workspace:
     def reserve(self, n_items, n_instances, n_pixels, n_tiles):
         self._chk(self._L.vg_workspace_reserve(self.h, n_items, n_instances, n_pixels, n_tiles))
 
+    def autotune(self, reps=3, stream=None):
+        """Pick pixels per thread for the blend kernels on the binned workload; returns (fwd, bwd)."""
+        f, b = ctypes.c_int32(0), ctypes.c_int32(0)
+        self._chk(self._L.vg_autotune(self.h, int(reps), ctypes.byref(f), ctypes.byref(b), _stream(stream)))
+        return f.value, b.value
+
     def preprocess(self, g: Gaussians, cams, opts: Opts, stream=None):
         self._keep = (g, _cams_array(cams), opts.c())
         self._chk(self._L.vg_preprocess(self.h, ctypes.byref(g.c()), self._keep[1], len(cams),
@@ -306,6 +315,16 @@ class Workspace:
         self._chk(self._L.vg_read_bins(self.h, ts.ctypes.data_as(ctypes.c_void_p),
                                        si.ctypes.data_as(ctypes.c_void_p)))
         return ts, si[: q["n_instances"]]
+
+    def read_bins_range(self, tile0, tile1, cap):
+        """Lists of tiles [tile0, tile1): (counts [tile1 - tile0], items concatenated)."""
+        import numpy as np
+        counts = np.zeros(max(1, tile1 - tile0), np.int64)
+        items = np.zeros(max(1, cap), np.int32)
+        n = ctypes.c_int64(0)
+        self._chk(self._L.vg_read_bins_range(self.h, int(tile0), int(tile1), counts.ctypes.data_as(ctypes.c_void_p),
+                                             items.ctypes.data_as(ctypes.c_void_p), int(cap), ctypes.byref(n)))
+        return counts[: tile1 - tile0], items[: n.value]
 
 
 def n_pixels(cams):

@@ -58,6 +58,7 @@ struct vg_workspace {
     DBuf<uint32_t> tord;                  // tile order buffer
     uint32_t *tile_order = nullptr;       // longest-first tile order of the last bin_sort
     int ppt_fwd = 2, ppt_bwd = 1;         // pixels per thread of the blend kernels
+    int tuned_fwd = 0, tuned_bwd = 0;     // vg_autotune's choice (0: none yet)
     uint32_t *h_total = nullptr;         // pinned: [0..1] instance total (u64), [2] look-back timeout flag
 
     // per-stage event timing (vg_profile_enable)
@@ -412,8 +413,8 @@ vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera
     ws->n_pixels = pix_base;
     ws->bp.tau_skip = opts->alpha_min > 0.0f ? (float)(-std::log1p(-(double)opts->alpha_min)) : 0.0f;
     ws->bp.tau_max = opts->tau_max;
-    ws->ppt_fwd = opts->pixels_per_thread ? opts->pixels_per_thread : kDefaultPixelsFwd;
-    ws->ppt_bwd = opts->pixels_per_thread ? opts->pixels_per_thread : kDefaultPixelsBwd;
+    ws->ppt_fwd = opts->pixels_per_thread ? opts->pixels_per_thread : (ws->tuned_fwd ? ws->tuned_fwd : kDefaultPixelsFwd);
+    ws->ppt_bwd = opts->pixels_per_thread ? opts->pixels_per_thread : (ws->tuned_bwd ? ws->tuned_bwd : kDefaultPixelsBwd);
     ws->bp.T_stop = opts->T_stop;
     for (int c = 0; c < 3; ++c) ws->bp.bg[c] = opts->bg[c];
     ws->bp.pixel_test = ws->bp.tau_skip < opts->tau_cut ? 1 : 0;
@@ -728,6 +729,71 @@ vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n
     return VG_OK;
 }
 
+vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t *ppt_bwd, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (ws->stage < 2) return fail(ws, VG_ERR_STATE, "vg_autotune before vg_bin_sort");
+    if (reps < 1) reps = 3;
+    cudaStream_t st = (cudaStream_t)stream;
+    VG_TRY(ensure(ws, ws->S_fin, (size_t)ws->n_pixels, "pixel state"));
+    VG_TRY(ensure(ws, ws->T_fin, (size_t)ws->n_pixels, "pixel state"));
+    VG_TRY(ensure(ws, ws->nlast, (size_t)ws->n_pixels, "pixel state"));
+    VG_TRY(ensure(ws, ws->grad, (size_t)ws->n_items * kGradN, "gradient accumulators"));
+    // scratch image and loss gradient (zero: the timing does not depend on the values)
+    float *rgb = nullptr, *dl = nullptr;
+    const size_t px3 = (size_t)std::max<long long>(ws->n_pixels, 1) * 3;
+    VG_CUDA(ws, cudaMalloc((void **)&rgb, px3 * sizeof(float)));
+    cudaError_t e = cudaMalloc((void **)&dl, px3 * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(rgb);
+        return fail(ws, VG_ERR_OOM, "autotune scratch");
+    }
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int cand[3] = {1, 2, 4};
+    float best_f = 1e30f, best_b = 1e30f;
+    int pf = kDefaultPixelsFwd, pb = kDefaultPixelsBwd;
+    e = cudaMemsetAsync(dl, 0, px3 * sizeof(float), st);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+        float tf = 0.0f, tb = 0.0f;
+        for (int r = 0; r <= reps && e == cudaSuccess; ++r) {   // the first round warms up
+            cudaEventRecord(a, st);
+            e = launch_render_fwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles, ws->ranges.p,
+                                  ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, cand[i], rgb, nullptr, ws->T_fin.p,
+                                  ws->S_fin.p, ws->nlast.p, nullptr, st, &ws->launches);
+            cudaEventRecord(b, st);
+            cudaEventSynchronize(b);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (r) tf += ms;
+            if (e != cudaSuccess) break;
+            e = cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st);
+            cudaEventRecord(a, st);
+            if (e == cudaSuccess)
+                e = launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
+                                      ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, cand[i], ws->T_fin.p,
+                                      ws->S_fin.p, ws->nlast.p, dl, nullptr, ws->grad.p, nullptr, st, &ws->launches);
+            cudaEventRecord(b, st);
+            cudaEventSynchronize(b);
+            cudaEventElapsedTime(&ms, a, b);
+            if (r) tb += ms;
+        }
+        if (tf < best_f) best_f = tf, pf = cand[i];
+        if (tb < best_b) best_b = tb, pb = cand[i];
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(rgb);
+    cudaFree(dl);
+    if (e != cudaSuccess) return fail(ws, VG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    ws->tuned_fwd = ws->ppt_fwd = pf;
+    ws->tuned_bwd = ws->ppt_bwd = pb;
+    ws->stage = 2;   // the replay state no longer belongs to a vg_render_fwd of the caller
+    if (ppt_fwd) *ppt_fwd = pf;
+    if (ppt_bwd) *ppt_bwd = pb;
+    return VG_OK;
+}
+
 vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream) {
     if (!ws || !out) return VG_ERR_INVALID_ARG;
     VG_CUDA(ws, cudaStreamSynchronize((cudaStream_t)stream));
@@ -811,6 +877,34 @@ vg_status vg_read_keys(vg_workspace *ws, uint32_t *depth_bits, int32_t *rect) {
         rect[4 * i + 2] = r[i].z;
         rect[4 * i + 3] = r[i].w;
     }
+    return VG_OK;
+}
+
+vg_status vg_read_bins_range(vg_workspace *ws, int64_t tile0, int64_t tile1, int64_t *counts, int32_t *sorted_item,
+                             int64_t cap, int64_t *n_out) {
+    if (!ws || !counts || !n_out || tile0 < 0 || tile1 < tile0) return VG_ERR_INVALID_ARG;
+    if (ws->stage < 2 && !ws->tomo_read) return fail(ws, VG_ERR_STATE, "no bin_sort to read");
+    if (tile1 > ws->n_tiles) return fail(ws, VG_ERR_INVALID_ARG, "tile range beyond the last tile");
+    VG_CUDA(ws, cudaDeviceSynchronize());
+    *n_out = 0;
+    if (tile1 == tile0) return VG_OK;
+    std::vector<uint2> rg((size_t)(tile1 - tile0));
+    VG_CUDA(ws, cudaMemcpy(rg.data(), ws->ranges.p + tile0, rg.size() * sizeof(uint2), cudaMemcpyDeviceToHost));
+    // the lists of consecutive tiles are consecutive in the sorted instance array
+    long long first = -1, last = -1, n = 0;
+    for (size_t t = 0; t < rg.size(); ++t) {
+        counts[t] = (int64_t)(rg[t].y - rg[t].x);
+        n += counts[t];
+        if (counts[t] > 0) {
+            if (first < 0) first = rg[t].x;
+            last = rg[t].y;
+        }
+    }
+    if (n > cap || (n > 0 && !sorted_item)) return fail(ws, VG_ERR_INVALID_ARG, "sorted_item capacity too small");
+    if (n > 0 && last - first != n) return fail(ws, VG_ERR_STATE, "tile lists are not contiguous");
+    if (n > 0)
+        VG_CUDA(ws, cudaMemcpy(sorted_item, ws->inst_item + first, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    *n_out = n;
     return VG_OK;
 }
 

@@ -1,0 +1,251 @@
+"""Parity at the full sizes of the workloads, on outputs the oracle computes one by one:
+sampled pixels (and the gradients those pixels induce), sampled Gaussians' keys and sampled
+tiles' lists, on a subset of the views (or tomography angles).  The GPU runs each workload in
+its own launch configuration."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import check_grads, dev_scene, grad_rel_err, run_backward, vg_opts
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+def _bases(cams):
+    pb, tb = [0], [0]
+    for c in cams:
+        pb.append(pb[-1] + c.width * c.height)
+        tb.append(tb[-1] + ((c.width + 15) // 16) * ((c.height + 15) // 16))
+    return pb, tb
+
+
+def _pixel_sample(cams, n_per_view, seed, whole_tiles=2):
+    """Per view: random pixels plus every pixel of a few random tiles."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in cams:
+        m = np.zeros(c.width * c.height, np.int32)
+        m[rng.choice(c.width * c.height, size=min(n_per_view, c.width * c.height), replace=False)] = 1
+        tx, ty = (c.width + 15) // 16, (c.height + 15) // 16
+        for t in rng.choice(tx * ty, size=whole_tiles, replace=False):
+            y0, x0 = (t // tx) * 16, (t % tx) * 16
+            for y in range(y0, min(y0 + 16, c.height)):
+                m[y * c.width + x0: y * c.width + min(x0 + 16, c.width)] = 1
+        out.append(m)
+    return out
+
+
+def _check_subset(vg, ws, scene, cams, views, o, rgb_gpu, seed, compat, n_key=200_000, n_tiles=40):
+    """keys of sampled Gaussians, lists of sampled tiles and sampled pixels, per view."""
+    sub = [cams[v] for v in views]
+    L = oracle.lists(scene, sub, o)
+    N = scene.n
+    depth, rect = ws.read_keys()
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(N, size=min(n_key, N), replace=False)
+    pb_gpu, tb_gpu = _bases(cams)
+    pb_sub, _ = _bases(sub)
+    masks = _pixel_sample(sub, 1500, seed)
+    ref_rgb, ref_T, _ = oracle.render(scene, sub, o, L=L, mask=np.concatenate(masks))
+    errs = {}
+    for i, v in enumerate(views):
+        od = L["depth"][i].reshape(-1)
+        orc = L["rect"][i].reshape(-1, 4)
+        assert np.array_equal(depth[v * N + pick], od[pick]), v
+        assert np.array_equal(rect[v * N + pick], orc[pick]), v
+        ntv = ((cams[v].width + 15) // 16) * ((cams[v].height + 15) // 16)
+        for t in rng.choice(ntv, size=min(n_tiles, ntv), replace=False):
+            a = int(L["tile_start"][L["tile_base"][i] + t])
+            b = int(L["tile_start"][L["tile_base"][i] + t + 1])
+            counts, items = ws.read_bins_range(tb_gpu[v] + t, tb_gpu[v] + t + 1, b - a)
+            assert counts[0] == b - a and np.array_equal(items - v * N, L["sorted_g"][a:b]), (v, t)
+        sel = masks[i].astype(bool)
+        got = rgb_gpu[pb_gpu[v]:pb_gpu[v + 1]][sel]
+        err = np.max(np.abs(got - ref_rgb[i].reshape(-1, 3)[sel]), axis=1)
+        errs[v] = (float(err.max()), float(np.mean(err > IMG_TOL)), int(sel.sum()))
+        if compat:   # threshold decisions (alpha_min, tau_max, T_stop) may flip at a few pixels
+            assert errs[v][1] < 0.005 and errs[v][0] < 0.02, (v, errs[v])
+        else:
+            assert errs[v][0] < IMG_TOL, (v, errs[v])
+    print("per-view image error vs the FP64 oracle (max abs, fraction > 1e-4, pixels):", errs)
+    return L, masks, pb_sub
+
+
+def _dequantised(scene, rec, sh):
+    import torch
+    dts = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+    r = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(dts[dt]).float().numpy()
+    return synth.Scene(r(scene.mu, rec), r(scene.scale, rec), r(scene.quat, rec), r(scene.kappa, rec),
+                       r(scene.sh, sh), scene.sh_degree), dts[rec], dts[sh]
+
+
+def test_config2_full_size_exact(gpu_lib):
+    """1M Gaussians at 1280x832, exact mode: all keys and lists bit-exact, sampled pixels, and
+    the gradient of a loss on those pixels."""
+    import torch
+    vg = gpu_lib
+    scene, cams, _ = synth.config2(1.0)
+    o = dict(oracle.EXACT, bg=(0.2, 0.4, 0.6))
+    g = dev_scene(vg, scene)
+    ws = vg.Workspace()
+    P = cams[0].width * cams[0].height
+    rgb, T = torch.empty(P, 3, device="cuda:0"), torch.empty(P, device="cuda:0")
+    ws.preprocess(g, cams, vg_opts(vg, o))
+    ws.bin_sort()
+    ws.render_fwd(rgb, T)
+    L = oracle.lists(scene, cams, o)
+    depth, rect = ws.read_keys()
+    assert np.array_equal(depth, L["depth"].reshape(-1)) and np.array_equal(rect, L["rect"].reshape(-1, 4))
+    ts, items = ws.read_bins()
+    assert np.array_equal(ts, L["tile_start"]) and np.array_equal(items, L["sorted_g"])
+    mask = _pixel_sample(cams, 3000, 11)[0]
+    sel = mask.astype(bool)
+    ref_rgb, ref_T, _ = oracle.render(scene, cams, o, L=L, mask=mask)
+    got = rgb.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got[sel] - ref_rgb[0].reshape(-1, 3)[sel])) < IMG_TOL
+    assert np.max(np.abs(T.cpu().numpy()[sel] - ref_T[0].reshape(-1)[sel])) < IMG_TOL
+    rng = np.random.default_rng(12)
+    wr = rng.normal(size=(P, 3)) * mask[:, None]
+    gg = run_backward(vg, ws, g, wr)
+    ref = oracle.render_grad(scene, cams, o, L, wr, mask=mask)
+    check_grads(gg, ref, scene, GRAD_TOL)
+
+
+def test_config2_full_size_compat(gpu_lib):
+    """The bench.py launch configuration (compat thresholds, default pixels per thread)."""
+    import torch
+    vg = gpu_lib
+    scene, cams, _ = synth.config2(1.0)
+    o = oracle.COMPAT
+    g = dev_scene(vg, scene)
+    ws = vg.Workspace()
+    P = cams[0].width * cams[0].height
+    rgb = torch.empty(P, 3, device="cuda:0")
+    ws.preprocess(g, cams, vg_opts(vg, o, flags=vg.FLAG_GRAD_ZERO))
+    ws.bin_sort()
+    ws.render_fwd(rgb)
+    _check_subset(vg, ws, scene, cams, [0], o, rgb.cpu().numpy().astype(np.float64), 13, compat=True,
+                  n_key=scene.n, n_tiles=200)
+
+
+def test_config3_graph_batched_bf16(gpu_lib):
+    """3M Gaussians (BF16 records, FP16 SH), 16 views 640x416..1920x1080 in one launch per stage,
+    fixed capacity, autotuned, the step replayed as a CUDA graph; views 0, 7 and 15 against the
+    oracle on the dequantised parameters."""
+    import torch
+    vg = gpu_lib
+    scene32, cams = synth.config3(1.0)
+    scene, rec_dt, sh_dt = _dequantised(scene32, "bf16", "f16")
+    o = oracle.COMPAT
+    g = dev_scene(vg, scene, rec_dtype=rec_dt, sh_dtype=sh_dt)
+    pb, tb = _bases(cams)
+    P, tiles = pb[-1], tb[-1]
+    ws = vg.Workspace()
+    ws.preprocess(g, cams, vg_opts(vg, o))
+    ws.bin_sort()
+    n_inst = ws.query()["n_instances"]
+    ws.autotune(reps=1)
+    ws.reserve(scene.n * len(cams), int(n_inst * 1.05) + 4096, P, tiles)
+    opts = vg_opts(vg, o, flags=vg.FLAG_FIXED_CAPACITY | vg.FLAG_GRAD_ZERO)
+    dev = torch.device("cuda:0")
+    rgb, dl, loss = torch.empty(P, 3, device=dev), torch.zeros(P, 3, device=dev), torch.zeros(1, device=dev)
+    tgt = torch.zeros(P, 3, device=dev)
+    grads = [torch.empty(g.n, 3, device=dev), torch.empty(g.n, 3, device=dev), torch.empty(g.n, 4, device=dev),
+             torch.empty(g.n, device=dev), torch.empty(tuple(g.sh.shape), device=dev)]
+
+    def step():
+        ws.preprocess(g, cams, opts)
+        ws.bin_sort()
+        ws.render_fwd(rgb)
+        ws.l2_loss(rgb, tgt, 1.0 / (3 * P), loss, dl)
+        ws.render_bwd(dl, None, *grads)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    rgb.fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert ws.query()["n_instances"] == n_inst
+    assert torch.isfinite(grads[0]).all() and torch.isfinite(grads[4]).all()
+    _check_subset(vg, ws, scene, cams, [0, 7, 15], o, rgb.cpu().numpy().astype(np.float64), 31, compat=True)
+
+
+def test_config4_full_size_tomography(gpu_lib):
+    """200,000 Gaussians, 256 angles, 512^2 detector, forward and backward over every angle;
+    three angles (across angle batches) against the oracle at sampled detector pixels, and the
+    gradient of a loss on those pixels."""
+    import torch
+    vg = gpu_lib
+    scene, beam, _ = synth.config4(1.0)
+    pick = [0, 97, 200]
+    rng = np.random.default_rng(41)
+    A, H, W = len(beam.angles), beam.det_h, beam.det_w
+    mask = np.zeros((A, H, W), np.int32)
+    for a in pick:
+        flat_ = mask[a].reshape(-1)
+        flat_[rng.choice(H * W, size=3000, replace=False)] = 1
+        flat_[(256 * W + 256 - 8):(256 * W + 256 + 8)] = 1
+    dL = rng.normal(size=(A, H, W)) * mask
+    g = dev_scene(vg, scene)
+    dev = torch.device("cuda:0")
+    proj = torch.empty(A, H, W, device=dev)
+    grads = [torch.zeros(g.n, 3, device=dev), torch.zeros(g.n, 3, device=dev), torch.zeros(g.n, 4, device=dev),
+             torch.zeros(g.n, device=dev)]
+    ws = vg.Workspace()
+    ws.project_tomo(g, beam, vg.Opts(tau_cut=1e-6), proj,
+                    torch.as_tensor(dL.astype(np.float32)).to(dev), *grads)
+    torch.cuda.synchronize()
+    sub = synth.Beam(beam.angles[pick], W, H, beam.pitch_u, beam.pitch_v, beam.u0, beam.v0)
+    Ls = oracle.tomo_lists(scene, sub, 1e-6)
+    msub = mask[pick]
+    _, ref = oracle.tomo(scene, sub, Ls, mask=msub)
+    got = proj.cpu().numpy()[pick]
+    sel = msub.astype(bool)
+    assert np.max(np.abs(got[sel] - ref[sel])) < IMG_TOL
+    refg = oracle.tomo_grad(scene, sub, Ls, dL[pick], mask=msub)
+    gg = {k: t.cpu().numpy().astype(np.float64) for k, t in zip(("mu", "scale", "quat", "kappa"), grads)}
+    # per Gaussian and parameter block (the render tests' metric): a Gaussian seen by a few
+    # sampled pixels only has tiny components whose FP32 error is small in absolute terms
+    worst = check_grads(gg, refg, scene, GRAD_TOL, keys=("mu", "scale", "quat", "kappa"))
+    print("config 4 gradient block errors (worst, flattened worst):", worst,
+          "element-wise:", {k: grad_rel_err(gg[k], refg[k]) for k in gg})
+
+
+def test_config5_full_size_bf16(gpu_lib):
+    """6M Gaussians (BF16 records), SH degree 3, 8 views of 1920x1080 in one launch per stage
+    with the backward recomputing from the stored per-pixel (T, S, last index); view 3 against
+    the oracle on the dequantised parameters; peak device memory reported."""
+    import torch
+    vg = gpu_lib
+    scene32, cams = synth.config5(1.0)
+    scene, rec_dt, sh_dt = _dequantised(scene32, "bf16", "f32")
+    o = oracle.COMPAT
+    g = dev_scene(vg, scene, rec_dtype=rec_dt, sh_dtype=sh_dt)
+    pb, _ = _bases(cams)
+    P = pb[-1]
+    dev = torch.device("cuda:0")
+    torch.cuda.reset_peak_memory_stats()
+    rgb = torch.empty(P, 3, device=dev)
+    ws = vg.Workspace()
+    ws.preprocess(g, cams, vg_opts(vg, o, flags=vg.FLAG_GRAD_ZERO))
+    ws.bin_sort()
+    ws.render_fwd(rgb)
+    grads = [torch.empty(g.n, 3, device=dev), torch.empty(g.n, 3, device=dev), torch.empty(g.n, 4, device=dev),
+             torch.empty(g.n, device=dev), torch.empty(tuple(g.sh.shape), device=dev)]
+    ws.render_bwd(torch.ones(P, 3, device=dev), None, *grads)
+    q = ws.query()
+    print("config 5: instances", q["n_instances"], "workspace bytes", q["device_bytes"],
+          "torch peak bytes", torch.cuda.max_memory_allocated())
+    assert torch.isfinite(grads[0]).all()
+    _check_subset(vg, ws, scene, cams, [3], o, rgb.cpu().numpy().astype(np.float64), 51, compat=True,
+                  n_key=300_000, n_tiles=30)

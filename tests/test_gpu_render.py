@@ -271,3 +271,32 @@ def test_bins_many_sort_tiles(gpu_lib, mode):
     assert len(items) > 20 * 2048
     assert np.array_equal(ts, L["tile_start"])
     assert np.array_equal(items, L["sorted_g"])
+
+
+def test_autotune_keeps_results(gpu_lib):
+    """vg_autotune times 1/2/4 pixels per thread on the binned workload and keeps the fastest
+    as the workspace default; the blend afterwards still matches the oracle."""
+    import torch
+    vg = gpu_lib
+    scene, cams = _multi_view_scene()
+    o = dict(oracle.EXACT, bg=(0.3, 0.2, 0.1))
+    g = dev_scene(vg, scene)
+    ws = vg.Workspace()
+    ws.preprocess(g, cams, vg_opts(vg, o))
+    ws.bin_sort()
+    pf, pb = ws.autotune(reps=2)
+    assert pf in (1, 2, 4) and pb in (1, 2, 4)
+    P = sum(c.width * c.height for c in cams)
+    rgb = torch.empty(P, 3, device="cuda:0")
+    with pytest.raises(RuntimeError):
+        ws.render_bwd(rgb, None, *[torch.zeros(1, device="cuda:0")] * 5)   # the replay state was reset
+    ws.preprocess(g, cams, vg_opts(vg, o))
+    ws.bin_sort()
+    ws.render_fwd(rgb)
+    ref_rgb, _, _ = oracle.render(scene, cams, o)
+    assert np.max(np.abs(rgb.cpu().numpy() - flat(ref_rgb))) < IMG_TOL
+    rng = np.random.default_rng(3)
+    wr = rng.normal(size=(P, 3))
+    gg = run_backward(vg, ws, g, wr)
+    ref = oracle.render_grad(scene, cams, o, oracle.lists(scene, cams, o), wr)
+    check_grads(gg, ref, scene, GRAD_TOL)
