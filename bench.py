@@ -151,28 +151,24 @@ def peaks():
 
 
 # ----------------------------------------------------------------------------- batched graph path
-def batched_graph(vg, scene, cam0, rgb_view0, n_views, steps, warmup, dev):
-    """The same scene with BF16 parameters and FP16 SH, n_views views at the same resolution
-    (the single-view camera first), fixed-capacity binning and the whole step (preprocess,
-    bin/sort, forward, L2 loss, backward) replayed as one CUDA graph."""
+def graph_step(vg, g, cams, steps, warmup, dev, target_seed=2102):
+    """A whole training step over all `cams` (preprocess, bin/sort, forward, L2 loss, backward)
+    with fixed-capacity binning, autotuned pixels per thread, captured once as a CUDA graph and
+    replayed `steps` times.  Returns the timing, the rendered images and the workspace."""
     import torch
 
     import synth
 
-    cams = [cam0] + synth.fibonacci_cameras(n_views - 1, 4.0, [(cam0.width, cam0.height)] * (n_views - 1))
-    cv = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev).to(dt).contiguous()
-    bf = torch.bfloat16
-    g = vg.Gaussians(cv(scene.mu, bf), cv(scene.scale, bf), cv(scene.quat, bf), cv(scene.kappa, bf),
-                     cv(scene.sh, torch.float16), scene.sh_degree)
     P = sum(c.width * c.height for c in cams)
     tiles = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in cams)
-    tgt = torch.as_tensor(synth.random_image(2102, (P, 3))).to(dev)
+    tgt = torch.as_tensor(synth.random_image(target_seed, (P, 3))).to(dev)
     ws = vg.Workspace()
-    # size the instance capacity from one eager pass (25% headroom)
+    # size the instance capacity from one eager pass (10% headroom), then tune on it
     ws.preprocess(g, cams, vg.Opts.compat())
     ws.bin_sort()
     n_inst = ws.query()["n_instances"]
-    ws.reserve(g.n * n_views, int(n_inst * 1.25) + 4096, P, tiles)
+    ppt = ws.autotune(reps=2)
+    ws.reserve(g.n * len(cams), int(n_inst * 1.10) + 4096, P, tiles)
     opts = vg.Opts.compat(flags=vg.FLAG_GRAD_ZERO | vg.FLAG_FIXED_CAPACITY)
     rgb, T, dl = torch.empty(P, 3, device=dev), torch.empty(P, device=dev), torch.empty(P, 3, device=dev)
     loss = torch.zeros(1, device=dev)
@@ -208,14 +204,69 @@ def batched_graph(vg, scene, cam0, rgb_view0, n_views, steps, warmup, dev):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     q = ws.query()   # raises if the fixed capacity overflowed during the run
+    out = {"views": len(cams), "sizes": sorted({f"{c.width}x{c.height}" for c in cams}),
+           "launch": "fixed-capacity binning, autotuned pixels per thread, whole step replayed as one CUDA graph",
+           "pixels_per_thread": {"fwd": ppt[0], "bwd": ppt[1]},
+           "steps_per_s": steps / t, "views_per_s": steps * len(cams) / t, "ms_per_step": t * 1e3 / steps,
+           "instances": q["n_instances"], "instance_capacity": q["instance_capacity"],
+           "workspace_bytes": q["device_bytes"]}
+    return out, rgb, ws
+
+
+def reduced_gaussians(vg, scene, dev, rec=None, sh=None):
+    import torch
+
+    rec = rec or torch.bfloat16
+    sh = sh or torch.float16
+    cv = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev).to(dt).contiguous()
+    return vg.Gaussians(cv(scene.mu, rec), cv(scene.scale, rec), cv(scene.quat, rec), cv(scene.kappa, rec),
+                        cv(scene.sh, sh), scene.sh_degree)
+
+
+def batched_graph(vg, scene, cam0, rgb_view0, n_views, steps, warmup, dev):
+    """The headline scene with BF16 parameters and FP16 SH, n_views views at the same resolution
+    (the single-view camera first), replayed as one CUDA graph per step."""
+    import synth
+
+    cams = [cam0] + synth.fibonacci_cameras(n_views - 1, 4.0, [(cam0.width, cam0.height)] * (n_views - 1))
+    g = reduced_gaussians(vg, scene, dev)
+    out, rgb, _ = graph_step(vg, g, cams, steps, warmup, dev)
+    out["storage"] = "bf16 mu/scale/quat/kappa, f16 SH; FP32 records and arithmetic"
     P0 = cam0.width * cam0.height
     err = (rgb[:P0] - rgb_view0).abs()
-    return {"views": n_views, "width": cam0.width, "height": cam0.height,
-            "storage": "bf16 mu/scale/quat/kappa, f16 SH; FP32 records and arithmetic",
-            "launch": "fixed-capacity binning, whole step replayed as one CUDA graph",
-            "steps_per_s": steps / t, "views_per_s": steps * n_views / t, "ms_per_step": t * 1e3 / steps,
-            "instances": q["n_instances"], "instance_capacity": q["instance_capacity"],
-            "view0_vs_fp32_max_abs": float(err.max()), "view0_vs_fp32_mean_abs": float(err.mean())}
+    out["view0_vs_fp32_params_max_abs"] = float(err.max())
+    out["view0_vs_fp32_params_mean_abs"] = float(err.mean())
+    out["view0_note"] = "difference from the FP32-parameter image: the quantisation of the inputs"
+    return out
+
+
+def run_batched_config(args):
+    """--workload cfg3 / cfg5: the batched configurations, one JSON line each."""
+    import torch
+
+    import paper_2412_03378_gb300 as vg
+    import synth
+
+    vg.load()
+    dev = torch.device("cuda:0")
+    if args.workload == "cfg3":
+        scene, cams = synth.config3(args.frac)
+        g = reduced_gaussians(vg, scene, dev, torch.bfloat16, torch.float16)
+        name = (f"{scene.n} Gaussians (cluster generator, 40% flattened, SH deg 3), BF16 parameters, FP16 SH, "
+                f"{len(cams)} views 640x416..1920x1080")
+    else:
+        scene, cams = synth.config5(args.frac)
+        g = reduced_gaussians(vg, scene, dev, torch.bfloat16, torch.float32)
+        name = f"{scene.n} Gaussians (cluster generator, SH deg 3), BF16 parameters, {len(cams)} views 1920x1080"
+    torch.cuda.reset_peak_memory_stats()
+    out, _, ws = graph_step(vg, g, cams, args.steps, args.warmup, dev)
+    res = {"metric": "fwd+bwd steps/s (all views per step)", "value": out["steps_per_s"], "unit": "steps/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
+           "higher_is_better": True, "dtype": "f32 arithmetic, bf16/f16 storage", "data": "synthetic",
+           "config": {"workload": name, "frac": args.frac}, "views_per_s": out["views_per_s"],
+           "detail": out, "peak_device_bytes": {"workspace": out["workspace_bytes"],
+                                                "torch": int(torch.cuda.max_memory_allocated())}}
+    print(json.dumps(res), flush=True)
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -561,8 +612,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-views", type=int, default=4,
                     help="views of the BF16 / graph-replayed batched measurement (0: skip it)")
-    ap.add_argument("--workload", choices=["render", "tomo"], default="render",
-                    help="render: the headline training step; tomo: the tomography step (config 4)")
+    ap.add_argument("--workload", choices=["render", "tomo", "cfg3", "cfg5"], default="render",
+                    help="render: the headline training step; tomo: the tomography step (config 4); "
+                         "cfg3 / cfg5: the batched BF16 configurations as one CUDA graph per step")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("note: fewer than 3 warm-up steps")
@@ -570,6 +622,8 @@ def main():
         run_reference(args)
     elif args.workload == "tomo":
         run_tomo(args)
+    elif args.workload in ("cfg3", "cfg5"):
+        run_batched_config(args)
     else:
         run_ours(args)
 
