@@ -29,10 +29,59 @@ _LOCK = threading.Lock()
 _LIB = None
 
 #: exact mode: no alpha skip, no clamp, no early stop; footprint truncated at tau_cut.
-EXACT = dict(alpha_min=0.0, tau_cut=1e-6, tau_max=math.inf, T_stop=0.0, bg=(0.0, 0.0, 0.0), z_near=0.2)
+#: density_theta: the density array holds Eq. 20's theta in [0, 1] instead of kappa;
+#: softplus_beta > 0: colour activation softplus(beta) instead of the clamp at 0 (Supp. D).
+EXACT = dict(alpha_min=0.0, tau_cut=1e-6, tau_max=math.inf, T_stop=0.0, bg=(0.0, 0.0, 0.0), z_near=0.2,
+             density_theta=False, softplus_beta=0.0)
 #: compat mode: the 3DGS thresholds (alpha >= 1/255 blended, alpha <= 0.99, stop at T < 1e-4).
 COMPAT = dict(alpha_min=1.0 / 255.0, tau_cut=-math.log1p(-1.0 / 255.0), tau_max=math.log(100.0),
-              T_stop=1e-4, bg=(0.0, 0.0, 0.0), z_near=0.2)
+              T_stop=1e-4, bg=(0.0, 0.0, 0.0), z_near=0.2, density_theta=False, softplus_beta=0.0)
+
+
+# ------------------------------------------------------------------------------ Eq. 20
+def kappa_from_theta(theta, scale):
+    """Eq. 20: kappa = -ln(1 - 0.99 theta) (1/s_x + 1/s_y + 1/s_z) / 3, in FP64."""
+    theta = np.asarray(theta, np.float64)
+    s = np.asarray(scale, np.float64)
+    return -np.log1p(-0.99 * theta) * (1.0 / s).sum(-1) / 3.0
+
+
+def kappa_from_theta_grad(theta, scale, d_kappa):
+    """Chain dL/dkappa through Eq. 20: returns (dL/dtheta, dL/dscale)."""
+    theta = np.asarray(theta, np.float64)
+    s = np.asarray(scale, np.float64)
+    m = (1.0 / s).sum(-1) / 3.0
+    lnv = -np.log1p(-0.99 * theta)
+    d_theta = d_kappa * 0.99 / (1.0 - 0.99 * theta) * m
+    d_scale = (d_kappa * lnv)[:, None] * (-1.0 / (3.0 * s * s))
+    return d_theta, d_scale
+
+
+def kappa_key_bound(theta, scale):
+    """The FP32 upper bound of Eq. 20's kappa that sizes the footprint, with the GPU's operation
+    order and only correctly rounded operations (no libm): with x = 0.99 theta and
+    1 - x = m 2^-e (m in [0.5, 1)), -ln(1 - x) <= min(x / (1 - x), (e + 1) ln 2)."""
+    f = np.float32
+    th = np.asarray(theta, f)
+    s = np.asarray(scale, f)
+    x = f(0.99) * th
+    om = f(1.0) - x
+    b1 = x / om
+    _, e = np.frexp(om)
+    b2 = (f(1.0) - e.astype(f)) * f(0.6931472)
+    lnb = np.minimum(b1, b2)
+    m = ((f(1.0) / s[:, 0] + f(1.0) / s[:, 1]) + f(1.0) / s[:, 2]) * f(1.0 / 3.0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        out = lnb * m
+    return np.where((th > 0) & (th <= 1), out, f(0.0)).astype(f)
+
+
+def _density(scene, o, key=False):
+    """The density each oracle function receives: kappa itself, or (density_theta) Eq. 20's
+    kappa in FP64, or for the FP32 key function its upper bound."""
+    if not (o or {}).get("density_theta"):
+        return scene.kappa
+    return kappa_key_bound(scene.kappa, scene.scale) if key else kappa_from_theta(scene.kappa, scene.scale)
 
 
 def build(force: bool = False) -> str:
@@ -131,7 +180,7 @@ def _opts_arr(opts):
     o.update(opts or {})
     bg = o["bg"]
     return np.array([o["alpha_min"], o["tau_cut"], o["tau_max"], o["T_stop"], bg[0], bg[1], bg[2],
-                     o["z_near"]], np.float64), o
+                     o["z_near"], o.get("softplus_beta", 0.0)], np.float64), o
 
 
 # ------------------------------------------------------------------------------------------
@@ -140,7 +189,8 @@ def keys(scene, cams, opts=None, tile=(16, 16), with_pixels=False):
     tile rectangles [V, N, 4] = (tx0, ty0, tx1, ty1) inclusive, -1 when culled, and (with
     with_pixels) the pixel footprint rectangles [V, N, 4] = (x0, y0, x1, y1) inclusive."""
     _, o = _opts_arr(opts)
-    mu, sc, q, k, _sh = _scene_arrays(scene)
+    mu, sc, q, _k, _sh = _scene_arrays(scene)
+    k = _c(_density(scene, o, key=True), np.float32)
     cf, wh = cam_arrays(cams)
     V, N = len(cams), scene.n
     depth = np.zeros((V, N), np.uint32)
@@ -182,7 +232,8 @@ def render(scene, cams, opts=None, L=None, brute=False, mask=None, tile=(16, 16)
     oa, o = _opts_arr(opts)
     if L is None:
         L = lists(scene, cams, o, tile)
-    mu, sc, q, k, sh = _scene_arrays(scene, np.float64)
+    mu, sc, q, _k, sh = _scene_arrays(scene, np.float64)
+    k = _c(_density(scene, o), np.float64)
     cf, wh = cam_arrays(cams)
     pb, P = pix_bases(cams)
     rgb = np.zeros((P, 3), np.float64)
@@ -206,7 +257,8 @@ def render_grad(scene, cams, opts, L, dL_drgb, dL_dT=None, mask=None):
     """Analytic FP64 gradient of sum(dL_drgb * rgb) + sum(dL_dT * T_final) with the tile
     lists `L` held fixed.  dL_drgb / dL_dT are per-view lists (or flat arrays)."""
     oa, o = _opts_arr(opts)
-    mu, sc, q, k, sh = _scene_arrays(scene, np.float64)
+    mu, sc, q, _k, sh = _scene_arrays(scene, np.float64)
+    k = _c(_density(scene, o), np.float64)
     cf, wh = cam_arrays(cams)
     pb, P = pix_bases(cams)
     g_rgb = _c(np.concatenate([np.asarray(a, np.float64).reshape(-1, 3) for a in dL_drgb])
@@ -224,6 +276,10 @@ def render_grad(scene, cams, opts, L, dL_drgb, dL_dT=None, mask=None):
                           _p(_c(L["tile_base"], np.int32)), _p(_c(L["prect"], np.int32)), _p(pb), _p(g_rgb),
                           _p(g_T), _p(m),
                           _p(out["mu"]), _p(out["scale"]), _p(out["quat"]), _p(out["kappa"]), _p(out["sh"]))
+    if o.get("density_theta"):   # chain dL/dkappa through Eq. 20: "kappa" becomes dL/dtheta
+        d_theta, d_scale = kappa_from_theta_grad(scene.kappa, scene.scale, out["kappa"])
+        out["kappa"] = d_theta
+        out["scale"] = out["scale"] + d_scale
     return out
 
 
@@ -246,8 +302,9 @@ def sh_basis(degree, direction):
 
 
 # ------------------------------------------------------------------------------ tomography
-def tomo_keys(scene, beam, tau_cut=1e-6, tile=(16, 16), with_pixels=False):
-    mu, sc, q, k, _ = _scene_arrays(scene)
+def tomo_keys(scene, beam, tau_cut=1e-6, tile=(16, 16), with_pixels=False, density_theta=False):
+    mu, sc, q, _k, _ = _scene_arrays(scene)
+    k = _c(_density(scene, dict(density_theta=density_theta), key=True), np.float32)
     A, N = len(beam.angles), scene.n
     rect = np.zeros((A, N, 4), np.int32)
     prect = np.zeros((A, N, 4), np.int32)
@@ -257,8 +314,8 @@ def tomo_keys(scene, beam, tau_cut=1e-6, tile=(16, 16), with_pixels=False):
     return (rect, prect) if with_pixels else rect
 
 
-def tomo_lists(scene, beam, tau_cut=1e-6, tile=(16, 16)):
-    rect, prect = tomo_keys(scene, beam, tau_cut, tile, with_pixels=True)
+def tomo_lists(scene, beam, tau_cut=1e-6, tile=(16, 16), density_theta=False):
+    rect, prect = tomo_keys(scene, beam, tau_cut, tile, with_pixels=True, density_theta=density_theta)
     A = len(beam.angles)
     tx = (beam.det_w + tile[0] - 1) // tile[0]
     ty = (beam.det_h + tile[1] - 1) // tile[1]
@@ -269,11 +326,12 @@ def tomo_lists(scene, beam, tau_cut=1e-6, tile=(16, 16)):
                 tile=tile)
 
 
-def tomo(scene, beam, L=None, brute=False, mask=None, tau_cut=1e-6, tile=(16, 16)):
+def tomo(scene, beam, L=None, brute=False, mask=None, tau_cut=1e-6, tile=(16, 16), density_theta=False):
     """Parallel-beam projection: returns (line_sum, proj = exp(-line_sum)), each [A, H, W]."""
     if L is None and not brute:
-        L = tomo_lists(scene, beam, tau_cut, tile)
-    mu, sc, q, k, _ = _scene_arrays(scene, np.float64)
+        L = tomo_lists(scene, beam, tau_cut, tile, density_theta)
+    mu, sc, q, _k, _ = _scene_arrays(scene, np.float64)
+    k = _c(_density(scene, dict(density_theta=density_theta)), np.float64)
     A = len(beam.angles)
     ls = np.zeros((A, beam.det_h, beam.det_w))
     proj_out = np.zeros((A, beam.det_h, beam.det_w))
@@ -288,8 +346,9 @@ def tomo(scene, beam, L=None, brute=False, mask=None, tau_cut=1e-6, tile=(16, 16
     return ls, proj_out
 
 
-def tomo_grad(scene, beam, L, dL_dproj, mask=None):
-    mu, sc, q, k, _ = _scene_arrays(scene, np.float64)
+def tomo_grad(scene, beam, L, dL_dproj, mask=None, density_theta=False):
+    mu, sc, q, _k, _ = _scene_arrays(scene, np.float64)
+    k = _c(_density(scene, dict(density_theta=density_theta)), np.float64)
     A, N = len(beam.angles), scene.n
     out = dict(mu=np.zeros((N, 3)), scale=np.zeros((N, 3)), quat=np.zeros((N, 4)), kappa=np.zeros(N))
     m = None if mask is None else _c(mask, np.int32)
@@ -298,4 +357,8 @@ def tomo_grad(scene, beam, L, dL_dproj, mask=None):
                         _p(L["tile_start"]), _p(L["sorted_g"]), _p(_c(L["prect"], np.int32)),
                         _p(_c(dL_dproj, np.float64)), _p(m),
                         _p(out["mu"]), _p(out["scale"]), _p(out["quat"]), _p(out["kappa"]))
+    if density_theta:
+        d_theta, d_scale = kappa_from_theta_grad(scene.kappa, scene.scale, out["kappa"])
+        out["kappa"] = d_theta
+        out["scale"] = out["scale"] + d_scale
     return out

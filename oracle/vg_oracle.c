@@ -483,9 +483,25 @@ static void pixel_dir(const cam64 *c, int x, int y, double d[3])
     for (int k = 0; k < 3; ++k) d[k] /= n;
 }
 
-/* View-dependent colour: rgb = max(sum_k sh_k Y_k(dir) + 0.5, 0), dir = (mu - o)/|mu - o|. */
+/* Output activation of the colour: the clamp max(x, 0), or with beta > 0 the softplus
+ * (1/beta) ln(1 + e^(beta x)) (Supp. D, beta = 10), and its derivative. */
+static double colour_act(double x, double beta)
+{
+    if (!(beta > 0)) return x > 0 ? x : 0;
+    const double t = beta * x;
+    return (t > 0 ? t + log1p(exp(-t)) : log1p(exp(t))) / beta;
+}
+
+static double colour_act_grad(double x, double beta)
+{
+    if (!(beta > 0)) return x > 0 ? 1.0 : 0.0;
+    return 1.0 / (1.0 + exp(-beta * x));
+}
+
+/* View-dependent colour: rgb = act(sum_k sh_k Y_k(dir) + 0.5), dir = (mu - o)/|mu - o|, act the
+ * clamp at 0 or the softplus (see colour_act). */
 static void colour64(const double *sh, int deg, const gauss64 *G, const double o[3], double rgb[3],
-                     double raw[3])
+                     double raw[3], double beta)
 {
     double dir[3], n2 = 0;
     for (int k = 0; k < 3; ++k) {
@@ -501,7 +517,7 @@ static void colour64(const double *sh, int deg, const gauss64 *G, const double o
         double acc = 0.5;
         for (int k = 0; k < K; ++k) acc += sh[3 * k + ch] * Y[k];
         raw[ch] = acc;
-        rgb[ch] = acc > 0 ? acc : 0;
+        rgb[ch] = colour_act(acc, beta);
     }
 }
 
@@ -555,7 +571,8 @@ void orc_render(int n, const double *mu, const double *scale, const double *quat
         cam64 cam;
         cam_setup(cam_f + 16 * v, cam_wh + 2 * v, &cam);
         double raw[3];
-        for (int g = 0; g < n; ++g) colour64(sh + (size_t)g * K * 3, sh_degree, &G[g], cam.o, col + 3 * g, raw);
+        for (int g = 0; g < n; ++g)
+            colour64(sh + (size_t)g * K * 3, sh_degree, &G[g], cam.o, col + 3 * g, raw, opts[8]);
         int64_t n_ord = 0;
         if (brute) {
             for (int g = 0; g < n; ++g) {
@@ -711,7 +728,8 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
         cam64 cam;
         cam_setup(cam_f + 16 * v, cam_wh + 2 * v, &cam);
         double raw[3];
-        for (int g = 0; g < n; ++g) colour64(sh + (size_t)g * K * 3, sh_degree, &G[g], cam.o, col + 3 * g, raw);
+        for (int g = 0; g < n; ++g)
+            colour64(sh + (size_t)g * K * 3, sh_degree, &G[g], cam.o, col + 3 * g, raw, opts[8]);
         memset(acc, 0, (size_t)(n > 0 ? n : 1) * ACC_N * sizeof(double));
         const int W = cam.W, H = cam.H;
         const int tiles_x = (W + tile_w - 1) / tile_w;
@@ -781,9 +799,9 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
             chain_P(&G[g], A, dscale + 3 * g, dquat + 4 * g);
             for (int k = 0; k < 3; ++k) dmu[3 * g + k] += A[9 + k];
             dkappa[g] += A[12];
-            /* colour: rgb = max(sh . Y(dir) + 0.5, 0), dir = (mu - o)/|mu - o| */
+            /* colour: rgb = act(sh . Y(dir) + 0.5), dir = (mu - o)/|mu - o| */
             double rgb[3], rw[3], dir[3], n2 = 0;
-            colour64(sh + (size_t)g * K * 3, sh_degree, &G[g], cam.o, rgb, rw);
+            colour64(sh + (size_t)g * K * 3, sh_degree, &G[g], cam.o, rgb, rw, opts[8]);
             for (int k = 0; k < 3; ++k) {
                 dir[k] = G[g].mu[k] - cam.o[k];
                 n2 += dir[k] * dir[k];
@@ -795,8 +813,8 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
             sh_grad(sh_degree, dir, dY);
             double gdir[3] = {0, 0, 0};
             for (int ch = 0; ch < 3; ++ch) {
-                if (!(rw[ch] > 0)) continue;
-                double gch = A[13 + ch];
+                const double gch = A[13 + ch] * colour_act_grad(rw[ch], opts[8]);
+                if (gch == 0) continue;
                 for (int k = 0; k < K; ++k) {
                     dsh[((size_t)g * K + k) * 3 + ch] += gch * Y[k];
                     for (int j = 0; j < 3; ++j) gdir[j] += gch * sh[((size_t)g * K + k) * 3 + ch] * dY[k][j];

@@ -11,7 +11,10 @@
  * The FP64 paths (render, gradient, tomography, tau) take double parameters so that
  * finite differences can perturb them; the key functions take the FP32 values the GPU sees.
  *
- * Options are double[8] = { alpha_min, tau_cut, tau_max, T_stop, bg_r, bg_g, bg_b, z_near }.
+ * Options are double[9] = { alpha_min, tau_cut, tau_max, T_stop, bg_r, bg_g, bg_b, z_near,
+ * softplus_beta }; softplus_beta > 0 replaces the colour clamp max(x, 0) by the softplus
+ * (1/beta) ln(1 + e^(beta x)) (Supp. D).  The density reparameterisation of Eq. 20 is applied
+ * by the Python wrapper (kappa from theta and the scales) before these functions are called.
  */
 #ifndef VG_ORACLE_H
 #define VG_ORACLE_H

@@ -313,7 +313,7 @@ def _fd_check(f, x, g_an, idx, h_rel=1e-5, rtol=1e-6):
         assert abs(fd - g_an.flat[i]) / den < rtol, (i, fd, g_an.flat[i])
 
 
-@pytest.mark.parametrize("variant", ["exact", "clamped"])
+@pytest.mark.parametrize("variant", ["exact", "clamped", "theta_softplus"])
 def test_render_gradient_matches_finite_differences(variant):
     """Analytic FP64 gradient of the blend (tile lists held fixed) vs central differences."""
     rng = np.random.default_rng(11)
@@ -326,6 +326,9 @@ def test_render_gradient_matches_finite_differences(variant):
     opts = dict(oracle.EXACT, bg=(0.3, 0.1, 0.6))
     if variant == "clamped":
         opts["tau_max"] = 1.2
+    if variant == "theta_softplus":   # Eq. 20 density (kappa holds theta) and softplus colour
+        opts.update(density_theta=True, softplus_beta=10.0)
+        scene.kappa = rng.uniform(0.05, 0.95, scene.n)
     L = oracle.lists(scene, cams, opts)
     wr = [rng.normal(size=(c.height, c.width, 3)) for c in cams]
     wT = [rng.normal(size=(c.height, c.width)) for c in cams]
@@ -379,19 +382,67 @@ def test_tomography_order_independent_and_tiled():
     assert np.max(np.abs(ls - lsb)) <= 1e-6 * scene.n
 
 
-def test_tomography_gradient_matches_finite_differences():
+@pytest.mark.parametrize("theta", [False, True])
+def test_tomography_gradient_matches_finite_differences(theta):
     rng = np.random.default_rng(4)
     scene = synth.tomo_scene(7, 77, log_scale=(-2.5, -1.8))
     scene = synth.Scene(*(np.asarray(getattr(scene, f), np.float64) for f in ("mu", "scale", "quat", "kappa", "sh")), 0)
+    if theta:   # Eq. 20: the density array holds theta
+        scene.kappa = rng.uniform(0.05, 0.95, scene.n)
     beam = synth.parallel_beam(2, det=24, extent=2.4)
-    L = oracle.tomo_lists(scene, beam)
+    L = oracle.tomo_lists(scene, beam, density_theta=theta)
     w = rng.normal(size=(2, 24, 24))
 
     def loss():
-        _, pr = oracle.tomo(scene, beam, L)
+        _, pr = oracle.tomo(scene, beam, L, density_theta=theta)
         return float(np.sum(pr * w))
 
-    g = oracle.tomo_grad(scene, beam, L, w)
+    g = oracle.tomo_grad(scene, beam, L, w, density_theta=theta)
     for name, arr in (("mu", scene.mu), ("scale", scene.scale), ("quat", scene.quat), ("kappa", scene.kappa)):
         assert np.max(np.abs(g[name])) > 0
         _fd_check(loss, arr, g[name], range(arr.size), rtol=2e-6)
+
+
+# ------------------------------------------------------------------ Eq. 20 and the softplus colour
+@pytest.mark.parametrize("theta", [0.0, 0.3, 0.9, 1.0])
+def test_density_reparam_centre_opacity_is_scale_independent(theta):
+    """Eq. 20 with an isotropic Gaussian: kappa = -ln(1 - 0.99 theta) / s, so the ray through
+    the mean sees tau = kappa sqrt(2 pi) s = -sqrt(2 pi) ln(1 - 0.99 theta) whatever the scale:
+    alpha = 1 - (1 - 0.99 theta)^sqrt(2 pi) (the reparameterisation's purpose, Sec. 5)."""
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 33, 33, 30.0)   # a pixel centre on the axis
+    th = float(np.float32(theta))                                              # theta as stored
+    want = 1.0 - (1.0 - 0.99 * th) ** math.sqrt(2.0 * math.pi)
+    q = synth.random_unit_quats(np.random.default_rng(5), 1)[0]
+    got = []
+    for s in (0.03, 0.1, 0.3):
+        scene = one_gaussian((0.0, 0.0, 0.0), (s, s, s), q, theta)
+        opts = dict(oracle.EXACT, density_theta=True)
+        _, T, _ = oracle.render(scene, [cam], opts, brute=True)
+        got.append(1.0 - T[0][16, 16])
+    assert np.max(np.abs(np.array(got) - want)) < 1e-12, (got, want)
+
+
+def test_density_key_bound_is_conservative():
+    """The FP32 bound that sizes footprints under Eq. 20 is never below the density and at most
+    ~1.6x above it, over theta in [0, 1] and scales over three decades."""
+    rng = np.random.default_rng(6)
+    theta = np.concatenate([[0.0, 1e-7, 1e-3, 0.5, 0.55, 0.6, 0.99, 1.0], rng.uniform(0, 1, 20000)]).astype(np.float32)
+    scale = np.exp(rng.uniform(-7, 0, (theta.size, 3))).astype(np.float32)
+    bound = oracle.kappa_key_bound(theta, scale).astype(np.float64)
+    exact = oracle.kappa_from_theta(theta.astype(np.float64), scale.astype(np.float64))
+    pos = theta > 0
+    assert np.all(bound[~pos] == 0)
+    assert np.all(bound[pos] >= exact[pos] * (1 - 1e-6))
+    assert np.max(bound[pos] / exact[pos]) < 1.6
+
+
+def test_softplus_colour_tends_to_the_clamp():
+    """softplus_beta(x) = ln(1 + e^(beta x)) / beta lies within ln 2 / beta of max(x, 0)."""
+    scene = synth.uniform_scene(40, 61, log_scale=(-2.5, -1.5), sh_degree=2, sh_std=0.6)
+    cams = [synth.look_at((0.2, 0.1, -4.0), (0.0, 0.0, 0.0), 24, 20, 40.0)]
+    base = dict(oracle.EXACT, bg=(0.1, 0.2, 0.3))
+    ref, _, _ = oracle.render(scene, cams, base)
+    for beta in (1e3, 1e5):
+        got, _, _ = oracle.render(scene, cams, dict(base, softplus_beta=beta))
+        err = np.max(np.abs(got[0] - ref[0]))
+        assert 0 < err <= math.log(2.0) / beta + 1e-12, (beta, err)
