@@ -107,6 +107,8 @@ typedef struct {
                                    0 = the library defaults (forward 2, backward 1, the
                                    fastest measured).  Results are identical; only speed
                                    differs. */
+    float softplus_beta;  /* 0: rgb = max(sh . Y + 0.5, 0); > 0: rgb = softplus of the same with
+                             this beta, ln(1 + e^(beta x)) / beta (Supp. D uses 10) */
 } vg_opts;
 
 #define VG_FLAG_FIXED_CAPACITY 1u  /* vg_bin_sort never synchronises: the instance count stays
@@ -119,6 +121,13 @@ typedef struct {
                                       synchronisation, so it can be captured in a CUDA graph. */
 #define VG_FLAG_GRAD_ZERO 4u       /* render_bwd / project_tomo zero their gradient outputs
                                       before accumulating into them                        */
+#define VG_FLAG_DENSITY_THETA 8u   /* the density input holds Eq. 20's theta in [0, 1]:
+                                      kappa = -ln(1 - 0.99 theta) (1/s_x + 1/s_y + 1/s_z) / 3;
+                                      dkappa then receives dL/dtheta and dscale includes the
+                                      scales' share through kappa.  Footprints are sized
+                                      with an FP32 upper bound of kappa (exact operations
+                                      only: min(x / (1 - x), (1 - e) ln 2) for -ln(1 - x),
+                                      1 - x = m 2^e) */
 #define VG_FLAG_COUNT_PAIRS 2u     /* render_fwd / render_bwd also count evaluated (pixel,
                                       Gaussian) pairs into vg_stats (slower; for roofline) */
 

@@ -190,6 +190,8 @@ GaussIn to_in(const vg_gaussians *g) {
     r.sh_dtype = g->sh_dtype;
     r.n = g->n;
     r.sh_degree = g->sh_degree;
+    r.density_theta = 0;
+    r.softplus_beta = 0.0f;
     return r;
 }
 
@@ -390,8 +392,12 @@ vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera
         pix_base += (long long)c.width * c.height;
         if (tile_base >= (1LL << 30)) return fail(ws, VG_ERR_INVALID_ARG, "too many tiles");
     }
+    if (!(opts->softplus_beta >= 0.0f) || !std::isfinite(opts->softplus_beta))
+        return fail(ws, VG_ERR_INVALID_ARG, "softplus_beta must be finite and >= 0");
     ws->opts = *opts;
     ws->g = to_in(g);
+    ws->g.density_theta = (opts->flags & VG_FLAG_DENSITY_THETA) ? 1 : 0;
+    ws->g.softplus_beta = opts->softplus_beta;
     ws->tomo_read = false;
     VG_TRY(reserve_items(ws, n_items));
     VG_TRY(ensure(ws, ws->views, (size_t)n_views, "views"));
@@ -620,6 +626,7 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
     const long long det_px = (long long)beam->det_w * beam->det_h;
     ws->opts = *opts;
     ws->g = to_in(g);
+    ws->g.density_theta = (opts->flags & VG_FLAG_DENSITY_THETA) ? 1 : 0;
     ws->stage = 0;   // the render state of this workspace is overwritten below
     ws->views_valid = false;
     std::vector<float> cs(2 * (size_t)A);

@@ -35,6 +35,55 @@ __device__ __forceinline__ void load_gauss(const GaussIn &g, long long i, float 
     kap = ld_f<RT>(k, i);
 }
 
+// ------------------------------------------------------------------ density (Eq. 20)
+// With GaussIn::density_theta the density input is theta in [0, 1] and
+//   kappa = -ln(1 - 0.99 theta) (1/s_x + 1/s_y + 1/s_z) / 3   (Eq. 20).
+// kap_key, which sizes the footprint in the bit-exact key function, is an upper bound of kappa
+// made of correctly rounded operations and the binary exponent only: with x = 0.99 theta and
+// 1 - x = m 2^e (m in [0.5, 1)), -ln(1 - x) <= min(x / (1 - x), (1 - e) ln 2).
+struct Density {
+    float kap_key;   // key function (validity and footprint)
+    float kap;       // the record's amplitude
+    float lnv;       // -ln(1 - 0.99 theta)    (density_theta only)
+    float m;         // (1/s_x + 1/s_y + 1/s_z) / 3
+};
+
+__device__ __forceinline__ Density density_of(const GaussIn &g, float kin, const float s[3]) {
+    Density d;
+    if (!g.density_theta) {
+        d.kap_key = d.kap = kin;
+        d.lnv = d.m = 0.0f;
+        return d;
+    }
+    d.m = __fmul_rn(__fadd_rn(__fadd_rn(__fdiv_rn(1.0f, s[0]), __fdiv_rn(1.0f, s[1])), __fdiv_rn(1.0f, s[2])),
+                    0.33333334f);
+    if (!(kin > 0.0f && kin <= 1.0f)) {   // outside (0, 1] (or NaN): no density, culled
+        d.kap_key = d.kap = d.lnv = 0.0f;
+        return d;
+    }
+    const float x = __fmul_rn(0.99f, kin);
+    const float om = __fsub_rn(1.0f, x);
+    const float b1 = __fdiv_rn(x, om);
+    const int e = (int)((__float_as_uint(om) >> 23) & 0xFFu) - 126;   // om = m 2^e, m in [0.5, 1)
+    const float b2 = __fmul_rn((float)(1 - e), 0.6931472f);
+    d.kap_key = __fmul_rn(fminf(b1, b2), d.m);
+    d.lnv = -log1pf(-x);
+    d.kap = d.lnv * d.m;
+    return d;
+}
+
+// Colour activation and its derivative: the clamp at 0, or the softplus (1/beta) ln(1 + e^(beta x))
+__device__ __forceinline__ float colour_act(float x, float beta) {
+    if (!(beta > 0.0f)) return fmaxf(x, 0.0f);
+    const float t = beta * x;
+    return (t > 0.0f ? t + log1pf(__expf(-t)) : log1pf(__expf(t))) / beta;
+}
+
+__device__ __forceinline__ float colour_act_grad(float x, float beta) {
+    if (!(beta > 0.0f)) return x > 0.0f ? 1.0f : 0.0f;
+    return 1.0f / (1.0f + __expf(-beta * x));
+}
+
 // Validity, unit quaternion, rotation Rq and world covariance Sigma = Rq S^2 Rq^T, FP32 with
 // a fixed operation order (the key function's first stage).
 __device__ __forceinline__ bool key_cov(const float mu[3], const float s[3], const float q[4], float kap,
@@ -447,7 +496,7 @@ __device__ __forceinline__ void warp_store_rows(float *dst, int rows, int w, con
 
 // view-dependent colour from a staged SH row (same operation order as eval_colour)
 __device__ __forceinline__ void eval_colour_row(int deg, const float *row, const float dir[3], float rgb[3],
-                                                float raw[3]) {
+                                                float raw[3], float beta = 0.0f) {
     float Y[16];
     sh_basis(deg, dir[0], dir[1], dir[2], Y);
     const int K = (deg + 1) * (deg + 1);
@@ -461,7 +510,7 @@ __device__ __forceinline__ void eval_colour_row(int deg, const float *row, const
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         raw[c] = acc[c];
-        rgb[c] = fmaxf(acc[c], 0.0f);
+        rgb[c] = colour_act(acc[c], beta);
     }
 }
 

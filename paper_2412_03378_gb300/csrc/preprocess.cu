@@ -38,18 +38,19 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
         uint32_t cnt = 0, dk = 0xFFFFFFFFu;
         short4 rc = make_short4(-1, -1, -1, -1), prc = rc;
         if (lane < nloc) {
-            float mu[3], s[3], q[4], kap;
-            load_gauss<RT>(g, gi, mu, s, q, kap);
+            float mu[3], s[3], q[4], kin;
+            load_gauss<RT>(g, gi, mu, s, q, kin);
+            const Density dn = density_of(g, kin, s);
             float Sig[9], Rq[9], qn[4], smax, Zf;
-            if (key_cov(mu, s, q, kap, Sig, Rq, qn, smax))
-                state = key_persp(V, mu, Sig, smax, kap, z_near, tau_cut, dk, rc, prc, Zf);
+            if (key_cov(mu, s, q, dn.kap_key, Sig, Rq, qn, smax))
+                state = key_persp(V, mu, Sig, smax, dn.kap_key, z_near, tau_cut, dk, rc, prc, Zf);
             if (state == 2) {
                 cnt = (uint32_t)(rc.z - rc.x + 1) * (uint32_t)(rc.w - rc.y + 1);
                 ItemGeom G;
                 item_geom(V, mu, s, Rq, G);
                 float dir[3], len, rgb[3], raw[3];
                 view_dir(V, mu, dir, len);
-                eval_colour_row(g.sh_degree, row, dir, rgb, raw);
+                eval_colour_row(g.sh_degree, row, dir, rgb, raw, g.softplus_beta);
 #pragma unroll
                 for (int k = 0; k < 9; ++k) {
                     rrow[k] = G.A[k];
@@ -57,7 +58,7 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
                 }
                 rrow[18] = G.px0;
                 rrow[19] = G.py0;
-                rrow[20] = log2f(kap) + kLog2Sqrt2Pi;
+                rrow[20] = log2f(dn.kap) + kLog2Sqrt2Pi;
                 rrow[21] = rgb[0];
                 rrow[22] = rgb[1];
                 rrow[23] = rgb[2];

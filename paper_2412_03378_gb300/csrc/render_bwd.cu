@@ -308,9 +308,11 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
         rows_wait();
         __syncwarp();
         if (lane < nloc) {
-        float mu[3], s[3], q[4], kap, Sig[9], Rq[9], qn[4], smax;
-        load_gauss<RT>(g, gi, mu, s, q, kap);
-        const bool valid = key_cov(mu, s, q, kap, Sig, Rq, qn, smax);
+        float mu[3], s[3], q[4], kin, Sig[9], Rq[9], qn[4], smax;
+        load_gauss<RT>(g, gi, mu, s, q, kin);
+        const Density dn = density_of(g, kin, s);
+        const float kap = dn.kap;
+        const bool valid = key_cov(mu, s, q, dn.kap_key, Sig, Rq, qn, smax);
         float am[3] = {0.0f, 0.0f, 0.0f}, asc[3] = {0.0f, 0.0f, 0.0f}, aq[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ak = 0.0f;
         for (int v = 0; valid && v < n_views; ++v) {
         const long long it = (long long)v * g.n + gi;
@@ -427,7 +429,7 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
             }
             float gc[3], w[16], gd[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) gc[c] = raw[c] > 0.0f ? ga[13 + c] : 0.0f;
+            for (int c = 0; c < 3; ++c) gc[c] = ga[13 + c] * colour_act_grad(raw[c], g.softplus_beta);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 w[k] = 0.0f;
@@ -452,6 +454,11 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
 #pragma unroll
         for (int c = 0; c < 4; ++c) aq[c] += (dqn[c] - qn[c] * dot) / qnorm;
         ak += ga[12] / kap;
+        }
+        if (g.density_theta && valid) {   // Eq. 20: kappa(theta, s); ak = dL/dkappa becomes dL/dtheta
+#pragma unroll
+            for (int c = 0; c < 3; ++c) asc[c] -= ak * dn.lnv / (3.0f * s[c] * s[c]);
+            ak = ak * 0.99f / (1.0f - 0.99f * kin) * dn.m;
         }
         if (zero) {
 #pragma unroll

@@ -86,11 +86,13 @@ k_tomo_preprocess(GaussIn g, const float *__restrict__ cs, int n_angles, int det
         const int a = (int)(it / g.n);
         const long long gi = it - (long long)a * g.n;
         const float ct = cs[2 * a], st = cs[2 * a + 1];
-        float mu[3], s[3], q[4], kap, Sig[9], Rq[9], qn[4], smax, k2;
-        load_gauss<RT>(g, gi, mu, s, q, kap);
+        float mu[3], s[3], q[4], kin, Sig[9], Rq[9], qn[4], smax, k2;
+        load_gauss<RT>(g, gi, mu, s, q, kin);
+        const Density dn = density_of(g, kin, s);
+        const float kap = dn.kap;
         short4 rc = make_short4(-1, -1, -1, -1), prc = rc;
         uint32_t cnt = 0;
-        if (key_cov(mu, s, q, kap, Sig, Rq, qn, smax) && key_k2(kap, smax, tau_cut, k2)) {
+        if (key_cov(mu, s, q, dn.kap_key, Sig, Rq, qn, smax) && key_k2(dn.kap_key, smax, tau_cut, k2)) {
             // key function: orthographic bounding box of the Mahalanobis-k ellipsoid (FP32, fixed order)
             const float um = VG_ADD(VG_MUL(-st, mu[0]), VG_MUL(ct, mu[1]));
             const float vm = mu[2];
@@ -361,9 +363,11 @@ k_tomo_chain(GaussIn g, const float *__restrict__ cs, int n_angles, long long it
         const int a = (int)(it / g.n);
         const long long gi = it - (long long)a * g.n;
         const float ct = cs[2 * a], st = cs[2 * a + 1];
-        float mu[3], s[3], q[4], kap, Sig[9], Rq[9], qn[4], smax;
-        load_gauss<RT>(g, gi, mu, s, q, kap);
-        if (!key_cov(mu, s, q, kap, Sig, Rq, qn, smax)) continue;
+        float mu[3], s[3], q[4], kin, Sig[9], Rq[9], qn[4], smax;
+        load_gauss<RT>(g, gi, mu, s, q, kin);
+        const Density dns = density_of(g, kin, s);
+        const float kap = dns.kap;
+        if (!key_cov(mu, s, q, dns.kap_key, Sig, Rq, qn, smax)) continue;
         TomoGeom G;
         tomo_geom(mu, s, Rq, ct, st, pu, pv, u0, v0, G);
         const float dc0[2] = {a4.x, a4.y}, dc1[2] = {a4.z, a4.w}, dys[2] = {b4.x, b4.y};
@@ -428,6 +432,12 @@ k_tomo_chain(GaussIn g, const float *__restrict__ cs, int n_angles, long long it
         const float gi_mu = -(G.c0[0] * dys[0] + G.c0[1] * dys[1]);
         const float gj_mu = -(G.c1[0] * dys[0] + G.c1[1] * dys[1]);
         const float dm[3] = {-st * gi_mu / pu, ct * gi_mu / pu, gj_mu / pv};
+        float dk = dlnA / kap;   // dL/dkappa; with Eq. 20 it becomes dL/dtheta plus a share of dL/ds
+        if (g.density_theta) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dsc[c] -= dk * dns.lnv / (3.0f * s[c] * s[c]);
+            dk = dk * 0.99f / (1.0f - 0.99f * kin) * dns.m;
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             atomicAdd(&dmu[3 * gi + c], dm[c]);
@@ -435,7 +445,7 @@ k_tomo_chain(GaussIn g, const float *__restrict__ cs, int n_angles, long long it
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) atomicAdd(&dquat[4 * gi + c], (dqn[c] - qn[c] * dot) / qnorm);
-        atomicAdd(&dkappa[gi], dlnA / kap);
+        atomicAdd(&dkappa[gi], dk);
     }
 }
 

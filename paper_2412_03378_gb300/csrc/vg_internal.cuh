@@ -32,6 +32,8 @@ struct ViewInfo {
 struct GaussIn {
     const void *mu, *scale, *quat, *kappa, *sh;
     int rec_dtype, sh_dtype, n, sh_degree;
+    int density_theta;     // the density array holds Eq. 20's theta
+    float softplus_beta;   // colour activation: 0 = clamp at 0, > 0 = softplus(beta)
 };
 
 struct BlendParams {

@@ -13,8 +13,11 @@ def dev_scene(vg, scene, rec_dtype=torch.float32, sh_dtype=torch.float32):
 
 
 def vg_opts(vg, o, flags=0, ppt=0):
+    if o.get("density_theta"):
+        flags |= vg.FLAG_DENSITY_THETA
     return vg.Opts(alpha_min=o["alpha_min"], tau_cut=o["tau_cut"], tau_max=o["tau_max"], T_stop=o["T_stop"],
-                   bg=tuple(o["bg"]), z_near=o["z_near"], flags=flags, pixels_per_thread=ppt)
+                   bg=tuple(o["bg"]), z_near=o["z_near"], flags=flags, pixels_per_thread=ppt,
+                   softplus_beta=o.get("softplus_beta", 0.0))
 
 
 def run_forward(vg, scene, cams, o, ws=None, flags=0, g=None, ppt=0):
@@ -66,8 +69,9 @@ FLAT_ANISO = 20.0     # Gaussians with s_max / s_min above this count as flatten
 FLAT_TOL = 5e-3       # FP32 conditioning of thin Gaussians: error ~ eps * distance / s_min
 
 
-def check_grads(gg, ref, scene, tol, keys=("mu", "scale", "quat", "kappa", "sh")):
-    """Non-flattened Gaussians within tol, flattened ones within FLAT_TOL; returns the worst."""
+def check_grads(gg, ref, scene, tol, keys=("mu", "scale", "quat", "kappa", "sh"), flat_tol=None):
+    """Non-flattened Gaussians within tol, flattened ones within FLAT_TOL (or flat_tol, a dict
+    by parameter or a number); returns the worst."""
     aniso = scene.scale.max(1) / scene.scale.min(1)
     flat_ = aniso > FLAT_ANISO
     worst = {}
@@ -76,5 +80,6 @@ def check_grads(gg, ref, scene, tol, keys=("mu", "scale", "quat", "kappa", "sh")
         assert np.max(np.abs(ref[k])) > 0, k
         worst[k] = (float(e[~flat_].max()) if (~flat_).any() else 0.0, float(e[flat_].max()) if flat_.any() else 0.0)
         assert worst[k][0] < tol, (k, worst[k])
-        assert worst[k][1] < FLAT_TOL, (k, worst[k])
+        ft = flat_tol.get(k, FLAT_TOL) if isinstance(flat_tol, dict) else (flat_tol or FLAT_TOL)
+        assert worst[k][1] < ft, (k, worst[k])
     return worst

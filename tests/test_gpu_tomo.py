@@ -138,3 +138,33 @@ def test_tomo_edge_cases(gpu_lib):
     _, proj, _ = _run(vg, sc, beam)
     _, ref = oracle.tomo(sc, beam)
     assert np.max(np.abs(proj - ref)) < IMG_TOL
+
+
+def test_tomo_density_reparam(gpu_lib):
+    """Tomography with Eq. 20's theta as the density input."""
+    import torch
+
+    from gpu_util import check_grads, dev_scene
+    vg = gpu_lib
+    scene, beam = _cfg4_sampling_case()
+    rng = np.random.default_rng(19)
+    scene.kappa = rng.uniform(0.02, 1.0, scene.n).astype(np.float32)
+    A = len(beam.angles)
+    dL = rng.normal(size=(A, beam.det_h, beam.det_w))
+    g = dev_scene(vg, scene)
+    dev = torch.device("cuda:0")
+    proj = torch.empty(A, beam.det_h, beam.det_w, device=dev)
+    grads = [torch.zeros(scene.n, 3, device=dev), torch.zeros(scene.n, 3, device=dev),
+             torch.zeros(scene.n, 4, device=dev), torch.zeros(scene.n, device=dev)]
+    ws = vg.Workspace()
+    ws.project_tomo(g, beam, vg.Opts(tau_cut=TAU_CUT, flags=vg.FLAG_DENSITY_THETA), proj,
+                    torch.as_tensor(dL.astype(np.float32)).to(dev), *grads)
+    torch.cuda.synchronize()
+    L = oracle.tomo_lists(scene, beam, TAU_CUT, density_theta=True)
+    _, rect = ws.read_keys()
+    assert np.array_equal(rect, L["rect"].reshape(-1, 4))
+    _, ref_proj = oracle.tomo(scene, beam, L, density_theta=True)
+    assert np.max(np.abs(proj.cpu().numpy() - ref_proj)) < IMG_TOL
+    ref = oracle.tomo_grad(scene, beam, L, dL, density_theta=True)
+    gg = {k: t.cpu().numpy().astype(np.float64) for k, t in zip(("mu", "scale", "quat", "kappa"), grads)}
+    check_grads(gg, ref, scene, GRAD_TOL, keys=("mu", "scale", "quat", "kappa"))
