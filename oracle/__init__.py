@@ -125,6 +125,10 @@ def lib():
         L.orc_tomo_grad.restype = None
         L.orc_tomo_grad.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, P, P, P, P, P,
                                     P, P, P, P]
+        L.orc_cone.restype = None
+        L.orc_cone.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, P, P, P, P, i32, P, P, P, P]
+        L.orc_cone_grad.restype = None
+        L.orc_cone_grad.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, P, P, P, P, P, P, P, P, P, P, P]
         L.orc_num_threads.restype = i32
         _LIB = L
     return _LIB
@@ -358,6 +362,59 @@ def tomo_grad(scene, beam, L, dL_dproj, mask=None, density_theta=False):
                         _p(_c(dL_dproj, np.float64)), _p(m),
                         _p(out["mu"]), _p(out["scale"]), _p(out["quat"]), _p(out["kappa"]))
     if density_theta:
+        d_theta, d_scale = kappa_from_theta_grad(scene.kappa, scene.scale, out["kappa"])
+        out["kappa"] = d_theta
+        out["scale"] = out["scale"] + d_scale
+    return out
+
+
+# ------------------------------------------------------------------------------ cone beam
+def cone(scene, cams, opts=None, L=None, brute=False, mask=None, tile=(16, 16)):
+    """Cone-beam projection (Eq. 21 with diverging rays): the source at each camera's centre and
+    the detector its image plane.  Returns per-view lists of (line_sum, proj = exp(-line_sum)),
+    each [H, W].  Tiled evaluation uses the perspective key function's lists and pixel
+    rectangles (opts' tau_cut); brute force sums every valid Gaussian."""
+    _, o = _opts_arr(opts)
+    if L is None and not brute:
+        L = lists(scene, cams, o, tile)
+    mu, sc, q, _k, _ = _scene_arrays(scene, np.float64)
+    k = _c(_density(scene, o), np.float64)
+    cf, wh = cam_arrays(cams)
+    pb, P = pix_bases(cams)
+    ls = np.zeros(P)
+    pr = np.zeros(P)
+    m = None if mask is None else _c(mask, np.int32)
+    tl = L["tile"] if L is not None else tile
+    ts = L["tile_start"] if L is not None else np.zeros(1, np.int64)
+    sg = L["sorted_g"] if L is not None else np.zeros(1, np.int32)
+    tb = _c(L["tile_base"], np.int32) if L is not None else np.zeros(len(cams), np.int32)
+    prc = _c(L["prect"], np.int32) if L is not None else None
+    lib().orc_cone(scene.n, _p(mu), _p(sc), _p(q), _p(k), len(cams), _p(cf), _p(wh), tl[0], tl[1], _p(ts), _p(sg),
+                   _p(tb), _p(prc), int(brute), _p(pb), _p(m), _p(ls), _p(pr))
+    out = []
+    for v, c in enumerate(cams):
+        sl = slice(pb[v], pb[v] + c.width * c.height)
+        out.append((ls[sl].reshape(c.height, c.width), pr[sl].reshape(c.height, c.width)))
+    return out
+
+
+def cone_grad(scene, cams, opts, L, dL_dproj, mask=None):
+    """Analytic FP64 gradient of sum(dL_dproj * proj) for the cone beam (lists held fixed)."""
+    _, o = _opts_arr(opts)
+    mu, sc, q, _k, _ = _scene_arrays(scene, np.float64)
+    k = _c(_density(scene, o), np.float64)
+    cf, wh = cam_arrays(cams)
+    pb, P = pix_bases(cams)
+    g = _c(np.concatenate([np.asarray(a, np.float64).reshape(-1) for a in dL_dproj])
+           if isinstance(dL_dproj, (list, tuple)) else np.asarray(dL_dproj).reshape(-1), np.float64)
+    N = scene.n
+    out = dict(mu=np.zeros((N, 3)), scale=np.zeros((N, 3)), quat=np.zeros((N, 4)), kappa=np.zeros(N))
+    m = None if mask is None else _c(mask, np.int32)
+    lib().orc_cone_grad(N, _p(mu), _p(sc), _p(q), _p(k), len(cams), _p(cf), _p(wh), L["tile"][0], L["tile"][1],
+                        _p(L["tile_start"]), _p(L["sorted_g"]), _p(_c(L["tile_base"], np.int32)),
+                        _p(_c(L["prect"], np.int32)), _p(pb), _p(g), _p(m),
+                        _p(out["mu"]), _p(out["scale"]), _p(out["quat"]), _p(out["kappa"]))
+    if o.get("density_theta"):
         d_theta, d_scale = kappa_from_theta_grad(scene.kappa, scene.scale, out["kappa"])
         out["kappa"] = d_theta
         out["scale"] = out["scale"] + d_scale

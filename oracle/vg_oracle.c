@@ -829,6 +829,115 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
     free(acc);
 }
 
+/* ================================== cone beam ================================== */
+/* Cone-beam tomography (Eq. 21 with diverging rays): a point source at the camera centre and
+ * a flat detector in the camera's image plane, so each detector pixel's ray is a pixel ray of
+ * the pinhole camera.  proj = exp(-sum_g tau_g) over the Gaussians of the pixel's tile list
+ * whose footprint rectangle contains the pixel (or, brute force, over every valid Gaussian). */
+void orc_cone(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
+              int n_views, const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
+              const int64_t *tile_start, const int32_t *sorted_g, const int32_t *view_tile_base,
+              const int32_t *prect, int brute, const int64_t *pix_base, const int32_t *pix_mask,
+              double *line_sum, double *proj)
+{
+    gauss64 *G = (gauss64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(gauss64));
+    char *ok = (char *)malloc((size_t)(n > 0 ? n : 1));
+    for (int g = 0; g < n; ++g) {
+        ok[g] = (char)valid64(mu + 3 * g, scale + 3 * g, quat + 4 * g, kappa[g]);
+        if (ok[g]) prep64(mu + 3 * g, scale + 3 * g, quat + 4 * g, kappa[g], &G[g]);
+    }
+    for (int v = 0; v < n_views; ++v) {
+        cam64 cam;
+        cam_setup(cam_f + 16 * v, cam_wh + 2 * v, &cam);
+        const int W = cam.W, H = cam.H;
+        const int tiles_x = (W + tile_w - 1) / tile_w;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t pix = 0; pix < (int64_t)W * H; ++pix) {
+            const int64_t gp = pix_base[v] + pix;
+            if (pix_mask && !pix_mask[gp]) continue;
+            const int x = (int)(pix % W), y = (int)(pix / W);
+            double d[3];
+            pixel_dir(&cam, x, y, d);
+            double sum = 0;
+            if (brute) {
+                for (int g = 0; g < n; ++g) {
+                    if (!ok[g]) continue;
+                    double a, b, c, p[3];
+                    sum += tau64(&G[g], cam.o, d, &a, &b, &c, p);
+                }
+            } else {
+                const int64_t tile = view_tile_base[v] + (int64_t)(y / tile_h) * tiles_x + x / tile_w;
+                for (int64_t k = tile_start[tile]; k < tile_start[tile + 1]; ++k) {
+                    const int64_t g = sorted_g[k];
+                    if (outside(prect, (int64_t)v * n + g, x, y)) continue;
+                    double a, b, c, p[3];
+                    sum += tau64(&G[g], cam.o, d, &a, &b, &c, p);
+                }
+            }
+            line_sum[gp] = sum;
+            proj[gp] = exp(-sum);
+        }
+    }
+    free(G);
+    free(ok);
+}
+
+/* Gradient of sum(dL_dproj * proj) for the cone beam: dL/dtau_g = -proj dL/dproj at every pair. */
+void orc_cone_grad(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
+                   int n_views, const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
+                   const int64_t *tile_start, const int32_t *sorted_g, const int32_t *view_tile_base,
+                   const int32_t *prect, const int64_t *pix_base, const double *dL_dproj,
+                   const int32_t *pix_mask, double *dmu, double *dscale, double *dquat, double *dkappa)
+{
+    gauss64 *G = (gauss64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(gauss64));
+    double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * ACC_N, sizeof(double));
+    for (int g = 0; g < n; ++g)
+        if (valid64(mu + 3 * g, scale + 3 * g, quat + 4 * g, kappa[g]))
+            prep64(mu + 3 * g, scale + 3 * g, quat + 4 * g, kappa[g], &G[g]);
+    for (int v = 0; v < n_views; ++v) {
+        cam64 cam;
+        cam_setup(cam_f + 16 * v, cam_wh + 2 * v, &cam);
+        memset(acc, 0, (size_t)(n > 0 ? n : 1) * ACC_N * sizeof(double));
+        const int W = cam.W, H = cam.H;
+        const int tiles_x = (W + tile_w - 1) / tile_w;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t pix = 0; pix < (int64_t)W * H; ++pix) {
+            const int64_t gp = pix_base[v] + pix;
+            if (pix_mask && !pix_mask[gp]) continue;
+            const int x = (int)(pix % W), y = (int)(pix / W);
+            double d[3];
+            pixel_dir(&cam, x, y, d);
+            const int64_t tile = view_tile_base[v] + (int64_t)(y / tile_h) * tiles_x + x / tile_w;
+            double sum = 0;
+            for (int64_t k = tile_start[tile]; k < tile_start[tile + 1]; ++k) {
+                const int64_t g = sorted_g[k];
+                if (outside(prect, (int64_t)v * n + g, x, y)) continue;
+                double a, b, c, p[3];
+                sum += tau64(&G[g], cam.o, d, &a, &b, &c, p);
+            }
+            const double dLdtau = -exp(-sum) * dL_dproj[gp];
+            for (int64_t k = tile_start[tile]; k < tile_start[tile + 1]; ++k) {
+                const int64_t g = sorted_g[k];
+                if (outside(prect, (int64_t)v * n + g, x, y)) continue;
+                double a, b, c, p[3];
+                const double tau = tau64(&G[g], cam.o, d, &a, &b, &c, p);
+                acc_tau(&acc[ACC_N * g], &G[g], dLdtau, tau, a, b, d, p);
+            }
+        }
+        for (int g = 0; g < n; ++g) {
+            double *A = &acc[ACC_N * g];
+            int any = 0;
+            for (int k = 0; k < ACC_N; ++k) any |= (A[k] != 0.0);
+            if (!any) continue;
+            chain_P(&G[g], A, dscale + 3 * g, dquat + 4 * g);
+            for (int k = 0; k < 3; ++k) dmu[3 * g + k] += A[9 + k];
+            dkappa[g] += A[12];
+        }
+    }
+    free(G);
+    free(acc);
+}
+
 /* ================================== tomography ================================== */
 
 void orc_tomo(int n, const double *mu, const double *scale, const double *quat, const double *kappa,

@@ -59,6 +59,18 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
                      const double *dL_drgb, const double *dL_dT, const int32_t *pix_mask,
                      double *dmu, double *dscale, double *dquat, double *dkappa, double *dsh);
 
+/* Cone-beam projection: the source at each camera's centre, the detector its image plane. */
+void orc_cone(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
+              int n_views, const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
+              const int64_t *tile_start, const int32_t *sorted_g, const int32_t *view_tile_base,
+              const int32_t *prect, int brute, const int64_t *pix_base, const int32_t *pix_mask,
+              double *line_sum, double *proj);
+void orc_cone_grad(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
+                   int n_views, const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
+                   const int64_t *tile_start, const int32_t *sorted_g, const int32_t *view_tile_base,
+                   const int32_t *prect, const int64_t *pix_base, const double *dL_dproj,
+                   const int32_t *pix_mask, double *dmu, double *dscale, double *dquat, double *dkappa);
+
 void orc_tomo(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
               int n_angles, const float *angles, int det_w, int det_h, float pitch_u,
               float pitch_v, float u0, float v0, int tile_w, int tile_h,

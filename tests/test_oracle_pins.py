@@ -446,3 +446,73 @@ def test_softplus_colour_tends_to_the_clamp():
         got, _, _ = oracle.render(scene, cams, dict(base, softplus_beta=beta))
         err = np.max(np.abs(got[0] - ref[0]))
         assert 0 < err <= math.log(2.0) / beta + 1e-12, (beta, err)
+
+
+# ------------------------------------------------------------------ cone-beam tomography
+def _far_cone_camera(beam, D):
+    """A pinhole camera on the -x axis at distance D looking along +x, whose pixel rays cross
+    the plane x = 0 at the parallel beam's (angle 0) detector pixel centres."""
+    R = np.array([[0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 0.0, 0.0]], np.float32)   # rows: u, v, forward
+    t = np.array([0.0, 0.0, D], np.float32)                                          # t = -R o, o = (-D, 0, 0)
+    f = D / beam.pitch_u
+    cx = -beam.u0 / beam.pitch_u
+    cy = -beam.v0 / beam.pitch_v
+    return synth.Camera(R, t, float(f), float(D / beam.pitch_v), float(cx), float(cy), beam.det_w, beam.det_h)
+
+
+def test_cone_beam_far_source_is_the_parallel_beam():
+    """With the source 1e8 away the cone's rays are parallel to within 1e-8 rad: the cone-beam
+    projection equals the (pinned) parallel-beam projection at angle 0."""
+    scene = synth.tomo_scene(30, 91, log_scale=(-3.0, -2.0))
+    beam = synth.parallel_beam(1, det=40, extent=2.2)
+    cam = _far_cone_camera(beam, 1e8)
+    ref_ls, _ = oracle.tomo(scene, beam, brute=True)
+    (ls, pr), = oracle.cone(scene, [cam], brute=True)
+    assert np.max(np.abs(ls - ref_ls[0])) < 1e-5 * max(1.0, float(np.max(ref_ls)))
+    assert np.allclose(pr, np.exp(-ls), rtol=0, atol=1e-15)
+
+
+def test_cone_beam_isotropic_sum_and_order():
+    """One isotropic Gaussian: the line sum through each pixel is kappa sqrt(2 pi) s exp(-r^2/2s^2)
+    (r the ray-to-mean distance, computed here from the camera model); permuting a scene's
+    Gaussians leaves the projection unchanged; tiled evaluation equals brute force within the
+    truncation bound."""
+    s, kap = 0.08, 3.0
+    scene = one_gaussian((0.1, -0.05, 0.2), (s, s, s), (0.9, 0.1, -0.3, 0.2), kap)
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 30, 26, 25.0)
+    (ls, _), = oracle.cone(scene, [cam], brute=True)
+    o, d = pixel_rays(cam)
+    pm = scene.mu[0].astype(np.float64) - o
+    r2 = np.sum(pm * pm) - (d @ pm) ** 2
+    s32 = float(scene.scale[0, 0])
+    want = kap * math.sqrt(2 * math.pi) * s32 * np.exp(-r2 / (2 * s32 * s32))
+    assert np.max(np.abs(ls - want)) < 1e-12
+    many = synth.tomo_scene(60, 92, log_scale=(-3.0, -2.0))
+    perm = many.subset(np.random.default_rng(1).permutation(many.n))
+    o_ = dict(oracle.EXACT)
+    (a, _), = oracle.cone(many, [cam], o_)
+    (b, _), = oracle.cone(perm, [cam], o_)
+    (c, _), = oracle.cone(many, [cam], o_, brute=True)
+    assert np.max(np.abs(a - b)) < 1e-12
+    assert np.max(np.abs(a - c)) < many.n * o_["tau_cut"]
+
+
+@pytest.mark.parametrize("theta", [False, True])
+def test_cone_beam_gradient_matches_finite_differences(theta):
+    rng = np.random.default_rng(8)
+    scene = synth.tomo_scene(7, 93, log_scale=(-2.5, -1.8))
+    scene = synth.Scene(*(np.asarray(getattr(scene, f), np.float64) for f in ("mu", "scale", "quat", "kappa", "sh")), 0)
+    opts = dict(oracle.EXACT, density_theta=theta)
+    if theta:
+        scene.kappa = rng.uniform(0.05, 0.95, scene.n)
+    cams = synth.small_views(2, 4, [(22, 18), (19, 21)])
+    L = oracle.lists(scene, cams, opts)
+    w = [rng.normal(size=(c.height, c.width)) for c in cams]
+
+    def loss():
+        return sum(float(np.sum(pr * ww)) for (_, pr), ww in zip(oracle.cone(scene, cams, opts, L), w))
+
+    g = oracle.cone_grad(scene, cams, opts, L, w)
+    for name, arr in (("mu", scene.mu), ("scale", scene.scale), ("quat", scene.quat), ("kappa", scene.kappa)):
+        assert np.max(np.abs(g[name])) > 0
+        _fd_check(loss, arr, g[name], range(arr.size), rtol=2e-6)
