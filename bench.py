@@ -150,6 +150,60 @@ def peaks():
         return {}
 
 
+# ----------------------------------------------------------------------------- cone beam
+def run_cone(args):
+    """Cone-beam tomography: config 4's Gaussians (200,000; --frac scales them) seen by 256 X-ray
+    sources on a circle of radius 4, each with a 512^2 detector; one step = the projections of
+    all sources, L2 loss against those of the 50,000 ground-truth Gaussians, and the backward."""
+    import torch
+
+    import paper_2412_03378_gb300 as vg
+    import synth
+
+    vg.load()
+    dev = torch.device("cuda:0")
+    scene, _, gt = synth.config4(args.frac)
+    cams = synth.cone_beam(256, det=512)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev).contiguous()
+    g = vg.Gaussians(t(scene.mu), t(scene.scale), t(scene.quat), t(scene.kappa), None, 0)
+    gg = vg.Gaussians(t(gt.mu), t(gt.scale), t(gt.quat), t(gt.kappa), None, 0)
+    P = sum(c.width * c.height for c in cams)
+    ws = vg.Workspace()
+    o = vg.Opts(tau_cut=1e-6, flags=vg.FLAG_GRAD_ZERO)
+    tgt = torch.empty(P, device=dev)
+    ws.project_cone(gg, cams, o, tgt)
+    proj, dl, loss = torch.empty(P, device=dev), torch.empty(P, device=dev), torch.zeros(1, device=dev)
+    grads = [torch.empty(g.n, 3, device=dev), torch.empty(g.n, 3, device=dev), torch.empty(g.n, 4, device=dev),
+             torch.empty(g.n, device=dev)]
+
+    def step():
+        ws.project_cone(g, cams, o, proj)
+        ws.l2_loss(proj, tgt, 1.0 / P, loss, dl)
+        ws.project_cone(g, cams, o, proj, dl, *grads)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ws.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    stages = ws.profile_read()
+    q = ws.query()
+    t_s = e0.elapsed_time(e1) / 1e3
+    out = {"metric": "cone-beam tomography fwd+bwd steps/s", "value": args.steps / t_s, "unit": "steps/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_s * 1e3 / args.steps,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"cone-beam tomography, {g.n} Gaussians, {len(cams)} sources at radius 4, "
+                                  "512x512 detectors", "frac": args.frac},
+           "stages_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in stages.items()},
+           "instances": q["n_instances"], "workspace_bytes": q["device_bytes"], "loss": float(loss.item())}
+    print(json.dumps(out), flush=True)
+
+
 # ----------------------------------------------------------------------------- batched graph path
 def graph_step(vg, g, cams, steps, warmup, dev, target_seed=2102):
     """A whole training step over all `cams` (preprocess, bin/sort, forward, L2 loss, backward)
@@ -612,8 +666,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-views", type=int, default=4,
                     help="views of the BF16 / graph-replayed batched measurement (0: skip it)")
-    ap.add_argument("--workload", choices=["render", "tomo", "cfg3", "cfg5"], default="render",
+    ap.add_argument("--workload", choices=["render", "tomo", "cone", "cfg3", "cfg5"], default="render",
                     help="render: the headline training step; tomo: the tomography step (config 4); "
+                         "cone: cone-beam tomography; "
                          "cfg3 / cfg5: the batched BF16 configurations as one CUDA graph per step")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -622,6 +677,8 @@ def main():
         run_reference(args)
     elif args.workload == "tomo":
         run_tomo(args)
+    elif args.workload == "cone":
+        run_cone(args)
     elif args.workload in ("cfg3", "cfg5"):
         run_batched_config(args)
     else:

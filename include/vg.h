@@ -244,6 +244,20 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
                           const vg_opts *opts, float *proj, const float *dL_dproj, float *dmu,
                           float *dscale, float *dquat, float *dkappa, void *stream);
 
+/* Cone-beam tomography (Eq. 21 with diverging rays; §8 next): for each of n_views cameras the
+ * X-ray source is the camera centre and the detector its image plane, so detector pixel (i, j)
+ * measures proj = exp(-sum_g tau_g) along that pixel's ray.  Same Gaussians (density only: sh
+ * is ignored), the same key function, tile lists and pixel footprint rectangles as vg_preprocess
+ * / vg_bin_sort, and the blend kernels in their exact form (no skip, clamp, early stop or
+ * background), whose final transmittance is exp(-sum tau).  opts: tau_cut, z_near, flags
+ * (VG_FLAG_DENSITY_THETA, VG_FLAG_GRAD_ZERO, VG_FLAG_FIXED_CAPACITY, VG_FLAG_COUNT_PAIRS) and
+ * pixels_per_thread are used.  proj [sum_v H_v W_v] float32, device; with dL_dproj non-NULL
+ * the gradients of sum(dL_dproj * proj) are accumulated into dmu/dscale/dquat/dkappa as in
+ * vg_render_bwd. */
+vg_status vg_project_cone(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams, int32_t n_views,
+                          const vg_opts *opts, float *proj, const float *dL_dproj, float *dmu, float *dscale,
+                          float *dquat, float *dkappa, void *stream);
+
 /* L2 image loss helper for training steps: loss = scale * sum_i (x_i - y_i)^2 written to the
  * device scalar *loss (overwritten), grad_i = 2 scale (x_i - y_i) (overwritten). */
 vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n, float scale,

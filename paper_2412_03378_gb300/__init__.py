@@ -86,6 +86,7 @@ _SIGS = {
     "vg_render_bwd": [ctypes.c_void_p] + [ctypes.c_void_p] * 7 + [ctypes.c_void_p],
     "vg_render_bwd_noalloc": [ctypes.c_void_p] + [ctypes.c_void_p] * 7 + [ctypes.c_void_p],
     "vg_project_tomo": [ctypes.c_void_p] * 11,
+    "vg_project_cone": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 8,
     "vg_l2_loss": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_query": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
@@ -281,6 +282,16 @@ class Workspace:
         self._chk(self._L.vg_project_tomo(self.h, ctypes.byref(g.c()), ctypes.byref(b), ctypes.byref(oc), _ptr(proj),
                                           _ptr(dL_dproj), _ptr(dmu), _ptr(dscale), _ptr(dquat), _ptr(dkappa),
                                           _stream(stream)))
+
+    def project_cone(self, g: Gaussians, cams, opts: Opts, proj, dL_dproj=None, dmu=None, dscale=None, dquat=None,
+                     dkappa=None, stream=None):
+        """Cone-beam projection exp(-sum tau) per detector pixel, the source at each camera's
+        centre; with dL_dproj also the gradients (see vg_project_cone)."""
+        self._keep = (g, _cams_array(cams), opts.c())
+        self._chk(self._L.vg_project_cone(self.h, ctypes.byref(g.c()), self._keep[1], len(cams),
+                                          ctypes.byref(self._keep[2]), _ptr(proj), _ptr(dL_dproj), _ptr(dmu),
+                                          _ptr(dscale), _ptr(dquat), _ptr(dkappa), _stream(stream)))
+        self.generation += 1
 
     def l2_loss(self, x, y, scale, loss, grad, stream=None):
         self._chk(self._L.vg_l2_loss(self.h, _ptr(x), _ptr(y), x.numel(), float(scale), _ptr(loss), _ptr(grad),

@@ -339,11 +339,11 @@ vg_status vg_workspace_reserve(vg_workspace *ws, int64_t n_items, int64_t n_inst
     return s;
 }
 
-vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams, int32_t n_views,
-                        const vg_opts *opts, void *stream) {
+static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams, int32_t n_views,
+                                 const vg_opts *opts, void *stream, bool need_sh) {
     if (!ws) return VG_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    VG_TRY(check_gauss(ws, g, true));
+    VG_TRY(check_gauss(ws, g, need_sh));
     if (!cams || n_views < 1) return fail(ws, VG_ERR_INVALID_ARG, "need at least one camera");
     if (!opts) return fail(ws, VG_ERR_INVALID_ARG, "opts is NULL");
     if (!finite_pos(opts->tau_cut)) return fail(ws, VG_ERR_INVALID_ARG, "tau_cut must be finite and > 0");
@@ -434,6 +434,11 @@ vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera
     return VG_OK;
 }
 
+vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams, int32_t n_views,
+                        const vg_opts *opts, void *stream) {
+    return preprocess_impl(ws, g, cams, n_views, opts, stream, true);
+}
+
 vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
     if (!ws) return VG_ERR_INVALID_ARG;
     if (ws->stage < 1) return fail(ws, VG_ERR_STATE, "vg_bin_sort before vg_preprocess");
@@ -497,10 +502,10 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
     return VG_OK;
 }
 
-vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stream) {
+static vg_status render_fwd_impl(vg_workspace *ws, float *rgb, float *T_final, void *stream, bool rgb_optional) {
     if (!ws) return VG_ERR_INVALID_ARG;
     if (ws->stage < 2) return fail(ws, VG_ERR_STATE, "vg_render_fwd before vg_bin_sort");
-    if (!rgb && ws->n_pixels > 0) return fail(ws, VG_ERR_INVALID_ARG, "rgb is NULL");
+    if (!rgb && ws->n_pixels > 0 && !rgb_optional) return fail(ws, VG_ERR_INVALID_ARG, "rgb is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     VG_TRY(ensure(ws, ws->S_fin, (size_t)ws->n_pixels, "pixel state"));
     VG_TRY(ensure(ws, ws->T_fin, (size_t)ws->n_pixels, "pixel state"));
@@ -520,11 +525,15 @@ vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stre
     return VG_OK;
 }
 
-vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_dT, float *dmu, float *dscale,
-                        float *dquat, float *dkappa, float *dsh, void *stream) {
+vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stream) {
+    return render_fwd_impl(ws, rgb, T_final, stream, false);
+}
+
+static vg_status render_bwd_impl(vg_workspace *ws, const float *dL_drgb, const float *dL_dT, float *dmu, float *dscale,
+                                 float *dquat, float *dkappa, float *dsh, void *stream, bool drgb_optional) {
     if (!ws) return VG_ERR_INVALID_ARG;
     if (ws->stage < 3) return fail(ws, VG_ERR_STATE, "vg_render_bwd before vg_render_fwd");
-    if ((!dL_drgb && ws->n_pixels > 0) || (ws->g.n > 0 && (!dmu || !dscale || !dquat || !dkappa)))
+    if ((!dL_drgb && ws->n_pixels > 0 && !drgb_optional) || (ws->g.n > 0 && (!dmu || !dscale || !dquat || !dkappa)))
         return fail(ws, VG_ERR_INVALID_ARG, "a gradient pointer is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     VG_TRY(ensure(ws, ws->grad, (size_t)ws->n_items * kGradN, "gradient accumulators"));
@@ -549,6 +558,35 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
         VG_CUDA(ws, launch_chain(ws->g, ws->views.p, ws->n_views, ws->grad.p, (ws->opts.flags & VG_FLAG_GRAD_ZERO) ? 1 : 0,
                                  dmu, dscale, dquat, dkappa, dsh, st, &ws->launches));
     }
+    return VG_OK;
+}
+
+vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_dT, float *dmu, float *dscale,
+                        float *dquat, float *dkappa, float *dsh, void *stream) {
+    return render_bwd_impl(ws, dL_drgb, dL_dT, dmu, dscale, dquat, dkappa, dsh, stream, false);
+}
+
+vg_status vg_project_cone(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams, int32_t n_views,
+                          const vg_opts *opts, float *proj, const float *dL_dproj, float *dmu, float *dscale,
+                          float *dquat, float *dkappa, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (!opts) return fail(ws, VG_ERR_INVALID_ARG, "opts is NULL");
+    // With no skip, clamp or early stop the blend's final transmittance is exp(-sum tau): the
+    // cone-beam projection.  Its gradient is the blend's dL/dT_final term alone.
+    vg_opts o = *opts;
+    o.alpha_min = 0.0f;
+    o.tau_max = INFINITY;
+    o.T_stop = 0.0f;
+    o.bg[0] = o.bg[1] = o.bg[2] = 0.0f;
+    o.softplus_beta = 0.0f;
+    vg_gaussians gd = g ? *g : vg_gaussians{};
+    gd.sh = nullptr;   // density only
+    gd.sh_degree = 0;
+    VG_TRY(preprocess_impl(ws, g ? &gd : nullptr, cams, n_views, &o, stream, false));
+    VG_TRY(vg_bin_sort(ws, stream));
+    if (!proj && ws->n_pixels > 0) return fail(ws, VG_ERR_INVALID_ARG, "proj is NULL");
+    VG_TRY(render_fwd_impl(ws, nullptr, proj, stream, true));
+    if (dL_dproj) VG_TRY(render_bwd_impl(ws, nullptr, dL_dproj, dmu, dscale, dquat, dkappa, nullptr, stream, true));
     return VG_OK;
 }
 

@@ -30,7 +30,7 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
         const long long gi = gbase + lane;
         const long long it = (long long)v * g.n + gi;
         // the SH rows of the warp's Gaussians, coalesced, before (and independent of) the key
-        warp_load_rows<ST>((const ST *)g.sh + gbase * K3, nloc, K3, buf, lane);
+        if (g.sh) warp_load_rows<ST>((const ST *)g.sh + gbase * K3, nloc, K3, buf, lane);
         rows_wait();
         __syncwarp();
         const ViewInfo &V = views[v];
@@ -48,9 +48,9 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
                 cnt = (uint32_t)(rc.z - rc.x + 1) * (uint32_t)(rc.w - rc.y + 1);
                 ItemGeom G;
                 item_geom(V, mu, s, Rq, G);
-                float dir[3], len, rgb[3], raw[3];
+                float dir[3], len, rgb[3] = {0.0f, 0.0f, 0.0f}, raw[3];
                 view_dir(V, mu, dir, len);
-                eval_colour_row(g.sh_degree, row, dir, rgb, raw, g.softplus_beta);
+                if (g.sh) eval_colour_row(g.sh_degree, row, dir, rgb, raw, g.softplus_beta);   // else density only
 #pragma unroll
                 for (int k = 0; k < 9; ++k) {
                     rrow[k] = G.A[k];

@@ -79,9 +79,11 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             my_last[k] = nlast[pix];
             S[k] = S_fin[pix];
             Tend = T_fin[pix];
-            g0[k] = dL_drgb[3 * pix];
-            g1[k] = dL_drgb[3 * pix + 1];
-            g2[k] = dL_drgb[3 * pix + 2];
+            if (dL_drgb) {   // absent for the cone-beam projection (dL/dT alone)
+                g0[k] = dL_drgb[3 * pix];
+                g1[k] = dL_drgb[3 * pix + 1];
+                g2[k] = dL_drgb[3 * pix + 2];
+            }
             gTterm[k] = dL_dT ? -dL_dT[pix] * Tend : 0.0f;
         }
         Tafter[k] = ex2_approx(__fmul_rn(-kLog2eF, S[k]));

@@ -122,9 +122,11 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
         const int x = x0 + L::ox(k), y = y0 + L::oy(k);
         if (x >= V.W || y >= V.H) continue;
         const long long pix = V.pix_base + (long long)y * V.W + x;
-        rgb[3 * pix + 0] = fmaf(T[k], bp.bg[0], c0[k]);
-        rgb[3 * pix + 1] = fmaf(T[k], bp.bg[1], c1[k]);
-        rgb[3 * pix + 2] = fmaf(T[k], bp.bg[2], c2[k]);
+        if (rgb) {   // absent for the cone-beam projection, which needs T alone
+            rgb[3 * pix + 0] = fmaf(T[k], bp.bg[0], c0[k]);
+            rgb[3 * pix + 1] = fmaf(T[k], bp.bg[1], c1[k]);
+            rgb[3 * pix + 2] = fmaf(T[k], bp.bg[2], c2[k]);
+        }
         T_ws[pix] = T[k];
         if (T_user) T_user[pix] = T[k];
         S_out[pix] = S[k];

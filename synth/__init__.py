@@ -252,6 +252,19 @@ def config4(frac=1.0, n_angles=256, det=512):
     return scene, parallel_beam(n_angles, det), gt
 
 
+def cone_beam(n_angles, det=512, source_dist=4.0, cover=1.1):
+    """Cone-beam geometry: n_angles X-ray sources on a circle of radius source_dist about the z
+    axis (angles 2 pi k / n_angles), each a det x det pinhole camera looking at the origin with
+    a field of view that covers a sphere of radius `cover`."""
+    fov = math.degrees(2.0 * math.atan(cover / source_dist))
+    cams = []
+    for k in range(n_angles):
+        a = 2.0 * math.pi * k / n_angles
+        cams.append(look_at((source_dist * math.cos(a), source_dist * math.sin(a), 0.0), (0.0, 0.0, 0.0),
+                            det, det, fov, down=(0.0, 0.0, -1.0)))
+    return cams
+
+
 def config5(frac=1.0, n_views=8, width=1920, height=1080):
     """6,000,000 Gaussians (cluster generator), SH degree 3, 8 views of 1920x1080."""
     n = max(1, int(round(6_000_000 * frac)))
