@@ -129,6 +129,10 @@ def lib():
         L.orc_cone.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, P, P, P, P, i32, P, P, P, P]
         L.orc_cone_grad.restype = None
         L.orc_cone_grad.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, P, P, P, P, P, P, P, P, P, P, P]
+        L.orc_voxel_boxes.restype = i64
+        L.orc_voxel_boxes.argtypes = [i32, P, P, P, P, P, P, P, f32, P]
+        L.orc_voxel_density.restype = None
+        L.orc_voxel_density.argtypes = [i32, P, P, P, P, P, i32, P, P, P, P, P]
         L.orc_num_threads.restype = i32
         _LIB = L
     return _LIB
@@ -419,3 +423,29 @@ def cone_grad(scene, cams, opts, L, dL_dproj, mask=None):
         out["kappa"] = d_theta
         out["scale"] = out["scale"] + d_scale
     return out
+
+
+# ------------------------------------------------------------------------------ voxel density
+def voxel_boxes(scene, origin, voxel, dims, sigma_cut=1e-6, density_theta=False):
+    """Per-Gaussian truncation boxes [N, 6] = (x0, y0, z0, x1, y1, z1) inclusive voxel indices
+    (-1 when empty), FP32 with the GPU's operation order; returns (boxes, total voxel pairs)."""
+    mu, sc, q, _k, _ = _scene_arrays(scene)
+    k = _c(_density(scene, dict(density_theta=density_theta), key=True), np.float32)
+    box = np.zeros((scene.n, 6), np.int32)
+    tot = lib().orc_voxel_boxes(scene.n, _p(mu), _p(sc), _p(q), _p(k), _p(_c(origin, np.float32)),
+                                _p(_c(voxel, np.float32)), _p(_c(dims, np.int32)), np.float32(sigma_cut), _p(box))
+    return box, int(tot)
+
+
+def voxel_density(scene, origin, voxel, dims, sigma_cut=1e-6, brute=False, mask=None, density_theta=False):
+    """sigma(x) = sum_g kappa_g G_g(x) at the voxel centres, [nz, ny, nx] (float64)."""
+    box, _ = voxel_boxes(scene, origin, voxel, dims, sigma_cut, density_theta)
+    mu, sc, q, _k, _ = _scene_arrays(scene, np.float64)
+    k = _c(_density(scene, dict(density_theta=density_theta)), np.float64)
+    nx, ny, nz = (int(d) for d in dims)
+    out = np.zeros(nx * ny * nz)
+    m = None if mask is None else _c(np.asarray(mask).reshape(-1), np.int32)
+    lib().orc_voxel_density(scene.n, _p(mu), _p(sc), _p(q), _p(k), _p(box), int(brute),
+                            _p(_c(origin, np.float32)), _p(_c(voxel, np.float32)), _p(_c(dims, np.int32)), _p(m),
+                            _p(out))
+    return out.reshape(nz, ny, nx)

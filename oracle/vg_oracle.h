@@ -59,6 +59,14 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
                      const double *dL_drgb, const double *dL_dT, const int32_t *pix_mask,
                      double *dmu, double *dscale, double *dquat, double *dkappa, double *dsh);
 
+/* Voxel density: truncation boxes (FP32 key-function style, bit-exact) and sigma at voxel centres. */
+int64_t orc_voxel_boxes(int n, const float *mu, const float *scale, const float *quat, const float *kappa,
+                        const float *origin, const float *voxel, const int32_t *dims, float sigma_cut,
+                        int32_t *box);
+void orc_voxel_density(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
+                       const int32_t *box, int brute, const float *origin, const float *voxel,
+                       const int32_t *dims, const int32_t *mask, double *out);
+
 /* Cone-beam projection: the source at each camera's centre, the detector its image plane. */
 void orc_cone(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
               int n_views, const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
