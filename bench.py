@@ -204,6 +204,53 @@ def run_cone(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------- voxel density query
+def run_voxel(args):
+    """Voxel density query: config 4's Gaussians (200,000; --frac scales them) evaluated on a
+    256^3 grid over [-1, 1]^3; one step = one full query (truncation boxes, binning into 8^3
+    bricks, per-brick sums)."""
+    import torch
+
+    import paper_2412_03378_gb300 as vg
+    import synth
+
+    vg.load()
+    dev = torch.device("cuda:0")
+    scene, _, _ = synth.config4(args.frac)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev).contiguous()
+    g = vg.Gaussians(t(scene.mu), t(scene.scale), t(scene.quat), t(scene.kappa), None, 0)
+    dims, origin, voxel = (256, 256, 256), (-1.0, -1.0, -1.0), (2.0 / 256,) * 3
+    ws = vg.Workspace()
+    o = vg.Opts(tau_cut=1e-6)
+    out = torch.empty(dims[::-1], device=dev)
+
+    def step():
+        ws.query_density(g, origin, voxel, dims, o, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ws.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    stages = ws.profile_read()
+    q = ws.query()
+    t_s = e0.elapsed_time(e1) / 1e3
+    nvox = dims[0] * dims[1] * dims[2]
+    out_ = {"metric": "voxel density queries/s", "value": args.steps / t_s, "unit": "queries/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_s * 1e3 / args.steps,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"voxel density, {g.n} Gaussians, 256^3 grid", "frac": args.frac},
+            "gvoxels_per_s": nvox * args.steps / t_s / 1e9,
+            "stages_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in stages.items()},
+            "instances": q["n_instances"], "sum": float(out.sum().item())}
+    print(json.dumps(out_), flush=True)
+
+
 # ----------------------------------------------------------------------------- batched graph path
 def graph_step(vg, g, cams, steps, warmup, dev, target_seed=2102):
     """A whole training step over all `cams` (preprocess, bin/sort, forward, L2 loss, backward)
@@ -666,9 +713,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-views", type=int, default=4,
                     help="views of the BF16 / graph-replayed batched measurement (0: skip it)")
-    ap.add_argument("--workload", choices=["render", "tomo", "cone", "cfg3", "cfg5"], default="render",
+    ap.add_argument("--workload", choices=["render", "tomo", "cone", "voxel", "cfg3", "cfg5"], default="render",
                     help="render: the headline training step; tomo: the tomography step (config 4); "
-                         "cone: cone-beam tomography; "
+                         "cone: cone-beam tomography; voxel: the voxel density query; "
                          "cfg3 / cfg5: the batched BF16 configurations as one CUDA graph per step")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -679,6 +726,8 @@ def main():
         run_tomo(args)
     elif args.workload == "cone":
         run_cone(args)
+    elif args.workload == "voxel":
+        run_voxel(args)
     elif args.workload in ("cfg3", "cfg5"):
         run_batched_config(args)
     else:

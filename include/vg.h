@@ -150,7 +150,8 @@ typedef struct {
 /* Per-stage device time recorded with CUDA events on the launching stream while
  * profiling is enabled (vg_profile_enable).  Stage names: "preprocess", "depth_sort",
  * "scan", "duplicate", "tile_sort", "ranges", "render_fwd", "render_bwd", "chain",
- * "l2_loss", "tomo_fwd", "tomo_bwd". */
+ * "l2_loss", "tomo_fwd", "tomo_bwd", "voxel_eval" (the voxel query records its own
+ * preprocess, scan, duplicate, tile_sort and ranges stages under the same names). */
 typedef struct {
     char name[24];
     int64_t calls;
@@ -257,6 +258,22 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
 vg_status vg_project_cone(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams, int32_t n_views,
                           const vg_opts *opts, float *proj, const float *dL_dproj, float *dmu, float *dscale,
                           float *dquat, float *dkappa, void *stream);
+
+/* Regular voxel grid: voxel (i, j, k) has its centre at origin + (i + 1/2, j + 1/2, k + 1/2) * voxel. */
+typedef struct {
+    float origin[3];
+    float voxel[3];
+    int32_t nx, ny, nz;   /* each 1..32767 */
+} vg_grid;
+
+/* Density on a grid (the density of Eq. 3-4, for volumetric comparisons; §8 next):
+ *   out[k][j][i] = sum_g kappa_g exp(-(x - mu_g)' Sigma_g^-1 (x - mu_g) / 2)   (float32, device)
+ * at the voxel centres x.  Each Gaussian is truncated to the voxel box of its ellipsoid
+ * (x - mu)' Sigma^-1 (x - mu) <= k^2, k^2 = 2 ln 2 e with kappa / sigma_cut = m 2^e, where
+ * sigma_cut = opts->tau_cut; with VG_FLAG_DENSITY_THETA the density input holds Eq. 20's theta.
+ * SH are not used.  Synchronises once (the instance count). */
+vg_status vg_query_density(vg_workspace *ws, const vg_gaussians *g, const vg_grid *grid, const vg_opts *opts,
+                           float *out, void *stream);
 
 /* L2 image loss helper for training steps: loss = scale * sum_i (x_i - y_i)^2 written to the
  * device scalar *loss (overwritten), grad_i = 2 scale (x_i - y_i) (overwritten). */

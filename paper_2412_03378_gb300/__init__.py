@@ -60,6 +60,11 @@ class _Opts(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("pixels_per_thread", ctypes.c_int32), ("softplus_beta", ctypes.c_float)]
 
 
+class _Grid(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("voxel", ctypes.c_float * 3), ("nx", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
 class _StageTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("calls", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -87,6 +92,7 @@ _SIGS = {
     "vg_render_bwd_noalloc": [ctypes.c_void_p] + [ctypes.c_void_p] * 7 + [ctypes.c_void_p],
     "vg_project_tomo": [ctypes.c_void_p] * 11,
     "vg_project_cone": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 8,
+    "vg_query_density": [ctypes.c_void_p] * 6,
     "vg_l2_loss": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_query": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
@@ -292,6 +298,16 @@ class Workspace:
                                           ctypes.byref(self._keep[2]), _ptr(proj), _ptr(dL_dproj), _ptr(dmu),
                                           _ptr(dscale), _ptr(dquat), _ptr(dkappa), _stream(stream)))
         self.generation += 1
+
+    def query_density(self, g: Gaussians, origin, voxel, dims, opts: Opts, out, stream=None):
+        """sigma = sum kappa G at the voxel centres of the grid, out [nz, ny, nx] float32 (see vg_query_density)."""
+        gr = _Grid()
+        for a in range(3):
+            gr.origin[a], gr.voxel[a] = float(origin[a]), float(voxel[a])
+        gr.nx, gr.ny, gr.nz = (int(d) for d in dims)
+        oc = opts.c()
+        self._chk(self._L.vg_query_density(self.h, ctypes.byref(g.c()), ctypes.byref(gr), ctypes.byref(oc), _ptr(out),
+                                           _stream(stream)))
 
     def l2_loss(self, x, y, scale, loss, grad, stream=None):
         self._chk(self._L.vg_l2_loss(self.h, _ptr(x), _ptr(y), x.numel(), float(scale), _ptr(loss), _ptr(grad),

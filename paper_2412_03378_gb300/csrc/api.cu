@@ -56,6 +56,7 @@ struct vg_workspace {
                                          // [6] instance total of the last scan, [7] look-back timeout flag
     DBuf<float> tomo_cs;
     DBuf<uint32_t> tord;                  // tile order buffer
+    DBuf<short4> vbox;                    // voxel query: truncation boxes (2 per Gaussian)
     uint32_t *tile_order = nullptr;       // longest-first tile order of the last bin_sort
     int ppt_fwd = 2, ppt_bwd = 1;         // pixels per thread of the blend kernels
     int tuned_fwd = 0, tuned_bwd = 0;     // vg_autotune's choice (0: none yet)
@@ -79,9 +80,10 @@ constexpr int kDefaultPixelsFwd = 2;
 constexpr int kDefaultPixelsBwd = 1;
 
 enum Stage { ST_PRE, ST_DEPTH, ST_SCAN, ST_DUP, ST_TILE, ST_RANGES, ST_FWD, ST_BWD, ST_CHAIN, ST_LOSS, ST_TFWD,
-             ST_TBWD, ST_COUNT };
+             ST_TBWD, ST_VOXEL, ST_COUNT };
 const char *kStageName[ST_COUNT] = {"preprocess", "depth_sort", "scan",     "duplicate", "tile_sort", "ranges",
-                                    "render_fwd", "render_bwd", "chain",    "l2_loss",   "tomo_fwd",  "tomo_bwd"};
+                                    "render_fwd", "render_bwd", "chain",    "l2_loss",   "tomo_fwd",  "tomo_bwd",
+                                    "voxel_eval"};
 
 cudaEvent_t prof_event(vg_workspace *ws) {
     if (!ws->prof_pool.empty()) {
@@ -255,6 +257,7 @@ vg_status vg_workspace_destroy(vg_workspace *ws) {
     release(ws->counters);
     release(ws->tomo_cs);
     release(ws->tord);
+    release(ws->vbox);
     if (ws->h_total) cudaFreeHost(ws->h_total);
     for (auto &r : ws->prof) {
         cudaEventDestroy(r.a);
@@ -587,6 +590,82 @@ vg_status vg_project_cone(vg_workspace *ws, const vg_gaussians *g, const vg_came
     if (!proj && ws->n_pixels > 0) return fail(ws, VG_ERR_INVALID_ARG, "proj is NULL");
     VG_TRY(render_fwd_impl(ws, nullptr, proj, stream, true));
     if (dL_dproj) VG_TRY(render_bwd_impl(ws, nullptr, dL_dproj, dmu, dscale, dquat, dkappa, nullptr, stream, true));
+    return VG_OK;
+}
+
+vg_status vg_query_density(vg_workspace *ws, const vg_gaussians *g, const vg_grid *grid, const vg_opts *opts,
+                           float *out, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    VG_TRY(check_gauss(ws, g, false));
+    if (!grid || !opts) return fail(ws, VG_ERR_INVALID_ARG, "grid or opts is NULL");
+    if (!finite_pos(opts->tau_cut)) return fail(ws, VG_ERR_INVALID_ARG, "tau_cut (sigma_cut) must be finite and > 0");
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nx > 32767 || grid->ny > 32767 || grid->nz > 32767)
+        return fail(ws, VG_ERR_INVALID_ARG, "grid sizes must be 1..32767");
+    for (int a = 0; a < 3; ++a)
+        if (!finite_pos(grid->voxel[a]) || !std::isfinite(grid->origin[a]))
+            return fail(ws, VG_ERR_INVALID_ARG, "invalid grid origin or voxel size");
+    if (!out) return fail(ws, VG_ERR_INVALID_ARG, "out is NULL");
+    VoxelGrid vgd;
+    vgd.ox = grid->origin[0];
+    vgd.oy = grid->origin[1];
+    vgd.oz = grid->origin[2];
+    vgd.vx = grid->voxel[0];
+    vgd.vy = grid->voxel[1];
+    vgd.vz = grid->voxel[2];
+    vgd.nx = grid->nx;
+    vgd.ny = grid->ny;
+    vgd.nz = grid->nz;
+    vgd.bx = (grid->nx + 7) / 8;
+    vgd.by = (grid->ny + 7) / 8;
+    vgd.bz = (grid->nz + 7) / 8;
+    const long long bricks = (long long)vgd.bx * vgd.by * vgd.bz, n = g->n;
+    if (bricks >= (1LL << 30)) return fail(ws, VG_ERR_INVALID_ARG, "too many bricks");
+    ws->opts = *opts;
+    ws->g = to_in(g);
+    ws->g.sh = nullptr;
+    ws->g.density_theta = (opts->flags & VG_FLAG_DENSITY_THETA) ? 1 : 0;
+    ws->stage = 0;   // the render state of this workspace is overwritten below
+    ws->views_valid = false;
+    VG_TRY(reserve_items(ws, n));
+    VG_TRY(reserve_sort_scratch(ws, n));
+    VG_TRY(ensure(ws, ws->vbox, (size_t)n * 2, "voxel boxes"));
+    {
+        ProfScope ps(ws, ST_PRE, st);
+        VG_CUDA(ws, launch_voxel_pre(ws->g, vgd, opts->tau_cut, ws->rec.p, ws->vbox.p, ws->count.p, st,
+                                     &ws->launches));
+    }
+    {
+        ProfScope ps(ws, ST_SCAN, st);
+        VG_CUDA(ws, launch_scan_gather(ws->count.p, nullptr, ws->offsets.p, n, ws->scan_tmp.p, total64_ptr(ws), ~0ull,
+                                       lookback_err_ptr(ws), st, &ws->launches));
+    }
+    long long total = 0;
+    VG_TRY(read_total(ws, st, &total));
+    if (total > (long long)(1u << 30) - 1) return fail(ws, VG_ERR_INVALID_ARG, "more than 2^30 - 1 (brick, Gaussian) pairs");
+    VG_TRY(reserve_instances(ws, total));
+    ws->n_inst = total;
+    VG_TRY(ensure(ws, ws->ranges, (size_t)bricks, "brick ranges"));
+    uint32_t *keys = nullptr, *vals = nullptr;
+    {
+        ProfScope ps(ws, ST_DUP, st);
+        VG_CUDA(ws, launch_voxel_dup(ws->offsets.p, ws->vbox.p, vgd, n, ws->ikey[0].p, ws->ival[0].p, ws->capacity,
+                                     st, &ws->launches));
+    }
+    {
+        ProfScope ps(ws, ST_TILE, st);
+        VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, ws->ikey[0].p,
+                                      ws->ival[0].p, total, nullptr, bits_for(bricks), ws->hist.p,
+                                      lookback_err_ptr(ws), &keys, &vals, st, &ws->launches));
+    }
+    {
+        ProfScope ps(ws, ST_RANGES, st);
+        VG_CUDA(ws, launch_ranges(keys, total, nullptr, ws->ranges.p, bricks, st, &ws->launches));
+    }
+    {
+        ProfScope ps(ws, ST_VOXEL, st);
+        VG_CUDA(ws, launch_voxel_eval(ws->ranges.p, vals, ws->rec.p, ws->vbox.p, vgd, out, st, &ws->launches));
+    }
     return VG_OK;
 }
 

@@ -129,6 +129,19 @@ cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, con
 cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *order, cudaStream_t st,
                               long long *launches);
 
+// Voxel density query (voxel.cu): grid origin, voxel size, voxel and brick (8^3) counts.
+struct VoxelGrid {
+    float ox, oy, oz, vx, vy, vz;
+    int nx, ny, nz, bx, by, bz;
+};
+cudaError_t launch_voxel_pre(const GaussIn &g, const VoxelGrid &grid, float sigma_cut, float4 *rec, short4 *box,
+                             uint32_t *count, cudaStream_t st, long long *launches);
+cudaError_t launch_voxel_dup(const uint32_t *offsets, const short4 *box, const VoxelGrid &grid, long long n,
+                             uint32_t *inst_key, uint32_t *inst_val, long long capacity, cudaStream_t st,
+                             long long *launches);
+cudaError_t launch_voxel_eval(const uint2 *ranges, const uint32_t *sorted, const float4 *rec, const short4 *box,
+                              const VoxelGrid &grid, float *out, cudaStream_t st, long long *launches);
+
 cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc, int zero,
                          float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st,
                          long long *launches);
