@@ -245,7 +245,7 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
                           const vg_opts *opts, float *proj, const float *dL_dproj, float *dmu,
                           float *dscale, float *dquat, float *dkappa, void *stream);
 
-/* Cone-beam tomography (Eq. 21 with diverging rays; §8 next): for each of n_views cameras the
+/* Cone-beam tomography (Eq. 21 with diverging rays): for each of n_views cameras the
  * X-ray source is the camera centre and the detector its image plane, so detector pixel (i, j)
  * measures proj = exp(-sum_g tau_g) along that pixel's ray.  Same Gaussians (density only: sh
  * is ignored), the same key function, tile lists and pixel footprint rectangles as vg_preprocess
@@ -266,7 +266,7 @@ typedef struct {
     int32_t nx, ny, nz;   /* each 1..32767 */
 } vg_grid;
 
-/* Density on a grid (the density of Eq. 3-4, for volumetric comparisons; §8 next):
+/* Density on a grid (the density of Eq. 3-4, for volumetric comparisons):
  *   out[k][j][i] = sum_g kappa_g exp(-(x - mu_g)' Sigma_g^-1 (x - mu_g) / 2)   (float32, device)
  * at the voxel centres x.  Each Gaussian is truncated to the voxel box of its ellipsoid
  * (x - mu)' Sigma^-1 (x - mu) <= k^2, k^2 = 2 ln 2 e with kappa / sigma_cut = m 2^e, where
