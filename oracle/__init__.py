@@ -9,7 +9,8 @@ compiles it with gcc on first use (no floating-point contraction, so the FP32 ke
 function is reproducible) and wraps it for numpy inputs produced by `synth`.
 
 Passages followed: Sec. 3.1-3.2 (Eq. 1-4), Sec. 4.1-4.2 (Eq. 8-19), Supp. B (the 1D
-Gaussian along the ray), Sec. 6.2 (Eq. 21, tomography), Sec. 7 ("per-tile sorting").
+Gaussian along the ray), Sec. 6.2 (Eq. 21, tomography), Sec. 7 ("per-tile sorting"), and for
+the 3DGS comparison mode Sec. 3.2 (Eq. 5-7: alpha = o G'(p), Sigma' = J W Sigma W^T J^T).
 """
 from __future__ import annotations
 
@@ -31,11 +32,17 @@ _LIB = None
 #: exact mode: no alpha skip, no clamp, no early stop; footprint truncated at tau_cut.
 #: density_theta: the density array holds Eq. 20's theta in [0, 1] instead of kappa;
 #: softplus_beta > 0: colour activation softplus(beta) instead of the clamp at 0 (Supp. D).
+#: splat: the 3DGS comparison mode (Eq. 5-7), where the density array holds the peak opacity o
+#: and alpha = o G'(p) with G' the projected 2D Gaussian (covariance + splat_dilation I).
 EXACT = dict(alpha_min=0.0, tau_cut=1e-6, tau_max=math.inf, T_stop=0.0, bg=(0.0, 0.0, 0.0), z_near=0.2,
-             density_theta=False, softplus_beta=0.0)
+             density_theta=False, softplus_beta=0.0, splat=False, splat_dilation=0.0)
 #: compat mode: the 3DGS thresholds (alpha >= 1/255 blended, alpha <= 0.99, stop at T < 1e-4).
 COMPAT = dict(alpha_min=1.0 / 255.0, tau_cut=-math.log1p(-1.0 / 255.0), tau_max=math.log(100.0),
-              T_stop=1e-4, bg=(0.0, 0.0, 0.0), z_near=0.2, density_theta=False, softplus_beta=0.0)
+              T_stop=1e-4, bg=(0.0, 0.0, 0.0), z_near=0.2, density_theta=False, softplus_beta=0.0,
+              splat=False, splat_dilation=0.0)
+#: the 3DGS rasterizer's own settings in splat mode: its thresholds, footprint cut at alpha 1/255
+#: and a 0.3 px^2 dilation of the 2D covariance.
+SPLAT_3DGS = dict(COMPAT, tau_cut=1.0 / 255.0, splat=True, splat_dilation=0.3)
 
 
 # ------------------------------------------------------------------------------ Eq. 20
@@ -109,6 +116,10 @@ def lib():
         L.orc_keys.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, f32, f32, P, P, P]
         L.orc_tomo_keys.restype = i64
         L.orc_tomo_keys.argtypes = [i32, P, P, P, P, i32, P, i32, i32, f32, f32, f32, f32, i32, i32, f32, P, P]
+        L.orc_keys_splat.restype = i64
+        L.orc_keys_splat.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, f32, f32, f32, P, P, P]
+        L.orc_splat2d.restype = None
+        L.orc_splat2d.argtypes = [P, P, P, P, P, ctypes.c_double, P]
         L.orc_bin.restype = i64
         L.orc_bin.argtypes = [i32, i32, P, P, P, P, i64, i64, P, P]
         L.orc_sh_basis.restype = None
@@ -188,7 +199,8 @@ def _opts_arr(opts):
     o.update(opts or {})
     bg = o["bg"]
     return np.array([o["alpha_min"], o["tau_cut"], o["tau_max"], o["T_stop"], bg[0], bg[1], bg[2],
-                     o["z_near"], o.get("softplus_beta", 0.0)], np.float64), o
+                     o["z_near"], o.get("softplus_beta", 0.0), 1.0 if o.get("splat") else 0.0,
+                     o.get("splat_dilation", 0.0)], np.float64), o
 
 
 # ------------------------------------------------------------------------------------------
@@ -204,8 +216,13 @@ def keys(scene, cams, opts=None, tile=(16, 16), with_pixels=False):
     depth = np.zeros((V, N), np.uint32)
     rect = np.zeros((V, N, 4), np.int32)
     prect = np.zeros((V, N, 4), np.int32)
-    lib().orc_keys(N, _p(mu), _p(sc), _p(q), _p(k), V, _p(cf), _p(wh), tile[0], tile[1],
-                   np.float32(o["z_near"]), np.float32(o["tau_cut"]), _p(depth), _p(rect), _p(prect))
+    if o.get("splat"):
+        lib().orc_keys_splat(N, _p(mu), _p(sc), _p(q), _p(k), V, _p(cf), _p(wh), tile[0], tile[1],
+                             np.float32(o["z_near"]), np.float32(o["tau_cut"]), np.float32(o["splat_dilation"]),
+                             _p(depth), _p(rect), _p(prect))
+    else:
+        lib().orc_keys(N, _p(mu), _p(sc), _p(q), _p(k), V, _p(cf), _p(wh), tile[0], tile[1],
+                       np.float32(o["z_near"]), np.float32(o["tau_cut"]), _p(depth), _p(rect), _p(prect))
     return (depth, rect, prect) if with_pixels else (depth, rect)
 
 
@@ -301,6 +318,18 @@ def tau(scene, g, o, d):
     lib().orc_tau(_p(mu), _p(sc), _p(q), float(scene.kappa[g]), _p(_c(o, np.float64)),
                   _p(_c(d, np.float64)), _p(out))
     return dict(zip(("tau", "a", "b", "c", "gamma", "beta", "gmax"), out.tolist()))
+
+
+def splat2d(scene, g, cam, dilation=0.0):
+    """The projected 2D Gaussian of Gaussian g (Eq. 7, FP64): (mu' [2], Sigma' [2, 2]) in pixel index
+    coordinates (pixel x has its centre at x), or None when it is not in front of the camera."""
+    out = np.zeros(6, np.float64)
+    cf, wh = cam_arrays([cam])
+    lib().orc_splat2d(_p(_c(scene.mu[g], np.float64)), _p(_c(scene.scale[g], np.float64)),
+                      _p(_c(scene.quat[g], np.float64)), _p(cf), _p(wh), float(dilation), _p(out))
+    if out[5] == 0:
+        return None
+    return out[:2].copy(), np.array([[out[2], out[3]], [out[3], out[4]]])
 
 
 def sh_basis(degree, direction):

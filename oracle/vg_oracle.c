@@ -12,6 +12,8 @@
  *   - front-to-back alpha blending of the depth-sorted per-tile list (Sec. 4.1, Eq. 14);
  *   - analytic gradient of the blend by the chain rule through a, b, c (derived from Eq. 19);
  *   - tomography: proj = exp(-sum_i tau_i) on a parallel beam (Sec. 6.2, Eq. 21);
+ *   - the 3DGS comparison mode (Sec. 3.2, Eq. 5-7): alpha = o G'(p) with the splatted 2D
+ *     Gaussian of covariance J W Sigma W^T J^T, blended with the same Eq. 14 / Eq. 5;
  *   - the per-tile binning that the paper inherits from 3DGS (Sec. 7, "per-tile sorting"),
  *     with a conservative footprint computed by an FP32 key function (readings in the
  *     design notes: the footprint is the screen bounding box of the Mahalanobis-k
@@ -191,6 +193,88 @@ int64_t orc_keys(int n, const float *mu, const float *scale, const float *quat, 
             if (key_persp(mu + 3 * g, scale + 3 * g, quat + 4 * g, kappa[g], cam_f + 16 * v,
                           cam_wh[2 * v], cam_wh[2 * v + 1], tile_w, tile_h, z_near, tau_cut,
                           depth_bits + it, r, prect + 4 * it))
+                total += (int64_t)(r[2] - r[0] + 1) * (r[3] - r[1] + 1);
+        }
+    }
+    return total;
+}
+
+/* Splat-mode key function (the 3DGS comparison mode, Eq. 5-7), FP32, fixed operation order.
+ * The depth key is the camera z of the mean, as in key_persp.  The footprint is the pixel
+ * bounding box of the ellipse w' Sigma'^-1 w <= k^2 of the 2D Gaussian, Sigma' = J W Sigma W' J'
+ * + dilation I (Eq. 7, J the affine Jacobian of the projection at the mean), with
+ * k^2 = 2 ln 2 * e where opacity / alpha_cut = m 2^e, so that every pixel outside it has
+ * alpha = o G' < alpha_cut.  Its half-widths are k sqrt(Sigma'_xx) and k sqrt(Sigma'_yy). */
+static int key_splat(const float *mu, const float *s, const float *q, float opac, const float *cf,
+                     int W, int H, int tw, int th, float z_near, float alpha_cut, float dil,
+                     uint32_t *depth, int32_t rect[4], int32_t prect[4])
+{
+    rect[0] = rect[1] = rect[2] = rect[3] = -1;
+    prect[0] = prect[1] = prect[2] = prect[3] = -1;
+    *depth = 0xFFFFFFFFu;
+    float Sig[9], smax;
+    if (!cov_fp32(mu, s, q, opac, Sig, &smax)) return 0;
+    const float *C = cf;
+    const float *t = cf + 9;
+    float X = ((C[0] * mu[0] + C[1] * mu[1]) + C[2] * mu[2]) + t[0];
+    float Y = ((C[3] * mu[0] + C[4] * mu[1]) + C[5] * mu[2]) + t[1];
+    float Z = ((C[6] * mu[0] + C[7] * mu[1]) + C[8] * mu[2]) + t[2];
+    if (!(Z > z_near)) return 0;
+    memcpy(depth, &Z, 4);
+    float xr = opac / alpha_cut;
+    if (!(xr > 1.0f)) return 0;
+    int e;
+    if (xr > FLT_MAX)
+        e = 128;
+    else
+        (void)frexpf(xr, &e);
+    float k2 = (float)e * 1.3862944f;
+    float T[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            T[3 * i + j] = (C[3 * i] * Sig[j] + C[3 * i + 1] * Sig[3 + j]) + C[3 * i + 2] * Sig[6 + j];
+    float sxx = (T[0] * C[0] + T[1] * C[1]) + T[2] * C[2];
+    float sxz = (T[0] * C[6] + T[1] * C[7]) + T[2] * C[8];
+    float syy = (T[3] * C[3] + T[4] * C[4]) + T[5] * C[5];
+    float syz = (T[3] * C[6] + T[4] * C[7]) + T[5] * C[8];
+    float szz = (T[6] * C[6] + T[7] * C[7]) + T[8] * C[8];
+    float u = X / Z, v = Y / Z;
+    float jx = cf[12] / Z, jy = cf[13] / Z;
+    float exx = (sxx - 2.0f * (u * sxz)) + (u * u) * szz;
+    float eyy = (syy - 2.0f * (v * syz)) + (v * v) * szz;
+    if (!(exx > 0.0f)) exx = 0.0f;
+    if (!(eyy > 0.0f)) eyy = 0.0f;
+    float vx = (jx * jx) * exx + dil, vy = (jy * jy) * eyy + dil;
+    float hx = sqrtf(k2 * vx), hy = sqrtf(k2 * vy);
+    float mx = (u * cf[12] + cf[14]) - 0.5f, my = (v * cf[13] + cf[15]) - 0.5f;
+    int ix0, ix1, iy0, iy1;
+    pixel_span(mx - hx, mx + hx, W, &ix0, &ix1);
+    pixel_span(my - hy, my + hy, H, &iy0, &iy1);
+    if (ix0 > ix1 || iy0 > iy1) return 0;
+    rect[0] = ix0 / tw;
+    rect[1] = iy0 / th;
+    rect[2] = ix1 / tw;
+    rect[3] = iy1 / th;
+    prect[0] = ix0;
+    prect[1] = iy0;
+    prect[2] = ix1;
+    prect[3] = iy1;
+    return 1;
+}
+
+int64_t orc_keys_splat(int n, const float *mu, const float *scale, const float *quat, const float *opac,
+                       int n_views, const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
+                       float z_near, float alpha_cut, float dilation, uint32_t *depth_bits, int32_t *rect,
+                       int32_t *prect)
+{
+    int64_t total = 0;
+    for (int v = 0; v < n_views; ++v) {
+        for (int g = 0; g < n; ++g) {
+            int64_t it = (int64_t)v * n + g;
+            int32_t *r = rect + 4 * it;
+            if (key_splat(mu + 3 * g, scale + 3 * g, quat + 4 * g, opac[g], cam_f + 16 * v, cam_wh[2 * v],
+                          cam_wh[2 * v + 1], tile_w, tile_h, z_near, alpha_cut, dilation, depth_bits + it, r,
+                          prect + 4 * it))
                 total += (int64_t)(r[2] - r[0] + 1) * (r[3] - r[1] + 1);
         }
     }
@@ -483,6 +567,109 @@ static void pixel_dir(const cam64 *c, int x, int y, double d[3])
     for (int k = 0; k < 3; ++k) d[k] /= n;
 }
 
+/* ------------------------------------------------------------------ splat mode (Eq. 5-7)
+ * The 3DGS comparison mode: alpha = o G'(p) (Eq. 6), G' the 2D Gaussian with mean mu' the
+ * projection of mu and covariance Sigma' = J W Sigma W^T J^T (Eq. 7) plus an optional isotropic
+ * dilation, J the Jacobian of the pinhole projection at the camera-space mean t:
+ *   J = [[fx/tz, 0, -fx tx/tz^2], [0, fy/tz, -fy ty/tz^2]].
+ * Pixel (x, y) has its centre at index coordinates (x, y), so mu' = (fx tx/tz + cx - 1/2,
+ * fy ty/tz + cy - 1/2) in the same coordinates. */
+typedef struct {
+    double t[3];     /* camera-space mean */
+    double J[6];     /* row-major 2 x 3 */
+    double V[9];     /* camera-space covariance W Sigma W^T */
+    double S2[4];    /* Sigma' (2 x 2, row-major) */
+    double Q[4];     /* Sigma'^-1 */
+    double m[2];     /* mu' */
+    int ok;
+} splat64;
+
+static void splat_setup(const gauss64 *G, const cam64 *c, double dil, splat64 *S)
+{
+    S->ok = 0;
+    for (int i = 0; i < 3; ++i)
+        S->t[i] = c->R[3 * i] * G->mu[0] + c->R[3 * i + 1] * G->mu[1] + c->R[3 * i + 2] * G->mu[2] + c->t[i];
+    const double tx = S->t[0], ty = S->t[1], tz = S->t[2];
+    if (!(tz > 0)) return;
+    double Sig[9], WS[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += G->R[3 * i + k] * G->s[k] * G->s[k] * G->R[3 * j + k];
+            Sig[3 * i + j] = acc;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += c->R[3 * i + k] * Sig[3 * k + j];
+            WS[3 * i + j] = acc;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += WS[3 * i + k] * c->R[3 * j + k];
+            S->V[3 * i + j] = acc;
+        }
+    double *J = S->J;
+    J[0] = c->fx / tz;
+    J[1] = 0;
+    J[2] = -c->fx * tx / (tz * tz);
+    J[3] = 0;
+    J[4] = c->fy / tz;
+    J[5] = -c->fy * ty / (tz * tz);
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double acc = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) acc += J[3 * i + a] * S->V[3 * a + b] * J[3 * j + b];
+            S->S2[2 * i + j] = acc + (i == j ? dil : 0.0);
+        }
+    const double det = S->S2[0] * S->S2[3] - S->S2[1] * S->S2[2];
+    if (!(det > 0)) return;
+    S->Q[0] = S->S2[3] / det;
+    S->Q[1] = -S->S2[1] / det;
+    S->Q[2] = -S->S2[2] / det;
+    S->Q[3] = S->S2[0] / det;
+    S->m[0] = c->fx * tx / tz + c->cx - 0.5;
+    S->m[1] = c->fy * ty / tz + c->cy - 0.5;
+    S->ok = 1;
+}
+
+/* o G'(p) at pixel (x, y): returns the unclamped opacity, w = p - mu' and q = w' Q w. */
+static double splat_alpha(const splat64 *S, double opac, int x, int y, double w[2], double *q)
+{
+    w[0] = x - S->m[0];
+    w[1] = y - S->m[1];
+    *q = S->Q[0] * w[0] * w[0] + (S->Q[1] + S->Q[2]) * w[0] * w[1] + S->Q[3] * w[1] * w[1];
+    return opac * exp(-0.5 * *q);
+}
+
+/* Largest splat opacity: the clamp 1 - exp(-tau_max) (0.99 in the 3DGS convention), and at most
+ * 1 - 2^-24, so that 1 - alpha and the log-transmittance stay finite. */
+static double splat_alpha_max(double tau_max)
+{
+    double a = -expm1(-tau_max);
+    const double cap = 1.0 - 5.9604644775390625e-8;
+    return a < cap ? a : cap;
+}
+
+void orc_splat2d(const double *mu, const double *scale, const double *quat, const float *cam_f,
+                 const int32_t *cam_wh, double dil, double *out)
+{
+    gauss64 G;
+    prep64(mu, scale, quat, 1.0, &G);
+    cam64 cam;
+    cam_setup(cam_f, cam_wh, &cam);
+    splat64 S;
+    splat_setup(&G, &cam, dil, &S);
+    out[0] = S.m[0];
+    out[1] = S.m[1];
+    out[2] = S.S2[0];
+    out[3] = S.S2[1];
+    out[4] = S.S2[3];
+    out[5] = S.ok;
+}
+
 /* Output activation of the colour: the clamp max(x, 0), or with beta > 0 the softplus
  * (1/beta) ln(1 + e^(beta x)) (Supp. D, beta = 10), and its derivative. */
 static double colour_act(double x, double beta)
@@ -562,17 +749,22 @@ void orc_render(int n, const double *mu, const double *scale, const double *quat
     const double tau_skip = tau_skip_of(opts[0]);
     const double tau_max = opts[2], T_stop = opts[3];
     const double bg[3] = {opts[4], opts[5], opts[6]};
+    const int splat = opts[9] != 0;
+    const double amax = splat_alpha_max(tau_max);
     const int K = (sh_degree + 1) * (sh_degree + 1);
     gauss64 *G = (gauss64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(gauss64));
     double *col = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
     order_t *ord = (order_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(order_t));
+    splat64 *SP = (splat64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(splat64));
     for (int g = 0; g < n; ++g) prep64(mu + 3 * g, scale + 3 * g, quat + 4 * g, kappa[g], &G[g]);
     for (int v = 0; v < n_views; ++v) {
         cam64 cam;
         cam_setup(cam_f + 16 * v, cam_wh + 2 * v, &cam);
         double raw[3];
-        for (int g = 0; g < n; ++g)
+        for (int g = 0; g < n; ++g) {
             colour64(sh + (size_t)g * K * 3, sh_degree, &G[g], cam.o, col + 3 * g, raw, opts[8]);
+            if (splat) splat_setup(&G[g], &cam, opts[10], &SP[g]);
+        }
         int64_t n_ord = 0;
         if (brute) {
             for (int g = 0; g < n; ++g) {
@@ -608,11 +800,21 @@ void orc_render(int n, const double *mu, const double *scale, const double *quat
             for (int64_t k = lo; k < hi; ++k) {
                 int64_t g = brute ? ord[k].g : sorted_g[k];
                 if (!brute && outside(prect, (int64_t)v * n + g, x, y)) continue;
-                double a, b, c, p[3];
-                double tau = tau64(&G[g], cam.o, d, &a, &b, &c, p);
-                if (tau > tau_max) tau = tau_max;
-                if (tau < tau_skip) continue;
-                double alpha = -expm1(-tau);
+                double tau, alpha;
+                if (splat) {   /* Eq. 6: alpha = o G'(p), clamped; tau = -ln(1 - alpha) */
+                    if (!SP[g].ok) continue;
+                    double w[2], q;
+                    alpha = splat_alpha(&SP[g], G[g].kap, x, y, w, &q);
+                    if (alpha > amax) alpha = amax;
+                    if (alpha < opts[0]) continue;
+                    tau = -log1p(-alpha);
+                } else {
+                    double a, b, c, p[3];
+                    tau = tau64(&G[g], cam.o, d, &a, &b, &c, p);
+                    if (tau > tau_max) tau = tau_max;
+                    if (tau < tau_skip) continue;
+                    alpha = -expm1(-tau);
+                }
                 for (int ch = 0; ch < 3; ++ch) C[ch] += col[3 * g + ch] * alpha * T;
                 T *= exp(-tau);
                 ++nb;
@@ -626,6 +828,7 @@ void orc_render(int n, const double *mu, const double *scale, const double *quat
     free(G);
     free(col);
     free(ord);
+    free(SP);
 }
 
 /* ============================ analytic gradient ============================ */
@@ -659,6 +862,8 @@ static void acc_tau(double *acc, const gauss64 *G, double dLdtau, double tau, do
     atomic_add(&acc[12], dl / G->kap);
 }
 
+static void chain_R(const gauss64 *G, const double dR[9], double *dquat);
+
 /* Chain dL/dP into dL/dscale and dL/dquat (through the unit quaternion). */
 static void chain_P(const gauss64 *G, const double Gm[9], double *dscale, double *dquat)
 {
@@ -680,6 +885,12 @@ static void chain_P(const gauss64 *G, const double Gm[9], double *dscale, double
             for (int j = 0; j < 3; ++j) acc += (Gm[3 * a + j] + Gm[3 * j + a]) * R[3 * j + b];
             dR[3 * a + b] = acc * Dg[b];
         }
+    chain_R(G, dR, dquat);
+}
+
+/* Chain dL/dR (row-major) into dL/dquat through the unit quaternion. */
+static void chain_R(const gauss64 *G, const double dR[9], double *dquat)
+{
     /* R(w, x, y, z) entries differentiated by hand. */
     double w = G->qn[0], x = G->qn[1], y = G->qn[2], z = G->qn[3];
     double J[9][4] = {
@@ -694,6 +905,67 @@ static void chain_P(const gauss64 *G, const double Gm[9], double *dscale, double
     double dot = 0;
     for (int c = 0; c < 4; ++c) dot += G->qn[c] * dqn[c];
     for (int c = 0; c < 4; ++c) dquat[c] += (dqn[c] - G->qn[c] * dot) / G->qnorm;
+}
+
+/* Splat mode: chain the per-(view, Gaussian) sums dL/dQ = sum dL/dq w w^T (A[0..2] = xx, xy, yy)
+ * and dL/dmu' (A[4..5]) through Q = Sigma'^-1, Sigma' = J V J^T + dil I, V = W Sigma W^T,
+ * Sigma = R diag(s^2) R^T, mu' = (fx tx/tz, fy ty/tz) + const and J(t), t = W mu + t_cam. */
+static void chain_splat(const gauss64 *G, const splat64 *S, const cam64 *c, const double *A, double *dmu,
+                        double *dscale, double *dquat)
+{
+    const double dQ[4] = {A[0], A[1], A[1], A[2]};
+    const double *Q = S->Q, *J = S->J, *V = S->V, *W = c->R;
+    double T1[4], dS[4];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) T1[2 * i + j] = Q[2 * i] * dQ[j] + Q[2 * i + 1] * dQ[2 + j];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) dS[2 * i + j] = -(T1[2 * i] * Q[j] + T1[2 * i + 1] * Q[2 + j]);
+    double dV[9], dJ[6];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0;
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) acc += J[3 * i + a] * dS[2 * i + j] * J[3 * j + b];
+            dV[3 * a + b] = acc;
+        }
+    for (int i = 0; i < 2; ++i)
+        for (int a = 0; a < 3; ++a) {
+            double acc = 0;
+            for (int j = 0; j < 2; ++j)
+                for (int b = 0; b < 3; ++b) acc += dS[2 * i + j] * J[3 * j + b] * V[3 * b + a];
+            dJ[3 * i + a] = 2.0 * acc;
+        }
+    double dSig[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) acc += W[3 * i + a] * dV[3 * i + j] * W[3 * j + b];
+            dSig[3 * a + b] = acc;
+        }
+    const double *R = G->R;
+    for (int k = 0; k < 3; ++k) {
+        double acc = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) acc += R[3 * i + k] * dSig[3 * i + j] * R[3 * j + k];
+        dscale[k] += 2.0 * G->s[k] * acc;
+    }
+    double dR[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0;
+            for (int j = 0; j < 3; ++j) acc += (dSig[3 * a + j] + dSig[3 * j + a]) * R[3 * j + b];
+            dR[3 * a + b] = acc * G->s[b] * G->s[b];
+        }
+    chain_R(G, dR, dquat);
+    const double tx = S->t[0], ty = S->t[1], tz = S->t[2], fx = c->fx, fy = c->fy;
+    const double iz = 1.0 / tz, iz2 = iz * iz, iz3 = iz2 * iz;
+    double dt[3];
+    dt[0] = A[4] * fx * iz - dJ[2] * fx * iz2;
+    dt[1] = A[5] * fy * iz - dJ[5] * fy * iz2;
+    dt[2] = -A[4] * fx * tx * iz2 - A[5] * fy * ty * iz2 - dJ[0] * fx * iz2 + dJ[2] * 2.0 * fx * tx * iz3 -
+            dJ[4] * fy * iz2 + dJ[5] * 2.0 * fy * ty * iz3;
+    for (int k = 0; k < 3; ++k) dmu[k] += W[k] * dt[0] + W[3 + k] * dt[1] + W[6 + k] * dt[2];
 }
 
 typedef struct {
@@ -713,10 +985,13 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
     const double tau_skip = tau_skip_of(opts[0]);
     const double tau_max = opts[2], T_stop = opts[3];
     const double bg[3] = {opts[4], opts[5], opts[6]};
+    const int splat = opts[9] != 0;
+    const double amax = splat_alpha_max(tau_max);
     const int K = (sh_degree + 1) * (sh_degree + 1);
     gauss64 *G = (gauss64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(gauss64));
     double *col = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
     double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * ACC_N, sizeof(double));
+    splat64 *SP = (splat64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(splat64));
     for (int g = 0; g < n; ++g) prep64(mu + 3 * g, scale + 3 * g, quat + 4 * g, kappa[g], &G[g]);
     int64_t maxlen = 1;
     for (int v = 0; v < n_views; ++v) {
@@ -728,8 +1003,10 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
         cam64 cam;
         cam_setup(cam_f + 16 * v, cam_wh + 2 * v, &cam);
         double raw[3];
-        for (int g = 0; g < n; ++g)
+        for (int g = 0; g < n; ++g) {
             colour64(sh + (size_t)g * K * 3, sh_degree, &G[g], cam.o, col + 3 * g, raw, opts[8]);
+            if (splat) splat_setup(&G[g], &cam, opts[10], &SP[g]);
+        }
         memset(acc, 0, (size_t)(n > 0 ? n : 1) * ACC_N * sizeof(double));
         const int W = cam.W, H = cam.H;
         const int tiles_x = (W + tile_w - 1) / tile_w;
@@ -750,17 +1027,31 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
                 for (int64_t k = lo; k < hi; ++k) {
                     int64_t g = sorted_g[k];
                     if (outside(prect, (int64_t)v * n + g, x, y)) continue;
-                    double a, b, c, p[3];
-                    double tau = tau64(&G[g], cam.o, d, &a, &b, &c, p);
+                    double tau, alpha;
                     int clamped = 0;
-                    if (tau > tau_max) {
-                        tau = tau_max;
-                        clamped = 1;
+                    if (splat) {
+                        if (!SP[g].ok) continue;
+                        double w[2], q;
+                        alpha = splat_alpha(&SP[g], G[g].kap, x, y, w, &q);
+                        if (alpha > amax) {
+                            alpha = amax;
+                            clamped = 1;
+                        }
+                        if (alpha < opts[0]) continue;
+                        tau = -log1p(-alpha);
+                    } else {
+                        double a, b, c, p[3];
+                        tau = tau64(&G[g], cam.o, d, &a, &b, &c, p);
+                        if (tau > tau_max) {
+                            tau = tau_max;
+                            clamped = 1;
+                        }
+                        if (tau < tau_skip) continue;
+                        alpha = -expm1(-tau);
                     }
-                    if (tau < tau_skip) continue;
                     rec[nr].g = g;
                     rec[nr].tau = tau;
-                    rec[nr].alpha = -expm1(-tau);
+                    rec[nr].alpha = alpha;
                     rec[nr].T = T;
                     rec[nr].clamped = clamped;
                     ++nr;
@@ -781,7 +1072,21 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
                         dLdtau += gc[ch] * (cc * Tn - Rs[ch]);
                         Rs[ch] += cc * al * Ti;
                     }
-                    if (!rec[r].clamped) {
+                    if (!rec[r].clamped && splat) {
+                        /* tau = -ln(1 - alpha), alpha = o exp(-q/2), q = w' Q w, w = p - mu' */
+                        double w[2], q;
+                        const splat64 *S = &SP[g];
+                        splat_alpha(S, G[g].kap, x, y, w, &q);
+                        const double dLda = dLdtau / (1.0 - al);
+                        const double dLdq = -0.5 * al * dLda;
+                        double *A = &acc[ACC_N * g];
+                        atomic_add(&A[0], dLdq * w[0] * w[0]);
+                        atomic_add(&A[1], dLdq * w[0] * w[1]);
+                        atomic_add(&A[2], dLdq * w[1] * w[1]);
+                        atomic_add(&A[4], -2.0 * dLdq * (S->Q[0] * w[0] + S->Q[1] * w[1]));
+                        atomic_add(&A[5], -2.0 * dLdq * (S->Q[2] * w[0] + S->Q[3] * w[1]));
+                        atomic_add(&A[12], dLda * al / G[g].kap);
+                    } else if (!rec[r].clamped) {
                         double a, b, c, p[3];
                         double tau = tau64(&G[g], cam.o, d, &a, &b, &c, p);
                         acc_tau(&acc[ACC_N * g], &G[g], dLdtau, tau, a, b, d, p);
@@ -796,8 +1101,12 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
             int any = 0;
             for (int k = 0; k < ACC_N; ++k) any |= (A[k] != 0.0);
             if (!any) continue;
-            chain_P(&G[g], A, dscale + 3 * g, dquat + 4 * g);
-            for (int k = 0; k < 3; ++k) dmu[3 * g + k] += A[9 + k];
+            if (splat) {
+                chain_splat(&G[g], &SP[g], &cam, A, dmu + 3 * g, dscale + 3 * g, dquat + 4 * g);
+            } else {
+                chain_P(&G[g], A, dscale + 3 * g, dquat + 4 * g);
+                for (int k = 0; k < 3; ++k) dmu[3 * g + k] += A[9 + k];
+            }
             dkappa[g] += A[12];
             /* colour: rgb = act(sh . Y(dir) + 0.5), dir = (mu - o)/|mu - o| */
             double rgb[3], rw[3], dir[3], n2 = 0;
@@ -827,6 +1136,7 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
     free(G);
     free(col);
     free(acc);
+    free(SP);
 }
 
 /* ================================ voxel density ================================ */

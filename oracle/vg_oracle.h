@@ -11,9 +11,13 @@
  * The FP64 paths (render, gradient, tomography, tau) take double parameters so that
  * finite differences can perturb them; the key functions take the FP32 values the GPU sees.
  *
- * Options are double[9] = { alpha_min, tau_cut, tau_max, T_stop, bg_r, bg_g, bg_b, z_near,
- * softplus_beta }; softplus_beta > 0 replaces the colour clamp max(x, 0) by the softplus
- * (1/beta) ln(1 + e^(beta x)) (Supp. D).  The density reparameterisation of Eq. 20 is applied
+ * Options are double[11] = { alpha_min, tau_cut, tau_max, T_stop, bg_r, bg_g, bg_b, z_near,
+ * softplus_beta, splat, splat_dilation }; softplus_beta > 0 replaces the colour clamp max(x, 0)
+ * by the softplus (1/beta) ln(1 + e^(beta x)) (Supp. D).  splat != 0 selects the 3DGS comparison
+ * mode (Eq. 5-7): the density array holds the peak opacity o, alpha = min(o G'(p), alpha_max)
+ * with G' the projected 2D Gaussian of covariance J W Sigma W^T J^T + splat_dilation I,
+ * alpha_max = min(1 - exp(-tau_max), 1 - 2^-24), pairs with alpha < alpha_min skipped, and the
+ * footprint from orc_keys_splat (alpha_cut = tau_cut).  The density reparameterisation of Eq. 20 is applied
  * by the Python wrapper (kappa from theta and the scales) before these functions are called.
  */
 #ifndef VG_ORACLE_H
@@ -34,6 +38,15 @@ int64_t orc_tomo_keys(int n, const float *mu, const float *scale, const float *q
                       const float *kappa, int n_angles, const float *angles, int det_w, int det_h,
                       float pitch_u, float pitch_v, float u0, float v0, int tile_w, int tile_h,
                       float tau_cut, int32_t *rect, int32_t *prect);
+/* Splat-mode key function: same depth key; footprint = pixel box of the 2D Gaussian's
+ * ellipse outside which alpha < alpha_cut. */
+int64_t orc_keys_splat(int n, const float *mu, const float *scale, const float *quat, const float *opac,
+                       int n_views, const float *cam_f, const int32_t *cam_wh, int tile_w, int tile_h,
+                       float z_near, float alpha_cut, float dilation, uint32_t *depth_bits, int32_t *rect,
+                       int32_t *prect);
+/* The projected 2D Gaussian of one Gaussian (FP64): out = { mu'_x, mu'_y, S'_xx, S'_xy, S'_yy, ok }. */
+void orc_splat2d(const double *mu, const double *scale, const double *quat, const float *cam_f,
+                 const int32_t *cam_wh, double dil, double *out);
 /* Stable sort of (tile, depth, Gaussian) instances; fills tile_start[n_tiles+1], sorted_g. */
 int64_t orc_bin(int n, int n_views, const uint32_t *depth_bits, const int32_t *rect,
                 const int32_t *view_tiles_x, const int32_t *view_tile_base, int64_t n_tiles_total,

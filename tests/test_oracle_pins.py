@@ -557,3 +557,163 @@ def test_voxel_boxes_are_conservative():
     assert np.all(b - a >= -1e-12)
     assert np.max(b - a) < scene.n * cut
     assert np.max(b - a) > 0            # truncation happens
+
+
+# ------------------------------------------------------------------ 3DGS splat mode (Eq. 5-7)
+def _project(cam, x):
+    """Pinhole projection of a world point to pixel index coordinates (pixel x has its centre
+    at x + 1/2 in the continuous image plane), written out from the camera model."""
+    R = np.asarray(cam.R, np.float64)
+    t = np.asarray(cam.t, np.float64)
+    fx, fy, cx, cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+    X, Y, Z = R @ np.asarray(x, np.float64) + t
+    return np.array([fx * X / Z + cx - 0.5, fy * Y / Z + cy - 0.5]), Z
+
+
+def _splat_alpha_all(scene, cam, dil):
+    """o G'(p) of every (Gaussian, pixel) from the oracle's 2D Gaussians, evaluated here."""
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    out = np.zeros((scene.n, cam.height, cam.width))
+    for g in range(scene.n):
+        sp = oracle.splat2d(scene, g, cam, dil)
+        if sp is None:
+            continue
+        m, S = sp
+        Q = np.linalg.inv(S)
+        wx, wy = xs - m[0], ys - m[1]
+        q = Q[0, 0] * wx * wx + 2 * Q[0, 1] * wx * wy + Q[1, 1] * wy * wy
+        out[g] = float(scene.kappa[g]) * np.exp(-0.5 * q)
+    return out
+
+
+@pytest.mark.parametrize("dil", [0.0, 0.3])
+def test_splat_isotropic_on_axis_is_the_scaled_disc(dil):
+    """A sphere of radius s on the optical axis at distance z projects to an isotropic 2D Gaussian
+    of standard deviation f s / z (plus the dilation) centred at the principal point:
+    alpha = o exp(-r^2 / (2 ((f s / z)^2 + dil))) at every pixel (brute force, black background)."""
+    mu, s, o = (0.2, -0.1, 0.3), 0.07, 0.8
+    eye = np.array([0.2, -0.1, 0.3]) + np.array([0.5, -0.3, -3.5])
+    cam = synth.look_at(eye, mu, 41, 33, 50.0)
+    scene = one_gaussian(mu, (s, s, s), (0.7, 0.2, -0.5, 0.1), o)
+    opts = dict(oracle.EXACT, splat=True, splat_dilation=dil)
+    L = oracle.lists(scene, [cam], opts)
+    _, T, _ = oracle.render(scene, [cam], opts, L, brute=True)
+    c, z = _project(cam, np.asarray(scene.mu[0], np.float64))
+    f = float(np.float32(cam.fx))
+    sig2 = (f * float(scene.scale[0, 0]) / z) ** 2 + dil
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    want = float(np.float32(o)) * np.exp(-((xs - c[0]) ** 2 + (ys - c[1]) ** 2) / (2 * sig2))
+    # the FP32 camera rotation is orthonormal to ~6e-8, which moves alpha by ~1e-8
+    assert np.max(np.abs((1.0 - T[0]) - want)) < 1e-7
+
+
+def test_splat_covariance_is_the_projection_jacobian():
+    """Off-axis anisotropic Gaussians: the oracle's mu' is the pinhole projection of mu and its
+    Sigma' equals J_fd Sigma J_fd^T with J_fd the central-difference Jacobian of that projection
+    (Eq. 7); a tiny Gaussian's projected samples have that covariance (the affine approximation)."""
+    rng = np.random.default_rng(31)
+    cam = synth.look_at((0.7, -1.2, -3.4), (0.1, 0.2, 0.0), 64, 48, 70.0)
+    for g_seed in range(6):
+        r = np.random.default_rng(100 + g_seed)
+        mu = r.uniform(-0.6, 0.6, 3)
+        sc = np.exp(r.uniform(-3.5, -1.5, 3))
+        q = r.normal(size=4)
+        scene = one_gaussian(mu, sc, q, 0.5)
+        m, S = oracle.splat2d(scene, 0, cam, 0.0)
+        x0 = np.asarray(scene.mu[0], np.float64)
+        c, _ = _project(cam, x0)
+        assert np.max(np.abs(m - c)) < 1e-9
+        J = np.zeros((2, 3))
+        for k in range(3):
+            h = 1e-5
+            e = np.zeros(3)
+            e[k] = h
+            J[:, k] = (_project(cam, x0 + e)[0] - _project(cam, x0 - e)[0]) / (2 * h)
+        Sfd = J @ cov_world(scene, 0) @ J.T
+        assert np.max(np.abs(S - Sfd)) < 1e-6 * np.max(np.abs(S)), (S, Sfd)
+    # sampling: 400,000 points of a Gaussian 1000x smaller than its distance
+    scene = one_gaussian((0.3, -0.2, 0.1), (0.004, 0.002, 0.001), (0.3, 0.8, -0.2, 0.4), 0.5)
+    m, S = oracle.splat2d(scene, 0, cam, 0.0)
+    x = rng.multivariate_normal(np.asarray(scene.mu[0], np.float64), cov_world(scene, 0), size=400_000)
+    R = np.asarray(cam.R, np.float64)
+    t = np.asarray(cam.t, np.float64)
+    Xc = x @ R.T + t
+    fx, fy = float(np.float32(cam.fx)), float(np.float32(cam.fy))
+    px = np.stack([fx * Xc[:, 0] / Xc[:, 2], fy * Xc[:, 1] / Xc[:, 2]], 1)
+    Ss = np.cov(px.T)
+    assert np.max(np.abs(Ss - S)) < 0.02 * np.max(np.abs(S))
+
+
+@pytest.mark.parametrize("mode", ["exact", "3dgs"])
+def test_splat_footprint_is_conservative(mode):
+    """Every (pixel, Gaussian) pair with o G' >= alpha_cut lies in the Gaussian's footprint
+    rectangle and tile lists (brute force over the 2,000-Gaussian 128x128 scene), and the tiled
+    blend equals the brute-force blend up to the truncation."""
+    opts = dict(oracle.EXACT, splat=True) if mode == "exact" else dict(oracle.SPLAT_3DGS)
+    scene, cams = synth.config1()
+    scene.kappa = np.random.default_rng(5).uniform(0.02, 1.0, scene.n).astype(np.float32)
+    cam = cams[0]
+    L = oracle.lists(scene, cams, opts)
+    al = _splat_alpha_all(scene, cam, opts["splat_dilation"])
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    tile = (ys // 16) * L["tiles_x"][0] + xs // 16
+    member = np.zeros((scene.n, L["n_tiles"]), bool)
+    for t in range(L["n_tiles"]):
+        member[L["sorted_g"][L["tile_start"][t]:L["tile_start"][t + 1]], t] = True
+    zc = (scene.mu.astype(np.float64) @ np.asarray(cam.R, np.float64).T + cam.t)[:, 2]
+    need = (al >= opts["tau_cut"]) & (zc > opts["z_near"])[:, None, None]
+    g_idx, py, px = np.nonzero(need)
+    assert g_idx.size > 1000
+    assert member[g_idx, tile[py, px]].all()
+    pr = L["prect"][0]
+    assert ((px >= pr[g_idx, 0]) & (px <= pr[g_idx, 2]) & (py >= pr[g_idx, 1]) & (py <= pr[g_idx, 3])).all()
+    rgb, T, _ = oracle.render(scene, cams, opts, L)
+    rgbb, Tb, _ = oracle.render(scene, cams, opts, L, brute=True)
+    bound = 0.0 if mode == "3dgs" else 2 * opts["tau_cut"] * scene.n
+    assert np.max(np.abs(rgb[0] - rgbb[0])) <= bound + 1e-15
+
+
+def test_splat_3dgs_thresholds():
+    """3DGS conventions in splat mode: alpha = min(o G', 0.99), pairs with alpha < 1/255 skipped:
+    one opaque Gaussian (o = 1) leaves T = 1 - min(G', 0.99) where G' >= 1/255, else T = 1."""
+    mu = (0.0, 0.0, 0.0)
+    cam = synth.look_at((0.0, 0.0, -4.0), mu, 33, 31, 40.0)
+    scene = one_gaussian(mu, (0.12, 0.08, 0.1), (0.9, 0.1, 0.3, -0.2), 1.0)
+    opts = dict(oracle.SPLAT_3DGS)
+    L = oracle.lists(scene, [cam], opts)
+    _, T, _ = oracle.render(scene, [cam], opts, L)
+    al = _splat_alpha_all(scene, cam, 0.3)[0]
+    want = np.where(al >= 1.0 / 255.0, 1.0 - np.minimum(al, 0.99), 1.0)
+    assert np.max(np.abs(T[0] - want)) < 1e-12
+    assert np.isclose(T[0].min(), 0.01) and (T[0] == 1.0).any()
+
+
+@pytest.mark.parametrize("variant", ["exact", "dilated_clamped"])
+def test_splat_gradient_matches_finite_differences(variant):
+    """Analytic FP64 gradient of the splat-mode blend (lists held fixed) vs central differences."""
+    rng = np.random.default_rng(12)
+    scene = synth.uniform_scene(9, 322, log_scale=(-2.5, -1.5), kappa=(0.5, 6.0), sh_degree=2, sh_std=0.3,
+                                flatten_frac=0.3, extent=0.4)
+    scene = synth.Scene(*(np.asarray(getattr(scene, f), np.float64) for f in ("mu", "scale", "quat", "kappa", "sh")),
+                        2)
+    scene.quat = scene.quat * rng.uniform(0.7, 1.3, (scene.n, 1))
+    scene.kappa = rng.uniform(0.1, 0.95, scene.n)
+    cams = synth.small_views(2, 1, [(20, 18), (17, 23)])
+    opts = dict(oracle.EXACT, splat=True, bg=(0.3, 0.1, 0.6))
+    if variant == "dilated_clamped":
+        opts.update(splat_dilation=0.3, tau_max=1.0, softplus_beta=10.0)
+        scene.kappa[:3] = 0.99
+    L = oracle.lists(scene, cams, opts)
+    wr = [rng.normal(size=(c.height, c.width, 3)) for c in cams]
+    wT = [rng.normal(size=(c.height, c.width)) for c in cams]
+
+    def loss():
+        rgb, T, _ = oracle.render(scene, cams, opts, L)
+        return sum(float(np.sum(a * b)) for a, b in zip(rgb, wr)) + sum(float(np.sum(a * b)) for a, b in zip(T, wT))
+
+    g = oracle.render_grad(scene, cams, opts, L, wr, wT)
+    for name, arr in (("mu", scene.mu), ("scale", scene.scale), ("quat", scene.quat), ("kappa", scene.kappa),
+                      ("sh", scene.sh)):
+        idx = range(arr.size) if arr.size <= 40 else rng.choice(arr.size, 40, replace=False)
+        assert np.max(np.abs(g[name])) > 0, name
+        _fd_check(loss, arr, g[name], idx, rtol=2e-6)
