@@ -109,6 +109,8 @@ typedef struct {
                                    differs. */
     float softplus_beta;  /* 0: rgb = max(sh . Y + 0.5, 0); > 0: rgb = softplus of the same with
                              this beta, ln(1 + e^(beta x)) / beta (Supp. D uses 10) */
+    float splat_dilation; /* VG_FLAG_SPLAT only: added to both variances of the 2D covariance
+                             (pixels^2; 0 = Eq. 7 as printed, 0.3 = the 3DGS rasterizer) */
 } vg_opts;
 
 #define VG_FLAG_FIXED_CAPACITY 1u  /* vg_bin_sort never synchronises: the instance count stays
@@ -130,6 +132,18 @@ typedef struct {
                                       1 - x = m 2^e) */
 #define VG_FLAG_COUNT_PAIRS 2u     /* render_fwd / render_bwd also count evaluated (pixel,
                                       Gaussian) pairs into vg_stats (slower; for roofline) */
+#define VG_FLAG_SPLAT 16u          /* the 3DGS comparison mode (Sec. 3.2, Eq. 5-7) in the same
+                                      pipeline: the density input holds the peak opacity o and
+                                      alpha = min(o G'(p), alpha_max), G' the 2D Gaussian with
+                                      the projected mean and covariance J W Sigma W^T J^T +
+                                      splat_dilation I (J the projection's Jacobian at the
+                                      mean), alpha_max = min(1 - exp(-tau_max), 1 - 2^-24);
+                                      pairs with alpha < alpha_min are skipped and footprints
+                                      cover every pixel with o G' >= tau_cut.  Keys, lists,
+                                      blending, the backward (dkappa receives dL/do) and the
+                                      outputs are otherwise those of the default mode.  Not
+                                      combined with VG_FLAG_DENSITY_THETA, tomography or the
+                                      cone beam. */
 
 typedef struct {
     int64_t n_items;          /* views x Gaussians of the last preprocess                    */

@@ -25,6 +25,7 @@ FLAG_FIXED_CAPACITY = 1
 FLAG_COUNT_PAIRS = 2
 FLAG_GRAD_ZERO = 4
 FLAG_DENSITY_THETA = 8
+FLAG_SPLAT = 16
 _STATUS = {0: "VG_OK", 1: "VG_ERR_INVALID_ARG", 2: "VG_ERR_CUDA", 3: "VG_ERR_OOM", 4: "VG_ERR_CAPACITY",
            5: "VG_ERR_TIMEOUT", 6: "VG_ERR_UNSUPPORTED", 7: "VG_ERR_STATE"}
 TILE = 16
@@ -57,7 +58,8 @@ class _Beam(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("alpha_min", ctypes.c_float), ("tau_cut", ctypes.c_float), ("tau_max", ctypes.c_float),
                 ("T_stop", ctypes.c_float), ("bg", ctypes.c_float * 3), ("z_near", ctypes.c_float),
-                ("flags", ctypes.c_uint32), ("pixels_per_thread", ctypes.c_int32), ("softplus_beta", ctypes.c_float)]
+                ("flags", ctypes.c_uint32), ("pixels_per_thread", ctypes.c_int32), ("softplus_beta", ctypes.c_float),
+                ("splat_dilation", ctypes.c_float)]
 
 
 class _Grid(ctypes.Structure):
@@ -148,6 +150,7 @@ class Opts:
     flags: int = 0
     pixels_per_thread: int = 0
     softplus_beta: float = 0.0
+    splat_dilation: float = 0.0
 
     @staticmethod
     def exact(**kw):
@@ -168,6 +171,7 @@ class Opts:
             o.bg[k] = self.bg[k]
         o.z_near, o.flags, o.pixels_per_thread = self.z_near, self.flags, self.pixels_per_thread
         o.softplus_beta = self.softplus_beta
+        o.splat_dilation = self.splat_dilation
         return o
 
 

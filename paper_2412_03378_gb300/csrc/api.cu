@@ -194,6 +194,8 @@ GaussIn to_in(const vg_gaussians *g) {
     r.sh_degree = g->sh_degree;
     r.density_theta = 0;
     r.softplus_beta = 0.0f;
+    r.splat = 0;
+    r.splat_dil = 0.0f;
     return r;
 }
 
@@ -397,10 +399,17 @@ static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const 
     }
     if (!(opts->softplus_beta >= 0.0f) || !std::isfinite(opts->softplus_beta))
         return fail(ws, VG_ERR_INVALID_ARG, "softplus_beta must be finite and >= 0");
+    const bool splat = (opts->flags & VG_FLAG_SPLAT) != 0;
+    if (splat && (opts->flags & VG_FLAG_DENSITY_THETA))
+        return fail(ws, VG_ERR_INVALID_ARG, "VG_FLAG_SPLAT and VG_FLAG_DENSITY_THETA exclude each other");
+    if (splat && !(opts->splat_dilation >= 0.0f && std::isfinite(opts->splat_dilation)))
+        return fail(ws, VG_ERR_INVALID_ARG, "splat_dilation must be finite and >= 0");
     ws->opts = *opts;
     ws->g = to_in(g);
     ws->g.density_theta = (opts->flags & VG_FLAG_DENSITY_THETA) ? 1 : 0;
     ws->g.softplus_beta = opts->softplus_beta;
+    ws->g.splat = splat ? 1 : 0;
+    ws->g.splat_dil = splat ? opts->splat_dilation : 0.0f;
     ws->tomo_read = false;
     VG_TRY(reserve_items(ws, n_items));
     VG_TRY(ensure(ws, ws->views, (size_t)n_views, "views"));
@@ -427,6 +436,11 @@ static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const 
     ws->bp.T_stop = opts->T_stop;
     for (int c = 0; c < 3; ++c) ws->bp.bg[c] = opts->bg[c];
     ws->bp.pixel_test = ws->bp.tau_skip < opts->tau_cut ? 1 : 0;
+    // splat mode: alpha <= min(1 - exp(-tau_max), 1 - 2^-24) keeps 1 - alpha and S = sum tau finite
+    ws->bp.splat = splat ? 1 : 0;
+    ws->bp.alpha_min = opts->alpha_min;
+    ws->bp.alpha_max = (float)std::min(-std::expm1(-(double)opts->tau_max), 1.0 - 5.9604644775390625e-8);
+    if (splat) ws->bp.pixel_test = opts->alpha_min < opts->tau_cut ? 1 : 0;
     VG_CUDA(ws, cudaMemsetAsync(ws->counters.p, 0, sizeof(unsigned long long), st));
     if (n_items > 0) {
         ProfScope ps(ws, ST_PRE, st);
@@ -574,6 +588,7 @@ vg_status vg_project_cone(vg_workspace *ws, const vg_gaussians *g, const vg_came
                           float *dquat, float *dkappa, void *stream) {
     if (!ws) return VG_ERR_INVALID_ARG;
     if (!opts) return fail(ws, VG_ERR_INVALID_ARG, "opts is NULL");
+    if (opts->flags & VG_FLAG_SPLAT) return fail(ws, VG_ERR_INVALID_ARG, "the cone beam has no splat mode");
     // With no skip, clamp or early stop the blend's final transmittance is exp(-sum tau): the
     // cone-beam projection.  Its gradient is the blend's dL/dT_final term alone.
     vg_opts o = *opts;
@@ -600,6 +615,7 @@ vg_status vg_query_density(vg_workspace *ws, const vg_gaussians *g, const vg_gri
     VG_TRY(check_gauss(ws, g, false));
     if (!grid || !opts) return fail(ws, VG_ERR_INVALID_ARG, "grid or opts is NULL");
     if (!finite_pos(opts->tau_cut)) return fail(ws, VG_ERR_INVALID_ARG, "tau_cut (sigma_cut) must be finite and > 0");
+    if (opts->flags & VG_FLAG_SPLAT) return fail(ws, VG_ERR_INVALID_ARG, "the density query has no splat mode");
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nx > 32767 || grid->ny > 32767 || grid->nz > 32767)
         return fail(ws, VG_ERR_INVALID_ARG, "grid sizes must be 1..32767");
     for (int a = 0; a < 3; ++a)
@@ -733,6 +749,7 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
         !std::isfinite(beam->v0))
         return fail(ws, VG_ERR_INVALID_ARG, "invalid beam geometry");
     if (!opts || !finite_pos(opts->tau_cut)) return fail(ws, VG_ERR_INVALID_ARG, "opts->tau_cut must be finite and > 0");
+    if (opts->flags & VG_FLAG_SPLAT) return fail(ws, VG_ERR_INVALID_ARG, "tomography has no splat mode");
     if (!proj) return fail(ws, VG_ERR_INVALID_ARG, "proj is NULL");
     if (dL_dproj && g->n > 0 && (!dmu || !dscale || !dquat || !dkappa))
         return fail(ws, VG_ERR_INVALID_ARG, "a gradient pointer is NULL");

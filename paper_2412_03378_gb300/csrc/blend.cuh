@@ -249,6 +249,58 @@ __device__ __forceinline__ void pair_eval_at(const float4 &r0, const float4 &r1,
     e.tau = __fmul_rn(ex2_approx(fmaf(e.m2, -kHalfLog2e, __fadd_rn(r5.x, Lp))), e.rs);
 }
 
+// ------------------------------------------------------------------ splat mode (Eq. 5-7)
+// The record's C rows hold L^T (Sigma'^-1 = L L^T) relative to the reference pixel, its third
+// row zero: q = |C u|^2 = w' Sigma'^-1 w needs two components per pixel, and
+//   alpha = min(o exp(-q/2), alpha_max) = min(ex2(log2 o - q log2(e)/2), alpha_max).
+// The blend runs on tau = -ln(1 - alpha) (log1pf, exact to rounding for small alpha), so the
+// transmittance update, the stored S = sum tau and the backward's log-space replay are those
+// of the default mode.  Forward and backward evaluate with the same operations.
+struct SplatBase {
+    float dx, dy;    // offset of the thread's first pixel from the reference pixel
+    float c0, c1;    // C u there (two components)
+};
+
+__device__ __forceinline__ void splat_base(const float4 &r2, const float4 &r3, const float4 &r4, float x0, float y0,
+                                           SplatBase &b) {
+    b.dx = __fsub_rn(x0, r4.z);
+    b.dy = __fsub_rn(y0, r4.w);
+    b.c0 = fmaf(r2.y, b.dx, fmaf(r3.x, b.dy, r3.w));
+    b.c1 = fmaf(r2.z, b.dx, fmaf(r3.y, b.dy, r4.x));
+}
+
+// (dx, dy) and q = |C u|^2 of the pixel at offset (sx, sy) from the thread's first pixel;
+// returns the unclamped opacity o G'(p).
+__device__ __forceinline__ float splat_at(const float4 &r2, const float4 &r3, const float4 &r5, const SplatBase &b,
+                                          bool sx, bool sy, float &dx, float &dy, float &q) {
+    float c0 = b.c0, c1 = b.c1;
+    dx = sx ? __fadd_rn(b.dx, 1.0f) : b.dx;
+    dy = sy ? __fadd_rn(b.dy, 1.0f) : b.dy;
+    if (sx) {
+        c0 = __fadd_rn(c0, r2.y);
+        c1 = __fadd_rn(c1, r2.z);
+    }
+    if (sy) {
+        c0 = __fadd_rn(c0, r3.x);
+        c1 = __fadd_rn(c1, r3.y);
+    }
+    q = fmaf(c0, c0, __fmul_rn(c1, c1));
+    return ex2_approx(fmaf(q, -kHalfLog2e, r5.x));
+}
+
+// The opacity box test of the splat mode: box_may_blend with the record's A = (0, 0, e_z)
+// (|A u| = 1) and the amplitude o alone, so the radius is r^2 = 2 ln(o / alpha_min).
+__device__ __forceinline__ BoxCull box_cull_splat(const WarpBox &b, float alpha_min) {
+    BoxCull c;
+    c.x0 = (float)b.x0;
+    c.y0 = (float)b.y0;
+    c.x1 = (float)b.x1;
+    c.y1 = (float)b.y1;
+    c.l2dmax = 1e-4f;
+    c.l2tskip = __log2f(alpha_min);
+    return c;
+}
+
 // Warp reduce-scatter of NP per-lane values (NP a power of two, 2..32).  Each exchange step
 // with partner lane^w keeps half of the lane's values and sends the other half while more than
 // one value is left (NP/2 + NP/4 + ... shuffles), then plain butterfly adds finish the sum.

@@ -208,6 +208,55 @@ __device__ __forceinline__ int key_persp(const ViewInfo &V, const float mu[3], c
     return 2;
 }
 
+// Splat-mode key function (the 3DGS comparison mode, Eq. 5-7): the depth key of key_persp and
+// the pixel bounding box of the 2D Gaussian's ellipse w' Sigma'^-1 w <= k^2, Sigma' = J W Sigma
+// W^T J^T + dil I with J the projection's Jacobian at the mean, k^2 = 2 ln 2 * e where
+// opacity / alpha_cut = m 2^e (so that every pixel outside has o G' < alpha_cut).  Its
+// half-widths are k sqrt(Sigma'_xx) and k sqrt(Sigma'_yy).  FP32, fixed operation order.
+// Returns 0 = invalid/behind z_near, 1 = valid but no footprint, 2 = visible.
+__device__ __forceinline__ int key_splat(const ViewInfo &V, const float mu[3], const float Sig[9], float opac,
+                                         float z_near, float alpha_cut, float dil, uint32_t &depth, short4 &rect,
+                                         short4 &prect) {
+    const float *C = V.R;
+    float X = VG_ADD(VG_ADD(VG_ADD(VG_MUL(C[0], mu[0]), VG_MUL(C[1], mu[1])), VG_MUL(C[2], mu[2])), V.t[0]);
+    float Y = VG_ADD(VG_ADD(VG_ADD(VG_MUL(C[3], mu[0]), VG_MUL(C[4], mu[1])), VG_MUL(C[5], mu[2])), V.t[1]);
+    float Z = VG_ADD(VG_ADD(VG_ADD(VG_MUL(C[6], mu[0]), VG_MUL(C[7], mu[1])), VG_MUL(C[8], mu[2])), V.t[2]);
+    if (!(Z > z_near)) return 0;
+    depth = __float_as_uint(Z);
+    const float xr = VG_DIV(opac, alpha_cut);
+    if (!(xr > 1.0f)) return 1;
+    const int e = (xr > FLT_MAX) ? 128 : (int)((__float_as_uint(xr) >> 23) & 0xFFu) - 126;
+    const float k2 = VG_MUL((float)e, 1.3862944f);
+    float T[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            T[3 * i + j] = VG_ADD(VG_ADD(VG_MUL(C[3 * i], Sig[j]), VG_MUL(C[3 * i + 1], Sig[3 + j])),
+                                  VG_MUL(C[3 * i + 2], Sig[6 + j]));
+    const float sxx = VG_ADD(VG_ADD(VG_MUL(T[0], C[0]), VG_MUL(T[1], C[1])), VG_MUL(T[2], C[2]));
+    const float sxz = VG_ADD(VG_ADD(VG_MUL(T[0], C[6]), VG_MUL(T[1], C[7])), VG_MUL(T[2], C[8]));
+    const float syy = VG_ADD(VG_ADD(VG_MUL(T[3], C[3]), VG_MUL(T[4], C[4])), VG_MUL(T[5], C[5]));
+    const float syz = VG_ADD(VG_ADD(VG_MUL(T[3], C[6]), VG_MUL(T[4], C[7])), VG_MUL(T[5], C[8]));
+    const float szz = VG_ADD(VG_ADD(VG_MUL(T[6], C[6]), VG_MUL(T[7], C[7])), VG_MUL(T[8], C[8]));
+    const float u = VG_DIV(X, Z), v = VG_DIV(Y, Z);
+    const float jx = VG_DIV(V.fx, Z), jy = VG_DIV(V.fy, Z);
+    float exx = VG_ADD(VG_SUB(sxx, VG_MUL(2.0f, VG_MUL(u, sxz))), VG_MUL(VG_MUL(u, u), szz));
+    float eyy = VG_ADD(VG_SUB(syy, VG_MUL(2.0f, VG_MUL(v, syz))), VG_MUL(VG_MUL(v, v), szz));
+    if (!(exx > 0.0f)) exx = 0.0f;
+    if (!(eyy > 0.0f)) eyy = 0.0f;
+    const float vx = VG_ADD(VG_MUL(VG_MUL(jx, jx), exx), dil), vy = VG_ADD(VG_MUL(VG_MUL(jy, jy), eyy), dil);
+    const float hx = VG_SQRT(VG_MUL(k2, vx)), hy = VG_SQRT(VG_MUL(k2, vy));
+    const float mx = VG_SUB(VG_ADD(VG_MUL(u, V.fx), V.cx), 0.5f), my = VG_SUB(VG_ADD(VG_MUL(v, V.fy), V.cy), 0.5f);
+    int ix0, ix1, iy0, iy1;
+    pixel_span(VG_SUB(mx, hx), VG_ADD(mx, hx), V.W, ix0, ix1);
+    pixel_span(VG_SUB(my, hy), VG_ADD(my, hy), V.H, iy0, iy1);
+    if (ix0 > ix1 || iy0 > iy1) return 1;
+    rect = make_short4((short)(ix0 / kTile), (short)(iy0 / kTile), (short)(ix1 / kTile), (short)(iy1 / kTile));
+    prect = make_short4((short)ix0, (short)iy0, (short)ix1, (short)iy1);
+    return 2;
+}
+
 // ------------------------------------------------------------------ double-float arithmetic
 // Error-free transformations in FP32: two_sum (Knuth) gives s + e == a + b exactly, two_prod
 // (via FMA) gives p + e == a * b exactly.  Sums of products accumulated with them as in the
@@ -346,6 +395,103 @@ __device__ __forceinline__ void item_geom(const ViewInfo &V, const float mu[3], 
     cross3(G.op, &G.A[3], &G.Cc[3]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) G.Cc[6 + i] = G.Cc[i] * G.Dx + G.Cc[3 + i] * G.Dy;
+}
+
+// ------------------------------------------------------------------ splat-mode geometry
+// The 2D Gaussian of one (view, Gaussian) in the 3DGS comparison mode (Eq. 5-7).  With t the
+// camera-space mean, u = tx/tz, v = ty/tz, jx = fx/tz, jy = fy/tz, the rows of J W are
+// a_0 = jx (W_0 - u W_2) and a_1 = jy (W_1 - v W_2) (W_i the rows of the view rotation), and
+// with B_ik = s_k (a_i . r_k) (r_k the Gaussian's axes) Sigma' = B B^T + dil I.  Its entries
+// and determinant det = |b_0 x b_1|^2 + dil (|b_0|^2 + |b_1|^2) + dil^2 are formed in FP64 from
+// the FP32 B: products of floats are exact there and no cancellation is left, so thin
+// footprints keep their accuracy.  The mean mu' = (fx u + cx - 1/2, fy v + cy - 1/2) is in
+// pixel index coordinates (FP64 camera-space mean), split into the reference pixel
+// (px0, py0) = mu' rounded to FP32 and the remainder (mx, my).
+struct SplatGeom {
+    float u, v, jx, jy, iz;   // iz = 1 / tz
+    float a[2][3];            // rows of J W
+    float ar[2][3];           // a_i . r_k
+    float B[2][3];
+    double g00, g01, g11, det;
+    float px0, py0, mx, my;
+};
+
+__device__ __forceinline__ bool splat_geom(const ViewInfo &V, const float mu[3], const float s[3], const float Rq[9],
+                                           float dil, SplatGeom &G) {
+    const float *W = V.R;
+    double t[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        t[k] = fma((double)W[3 * k], (double)mu[0],
+                   fma((double)W[3 * k + 1], (double)mu[1], fma((double)W[3 * k + 2], (double)mu[2], (double)V.t[k])));
+    if (!(t[2] > 0.0)) return false;
+    const double iz = 1.0 / t[2], ud = t[0] * iz, vd = t[1] * iz;
+    G.u = (float)ud;
+    G.v = (float)vd;
+    G.iz = (float)iz;
+    G.jx = (float)(V.fx * iz);
+    G.jy = (float)(V.fy * iz);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        G.a[0][c] = G.jx * fmaf(-G.u, W[6 + c], W[c]);
+        G.a[1][c] = G.jy * fmaf(-G.v, W[6 + c], W[3 + c]);
+    }
+    double b[2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            G.ar[i][k] = fmaf(G.a[i][0], Rq[k], fmaf(G.a[i][1], Rq[3 + k], G.a[i][2] * Rq[6 + k]));
+            G.B[i][k] = s[k] * G.ar[i][k];
+            b[i][k] = (double)G.B[i][k];
+        }
+    const double n0 = b[0][1] * b[1][2] - b[0][2] * b[1][1];
+    const double n1 = b[0][2] * b[1][0] - b[0][0] * b[1][2];
+    const double n2 = b[0][0] * b[1][1] - b[0][1] * b[1][0];
+    const double s00 = b[0][0] * b[0][0] + b[0][1] * b[0][1] + b[0][2] * b[0][2];
+    const double s11 = b[1][0] * b[1][0] + b[1][1] * b[1][1] + b[1][2] * b[1][2];
+    const double dd = (double)dil;
+    G.g00 = s00 + dd;
+    G.g11 = s11 + dd;
+    G.g01 = b[0][0] * b[1][0] + b[0][1] * b[1][1] + b[0][2] * b[1][2];
+    G.det = (n0 * n0 + n1 * n1 + n2 * n2) + dd * (s00 + s11) + dd * dd;
+    const double mxd = fma((double)V.fx, ud, (double)V.cx - 0.5), myd = fma((double)V.fy, vd, (double)V.cy - 0.5);
+    G.px0 = (float)mxd;
+    G.py0 = (float)myd;
+    G.mx = (float)(mxd - (double)G.px0);
+    G.my = (float)(myd - (double)G.py0);
+    return G.det > 0.0;
+}
+
+// Splat-mode blend record in the layout of the default mode: q = w' Sigma'^-1 w = |C u|^2 with
+// u = (dx, dy, 1), w = (dx - mx, dy - my) and C's rows L^T (Sigma'^-1 = L L^T, Cholesky):
+//   L00 = sqrt(g11 / det), L10 = -g01 / (det L00), L11 = 1 / sqrt(g11);
+// A = (0, 0, e_z) makes |A u| = 1, unused by the splat kernels except in the opacity box test.
+// A non-finite factor (a footprint far below a pixel) yields alpha = 0 through log2 o = -inf.
+// Writes A, C and the reference pixel to out[0..19]; returns the record's log2 o.
+__device__ __forceinline__ float splat_record(const SplatGeom &G, float opac, float out[20]) {
+    const float q00 = (float)(G.g11 / G.det), q01 = (float)(-G.g01 / G.det);
+    float L00 = sqrtf(q00), L10 = q01 / L00, L11 = 1.0f / sqrtf((float)G.g11);
+    float l2o = log2f(opac);
+    if (!(isfinite(L00) && isfinite(L10) && isfinite(L11))) {
+        L00 = L10 = L11 = 0.0f;
+        l2o = -INFINITY;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out[k] = 0.0f;
+    out[8] = 1.0f;
+    out[9] = L00;
+    out[10] = 0.0f;
+    out[11] = 0.0f;
+    out[12] = L10;
+    out[13] = L11;
+    out[14] = 0.0f;
+    out[15] = -fmaf(L00, G.mx, L10 * G.my);
+    out[16] = -(L11 * G.my);
+    out[17] = 0.0f;
+    out[18] = G.px0;
+    out[19] = G.py0;
+    return l2o;
 }
 
 // ------------------------------------------------------------------ spherical harmonics

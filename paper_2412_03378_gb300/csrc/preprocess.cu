@@ -42,23 +42,38 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
             load_gauss<RT>(g, gi, mu, s, q, kin);
             const Density dn = density_of(g, kin, s);
             float Sig[9], Rq[9], qn[4], smax, Zf;
-            if (key_cov(mu, s, q, dn.kap_key, Sig, Rq, qn, smax))
-                state = key_persp(V, mu, Sig, smax, dn.kap_key, z_near, tau_cut, dk, rc, prc, Zf);
+            if (key_cov(mu, s, q, dn.kap_key, Sig, Rq, qn, smax)) {
+                if (g.splat)
+                    state = key_splat(V, mu, Sig, dn.kap_key, z_near, tau_cut, g.splat_dil, dk, rc, prc);
+                else
+                    state = key_persp(V, mu, Sig, smax, dn.kap_key, z_near, tau_cut, dk, rc, prc, Zf);
+            }
             if (state == 2) {
                 cnt = (uint32_t)(rc.z - rc.x + 1) * (uint32_t)(rc.w - rc.y + 1);
-                ItemGeom G;
-                item_geom(V, mu, s, Rq, G);
                 float dir[3], len, rgb[3] = {0.0f, 0.0f, 0.0f}, raw[3];
                 view_dir(V, mu, dir, len);
                 if (g.sh) eval_colour_row(g.sh_degree, row, dir, rgb, raw, g.softplus_beta);   // else density only
+                if (g.splat) {
+                    SplatGeom SG;
+                    if (splat_geom(V, mu, s, Rq, g.splat_dil, SG)) {
+                        rrow[20] = splat_record(SG, dn.kap, rrow);
+                    } else {   // degenerate 2D covariance: listed by the key, but alpha = 0
 #pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    rrow[k] = G.A[k];
-                    rrow[9 + k] = G.Cc[k];
+                        for (int k = 0; k < 20; ++k) rrow[k] = 0.0f;
+                        rrow[20] = -INFINITY;
+                    }
+                } else {
+                    ItemGeom G;
+                    item_geom(V, mu, s, Rq, G);
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        rrow[k] = G.A[k];
+                        rrow[9 + k] = G.Cc[k];
+                    }
+                    rrow[18] = G.px0;
+                    rrow[19] = G.py0;
+                    rrow[20] = log2f(dn.kap) + kLog2Sqrt2Pi;
                 }
-                rrow[18] = G.px0;
-                rrow[19] = G.py0;
-                rrow[20] = log2f(dn.kap) + kLog2Sqrt2Pi;
                 rrow[21] = rgb[0];
                 rrow[22] = rgb[1];
                 rrow[23] = rgb[2];

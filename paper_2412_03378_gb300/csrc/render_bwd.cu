@@ -34,7 +34,7 @@ template <> struct BwdBounds<4> { static constexpr int kMinBlocks = 8; };
 // ballots which records of the staged chunk it needs (some pixel of the warp reached the record,
 // the record's footprint touches the warp's pixels and, when pairs below tau_skip are skipped,
 // its opacity can reach tau_skip there), then visits only those, back to front.
-template <int P, bool COUNT, bool PIXTEST>
+template <int P, bool COUNT, bool PIXTEST, bool SPLAT>
 __global__ void __launch_bounds__(PixLayout<P>::kThreads, BwdBounds<P>::kMinBlocks)
 k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
@@ -69,7 +69,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         const int x = x0 + L::ox(k), y = y0 + L::oy(k);
-        Lp[k] = pixel_ray(V, x, y).Lp;
+        Lp[k] = SPLAT ? 0.0f : pixel_ray(V, x, y).Lp;
         my_last[k] = rg.x;
         S[k] = 0.0f;
         float Tend = 1.0f;
@@ -99,7 +99,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     const uint32_t tile_last = s_last;
     const uint32_t warp_last = __reduce_max_sync(0xffffffffu, thr_last);
     const WarpBox wb = warp_box<P>(x0, y0);
-    const BoxCull bc = box_cull(V, wb, bp.tau_skip);
+    const BoxCull bc = SPLAT ? box_cull_splat(wb, bp.alpha_min) : box_cull(V, wb, bp.tau_skip);
     const float xf = (float)x0, yf = (float)y0;
     unsigned long long pairs = 0, blended = 0;   // evaluated / blended pairs (COUNT only)
 
@@ -145,21 +145,49 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                     short4 pr;
                     if (PIXTEST) pr = srect[j];
                     QuadBase qb;
-                    quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
+                    SplatBase sb;
+                    if constexpr (SPLAT)
+                        splat_base(r2, r3, r4, xf, yf, sb);
+                    else
+                        quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
 #pragma unroll
                     for (int k = 0; k < P; ++k) {
                         if (idx >= my_last[k]) continue;
                         if (PIXTEST && pixel_outside(x0 + L::ox(k), y0 + L::oy(k), pr)) continue;
-                        PairEval e;
-                        pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
-                        if (COUNT) ++pairs;
-                        const bool clamped = e.tau > bp.tau_max;
-                        const float tau = fminf(e.tau, bp.tau_max);
-                        if (tau < bp.tau_skip) continue;
+                        // per mode: tau, 1 - alpha, alpha, whether a clamp cut the gradient, the
+                        // pixel offset, dln(tau)/dln(amplitude) and 2 dL/da, 2 dL/dq per dL/dln(amplitude)
+                        float tau, e2, alpha, pdx, pdy, kG, ca, cq;
+                        bool clamped;
+                        if constexpr (SPLAT) {
+                            float q;
+                            const float ar = splat_at(r2, r3, r5, sb, L::ox(k) != 0, L::oy(k) != 0, pdx, pdy, q);
+                            if (COUNT) ++pairs;
+                            clamped = ar > bp.alpha_max;
+                            alpha = fminf(ar, bp.alpha_max);
+                            if (alpha < bp.alpha_min) continue;
+                            e2 = __fsub_rn(1.0f, alpha);
+                            tau = -log1pf(-alpha);
+                            kG = alpha / e2;   // tau = -ln(1 - o G'): dtau/dln o = alpha / (1 - alpha)
+                            ca = 0.0f;
+                            cq = -1.0f;        // ln(o G') = ln o - q/2
+                        } else {
+                            PairEval e;
+                            pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
+                            if (COUNT) ++pairs;
+                            clamped = e.tau > bp.tau_max;
+                            tau = fminf(e.tau, bp.tau_max);
+                            if (tau < bp.tau_skip) continue;
+                            e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
+                            alpha = __fsub_rn(1.0f, e2);
+                            pdx = e.dx;
+                            pdy = e.dy;
+                            kG = tau;
+                            const float r2s = e.rs * e.rs;
+                            ca = r2s * (e.m2 - 1.0f);
+                            cq = -r2s;
+                        }
                         if (COUNT) ++blended;
                         any = true;
-                        const float e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
-                        const float alpha = __fsub_rn(1.0f, e2);
                         const float Sb = S[k] - tau;
                         const float Tb = ex2_approx(-kLog2eF * Sb);
                         const float aT = alpha * Tb;
@@ -174,22 +202,23 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                         S[k] = Sb;
                         Tafter[k] = Tb;
                         if (!clamped) {
-                            const float G = dtau * tau;                  // dL / d ln(tau)
-                            const float r2s = e.rs * e.rs;
-                            const float ga = G * r2s * (e.m2 - 1.0f);    // 2 dL/da
-                            const float gq = -G * r2s;                   // 2 dL/dq
-                            const float xx = e.dx * e.dx, xy = e.dx * e.dy, yy = e.dy * e.dy;
-                            gv[0] = fmaf(ga, xx, gv[0]);
-                            gv[1] = fmaf(ga, xy, gv[1]);
-                            gv[2] = fmaf(ga, e.dx, gv[2]);
-                            gv[3] = fmaf(ga, yy, gv[3]);
-                            gv[4] = fmaf(ga, e.dy, gv[4]);
-                            gv[5] += ga;
+                            const float G = dtau * kG;                   // dL / d ln(amplitude)
+                            const float gq = G * cq;                     // 2 dL/dq
+                            const float xx = pdx * pdx, xy = pdx * pdy, yy = pdy * pdy;
+                            if constexpr (!SPLAT) {
+                                const float ga = G * ca;                 // 2 dL/da
+                                gv[0] = fmaf(ga, xx, gv[0]);
+                                gv[1] = fmaf(ga, xy, gv[1]);
+                                gv[2] = fmaf(ga, pdx, gv[2]);
+                                gv[3] = fmaf(ga, yy, gv[3]);
+                                gv[4] = fmaf(ga, pdy, gv[4]);
+                                gv[5] += ga;
+                            }
                             gv[6] = fmaf(gq, xx, gv[6]);
                             gv[7] = fmaf(gq, xy, gv[7]);
-                            gv[8] = fmaf(gq, e.dx, gv[8]);
+                            gv[8] = fmaf(gq, pdx, gv[8]);
                             gv[9] = fmaf(gq, yy, gv[9]);
-                            gv[10] = fmaf(gq, e.dy, gv[10]);
+                            gv[10] = fmaf(gq, pdy, gv[10]);
                             gv[11] += gq;
                             gv[12] += G;
                         }
@@ -221,21 +250,35 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
 }
 
+template <int P, bool PIXTEST, bool SPLAT>
+static void launch_bwd_pts(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                           const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                           const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
+                           const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
+                           cudaStream_t st) {
+    const unsigned threads = PixLayout<P>::kThreads;
+    if (pair_count)
+        k_render_bwd<P, true, PIXTEST, SPLAT><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
+            grad_acc, pair_count);
+    else
+        k_render_bwd<P, false, PIXTEST, SPLAT><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
+            grad_acc, nullptr);
+}
+
 template <int P, bool PIXTEST>
 static void launch_bwd_pt(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                           const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                           const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
                           const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
                           cudaStream_t st) {
-    const unsigned threads = PixLayout<P>::kThreads;
-    if (pair_count)
-        k_render_bwd<P, true, PIXTEST><<<(unsigned)n_tiles, threads, 0, st>>>(
-            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
-            grad_acc, pair_count);
+    if (bp.splat)
+        launch_bwd_pts<P, PIXTEST, true>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp,
+                                         T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
     else
-        k_render_bwd<P, false, PIXTEST><<<(unsigned)n_tiles, threads, 0, st>>>(
-            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
-            grad_acc, nullptr);
+        launch_bwd_pts<P, PIXTEST, false>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
+                                          bp, T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
 }
 
 template <int P>
@@ -278,13 +321,73 @@ __device__ __forceinline__ void cross_add(const float a[3], const float b[3], fl
     c[2] += a[0] * b[1] - a[1] * b[0];
 }
 
+// Splat mode (Eq. 5-7): the moments Mq = sum gq u u^T (gq = 2 dL/dq, u = (dx, dy, 1) from the
+// reference pixel; accumulator entries 6..11) of one (view, Gaussian) give, with w = u - m,
+//   dL/dQ = (1/2) sum gq w w^T,   dL/dmu' = -Q sum gq w      (q = w' Q w, Q = Sigma'^-1),
+// then dL/dSigma' = -Q dL/dQ Q (FP64, Q from the FP64 Gram of B), dL/dB = 2 dL/dSigma' B
+// (Sigma' = B B^T + dil I), and through B_ik = s_k (a_i . r_k), a_i the rows of J W and
+// J(t), mu'(t) to the rotation (dR, row-major), scale and mean.
+__device__ __forceinline__ void splat_chain(const ViewInfo &V, const float mu[3], const float s[3], const float Rq[9],
+                                            float dil, const float ga[kGradN], float dR[9], float dm[3],
+                                            float dsc[3]) {
+    SplatGeom G;
+    if (!splat_geom(V, mu, s, Rq, dil, G)) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dR[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dm[k] = dsc[k] = 0.0f;
+        return;
+    }
+    const float mx = G.mx, my = G.my;
+    const float M00 = ga[6], M01 = ga[7], M02 = ga[8], M11 = ga[9], M12 = ga[10], M22 = ga[11];
+    const float Sx = fmaf(-mx, M22, M02), Sy = fmaf(-my, M22, M12);
+    const float Sxx = fmaf(-mx, M02 + Sx, M00);
+    const float Sxy = fmaf(-mx, Sy, fmaf(-my, M02, M01));
+    const float Syy = fmaf(-my, M12 + Sy, M11);
+    const double idet = 1.0 / G.det;
+    const double Q00 = G.g11 * idet, Q01 = -G.g01 * idet, Q11 = G.g00 * idet;
+    const double dQ00 = 0.5 * Sxx, dQ01 = 0.5 * Sxy, dQ11 = 0.5 * Syy;
+    const float dmx = (float)-(Q00 * Sx + Q01 * Sy), dmy = (float)-(Q01 * Sx + Q11 * Sy);
+    const double T00 = Q00 * dQ00 + Q01 * dQ01, T01 = Q00 * dQ01 + Q01 * dQ11;
+    const double T10 = Q01 * dQ00 + Q11 * dQ01, T11 = Q01 * dQ01 + Q11 * dQ11;
+    const float dS00 = (float)-(T00 * Q00 + T01 * Q01), dS01 = (float)-(T00 * Q01 + T01 * Q11);
+    const float dS11 = (float)-(T10 * Q01 + T11 * Q11);
+    float dB[2][3], da[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dB[0][k] = 2.0f * fmaf(dS00, G.B[0][k], dS01 * G.B[1][k]);
+        dB[1][k] = 2.0f * fmaf(dS01, G.B[0][k], dS11 * G.B[1][k]);
+        dsc[k] = fmaf(dB[0][k], G.ar[0][k], dB[1][k] * G.ar[1][k]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dR[3 * c + k] = s[k] * fmaf(dB[0][k], G.a[0][c], dB[1][k] * G.a[1][c]);
+            da[0][c] = fmaf(dB[0][k] * s[k], Rq[3 * c + k], da[0][c]);
+            da[1][c] = fmaf(dB[1][k] * s[k], Rq[3 * c + k], da[1][c]);
+        }
+    const float *W = V.R;
+    const float dJ00 = da[0][0] * W[0] + da[0][1] * W[1] + da[0][2] * W[2];
+    const float dJ02 = da[0][0] * W[6] + da[0][1] * W[7] + da[0][2] * W[8];
+    const float dJ11 = da[1][0] * W[3] + da[1][1] * W[4] + da[1][2] * W[5];
+    const float dJ12 = da[1][0] * W[6] + da[1][1] * W[7] + da[1][2] * W[8];
+    const float jx = G.jx, jy = G.jy, u = G.u, v = G.v, iz = G.iz;
+    const float dt0 = jx * fmaf(-dJ02, iz, dmx);
+    const float dt1 = jy * fmaf(-dJ12, iz, dmy);
+    const float dt2 = -jx * u * dmx - jy * v * dmy + jx * iz * fmaf(2.0f * u, dJ02, -dJ00) +
+                      jy * iz * fmaf(2.0f * v, dJ12, -dJ11);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dm[c] = W[c] * dt0 + W[3 + c] * dt1 + W[6 + c] * dt2;
+}
+
 // One thread per Gaussian: it visits the Gaussian's item in every view, sums the parameter
 // gradients in registers and writes them once (overwriting when `zero`, else adding), so no
 // atomics are needed.  A warp owns 32 consecutive Gaussians: their SH rows are read, and their
 // SH-gradient rows accumulated and written, through shared memory with coalesced instructions.
 constexpr int kChainWarps = 2;
 
-template <typename RT, typename ST>
+template <typename RT, typename ST, bool SPLAT>
 __global__ void __launch_bounds__(32 * kChainWarps, 8)
 k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float *__restrict__ grad_acc, int zero,
         float *__restrict__ dmu, float *__restrict__ dscale, float *__restrict__ dquat, float *__restrict__ dkappa,
@@ -332,6 +435,10 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
         }
         if (!any) continue;
         const ViewInfo &V = views[v];
+        float dR[9], dm[3], dsc[3];
+        if constexpr (SPLAT) {
+            splat_chain(V, mu, s, Rq, g.splat_dil, ga, dR, dm, dsc);
+        } else {
         ItemGeom G;
         item_geom(V, mu, s, Rq, G);
         // dA_j = sum_k A_k Ma[k][j], dC_j = sum_k C_k Mq[k][j] with the symmetric moments
@@ -386,7 +493,7 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
 #pragma unroll
         for (int j = 0; j < 3; ++j) dmuc[j] = -(G.M[j] * dop[0] + G.M[3 + j] * dop[1] + G.M[6 + j] * dop[2]);
         // M[i][j] = B[j][i] / s_i
-        float dsc[3], dB[9];
+        float dB[9];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const float is = 1.0f / s[i];
@@ -396,12 +503,12 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
         }
         // B = Rc Rq  =>  dRq = Rc^T dB;  mu_c = Rc mu + t  =>  dmu = Rc^T dmu_c
         const float *Rc = V.R;
-        float dR[9], dm[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
 #pragma unroll
             for (int b = 0; b < 3; ++b) dR[3 * a + b] = Rc[a] * dB[b] + Rc[3 + a] * dB[3 + b] + Rc[6 + a] * dB[6 + b];
             dm[a] = Rc[a] * dmuc[0] + Rc[3 + a] * dmuc[1] + Rc[6 + a] * dmuc[2];
+        }
         }
         // rotation matrix of the unit quaternion (w, x, y, z), differentiated entry by entry
         const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
@@ -494,7 +601,12 @@ static cudaError_t launch_chain_t(const GaussIn &g, const ViewInfo *views_d, int
     long long b = ((long long)g.n + 32 * kChainWarps - 1) / (32 * kChainWarps);
     if (b > 152 * 64) b = 152 * 64;
     if (b < 1) b = 1;
-    k_chain<RT, ST><<<(unsigned)b, 32 * kChainWarps, 0, st>>>(g, views_d, n_views, grad_acc, zero, dmu, dscale, dquat, dkappa, dsh);
+    if (g.splat)
+        k_chain<RT, ST, true><<<(unsigned)b, 32 * kChainWarps, 0, st>>>(g, views_d, n_views, grad_acc, zero, dmu, dscale,
+                                                                        dquat, dkappa, dsh);
+    else
+        k_chain<RT, ST, false><<<(unsigned)b, 32 * kChainWarps, 0, st>>>(g, views_d, n_views, grad_acc, zero, dmu, dscale,
+                                                                         dquat, dkappa, dsh);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,8 @@
 // depth-ordered chunks (one record per thread); every record is read once per thread and
 // serves its P pixels, whose d' and o' x d' follow from the first pixel's by one add per
 // component.  The closed form is evaluated in FP32 (FMA pipe + 3 MUFU ops per pair); the CTA
-// leaves once all of its pixels have reached T < T_stop.  No tensor cores: the work is not a
+// leaves once all of its pixels have reached T < T_stop.  SPLAT selects the 3DGS comparison
+// mode's alpha (Eq. 6) in the same loop.  No tensor cores: the work is not a
 // dense contraction.
 #include "blend.cuh"
 
@@ -20,7 +21,7 @@ template <> struct FwdBounds<1> { static constexpr int kMinBlocks = 3; };
 template <> struct FwdBounds<2> { static constexpr int kMinBlocks = 7; };
 template <> struct FwdBounds<4> { static constexpr int kMinBlocks = 12; };
 
-template <int P, bool COUNT, bool PIXTEST>
+template <int P, bool COUNT, bool PIXTEST, bool SPLAT>
 __global__ void __launch_bounds__(PixLayout<P>::kThreads, FwdBounds<P>::kMinBlocks)
 k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
@@ -45,7 +46,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         const int x = x0 + L::ox(k), y = y0 + L::oy(k);
-        Lp[k] = pixel_ray(V, x, y).Lp;
+        Lp[k] = SPLAT ? 0.0f : pixel_ray(V, x, y).Lp;
         T[k] = 1.0f;
         S[k] = c0[k] = c1[k] = c2[k] = 0.0f;
         last[k] = rg.x;
@@ -53,7 +54,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
     const float xf = (float)x0, yf = (float)y0;
     const WarpBox wb = warp_box<P>(x0, y0);
-    const BoxCull bc = box_cull(V, wb, bp.tau_skip);
+    const BoxCull bc = SPLAT ? box_cull_splat(wb, bp.alpha_min) : box_cull(V, wb, bp.tau_skip);
     const int lane = threadIdx.x & 31;
     unsigned long long pairs = 0, blended = 0;   // evaluated / blended pairs (COUNT only)
     for (uint32_t base = rg.x; base < rg.y; base += kChunk) {
@@ -92,19 +93,36 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                 short4 pr;
                 if (PIXTEST) pr = srect[j];
                 QuadBase qb;
-                quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
+                SplatBase sb;
+                if constexpr (SPLAT)
+                    splat_base(r2, r3, r4, xf, yf, sb);
+                else
+                    quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
 #pragma unroll
                 for (int k = 0; k < P; ++k) {
                     if (!(live & (1u << k))) continue;
                     if (PIXTEST && pixel_outside(x0 + L::ox(k), y0 + L::oy(k), pr)) continue;
-                    PairEval e;
-                    pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
-                    if (COUNT) ++pairs;
-                    const float tau = fminf(e.tau, bp.tau_max);
-                    if (tau < bp.tau_skip) continue;
-                    if (COUNT) ++blended;
-                    const float e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
-                    const float w = __fmul_rn(__fsub_rn(1.0f, e2), T[k]);
+                    float tau, e2, w;
+                    if constexpr (SPLAT) {   // Eq. 6: alpha = min(o G'(p), alpha_max)
+                        float dx, dy, q;
+                        const float alpha =
+                            fminf(splat_at(r2, r3, r5, sb, L::ox(k) != 0, L::oy(k) != 0, dx, dy, q), bp.alpha_max);
+                        if (COUNT) ++pairs;
+                        if (alpha < bp.alpha_min) continue;
+                        if (COUNT) ++blended;
+                        e2 = __fsub_rn(1.0f, alpha);
+                        tau = -log1pf(-alpha);
+                        w = __fmul_rn(alpha, T[k]);
+                    } else {
+                        PairEval e;
+                        pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
+                        if (COUNT) ++pairs;
+                        tau = fminf(e.tau, bp.tau_max);
+                        if (tau < bp.tau_skip) continue;
+                        if (COUNT) ++blended;
+                        e2 = ex2_approx(__fmul_rn(-kLog2eF, tau));
+                        w = __fmul_rn(__fsub_rn(1.0f, e2), T[k]);
+                    }
                     c0[k] = fmaf(r5.y, w, c0[k]);
                     c1[k] = fmaf(r5.z, w, c1[k]);
                     c2[k] = fmaf(r5.w, w, c2[k]);
@@ -143,20 +161,33 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
 }
 
+template <int P, bool PIXTEST, bool SPLAT>
+static void launch_fwd_pts(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                           const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                           const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
+                           uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
+    const unsigned threads = PixLayout<P>::kThreads;
+    if (pair_count)
+        k_render_fwd<P, true, PIXTEST, SPLAT><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
+            pair_count);
+    else
+        k_render_fwd<P, false, PIXTEST, SPLAT><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
+            nullptr);
+}
+
 template <int P, bool PIXTEST>
 static void launch_fwd_pt(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                           const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                           const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
                           uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
-    const unsigned threads = PixLayout<P>::kThreads;
-    if (pair_count)
-        k_render_fwd<P, true, PIXTEST><<<(unsigned)n_tiles, threads, 0, st>>>(
-            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
-            pair_count);
+    if (bp.splat)
+        launch_fwd_pts<P, PIXTEST, true>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp,
+                                         rgb, T_user, T_ws, S_out, nlast_out, pair_count, st);
     else
-        k_render_fwd<P, false, PIXTEST><<<(unsigned)n_tiles, threads, 0, st>>>(
-            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
-            nullptr);
+        launch_fwd_pts<P, PIXTEST, false>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp,
+                                          rgb, T_user, T_ws, S_out, nlast_out, pair_count, st);
 }
 
 template <int P>

@@ -34,6 +34,8 @@ struct GaussIn {
     int rec_dtype, sh_dtype, n, sh_degree;
     int density_theta;     // the density array holds Eq. 20's theta
     float softplus_beta;   // colour activation: 0 = clamp at 0, > 0 = softplus(beta)
+    int splat;             // 3DGS comparison mode: the density array holds the peak opacity
+    float splat_dil;       // its 2D covariance dilation (pixels^2)
 };
 
 struct BlendParams {
@@ -43,6 +45,9 @@ struct BlendParams {
     float bg[3];
     int pixel_test;       // test every pixel against the Gaussian's footprint rectangle
                           // (needed when tau_skip < tau_cut; otherwise implied by the skip)
+    int splat;            // 3DGS comparison mode: alpha = min(o G', alpha_max), skipped below
+    float alpha_min;      // alpha_min, instead of the tau bounds above
+    float alpha_max;
 };
 
 // ------------------------------------------------------------------ device helpers

@@ -15,9 +15,11 @@ def dev_scene(vg, scene, rec_dtype=torch.float32, sh_dtype=torch.float32):
 def vg_opts(vg, o, flags=0, ppt=0):
     if o.get("density_theta"):
         flags |= vg.FLAG_DENSITY_THETA
+    if o.get("splat"):
+        flags |= vg.FLAG_SPLAT
     return vg.Opts(alpha_min=o["alpha_min"], tau_cut=o["tau_cut"], tau_max=o["tau_max"], T_stop=o["T_stop"],
                    bg=tuple(o["bg"]), z_near=o["z_near"], flags=flags, pixels_per_thread=ppt,
-                   softplus_beta=o.get("softplus_beta", 0.0))
+                   softplus_beta=o.get("softplus_beta", 0.0), splat_dilation=o.get("splat_dilation", 0.0))
 
 
 def run_forward(vg, scene, cams, o, ws=None, flags=0, g=None, ppt=0):
