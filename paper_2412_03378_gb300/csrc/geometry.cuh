@@ -398,80 +398,101 @@ __device__ __forceinline__ void item_geom(const ViewInfo &V, const float mu[3], 
 }
 
 // ------------------------------------------------------------------ splat-mode geometry
+// a b - c d to within about 1.5 ulp with one FMA-exact product (Kahan's 2x2 determinant;
+// Jeannerod, Louvet, Muller, "Further analysis of Kahan's algorithm for the accurate
+// computation of 2x2 determinants", Math. Comp. 82, 2013).
+__device__ __forceinline__ float diff_prod(float a, float b, float c, float d) {
+    const float w = __fmul_rn(c, d);
+    const float e = fmaf(-c, d, w);
+    const float f = fmaf(a, b, -w);
+    return __fadd_rn(f, e);
+}
+
+// x / y in double-float: the remainder x.hi - q1 y.hi of the rounded quotient is exact
+// through an FMA, the low parts enter its correction.
+__device__ __forceinline__ DF df_div(DF x, DF y) {
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const float r = __fsub_rn(__fadd_rn(fmaf(-q1, y.hi, x.hi), x.lo), __fmul_rn(q1, y.lo));
+    return DF{q1, __fdiv_rn(r, y.hi)};
+}
+
 // The 2D Gaussian of one (view, Gaussian) in the 3DGS comparison mode (Eq. 5-7).  With t the
 // camera-space mean, u = tx/tz, v = ty/tz, jx = fx/tz, jy = fy/tz, the rows of J W are
 // a_0 = jx (W_0 - u W_2) and a_1 = jy (W_1 - v W_2) (W_i the rows of the view rotation), and
-// with B_ik = s_k (a_i . r_k) (r_k the Gaussian's axes) Sigma' = B B^T + dil I.  Its entries
-// and determinant det = |b_0 x b_1|^2 + dil (|b_0|^2 + |b_1|^2) + dil^2 are formed in FP64 from
-// the FP32 B: products of floats are exact there and no cancellation is left, so thin
-// footprints keep their accuracy.  The mean mu' = (fx u + cx - 1/2, fy v + cy - 1/2) is in
-// pixel index coordinates (FP64 camera-space mean), split into the reference pixel
-// (px0, py0) = mu' rounded to FP32 and the remainder (mx, my).
+// with B_ik = s_k (a_i . r_k) (r_k the Gaussian's axes) Sigma' = B B^T + dil I.  Its
+// determinant is formed without cancellation, det = |n|^2 + dil (|b_0|^2 + |b_1|^2) + dil^2
+// with n = b_0 x b_1 from Kahan's 2x2 determinants, so that thin footprints keep their
+// accuracy in FP32.  The mean mu' = (fx u + cx - 1/2, fy v + cy - 1/2) (pixel index
+// coordinates) is formed in double-float from the double-float camera-space mean and split
+// into the reference pixel (px0, py0) (its leading part) and the remainder (mx, my).
 struct SplatGeom {
     float u, v, jx, jy, iz;   // iz = 1 / tz
     float a[2][3];            // rows of J W
     float ar[2][3];           // a_i . r_k
     float B[2][3];
-    double g00, g01, g11, det;
+    float n[3];               // b_0 x b_1
+    float g00, g01, g11, det; // Sigma' = [[g00, g01], [g01, g11]] and its determinant
     float px0, py0, mx, my;
 };
 
 __device__ __forceinline__ bool splat_geom(const ViewInfo &V, const float mu[3], const float s[3], const float Rq[9],
                                            float dil, SplatGeom &G) {
     const float *W = V.R;
-    double t[3];
+    DF t[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-        t[k] = fma((double)W[3 * k], (double)mu[0],
-                   fma((double)W[3 * k + 1], (double)mu[1], fma((double)W[3 * k + 2], (double)mu[2], (double)V.t[k])));
-    if (!(t[2] > 0.0)) return false;
-    const double iz = 1.0 / t[2], ud = t[0] * iz, vd = t[1] * iz;
-    G.u = (float)ud;
-    G.v = (float)vd;
-    G.iz = (float)iz;
-    G.jx = (float)(V.fx * iz);
-    G.jy = (float)(V.fy * iz);
+    for (int k = 0; k < 3; ++k) {
+        DF acc = DF{V.t[k], 0.0f};
+        acc = df_fma(acc, W[3 * k], mu[0]);
+        acc = df_fma(acc, W[3 * k + 1], mu[1]);
+        acc = df_fma(acc, W[3 * k + 2], mu[2]);
+        t[k] = df_norm(acc);
+    }
+    if (!(t[2].hi > 0.0f)) return false;
+    const DF ud = df_div(t[0], t[2]), vd = df_div(t[1], t[2]);
+    G.u = ud.hi;
+    G.v = vd.hi;
+    G.iz = 1.0f / t[2].hi;
+    G.jx = V.fx * G.iz;
+    G.jy = V.fy * G.iz;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         G.a[0][c] = G.jx * fmaf(-G.u, W[6 + c], W[c]);
         G.a[1][c] = G.jy * fmaf(-G.v, W[6 + c], W[3 + c]);
     }
-    double b[2][3];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             G.ar[i][k] = fmaf(G.a[i][0], Rq[k], fmaf(G.a[i][1], Rq[3 + k], G.a[i][2] * Rq[6 + k]));
             G.B[i][k] = s[k] * G.ar[i][k];
-            b[i][k] = (double)G.B[i][k];
         }
-    const double n0 = b[0][1] * b[1][2] - b[0][2] * b[1][1];
-    const double n1 = b[0][2] * b[1][0] - b[0][0] * b[1][2];
-    const double n2 = b[0][0] * b[1][1] - b[0][1] * b[1][0];
-    const double s00 = b[0][0] * b[0][0] + b[0][1] * b[0][1] + b[0][2] * b[0][2];
-    const double s11 = b[1][0] * b[1][0] + b[1][1] * b[1][1] + b[1][2] * b[1][2];
-    const double dd = (double)dil;
-    G.g00 = s00 + dd;
-    G.g11 = s11 + dd;
-    G.g01 = b[0][0] * b[1][0] + b[0][1] * b[1][1] + b[0][2] * b[1][2];
-    G.det = (n0 * n0 + n1 * n1 + n2 * n2) + dd * (s00 + s11) + dd * dd;
-    const double mxd = fma((double)V.fx, ud, (double)V.cx - 0.5), myd = fma((double)V.fy, vd, (double)V.cy - 0.5);
-    G.px0 = (float)mxd;
-    G.py0 = (float)myd;
-    G.mx = (float)(mxd - (double)G.px0);
-    G.my = (float)(myd - (double)G.py0);
-    return G.det > 0.0;
+    const float *b0 = G.B[0], *b1 = G.B[1];
+    G.n[0] = diff_prod(b0[1], b1[2], b0[2], b1[1]);
+    G.n[1] = diff_prod(b0[2], b1[0], b0[0], b1[2]);
+    G.n[2] = diff_prod(b0[0], b1[1], b0[1], b1[0]);
+    const float s00 = fmaf(b0[0], b0[0], fmaf(b0[1], b0[1], b0[2] * b0[2]));
+    const float s11 = fmaf(b1[0], b1[0], fmaf(b1[1], b1[1], b1[2] * b1[2]));
+    G.g00 = s00 + dil;
+    G.g11 = s11 + dil;
+    G.g01 = fmaf(b0[0], b1[0], fmaf(b0[1], b1[1], b0[2] * b1[2]));
+    G.det = fmaf(G.n[0], G.n[0], fmaf(G.n[1], G.n[1], G.n[2] * G.n[2])) + dil * (s00 + s11 + dil);
+    DF mx = df_norm(df_add(df_fma(DF{V.cx, 0.0f}, V.fx, ud), DF{-0.5f, 0.0f}));
+    DF my = df_norm(df_add(df_fma(DF{V.cy, 0.0f}, V.fy, vd), DF{-0.5f, 0.0f}));
+    G.px0 = mx.hi;
+    G.py0 = my.hi;
+    G.mx = mx.lo;
+    G.my = my.lo;
+    return G.det > 0.0f && isfinite(G.det);
 }
 
 // Splat-mode blend record in the layout of the default mode: q = w' Sigma'^-1 w = |C u|^2 with
 // u = (dx, dy, 1), w = (dx - mx, dy - my) and C's rows L^T (Sigma'^-1 = L L^T, Cholesky):
-//   L00 = sqrt(g11 / det), L10 = -g01 / (det L00), L11 = 1 / sqrt(g11);
+//   L00 = sqrt(g11 / det), L10 = -g01 / sqrt(g11 det), L11 = 1 / sqrt(g11);
 // A = (0, 0, e_z) makes |A u| = 1, unused by the splat kernels except in the opacity box test.
 // A non-finite factor (a footprint far below a pixel) yields alpha = 0 through log2 o = -inf.
 // Writes A, C and the reference pixel to out[0..19]; returns the record's log2 o.
 __device__ __forceinline__ float splat_record(const SplatGeom &G, float opac, float out[20]) {
-    const float q00 = (float)(G.g11 / G.det), q01 = (float)(-G.g01 / G.det);
-    float L00 = sqrtf(q00), L10 = q01 / L00, L11 = 1.0f / sqrtf((float)G.g11);
+    float L00 = sqrtf(G.g11 / G.det), L10 = -G.g01 / sqrtf(G.g11 * G.det), L11 = 1.0f / sqrtf(G.g11);
     float l2o = log2f(opac);
     if (!(isfinite(L00) && isfinite(L10) && isfinite(L11))) {
         L00 = L10 = L11 = 0.0f;

@@ -324,9 +324,10 @@ __device__ __forceinline__ void cross_add(const float a[3], const float b[3], fl
 // Splat mode (Eq. 5-7): the moments Mq = sum gq u u^T (gq = 2 dL/dq, u = (dx, dy, 1) from the
 // reference pixel; accumulator entries 6..11) of one (view, Gaussian) give, with w = u - m,
 //   dL/dQ = (1/2) sum gq w w^T,   dL/dmu' = -Q sum gq w      (q = w' Q w, Q = Sigma'^-1),
-// then dL/dSigma' = -Q dL/dQ Q (FP64, Q from the FP64 Gram of B), dL/dB = 2 dL/dSigma' B
-// (Sigma' = B B^T + dil I), and through B_ik = s_k (a_i . r_k), a_i the rows of J W and
-// J(t), mu'(t) to the rotation (dR, row-major), scale and mean.
+// then dL/dSigma' = -Q dL/dQ Q and, with Sigma' = B B^T + dil I, dL/dB = -2 Q dL/dQ P where
+// P = Q B has the rows (b_1 x n + dil b_0) / det and (n x b_0 + dil b_1) / det (n = b_0 x b_1:
+// no cancellation for thin footprints), and through B_ik = s_k (a_i . r_k), a_i the rows of
+// J W, and J(t), mu'(t) to the rotation (dR, row-major), scale and mean.
 __device__ __forceinline__ void splat_chain(const ViewInfo &V, const float mu[3], const float s[3], const float Rq[9],
                                             float dil, const float ga[kGradN], float dR[9], float dm[3],
                                             float dsc[3]) {
@@ -344,19 +345,28 @@ __device__ __forceinline__ void splat_chain(const ViewInfo &V, const float mu[3]
     const float Sxx = fmaf(-mx, M02 + Sx, M00);
     const float Sxy = fmaf(-mx, Sy, fmaf(-my, M02, M01));
     const float Syy = fmaf(-my, M12 + Sy, M11);
-    const double idet = 1.0 / G.det;
-    const double Q00 = G.g11 * idet, Q01 = -G.g01 * idet, Q11 = G.g00 * idet;
-    const double dQ00 = 0.5 * Sxx, dQ01 = 0.5 * Sxy, dQ11 = 0.5 * Syy;
-    const float dmx = (float)-(Q00 * Sx + Q01 * Sy), dmy = (float)-(Q01 * Sx + Q11 * Sy);
-    const double T00 = Q00 * dQ00 + Q01 * dQ01, T01 = Q00 * dQ01 + Q01 * dQ11;
-    const double T10 = Q01 * dQ00 + Q11 * dQ01, T11 = Q01 * dQ01 + Q11 * dQ11;
-    const float dS00 = (float)-(T00 * Q00 + T01 * Q01), dS01 = (float)-(T00 * Q01 + T01 * Q11);
-    const float dS11 = (float)-(T10 * Q01 + T11 * Q11);
+    const float idet = 1.0f / G.det;
+    const float Q00 = G.g11 * idet, Q01 = -G.g01 * idet, Q11 = G.g00 * idet;
+    const float dmx = -fmaf(Q00, Sx, Q01 * Sy), dmy = -fmaf(Q01, Sx, Q11 * Sy);
+    // T = Q dL/dQ with dL/dQ = (1/2) [[Sxx, Sxy], [Sxy, Syy]]
+    const float T00 = 0.5f * fmaf(Q00, Sxx, Q01 * Sxy), T01 = 0.5f * fmaf(Q00, Sxy, Q01 * Syy);
+    const float T10 = 0.5f * fmaf(Q01, Sxx, Q11 * Sxy), T11 = 0.5f * fmaf(Q01, Sxy, Q11 * Syy);
+    float P[2][3];
+    {
+        const float *b0 = G.B[0], *b1 = G.B[1], *n = G.n;
+        const float c0[3] = {b1[1] * n[2] - b1[2] * n[1], b1[2] * n[0] - b1[0] * n[2], b1[0] * n[1] - b1[1] * n[0]};
+        const float c1[3] = {n[1] * b0[2] - n[2] * b0[1], n[2] * b0[0] - n[0] * b0[2], n[0] * b0[1] - n[1] * b0[0]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            P[0][k] = fmaf(dil, b0[k], c0[k]) * idet;
+            P[1][k] = fmaf(dil, b1[k], c1[k]) * idet;
+        }
+    }
     float dB[2][3], da[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        dB[0][k] = 2.0f * fmaf(dS00, G.B[0][k], dS01 * G.B[1][k]);
-        dB[1][k] = 2.0f * fmaf(dS01, G.B[0][k], dS11 * G.B[1][k]);
+        dB[0][k] = -2.0f * fmaf(T00, P[0][k], T01 * P[1][k]);
+        dB[1][k] = -2.0f * fmaf(T10, P[0][k], T11 * P[1][k]);
         dsc[k] = fmaf(dB[0][k], G.ar[0][k], dB[1][k] * G.ar[1][k]);
     }
 #pragma unroll
