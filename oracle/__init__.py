@@ -140,6 +140,9 @@ def lib():
         L.orc_cone.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, P, P, P, P, i32, P, P, P, P]
         L.orc_cone_grad.restype = None
         L.orc_cone_grad.argtypes = [i32, P, P, P, P, i32, P, P, i32, i32, P, P, P, P, P, P, P, P, P, P, P]
+        L.orc_ray_march.restype = None
+        L.orc_ray_march.argtypes = [i32, P, P, P, P, P, i32, i32, P, P, P, P, ctypes.c_double, ctypes.c_double,
+                                    i32, P, P, P, P]
         L.orc_voxel_boxes.restype = i64
         L.orc_voxel_boxes.argtypes = [i32, P, P, P, P, P, P, P, f32, P]
         L.orc_voxel_density.restype = None
@@ -306,6 +309,32 @@ def render_grad(scene, cams, opts, L, dL_drgb, dL_dT=None, mask=None):
         out["kappa"] = d_theta
         out["scale"] = out["scale"] + d_scale
     return out
+
+
+def ray_march(scene, cams, opts=None, t_near=0.2, t_far=10.0, n_samples=256, mask=None, depth=None):
+    """Supp. A's ray-marching reference: NeRF's quadrature of Eq. 1 with sigma = sum kappa G and
+    c = sum c kappa G / sigma at n_samples midpoints of [t_near, t_far] along each pixel's unit
+    ray, over every Gaussian with a valid depth key (no lists, no order, no overlap assumption).
+    Returns per-view lists of rgb [H, W, 3] and T [H, W] (float64)."""
+    oa, o = _opts_arr(opts)
+    if depth is None:
+        depth, _ = keys(scene, cams, o)
+    mu, sc, q, _k, sh = _scene_arrays(scene, np.float64)
+    k = _c(_density(scene, o), np.float64)
+    cf, wh = cam_arrays(cams)
+    pb, P = pix_bases(cams)
+    rgb = np.zeros((P, 3), np.float64)
+    T = np.zeros(P, np.float64)
+    m = None if mask is None else _c(mask, np.int32)
+    lib().orc_ray_march(scene.n, _p(mu), _p(sc), _p(q), _p(k), _p(sh), scene.sh_degree, len(cams), _p(cf), _p(wh),
+                        _p(oa), _p(_c(depth, np.uint32)), float(t_near), float(t_far), int(n_samples), _p(pb), _p(m),
+                        _p(rgb), _p(T))
+    out_rgb, out_T = [], []
+    for v, c in enumerate(cams):
+        s_ = slice(pb[v], pb[v] + c.width * c.height)
+        out_rgb.append(rgb[s_].reshape(c.height, c.width, 3))
+        out_T.append(T[s_].reshape(c.height, c.width))
+    return out_rgb, out_T
 
 
 def tau(scene, g, o, d):

@@ -1139,6 +1139,76 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
     free(SP);
 }
 
+/* ======================== ray-marching reference (Supp. A) ======================== */
+/* Eq. 1 discretised with the quadrature of NeRF (Mildenhall et al. 2020, its Eq. 3) on
+ * n_samples midpoint samples t_k = t_near + (k + 1/2) delta of [t_near, t_far] along each pixel's
+ * unit ray from the camera centre, with the fields of Supp. A (with kappa, reading 11):
+ *   sigma(x) = sum_i kappa_i G_i(x),  c(x) = sum_i c_i kappa_i G_i(x) / sigma(x),
+ *   C = sum_k T_k (1 - exp(-sigma_k delta)) c(x_k) + T bg,  T_k = exp(-delta sum_{j<k} sigma_j).
+ * c_i is the Gaussian's colour for the view (the rasterizer's).  Every Gaussian with a valid depth
+ * key takes part, with no lists and no order; T_stop (opts[3]) ends a pixel's march. */
+void orc_ray_march(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
+                   const double *sh, int sh_degree, int n_views, const float *cam_f, const int32_t *cam_wh,
+                   const double *opts, const uint32_t *depth_bits, double t_near, double t_far, int n_samples,
+                   const int64_t *pix_base, const int32_t *pix_mask, double *rgb, double *T_final)
+{
+    const double T_stop = opts[3];
+    const double bg[3] = {opts[4], opts[5], opts[6]};
+    const int K = (sh_degree + 1) * (sh_degree + 1);
+    const double delta = (t_far - t_near) / n_samples;
+    gauss64 *G = (gauss64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(gauss64));
+    double *col = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
+    int *use = (int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
+    for (int g = 0; g < n; ++g) prep64(mu + 3 * g, scale + 3 * g, quat + 4 * g, kappa[g], &G[g]);
+    for (int v = 0; v < n_views; ++v) {
+        cam64 cam;
+        cam_setup(cam_f + 16 * v, cam_wh + 2 * v, &cam);
+        double raw[3];
+        int nu = 0;
+        for (int g = 0; g < n; ++g) {
+            if (depth_bits[(int64_t)v * n + g] == 0xFFFFFFFFu) continue;
+            colour64(sh + (size_t)g * K * 3, sh_degree, &G[g], cam.o, col + 3 * g, raw, opts[8]);
+            use[nu++] = g;
+        }
+        const int W = cam.W, H = cam.H;
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t pix = 0; pix < (int64_t)W * H; ++pix) {
+            const int64_t gp = pix_base[v] + pix;
+            if (pix_mask && !pix_mask[gp]) continue;
+            const int x = (int)(pix % W), y = (int)(pix / W);
+            double d[3];
+            pixel_dir(&cam, x, y, d);
+            double T = 1.0, C[3] = {0, 0, 0};
+            for (int k = 0; k < n_samples; ++k) {
+                const double t = t_near + (k + 0.5) * delta;
+                double xk[3], sig = 0, cs[3] = {0, 0, 0};
+                for (int a = 0; a < 3; ++a) xk[a] = cam.o[a] + t * d[a];
+                for (int u = 0; u < nu; ++u) {
+                    const gauss64 *Gg = &G[use[u]];
+                    double e[3], m2 = 0;
+                    for (int a = 0; a < 3; ++a) e[a] = xk[a] - Gg->mu[a];
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) m2 += e[a] * Gg->P[3 * a + b] * e[b];
+                    const double val = Gg->kap * exp(-0.5 * m2);
+                    sig += val;
+                    for (int ch = 0; ch < 3; ++ch) cs[ch] += col[3 * use[u] + ch] * val;
+                }
+                if (sig > 0) {
+                    const double w = -expm1(-sig * delta) / sig;   /* (1 - e^{-sigma delta}) / sigma */
+                    for (int ch = 0; ch < 3; ++ch) C[ch] += T * w * cs[ch];
+                    T *= exp(-sig * delta);
+                }
+                if (T < T_stop) break;
+            }
+            for (int ch = 0; ch < 3; ++ch) rgb[3 * gp + ch] = C[ch] + T * bg[ch];
+            T_final[gp] = T;
+        }
+    }
+    free(G);
+    free(col);
+    free(use);
+}
+
 /* ================================ voxel density ================================ */
 /* Density on a grid (for volumetric metrics): sigma(x) = sum_g kappa_g G_g(x) (Eq. 3-4) at the
  * voxel centres x = origin + (i + 1/2, j + 1/2, k + 1/2) * voxel.  Each Gaussian is truncated

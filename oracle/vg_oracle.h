@@ -72,6 +72,13 @@ void orc_render_grad(int n, const double *mu, const double *scale, const double 
                      const double *dL_drgb, const double *dL_dT, const int32_t *pix_mask,
                      double *dmu, double *dscale, double *dquat, double *dkappa, double *dsh);
 
+/* Ray-marching reference (Supp. A): NeRF quadrature of Eq. 1 with sigma = sum kappa G and the
+ * density-weighted colour, midpoint samples on [t_near, t_far]; every Gaussian with a valid depth key. */
+void orc_ray_march(int n, const double *mu, const double *scale, const double *quat, const double *kappa,
+                   const double *sh, int sh_degree, int n_views, const float *cam_f, const int32_t *cam_wh,
+                   const double *opts, const uint32_t *depth_bits, double t_near, double t_far, int n_samples,
+                   const int64_t *pix_base, const int32_t *pix_mask, double *rgb, double *T_final);
+
 /* Voxel density: truncation boxes (FP32 key-function style, bit-exact) and sigma at voxel centres. */
 int64_t orc_voxel_boxes(int n, const float *mu, const float *scale, const float *quat, const float *kappa,
                         const float *origin, const float *voxel, const int32_t *dims, float sigma_cut,

@@ -717,3 +717,50 @@ def test_splat_gradient_matches_finite_differences(variant):
         idx = range(arr.size) if arr.size <= 40 else rng.choice(arr.size, 40, replace=False)
         assert np.max(np.abs(g[name])) > 0, name
         _fd_check(loss, arr, g[name], idx, rtol=2e-6)
+
+
+# ------------------------------------------------------------------ ray-marching reference (Supp. A)
+def test_ray_march_single_gaussian_is_the_closed_form():
+    """One Gaussian: the marched transmittance is exp(-tau) with tau the closed form of Eq. 19 up to
+    the midpoint rule's O(delta^2) error, and the colour is c (1 - T) (constant c(x))."""
+    scene = one_gaussian((0.05, -0.03, 0.1), (0.12, 0.07, 0.1), (0.8, 0.3, -0.2, 0.4), 5.0, (0.6, -0.3, 0.9))
+    cam = synth.look_at((0.3, 0.2, -4.0), (0.0, 0.0, 0.0), 9, 7, 8.0)
+    rgb, T = oracle.ray_march(scene, [cam], oracle.EXACT, 2.0, 6.0, 20000)
+    o, d = pixel_rays(cam)
+    want = np.zeros((cam.height, cam.width))
+    for yy in range(cam.height):
+        for xx in range(cam.width):
+            want[yy, xx] = oracle.tau(scene, 0, o, d[yy, xx])["tau"]
+    assert want.max() > 0.5
+    assert np.max(np.abs(T[0] - np.exp(-want))) < 1e-7
+    c = np.clip(scene.sh[0, 0].astype(np.float64) * oracle.sh_basis(0, np.array([0.0, 0.0, 1.0]))[0] + 0.5, 0, None)
+    assert np.max(np.abs(rgb[0] - c[None, None, :] * (1.0 - T[0])[..., None])) < 1e-12
+    # starting the march at the maximiser gamma of the 1D Gaussian along a ray integrates its
+    # second half: T = exp(-tau / 2) (this fixes the sample positions at the interval midpoints)
+    yy, xx = cam.height // 2, cam.width // 2
+    info = oracle.tau(scene, 0, o, d[yy, xx])
+    _, Th = oracle.ray_march(scene, [cam], oracle.EXACT, info["gamma"], info["gamma"] + 3.0, 2000)
+    assert abs(Th[0][yy, xx] - math.exp(-0.5 * info["tau"])) < 1e-7
+
+
+def test_ray_march_matches_an_independent_march_and_the_blend_without_overlap():
+    """The oracle's march equals the test-side march (same quadrature, written independently) on a
+    random scene; without overlap it equals the Eq. 14 blend; with heavy overlap it does not."""
+    sc = synth.uniform_scene(12, 77, log_scale=(-2.5, -1.8), kappa=(0.5, 8.0), extent=0.5)
+    cam = synth.look_at((0.2, -0.1, -3.0), (0.0, 0.0, 0.0), 8, 6, 30.0)
+    rgb, _ = oracle.ray_march(sc, [cam], oracle.EXACT, 1.5, 4.5, 3000)
+    ref = _ray_march(sc, cam, 1.5, 4.5, 3000)
+    assert np.max(np.abs(rgb[0] - ref)) < 1e-10
+    q = synth.random_unit_quats(np.random.default_rng(6), 3)
+    sep = concat(one_gaussian((0.01, 0.0, -1.0), (0.08, 0.06, 0.1), q[0], 3.0, (1.0, -0.5, 0.2)),
+                 one_gaussian((-0.02, 0.01, 0.0), (0.07, 0.09, 0.05), q[1], 6.0, (-0.4, 0.9, 0.3)),
+                 one_gaussian((0.0, -0.01, 1.0), (0.1, 0.08, 0.09), q[2], 1.5, (0.3, 0.3, -0.8)))
+    cam2 = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 6, 6, 4.0)
+    blend, _, _ = oracle.render(sep, [cam2], oracle.EXACT, brute=True)
+    march, _ = oracle.ray_march(sep, [cam2], oracle.EXACT, 1.0, 7.0, 120000)
+    assert np.max(np.abs(blend[0] - march[0])) < 2e-6
+    ovl = concat(one_gaussian((0.0, 0.0, 0.0), (0.1, 0.1, 0.1), q[0], 4.0, (1.0, -0.5, 0.2)),
+                 one_gaussian((0.0, 0.0, 0.02), (0.1, 0.1, 0.1), q[1], 4.0, (-0.4, 0.9, 0.3)))
+    blend2, _, _ = oracle.render(ovl, [cam2], oracle.EXACT, brute=True)
+    march2, _ = oracle.ray_march(ovl, [cam2], oracle.EXACT, 2.0, 6.0, 60000)
+    assert np.max(np.abs(blend2[0] - march2[0])) > 1e-2
