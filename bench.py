@@ -251,6 +251,70 @@ def run_voxel(args):
     print(json.dumps(out_), flush=True)
 
 
+# ----------------------------------------------------------------------------- ray-march reference
+def run_march(args):
+    """Supp. A at scale: config 1's scene (2,000 Gaussians, uniform in [-1, 1]^3, scales 0.018-0.135)
+    seen by a 1280x832 camera, rasterized (exact mode) and ray-marched with 1,024 samples on
+    [2.5, 5.5] (spacing 0.003, well below the smallest scale); one step = one march with the
+    overlap-error map.  Also times the march on config 2's 1M Gaussians (512 samples), where the
+    thinnest Gaussians are below the sample spacing (a timing, not a reference image)."""
+    import torch
+
+    import paper_2412_03378_gb300 as vg
+    import synth
+
+    vg.load()
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev).contiguous()
+
+    def setup(scene, cam):
+        g = vg.Gaussians(t(scene.mu), t(scene.scale), t(scene.quat), t(scene.kappa), t(scene.sh), scene.sh_degree)
+        ws = vg.Workspace()
+        P = cam.width * cam.height
+        raster, T = torch.empty(P, 3, device=dev), torch.empty(P, device=dev)
+        ws.preprocess(g, [cam], vg.Opts.exact())
+        ws.bin_sort()
+        ws.render_fwd(raster, T)
+        return g, ws, raster, P
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    scene, _ = synth.config1()
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 1280, 832, 60.0)
+    g, ws, raster, P = setup(scene, cam)
+    rgb, T, err = torch.empty(P, 3, device=dev), torch.empty(P, device=dev), torch.empty(P, device=dev)
+    ms = timed(lambda: ws.ray_march(2.5, 5.5, 1024, rgb, T, raster, err), args.steps, args.warmup)
+    e = err.cpu().numpy()
+    q = ws.query()
+    scene2, cams2, _ = synth.config2(args.frac)
+    g2, ws2, raster2, P2 = setup(scene2, cams2[0])
+    rgb2 = torch.empty(P2, 3, device=dev)
+    ms2 = timed(lambda: ws2.ray_march(2.2, 5.8, 512, rgb2), max(1, args.steps // 4), 1)
+    q2 = ws2.query()
+    out = {"metric": "ray-march reference (Supp. A) marches/s", "value": 1e3 / ms, "unit": "marches/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "config 1 scene (2,000 Gaussians) at 1280x832, 1,024 samples on [2.5, 5.5], "
+                                  "overlap-error map against the exact-mode raster"},
+           "instances": q["n_instances"],
+           "overlap_error": {"mean": float(e.mean()), "p99": float(np.quantile(e, 0.99)), "max": float(e.max()),
+                             "frac_above_1e-2": float((e > 1e-2).mean())},
+           "config2_march_ms": ms2, "config2_instances": q2["n_instances"],
+           "config2_note": "1M Gaussians, 1280x832, 512 samples on [2.2, 5.8]; the thinnest Gaussians are "
+                           "narrower than the sample spacing, so this is a timing only"}
+    print(json.dumps(out), flush=True)
+
+
 # ----------------------------------------------------------------------------- batched graph path
 def graph_step(vg, g, cams, steps, warmup, dev, target_seed=2102):
     """A whole training step over all `cams` (preprocess, bin/sort, forward, L2 loss, backward)
@@ -784,9 +848,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-views", type=int, default=4,
                     help="views of the BF16 / graph-replayed batched measurement (0: skip it)")
-    ap.add_argument("--workload", choices=["render", "tomo", "cone", "voxel", "cfg3", "cfg5"], default="render",
+    ap.add_argument("--workload", choices=["render", "tomo", "cone", "voxel", "march", "cfg3", "cfg5"], default="render",
                     help="render: the headline training step; tomo: the tomography step (config 4); "
                          "cone: cone-beam tomography; voxel: the voxel density query; "
+                         "march: the ray-marching reference and its overlap-error map; "
                          "cfg3 / cfg5: the batched BF16 configurations as one CUDA graph per step")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -799,6 +864,8 @@ def main():
         run_cone(args)
     elif args.workload == "voxel":
         run_voxel(args)
+    elif args.workload == "march":
+        run_march(args)
     elif args.workload in ("cfg3", "cfg5"):
         run_batched_config(args)
     else:

@@ -164,7 +164,7 @@ typedef struct {
 /* Per-stage device time recorded with CUDA events on the launching stream while
  * profiling is enabled (vg_profile_enable).  Stage names: "preprocess", "depth_sort",
  * "scan", "duplicate", "tile_sort", "ranges", "render_fwd", "render_bwd", "chain",
- * "l2_loss", "tomo_fwd", "tomo_bwd", "voxel_eval" (the voxel query records its own
+ * "l2_loss", "tomo_fwd", "tomo_bwd", "voxel_eval", "ray_march" (the voxel query records its own
  * preprocess, scan, duplicate, tile_sort and ranges stages under the same names). */
 typedef struct {
     char name[24];
@@ -272,6 +272,20 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
 vg_status vg_project_cone(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams, int32_t n_views,
                           const vg_opts *opts, float *proj, const float *dL_dproj, float *dmu, float *dscale,
                           float *dquat, float *dkappa, void *stream);
+
+/* Ray-marching reference (Supp. A) of the views binned by the last vg_preprocess / vg_bin_sort
+ * (default mode only): Eq. 1 with sigma(x) = sum kappa G(x) and c(x) = sum c kappa G(x) / sigma(x)
+ * (c the Gaussians' colours of the view) by NeRF's quadrature on n_samples (1..2^20) midpoint
+ * samples of [t_near, t_far] (0 <= t_near < t_far) along each pixel's unit ray:
+ *   rgb = sum_k T_k (1 - exp(-sigma_k delta)) c(x_k) + T bg,   T = exp(-delta sum_k sigma_k),
+ * ending a pixel once T < opts.T_stop.  Unlike the blend it assumes neither order nor the absence
+ * of overlap, so |rgb - blend| measures those approximations: with raster_rgb (the vg_render_fwd
+ * image of the same views) err_map[p] = max over channels |rgb - raster_rgb| (the overlap-error
+ * map).  Each Gaussian enters the pixels of its footprint rectangle (opts.tau_cut bounds what
+ * the rest adds to a ray's optical depth).  rgb [P][3], T [P], err_map [P] are float32 device
+ * buffers, each optional (err_map needs raster_rgb). */
+vg_status vg_ray_march(vg_workspace *ws, float t_near, float t_far, int32_t n_samples, const float *raster_rgb,
+                       float *rgb, float *T, float *err_map, void *stream);
 
 /* Regular voxel grid: voxel (i, j, k) has its centre at origin + (i + 1/2, j + 1/2, k + 1/2) * voxel. */
 typedef struct {

@@ -95,6 +95,7 @@ _SIGS = {
     "vg_project_tomo": [ctypes.c_void_p] * 11,
     "vg_project_cone": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 8,
     "vg_query_density": [ctypes.c_void_p] * 6,
+    "vg_ray_march": [ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_int32] + [ctypes.c_void_p] * 5,
     "vg_l2_loss": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_query": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
@@ -312,6 +313,12 @@ class Workspace:
         oc = opts.c()
         self._chk(self._L.vg_query_density(self.h, ctypes.byref(g.c()), ctypes.byref(gr), ctypes.byref(oc), _ptr(out),
                                            _stream(stream)))
+
+    def ray_march(self, t_near, t_far, n_samples, rgb=None, T=None, raster_rgb=None, err_map=None, stream=None):
+        """Ray-marching reference of the binned views (see vg_ray_march): rgb [P, 3], T [P] and the
+        overlap-error map err_map [P] (needs raster_rgb, the vg_render_fwd image)."""
+        self._chk(self._L.vg_ray_march(self.h, float(t_near), float(t_far), int(n_samples), _ptr(raster_rgb), _ptr(rgb),
+                                       _ptr(T), _ptr(err_map), _stream(stream)))
 
     def l2_loss(self, x, y, scale, loss, grad, stream=None):
         self._chk(self._L.vg_l2_loss(self.h, _ptr(x), _ptr(y), x.numel(), float(scale), _ptr(loss), _ptr(grad),

@@ -57,6 +57,7 @@ struct vg_workspace {
     DBuf<float> tomo_cs;
     DBuf<uint32_t> tord;                  // tile order buffer
     DBuf<short4> vbox;                    // voxel query: truncation boxes (2 per Gaussian)
+    DBuf<float4> march_E;                 // ray march: o'.A_k per item
     uint32_t *tile_order = nullptr;       // longest-first tile order of the last bin_sort
     int ppt_fwd = 2, ppt_bwd = 1;         // pixels per thread of the blend kernels
     int tuned_fwd = 0, tuned_bwd = 0;     // vg_autotune's choice (0: none yet)
@@ -80,10 +81,10 @@ constexpr int kDefaultPixelsFwd = 2;
 constexpr int kDefaultPixelsBwd = 1;
 
 enum Stage { ST_PRE, ST_DEPTH, ST_SCAN, ST_DUP, ST_TILE, ST_RANGES, ST_FWD, ST_BWD, ST_CHAIN, ST_LOSS, ST_TFWD,
-             ST_TBWD, ST_VOXEL, ST_COUNT };
+             ST_TBWD, ST_VOXEL, ST_MARCH, ST_COUNT };
 const char *kStageName[ST_COUNT] = {"preprocess", "depth_sort", "scan",     "duplicate", "tile_sort", "ranges",
                                     "render_fwd", "render_bwd", "chain",    "l2_loss",   "tomo_fwd",  "tomo_bwd",
-                                    "voxel_eval"};
+                                    "voxel_eval", "ray_march"};
 
 cudaEvent_t prof_event(vg_workspace *ws) {
     if (!ws->prof_pool.empty()) {
@@ -260,6 +261,7 @@ vg_status vg_workspace_destroy(vg_workspace *ws) {
     release(ws->tomo_cs);
     release(ws->tord);
     release(ws->vbox);
+    release(ws->march_E);
     if (ws->h_total) cudaFreeHost(ws->h_total);
     for (auto &r : ws->prof) {
         cudaEventDestroy(r.a);
@@ -605,6 +607,25 @@ vg_status vg_project_cone(vg_workspace *ws, const vg_gaussians *g, const vg_came
     if (!proj && ws->n_pixels > 0) return fail(ws, VG_ERR_INVALID_ARG, "proj is NULL");
     VG_TRY(render_fwd_impl(ws, nullptr, proj, stream, true));
     if (dL_dproj) VG_TRY(render_bwd_impl(ws, nullptr, dL_dproj, dmu, dscale, dquat, dkappa, nullptr, stream, true));
+    return VG_OK;
+}
+
+vg_status vg_ray_march(vg_workspace *ws, float t_near, float t_far, int32_t n_samples, const float *raster_rgb,
+                       float *rgb, float *T, float *err_map, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (ws->stage < 2) return fail(ws, VG_ERR_STATE, "vg_ray_march before vg_bin_sort");
+    if (ws->g.splat) return fail(ws, VG_ERR_INVALID_ARG, "the ray march needs the default (volumetric) mode");
+    if (!(t_near >= 0.0f) || !(t_far > t_near) || !std::isfinite(t_far))
+        return fail(ws, VG_ERR_INVALID_ARG, "need 0 <= t_near < t_far, finite");
+    if (n_samples < 1 || n_samples > (1 << 20)) return fail(ws, VG_ERR_INVALID_ARG, "n_samples must be 1..2^20");
+    if (err_map && !raster_rgb) return fail(ws, VG_ERR_INVALID_ARG, "err_map needs raster_rgb");
+    cudaStream_t st = (cudaStream_t)stream;
+    VG_TRY(ensure(ws, ws->march_E, (size_t)ws->n_items, "ray-march scratch"));
+    ProfScope ps(ws, ST_MARCH, st);
+    VG_CUDA(ws, launch_ray_march(ws->g, ws->views.p, ws->tile_view.p, ws->n_tiles, ws->n_items, ws->ranges.p,
+                                 ws->inst_item, ws->rec.p, ws->count.p, ws->prect.p, ws->march_E.p, t_near, t_far,
+                                 n_samples, ws->opts.T_stop, ws->opts.bg, raster_rgb, rgb, T, err_map, st,
+                                 &ws->launches));
     return VG_OK;
 }
 

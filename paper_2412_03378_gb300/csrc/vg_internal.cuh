@@ -147,6 +147,14 @@ cudaError_t launch_voxel_dup(const uint32_t *offsets, const short4 *box, const V
 cudaError_t launch_voxel_eval(const uint2 *ranges, const uint32_t *sorted, const float4 *rec, const short4 *box,
                               const VoxelGrid &grid, float *out, cudaStream_t st, long long *launches);
 
+// Ray-marching reference (march.cu): E receives (o'.A0, o'.A1, o'.A2) per item (scratch);
+// rgb / T_out / err (max over channels of |rgb - raster|) are each optional.
+cudaError_t launch_ray_march(const GaussIn &g, const ViewInfo *views_d, const int *tile_view, long long n_tiles,
+                             long long n_items, const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
+                             const uint32_t *count, const short4 *prect, float4 *E, float t_near, float t_far,
+                             int n_samples, float T_stop, const float bg[3], const float *raster, float *rgb,
+                             float *T_out, float *err, cudaStream_t st, long long *launches);
+
 cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc, int zero,
                          float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st,
                          long long *launches);
