@@ -63,6 +63,8 @@ typedef struct {
     int32_t sh_dtype;    /* vg_dtype of sh */
     int32_t n;
     int32_t sh_degree;   /* 0..3 */
+    int32_t mu_f32;      /* nonzero: mu is float32 whatever rec_dtype says (mixed storage: BF16 / FP16
+                            records with FP32 means keep image errors near 1e-4) */
 } vg_gaussians;
 
 /* Pinhole camera, OpenCV axes (x right, y down, z forward).  A world point x maps to

@@ -40,7 +40,8 @@ class VGError(RuntimeError):
 class _Gaussians(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("quat", ctypes.c_void_p),
                 ("kappa", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("rec_dtype", ctypes.c_int32),
-                ("sh_dtype", ctypes.c_int32), ("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32)]
+                ("sh_dtype", ctypes.c_int32), ("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
+                ("mu_f32", ctypes.c_int32)]
 
 
 class _Camera(ctypes.Structure):
@@ -197,7 +198,14 @@ class Gaussians:
         g = _Gaussians()
         g.mu, g.scale, g.quat, g.kappa = (t.data_ptr() for t in (self.mu, self.scale, self.quat, self.kappa))
         g.sh = self.sh.data_ptr() if self.sh is not None else None
-        g.rec_dtype = _DT[self.mu.dtype]
+        # scale, quat and kappa share one dtype; mu has it too or is float32 (mixed storage)
+        rec = _DT[self.scale.dtype]
+        if self.quat.dtype != self.scale.dtype or self.kappa.dtype != self.scale.dtype:
+            raise ValueError("scale, quat and kappa must share one dtype")
+        if self.mu.dtype != self.scale.dtype and self.mu.dtype != torch.float32:
+            raise ValueError("mu must have the dtype of scale/quat/kappa or be float32")
+        g.rec_dtype = rec
+        g.mu_f32 = 1 if self.mu.dtype == torch.float32 else 0
         g.sh_dtype = _DT[self.sh.dtype] if self.sh is not None else VG_F32
         g.n = self.n
         g.sh_degree = self.sh_degree

@@ -193,6 +193,7 @@ GaussIn to_in(const vg_gaussians *g) {
     r.sh_dtype = g->sh_dtype;
     r.n = g->n;
     r.sh_degree = g->sh_degree;
+    r.mu_f32 = g->mu_f32 ? 1 : 0;
     r.density_theta = 0;
     r.softplus_beta = 0.0f;
     r.splat = 0;

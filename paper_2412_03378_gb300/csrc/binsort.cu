@@ -268,6 +268,16 @@ k_onesweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
     const long long tile = s_tile;
     if (n_dev && (long long)*n_dev < n) n = (long long)*n_dev;   // the count is known on the device only
     if (tile * kRsTile >= n) return;                             // the grid covers a larger capacity
+    // a pass whose digit is the same for every key (the exponent byte of depth keys, often) is the
+    // identity permutation: every CTA sees the same digit count and copies its tile instead
+    if (ghist[(keys[tile * kRsTile] >> shift) & mask] == (uint32_t)n) {
+        const long long t0 = tile * kRsTile, t1 = min(t0 + kRsTile, n);
+        for (long long i = t0 + threadIdx.x; i < t1; i += kRsThreads) {
+            ko[i] = keys[i];
+            vo[i] = vals ? vals[i] : (uint32_t)i;
+        }
+        return;
+    }
     // 1. stable rank inside the tile: warp w ranks keys [w*256, (w+1)*256) of the tile in order,
     //    32 at a time, with __match_any_sync
     const long long base = tile * kRsTile + w * (kRsItems * 32);

@@ -27,7 +27,7 @@ __device__ __forceinline__ void load_gauss(const GaussIn &g, long long i, float 
     const RT *m = (const RT *)g.mu, *sc = (const RT *)g.scale, *qq = (const RT *)g.quat, *k = (const RT *)g.kappa;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        mu[c] = ld_f<RT>(m, 3 * i + c);
+        mu[c] = g.mu_f32 ? ld_f<float>((const float *)g.mu, 3 * i + c) : ld_f<RT>(m, 3 * i + c);
         s[c] = ld_f<RT>(sc, 3 * i + c);
     }
 #pragma unroll

@@ -29,8 +29,11 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
         const int nloc = (int)min(32LL, (long long)g.n - gbase);
         const long long gi = gbase + lane;
         const long long it = (long long)v * g.n + gi;
-        // the SH rows of the warp's Gaussians, coalesced, before (and independent of) the key
+        // the SH rows of the warp's Gaussians, coalesced, before (and independent of) the key; the
+        // parameter loads are issued before the wait so that both round trips overlap
         if (g.sh) warp_load_rows<ST>((const ST *)g.sh + gbase * K3, nloc, K3, buf, lane);
+        float mu[3], s[3], q[4], kin;
+        if (lane < nloc) load_gauss<RT>(g, gi, mu, s, q, kin);
         rows_wait();
         __syncwarp();
         const ViewInfo &V = views[v];
@@ -38,8 +41,6 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
         uint32_t cnt = 0, dk = 0xFFFFFFFFu;
         short4 rc = make_short4(-1, -1, -1, -1), prc = rc;
         if (lane < nloc) {
-            float mu[3], s[3], q[4], kin;
-            load_gauss<RT>(g, gi, mu, s, q, kin);
             const Density dn = density_of(g, kin, s);
             float Sig[9], Rq[9], qn[4], smax, Zf;
             if (key_cov(mu, s, q, dn.kap_key, Sig, Rq, qn, smax)) {

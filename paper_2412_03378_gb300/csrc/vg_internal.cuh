@@ -32,6 +32,7 @@ struct ViewInfo {
 struct GaussIn {
     const void *mu, *scale, *quat, *kappa, *sh;
     int rec_dtype, sh_dtype, n, sh_degree;
+    int mu_f32;            // mu is float32 whatever rec_dtype says
     int density_theta;     // the density array holds Eq. 20's theta
     float softplus_beta;   // colour activation: 0 = clamp at 0, > 0 = softplus(beta)
     int splat;             // 3DGS comparison mode: the density array holds the peak opacity

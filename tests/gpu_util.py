@@ -5,10 +5,10 @@ import torch
 import oracle
 
 
-def dev_scene(vg, scene, rec_dtype=torch.float32, sh_dtype=torch.float32):
+def dev_scene(vg, scene, rec_dtype=torch.float32, sh_dtype=torch.float32, mu_dtype=None):
     d = torch.device("cuda:0")
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(d, dt).contiguous()
-    return vg.Gaussians(t(scene.mu, rec_dtype), t(scene.scale, rec_dtype), t(scene.quat, rec_dtype),
+    return vg.Gaussians(t(scene.mu, mu_dtype or rec_dtype), t(scene.scale, rec_dtype), t(scene.quat, rec_dtype),
                         t(scene.kappa, rec_dtype), t(scene.sh, sh_dtype), scene.sh_degree)
 
 

@@ -224,18 +224,21 @@ def test_sh_degrees(gpu_lib, deg):
     check_grads(gg, ref, scene, GRAD_TOL)
 
 
-@pytest.mark.parametrize("rec_dtype,sh_dtype", [("bf16", "bf16"), ("f16", "f16"), ("f32", "bf16"), ("bf16", "f32")])
+@pytest.mark.parametrize("rec_dtype,sh_dtype", [("bf16", "bf16"), ("f16", "f16"), ("f32", "bf16"), ("bf16", "f32"),
+                                               ("bf16+mu32", "f16"), ("f16+mu32", "f16")])
 def test_reduced_precision_storage(gpu_lib, rec_dtype, sh_dtype):
-    """Parameters stored as bf16 / f16 are widened to FP32 on load: the result equals the
-    oracle's on the same (rounded) parameter values."""
+    """Parameters stored as bf16 / f16 (optionally with FP32 means) are widened to FP32 on load:
+    the result equals the oracle's on the same (rounded) parameter values."""
     import torch
     vg = gpu_lib
     dts = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
     scene, cams = _multi_view_scene()
+    rec_dtype, _, mu32 = rec_dtype.partition("+")
+    mu_dtype = "f32" if mu32 else rec_dtype
     rnd = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(dts[dt]).float().numpy()
-    sq = synth.Scene(rnd(scene.mu, rec_dtype), rnd(scene.scale, rec_dtype), rnd(scene.quat, rec_dtype),
+    sq = synth.Scene(rnd(scene.mu, mu_dtype), rnd(scene.scale, rec_dtype), rnd(scene.quat, rec_dtype),
                      rnd(scene.kappa, rec_dtype), rnd(scene.sh, sh_dtype), scene.sh_degree)
-    g = dev_scene(vg, sq, rec_dtype=dts[rec_dtype], sh_dtype=dts[sh_dtype])
+    g = dev_scene(vg, sq, rec_dtype=dts[rec_dtype], sh_dtype=dts[sh_dtype], mu_dtype=dts[mu_dtype])
     o = dict(oracle.EXACT, bg=(0.3, 0.2, 0.1))
     ws, g, rgb, T = run_forward(vg, sq, cams, o, g=g)
     ref_rgb, _, _ = oracle.render(sq, cams, o)
