@@ -439,6 +439,24 @@ def run_batched_config(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def max_over_ranks(t_local, dev, world):
+    """The timed region's duration of the slowest rank (every rank calls this after its own
+    barrier-bracketed region): the job finishes when its last replica does."""
+    if world <= 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(steps, world, t_max):
+    """Whole-job throughput: the steps all ranks processed over the slowest rank's time."""
+    return steps * world / t_max
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -511,14 +529,8 @@ def run_ours(args):
     launches = ws.query()["launches"] - l0
     ms = e0.elapsed_time(e1)
     t_local = ms / 1e3
-    if world > 1:
-        tt = torch.tensor([t_local], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    else:
-        t_max = t_local
-    total_steps = args.steps * world
-    value = total_steps / t_max
+    t_max = max_over_ranks(t_local, dev, world)
+    value = job_value(args.steps, world, t_max)
 
     # ---- forward-only frames/s (same protocol, not part of the headline value)
     for _ in range(2):
@@ -564,12 +576,8 @@ def run_ours(args):
     for _ in range(args.steps):
         e2e_step()
     barrier()
-    e2e_t = time.perf_counter() - w0
-    if world > 1:
-        tt = torch.tensor([e2e_t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
-    e2e_value = args.steps * world / e2e_t
+    e2e_t = max_over_ranks(time.perf_counter() - w0, dev, world)
+    e2e_value = job_value(args.steps, world, e2e_t)
 
     if rank != 0:
         if world > 1:
