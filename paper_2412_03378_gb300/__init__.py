@@ -411,6 +411,67 @@ class _RenderFn(torch.autograd.Function):
                 dkappa.to(g.kappa.dtype), dsh.to(g.sh.dtype))
 
 
+class _TomoFn(torch.autograd.Function):
+    """proj = exp(-sum tau) of a parallel beam (vg_project_tomo); the backward calls it again
+    with dL/dproj, which recomputes the projection and accumulates the gradients."""
+
+    @staticmethod
+    def forward(ctx, ws, beam, opts, mu, scale, quat, kappa):
+        g = Gaussians(mu.detach().contiguous(), scale.detach().contiguous(), quat.detach().contiguous(),
+                      kappa.detach().contiguous(), None, 0)
+        proj = torch.empty((len(beam.angles), int(beam.det_h), int(beam.det_w)), device=mu.device,
+                           dtype=torch.float32)
+        ws.project_tomo(g, beam, opts, proj)
+        ctx.ws, ctx.beam, ctx.opts, ctx.g = ws, beam, opts, g
+        return proj
+
+    @staticmethod
+    def backward(ctx, g_proj):
+        g = ctx.g
+        grads = [torch.zeros_like(t, dtype=torch.float32) for t in (g.mu, g.scale, g.quat, g.kappa)]
+        proj = torch.empty_like(g_proj, dtype=torch.float32)
+        ctx.ws.project_tomo(g, ctx.beam, ctx.opts, proj, g_proj.contiguous().float(), *grads)
+        return (None, None, None) + tuple(d.to(t.dtype) for d, t in zip(grads, (g.mu, g.scale, g.quat, g.kappa)))
+
+
+class _ConeFn(torch.autograd.Function):
+    """Cone-beam projection (vg_project_cone) with the same recompute-in-backward scheme."""
+
+    @staticmethod
+    def forward(ctx, ws, cams, opts, mu, scale, quat, kappa):
+        g = Gaussians(mu.detach().contiguous(), scale.detach().contiguous(), quat.detach().contiguous(),
+                      kappa.detach().contiguous(), None, 0)
+        proj = torch.empty((n_pixels(cams),), device=mu.device, dtype=torch.float32)
+        ws.project_cone(g, cams, opts, proj)
+        ctx.ws, ctx.cams, ctx.opts, ctx.g = ws, cams, opts, g
+        return proj
+
+    @staticmethod
+    def backward(ctx, g_proj):
+        g = ctx.g
+        grads = [torch.zeros_like(t, dtype=torch.float32) for t in (g.mu, g.scale, g.quat, g.kappa)]
+        proj = torch.empty_like(g_proj, dtype=torch.float32)
+        ctx.ws.project_cone(g, ctx.cams, ctx.opts, proj, g_proj.contiguous().float(), *grads)
+        return (None, None, None) + tuple(d.to(t.dtype) for d, t in zip(grads, (g.mu, g.scale, g.quat, g.kappa)))
+
+
+class Projector:
+    """Differentiable tomography bound to one workspace (Sec. 6.2, Eq. 21): `parallel` for a
+    parallel beam, `cone` for point sources (density only; colour coefficients unused)."""
+
+    def __init__(self, opts: Opts | None = None):
+        self.ws = Workspace()
+        self.opts = opts or Opts(tau_cut=1e-6)
+
+    def parallel(self, mu, scale, quat, kappa, beam):
+        """proj [A, det_h, det_w] = exp(-sum of the line integrals)."""
+        return _TomoFn.apply(self.ws, beam, self.opts, mu, scale, quat, kappa)
+
+    def cone(self, mu, scale, quat, kappa, cams: Sequence):
+        """proj [sum H*W] over the cameras' detectors."""
+        return _ConeFn.apply(self.ws, list(cams), self.opts, mu, scale, quat, kappa)
+
+
 def n_pixels_ws(ws):
     return ws.query()["n_pixels"]
 
