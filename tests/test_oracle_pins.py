@@ -764,3 +764,25 @@ def test_ray_march_matches_an_independent_march_and_the_blend_without_overlap():
     blend2, _, _ = oracle.render(ovl, [cam2], oracle.EXACT, brute=True)
     march2, _ = oracle.ray_march(ovl, [cam2], oracle.EXACT, 2.0, 6.0, 60000)
     assert np.max(np.abs(blend2[0] - march2[0])) > 1e-2
+
+
+# ------------------------------------------------------------------ values printed by the paper
+def _paper_values():
+    import os
+    out = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")):
+        if line.strip() and not line.startswith("#"):
+            name, value = line.split()[:2]
+            out[name] = float(value)
+    return out
+
+
+def test_eq20_constant_from_the_paper():
+    """Eq. 20 with the printed constant: theta = 1 gives kappa = -ln(1 - 0.99) times the mean
+    inverse scale; the oracle's kappa_from_theta follows it at every theta."""
+    c = _paper_values()["eq20_theta_scale"]
+    s = np.array([[0.1, 0.2, 0.4], [0.05, 0.05, 0.05]])
+    th = np.array([1.0, 0.37])
+    want = -np.log(1.0 - c * th) * (1.0 / s).sum(1) / 3.0
+    assert np.allclose(oracle.kappa_from_theta(th, s), want, rtol=1e-15, atol=0)
+    assert abs(oracle.kappa_from_theta(np.array([1.0]), np.array([[1.0, 1.0, 1.0]]))[0] - math.log(100.0)) < 1e-12
