@@ -134,6 +134,9 @@ typedef struct {
                                       1 - x = m 2^e) */
 #define VG_FLAG_COUNT_PAIRS 2u     /* render_fwd / render_bwd also count evaluated (pixel,
                                       Gaussian) pairs into vg_stats (slower; for roofline) */
+#define VG_FLAG_PROJ_GIVEN 32u     /* vg_project_tomo with dL_dproj: proj already holds the
+                                      projection of the same Gaussians, beam and options (from an
+                                      earlier call), so it is not recomputed before the backward */
 #define VG_FLAG_SPLAT 16u          /* the 3DGS comparison mode (Sec. 3.2, Eq. 5-7) in the same
                                       pipeline: the density input holds the peak opacity o and
                                       alpha = min(o G'(p), alpha_max), G' the 2D Gaussian with
@@ -260,6 +263,16 @@ vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const fl
 vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam *beam,
                           const vg_opts *opts, float *proj, const float *dL_dproj, float *dmu,
                           float *dscale, float *dquat, float *dkappa, void *stream);
+
+/* One tomography training step with the L2 loss, fused per angle batch: proj (written, as in
+ * vg_project_tomo), *loss = scale * sum_i (proj_i - target_i)^2 (device scalar, overwritten) and
+ * the gradients of *loss accumulated into dmu, dscale, dquat, dkappa (overwritten with
+ * VG_FLAG_GRAD_ZERO).  target [n_angles][det_h][det_w] float32, device.  Each angle batch is
+ * preprocessed, binned and projected once, where the two-call form (project, then project with
+ * dL_dproj) does it twice. */
+vg_status vg_tomo_l2_step(vg_workspace *ws, const vg_gaussians *g, const vg_beam *beam, const vg_opts *opts,
+                          const float *target, float scale, float *proj, float *loss, float *dmu, float *dscale,
+                          float *dquat, float *dkappa, void *stream);
 
 /* Cone-beam tomography (Eq. 21 with diverging rays): for each of n_views cameras the
  * X-ray source is the camera centre and the detector its image plane, so detector pixel (i, j)

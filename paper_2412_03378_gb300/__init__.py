@@ -26,6 +26,7 @@ FLAG_COUNT_PAIRS = 2
 FLAG_GRAD_ZERO = 4
 FLAG_DENSITY_THETA = 8
 FLAG_SPLAT = 16
+FLAG_PROJ_GIVEN = 32
 _STATUS = {0: "VG_OK", 1: "VG_ERR_INVALID_ARG", 2: "VG_ERR_CUDA", 3: "VG_ERR_OOM", 4: "VG_ERR_CAPACITY",
            5: "VG_ERR_TIMEOUT", 6: "VG_ERR_UNSUPPORTED", 7: "VG_ERR_STATE"}
 TILE = 16
@@ -96,6 +97,7 @@ _SIGS = {
     "vg_project_tomo": [ctypes.c_void_p] * 11,
     "vg_project_cone": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 8,
     "vg_query_density": [ctypes.c_void_p] * 6,
+    "vg_tomo_l2_step": [ctypes.c_void_p] * 5 + [ctypes.c_float] + [ctypes.c_void_p] * 7,
     "vg_ray_march": [ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_int32] + [ctypes.c_void_p] * 5,
     "vg_l2_loss": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
@@ -301,6 +303,19 @@ class Workspace:
         self._chk(self._L.vg_project_tomo(self.h, ctypes.byref(g.c()), ctypes.byref(b), ctypes.byref(oc), _ptr(proj),
                                           _ptr(dL_dproj), _ptr(dmu), _ptr(dscale), _ptr(dquat), _ptr(dkappa),
                                           _stream(stream)))
+
+    def tomo_l2_step(self, g: Gaussians, beam, opts: Opts, target, scale, proj, loss, dmu, dscale, dquat, dkappa,
+                     stream=None):
+        """Fused tomography training step with the L2 loss (see vg_tomo_l2_step)."""
+        ang = (ctypes.c_float * len(beam.angles))(*[float(a) for a in beam.angles])
+        b = _Beam()
+        b.n_angles, b.angles = len(beam.angles), ctypes.cast(ang, ctypes.c_void_p)
+        b.det_w, b.det_h = int(beam.det_w), int(beam.det_h)
+        b.pitch_u, b.pitch_v, b.u0, b.v0 = float(beam.pitch_u), float(beam.pitch_v), float(beam.u0), float(beam.v0)
+        oc = opts.c()
+        self._chk(self._L.vg_tomo_l2_step(self.h, ctypes.byref(g.c()), ctypes.byref(b), ctypes.byref(oc), _ptr(target),
+                                          float(scale), _ptr(proj), _ptr(loss), _ptr(dmu), _ptr(dscale), _ptr(dquat),
+                                          _ptr(dkappa), _stream(stream)))
 
     def project_cone(self, g: Gaussians, cams, opts: Opts, proj, dL_dproj=None, dmu=None, dscale=None, dquat=None,
                      dkappa=None, stream=None):

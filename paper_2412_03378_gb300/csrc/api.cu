@@ -58,6 +58,7 @@ struct vg_workspace {
     DBuf<uint32_t> tord;                  // tile order buffer
     DBuf<short4> vbox;                    // voxel query: truncation boxes (2 per Gaussian)
     DBuf<float4> march_E;                 // ray march: o'.A_k per item
+    DBuf<float> tomo_dl;                  // fused tomography step: dL/dproj of one angle batch
     uint32_t *tile_order = nullptr;       // longest-first tile order of the last bin_sort
     int ppt_fwd = 2, ppt_bwd = 1;         // pixels per thread of the blend kernels
     int tuned_fwd = 0, tuned_bwd = 0;     // vg_autotune's choice (0: none yet)
@@ -263,6 +264,7 @@ vg_status vg_workspace_destroy(vg_workspace *ws) {
     release(ws->tord);
     release(ws->vbox);
     release(ws->march_E);
+    release(ws->tomo_dl);
     if (ws->h_total) cudaFreeHost(ws->h_total);
     for (auto &r : ws->prof) {
         cudaEventDestroy(r.a);
@@ -760,11 +762,16 @@ vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const fl
     return VG_OK;
 }
 
-vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam *beam, const vg_opts *opts,
-                          float *proj, const float *dL_dproj, float *dmu, float *dscale, float *dquat, float *dkappa,
-                          void *stream) {
-    if (!ws) return VG_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
+// Parallel-beam projection in angle batches.  With dL_dproj the backward follows each batch's
+// projection; with target (and dL_dproj NULL) the L2 loss scale * sum (proj - target)^2 is
+// accumulated into *loss and its gradient drives the backward, so that each batch is
+// preprocessed, binned and projected once for the whole training step.
+static vg_status tomo_impl(vg_workspace *ws, const vg_gaussians *g, const vg_beam *beam, const vg_opts *opts,
+                           float *proj, const float *dL_dproj, const float *target, float scale, float *loss,
+                           float *dmu, float *dscale, float *dquat, float *dkappa, cudaStream_t st) {
+    const bool fused = target != nullptr;
+    const bool backward = dL_dproj != nullptr || fused;
+    const bool proj_given = dL_dproj && !fused && (opts && (opts->flags & VG_FLAG_PROJ_GIVEN));
     VG_TRY(check_gauss(ws, g, false));
     if (!beam || beam->n_angles < 1 || !beam->angles || beam->det_w <= 0 || beam->det_h <= 0 ||
         !finite_pos(beam->pitch_u) || !finite_pos(beam->pitch_v) || !std::isfinite(beam->u0) ||
@@ -773,8 +780,9 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
     if (!opts || !finite_pos(opts->tau_cut)) return fail(ws, VG_ERR_INVALID_ARG, "opts->tau_cut must be finite and > 0");
     if (opts->flags & VG_FLAG_SPLAT) return fail(ws, VG_ERR_INVALID_ARG, "tomography has no splat mode");
     if (!proj) return fail(ws, VG_ERR_INVALID_ARG, "proj is NULL");
-    if (dL_dproj && g->n > 0 && (!dmu || !dscale || !dquat || !dkappa))
+    if (backward && g->n > 0 && (!dmu || !dscale || !dquat || !dkappa))
         return fail(ws, VG_ERR_INVALID_ARG, "a gradient pointer is NULL");
+    if (fused && (!loss || !std::isfinite(scale))) return fail(ws, VG_ERR_INVALID_ARG, "loss is NULL or scale not finite");
     const int A = beam->n_angles, N = g->n;
     const int tiles_x = (beam->det_w + kTile - 1) / kTile, tiles_y = (beam->det_h + kTile - 1) / kTile;
     if (tiles_x > 32767 || tiles_y > 32767) return fail(ws, VG_ERR_INVALID_ARG, "detector too large");
@@ -793,7 +801,8 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
     }
     VG_TRY(ensure(ws, ws->tomo_cs, cs.size(), "beam angles"));
     VG_CUDA(ws, cudaMemcpyAsync(ws->tomo_cs.p, cs.data(), cs.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-    if (dL_dproj && (opts->flags & VG_FLAG_GRAD_ZERO) && N > 0) {
+    if (fused) VG_CUDA(ws, cudaMemsetAsync(loss, 0, sizeof(float), st));
+    if (backward && (opts->flags & VG_FLAG_GRAD_ZERO) && N > 0) {
         VG_CUDA(ws, cudaMemsetAsync(dmu, 0, (size_t)N * 3 * sizeof(float), st));
         VG_CUDA(ws, cudaMemsetAsync(dscale, 0, (size_t)N * 3 * sizeof(float), st));
         VG_CUDA(ws, cudaMemsetAsync(dquat, 0, (size_t)N * 4 * sizeof(float), st));
@@ -856,18 +865,26 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
             VG_CUDA(ws, launch_ranges(ws->inst_key, total, nullptr, ws->ranges.p, n_tiles, st, &ws->launches));
         }
         float *proj_b = proj + (size_t)a0 * det_px;
-        {
+        if (!proj_given) {
             ProfScope ps(ws, ST_TFWD, st);
             VG_CUDA(ws, launch_tomo_fwd(ws->ranges.p, n_tiles, tiles_x, (int)tpv, beam->det_w, beam->det_h,
                                         ws->inst_item, ws->rec.p, ws->prect.p, proj_b, st, &ws->launches));
         }
-        if (dL_dproj && items > 0) {
+        const float *dl_b = dL_dproj ? dL_dproj + (size_t)a0 * det_px : nullptr;
+        if (fused) {   // the batch's share of the loss and its gradient dL/dproj
+            VG_TRY(ensure(ws, ws->tomo_dl, (size_t)nb * det_px, "loss gradient"));
+            ProfScope ps(ws, ST_LOSS, st);
+            VG_CUDA(ws, launch_l2_loss_acc(proj_b, target + (size_t)a0 * det_px, (long long)nb * det_px, scale, loss,
+                                           ws->tomo_dl.p, st, &ws->launches));
+            dl_b = ws->tomo_dl.p;
+        }
+        if (backward && items > 0) {
             VG_TRY(ensure(ws, ws->grad, (size_t)items * 8, "gradient accumulators"));
             VG_CUDA(ws, cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)items * 8, st));
             ProfScope ps(ws, ST_TBWD, st);
             VG_CUDA(ws, launch_tomo_bwd(ws->ranges.p, n_tiles, tiles_x, (int)tpv, beam->det_w, beam->det_h,
-                                        ws->inst_item, ws->rec.p, ws->prect.p, proj_b, dL_dproj + (size_t)a0 * det_px,
-                                        ws->grad.p, st, &ws->launches));
+                                        ws->inst_item, ws->rec.p, ws->prect.p, proj_b, dl_b, ws->grad.p, st,
+                                        &ws->launches));
             VG_CUDA(ws, launch_tomo_chain(ws->g, ws->tomo_cs.p, A, (long long)a0 * N, items, beam->pitch_u,
                                           beam->pitch_v, beam->u0, beam->v0, ws->grad.p, dmu, dscale, dquat, dkappa,
                                           st, &ws->launches));
@@ -881,6 +898,23 @@ vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam
     ws->stage = 0;
     ws->tomo_read = true;
     return VG_OK;
+}
+
+vg_status vg_project_tomo(vg_workspace *ws, const vg_gaussians *g, const vg_beam *beam, const vg_opts *opts,
+                          float *proj, const float *dL_dproj, float *dmu, float *dscale, float *dquat, float *dkappa,
+                          void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    return tomo_impl(ws, g, beam, opts, proj, dL_dproj, nullptr, 0.0f, nullptr, dmu, dscale, dquat, dkappa,
+                     (cudaStream_t)stream);
+}
+
+vg_status vg_tomo_l2_step(vg_workspace *ws, const vg_gaussians *g, const vg_beam *beam, const vg_opts *opts,
+                          const float *target, float scale, float *proj, float *loss, float *dmu, float *dscale,
+                          float *dquat, float *dkappa, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (!target) return fail(ws, VG_ERR_INVALID_ARG, "target is NULL");
+    return tomo_impl(ws, g, beam, opts, proj, nullptr, target, scale, loss, dmu, dscale, dquat, dkappa,
+                     (cudaStream_t)stream);
 }
 
 vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n, float scale, float *loss,

@@ -505,6 +505,11 @@ cudaError_t launch_l2_loss(const float *x, const float *y, long long n, float sc
                            cudaStream_t st, long long *launches) {
     cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), st);
     if (e != cudaSuccess) return e;
+    return launch_l2_loss_acc(x, y, n, scale, loss, grad, st, launches);
+}
+
+cudaError_t launch_l2_loss_acc(const float *x, const float *y, long long n, float scale, float *loss, float *grad,
+                               cudaStream_t st, long long *launches) {
     long long b = (n + 255) / 256;
     if (b > 152 * 8) b = 152 * 8;
     if (b < 1) b = 1;

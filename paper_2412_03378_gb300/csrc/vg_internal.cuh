@@ -175,5 +175,8 @@ cudaError_t launch_tomo_chain(const GaussIn &g, const float *cs_d, int n_angles,
 
 cudaError_t launch_l2_loss(const float *x, const float *y, long long n, float scale, float *loss, float *grad,
                            cudaStream_t st, long long *launches);
+// The same without zeroing *loss first (accumulates across calls).
+cudaError_t launch_l2_loss_acc(const float *x, const float *y, long long n, float scale, float *loss, float *grad,
+                               cudaStream_t st, long long *launches);
 
 }  // namespace vg

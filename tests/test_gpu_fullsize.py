@@ -219,6 +219,20 @@ def test_config4_full_size_tomography(gpu_lib):
     worst = check_grads(gg, refg, scene, GRAD_TOL, keys=("mu", "scale", "quat", "kappa"))
     print("config 4 gradient block errors (worst, flattened worst):", worst,
           "element-wise:", {k: grad_rel_err(gg[k], refg[k]) for k in gg})
+    # the fused L2 step over all 13 angle batches equals the two-call form
+    tgt = torch.as_tensor(rng.uniform(0.5, 1.0, size=(A, H, W)).astype(np.float32)).to(dev)
+    scale = 1.0 / tgt.numel()
+    mk = lambda: [torch.zeros_like(t) for t in grads]
+    p1, l1, g1 = torch.empty_like(proj), torch.zeros(1, device=dev), mk()
+    ws.tomo_l2_step(g, beam, vg.Opts(tau_cut=1e-6), tgt, scale, p1, l1, *g1)
+    l2, dl, g2 = torch.zeros(1, device=dev), torch.empty_like(proj), mk()
+    ws.l2_loss(p1, tgt, scale, l2, dl)
+    ws.project_tomo(g, beam, vg.Opts(tau_cut=1e-6, flags=vg.FLAG_PROJ_GIVEN), p1.clone(), dl, *g2)
+    torch.cuda.synchronize()
+    assert torch.equal(p1, proj)
+    assert abs(float(l1) - float(l2)) <= 1e-5 * abs(float(l2))
+    for a, b in zip(g1, g2):
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * float(b.abs().max()))
 
 
 def test_config5_full_size_bf16(gpu_lib):

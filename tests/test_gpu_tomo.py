@@ -168,3 +168,52 @@ def test_tomo_density_reparam(gpu_lib):
     ref = oracle.tomo_grad(scene, beam, L, dL, density_theta=True)
     gg = {k: t.cpu().numpy().astype(np.float64) for k, t in zip(("mu", "scale", "quat", "kappa"), grads)}
     check_grads(gg, ref, scene, GRAD_TOL, keys=("mu", "scale", "quat", "kappa"))
+
+
+def test_tomo_fused_l2_step_and_given_projection(gpu_lib):
+    """vg_tomo_l2_step equals the two-call form (project; L2 loss; project with dL/dproj), and a
+    backward call with VG_FLAG_PROJ_GIVEN (projection reused, not recomputed) gives the same
+    gradients."""
+    import torch
+    from gpu_util import dev_scene
+    vg = gpu_lib
+    scene, beam = _cfg4_sampling_case(n_angles=7)
+    gt, _ = _cfg4_sampling_case(n_angles=7)
+    gt.mu = gt.mu[::-1].copy()
+    dev = torch.device("cuda:0")
+    g, gg = dev_scene(vg, scene), dev_scene(vg, gt)
+    A = len(beam.angles)
+    ws = vg.Workspace()
+    tgt = torch.empty(A, beam.det_h, beam.det_w, device=dev)
+    ws.project_tomo(gg, beam, vg.Opts(tau_cut=TAU_CUT), tgt)
+    scale = 1.0 / tgt.numel()
+    mk = lambda: [torch.zeros(scene.n, 3, device=dev), torch.zeros(scene.n, 3, device=dev),
+                  torch.zeros(scene.n, 4, device=dev), torch.zeros(scene.n, device=dev)]
+    # fused
+    p1, l1, g1 = torch.empty_like(tgt), torch.zeros(1, device=dev), mk()
+    ws.tomo_l2_step(g, beam, vg.Opts(tau_cut=TAU_CUT, flags=vg.FLAG_GRAD_ZERO), tgt, scale, p1, l1, *g1)
+    # two calls, the second recomputing the projection
+    p2, l2, dl, g2 = torch.empty_like(tgt), torch.zeros(1, device=dev), torch.empty_like(tgt), mk()
+    ws.project_tomo(g, beam, vg.Opts(tau_cut=TAU_CUT), p2)
+    ws.l2_loss(p2, tgt, scale, l2, dl)
+    ws.project_tomo(g, beam, vg.Opts(tau_cut=TAU_CUT), p2, dl, *g2)
+    # two calls, the second reusing the given projection
+    g3 = mk()
+    p3 = p2.clone()
+    ws.project_tomo(g, beam, vg.Opts(tau_cut=TAU_CUT, flags=vg.FLAG_PROJ_GIVEN), p3, dl, *g3)
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p2) and torch.equal(p3, p2)
+    assert abs(float(l1) - float(l2)) <= 1e-6 * abs(float(l2))
+    for a, b, c in zip(g1, g2, g3):   # atomics: equal up to the summation order
+        tol = 1e-6 * float(b.abs().max())
+        assert torch.allclose(b, c, rtol=1e-5, atol=tol) and torch.allclose(a, b, rtol=1e-5, atol=tol)
+    # against the oracle: loss and gradient of the L2 loss
+    L = oracle.tomo_lists(scene, beam, TAU_CUT)
+    _, ref_proj = oracle.tomo(scene, beam, L)
+    t_np = tgt.cpu().numpy().astype(np.float64)
+    ref_loss = scale * np.sum((ref_proj - t_np) ** 2)
+    assert abs(float(l1) - ref_loss) <= 1e-4 * ref_loss
+    ref = oracle.tomo_grad(scene, beam, L, 2.0 * scale * (ref_proj - t_np))
+    for k, t in zip(("mu", "scale", "quat", "kappa"), g1):
+        e = grad_rel_err(t.cpu().numpy().astype(np.float64), ref[k])
+        assert e < GRAD_TOL, (k, e)
