@@ -632,6 +632,12 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    try:   # the same FP32 single-view step replayed as one CUDA graph (fixed capacity, autotuned)
+        gs, _, _ = graph_step(vg, g, cams, args.steps, args.warmup, dev)
+        out["graph_single_view"] = {"steps_per_s": gs["steps_per_s"], "ms_per_step": gs["ms_per_step"],
+                                    "pixels_per_thread": gs["pixels_per_thread"], "launch": gs["launch"]}
+    except Exception as e:  # a side measurement, never the headline
+        out["graph_single_view"] = {"error": str(e)}
     if args.batch_views > 1:
         bg_ = batched_graph(vg, scene, cams[0], rgb.detach().clone(), args.batch_views, args.steps, args.warmup, dev)
         bg_["ratio_vs_plain_views_per_s"] = bg_["views_per_s"] / value * world
