@@ -9,9 +9,9 @@
 //   dL/dA = A sum_p ga u u^T,   dL/dC = C sum_p gq u u^T:
 // per Gaussian only the two symmetric 3x3 moment matrices (6 + 6 values), sum dL/dln(kappa) and
 // the three colour partials are summed -- 16 values.  They are reduce-scattered over the warp
-// with shuffles, summed over the CTA in shared memory, and added to the per-item accumulator
-// with one set of global atomics per (tile, Gaussian).  k_chain multiplies by A and C and maps
-// the result to dmu, dscale, dquat, dkappa, dsh.
+// with shuffles and added to the per-item accumulator by 16 writer lanes, one coalesced global
+// reduction per (warp, Gaussian) (shared-memory float atomics measured slower).  k_chain
+// multiplies by A and C and maps the result to dmu, dscale, dquat, dkappa, dsh.
 #include "blend.cuh"
 #include "geometry.cuh"
 
@@ -45,7 +45,6 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     constexpr int kThreads = L::kThreads;
     constexpr int kChunk = VG_BWD_CHUNK;   // records per shared-memory chunk
     __shared__ float4 srec[kChunk * kRecF4];
-    __shared__ float sacc[kChunk * kGradUsed];
     __shared__ uint32_t sitem[kChunk];
     __shared__ short4 srect[kChunk];
     __shared__ float4 scull[PIXTEST ? 1 : kChunk * kCullF4];   // Gram matrices for the opacity test
@@ -119,7 +118,6 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             srect[r] = prect[item];
             if (!PIXTEST) cull_row(q[0], q[1], q[2], q[3], q[4], &scull[r * kCullF4]);
         }
-        for (int k = threadIdx.x; k < kChunk * kGradUsed; k += kThreads) sacc[k] = 0.0f;
         __syncthreads();
         for (int w0 = (n - 1) & ~31; w0 >= 0; w0 -= 32) {
             const int jl = w0 + lane;
@@ -226,17 +224,12 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                 }
                 if (__any_sync(0xffffffffu, any)) {
                     const float mine = warp_reduce_scatter<kGradUsed>(gv, lane);
-                    if (swrite && mine != 0.0f) atomicAdd(&sacc[j * kGradUsed + sidx], mine);
+                    // the 16 writer lanes add 16 consecutive floats: one coalesced reduction in L2
+                    if (swrite && mine != 0.0f) atomicAdd(&grad_acc[(size_t)sitem[j] * kGradN + sidx], mine);
                 }
             }
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < n * kGradUsed; k += kThreads) {
-            const int jj = k / kGradUsed, c = k - jj * kGradUsed;
-            const float v = sacc[k];
-            if (v != 0.0f) atomicAdd(&grad_acc[(size_t)sitem[jj] * kGradN + c], v);
-        }
-        __syncthreads();
+        __syncthreads();   // the chunk's records are restaged next
         end = start;
     }
     if (COUNT) {

@@ -241,7 +241,8 @@ cudaError_t launch_tomo_fwd(const uint2 *ranges, long long n_tiles, int tiles_x,
 // ---------------------------------------------------------------------------- backward
 // proj = exp(-sum tau)  =>  dL/dtau = -proj dL/dproj for every Gaussian on the ray;
 // ln tau = lnA - |y|^2/2  =>  dL/dy = -dL/dln(tau) y.  Seven partials per (pixel, Gaussian)
-// are summed over the quad, reduce-scattered over the warp and summed over the CTA.
+// are summed over the quad, reduce-scattered over the warp and added to the per-item
+// accumulator with one coalesced global reduction per (warp, Gaussian).
 __global__ void __launch_bounds__(kQuadThreads, 12)
 k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, int det_w, int det_h,
            const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, const short4 *__restrict__ prect,
@@ -249,7 +250,6 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
     constexpr int NV = 7, NP = 8;   // partials used, and padded to a power of two
     __shared__ float4 srec[kTomoChunk * 2];
     __shared__ short4 srect[kTomoChunk];
-    __shared__ float sacc[kTomoChunk * NV];
     __shared__ uint32_t sitem[kTomoChunk];
     const int tile = blockIdx.x;
     const int view = tile / tiles_per_view, local = tile - view * tiles_per_view;
@@ -280,7 +280,6 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
             srec[2 * threadIdx.x + 1] = __ldg(rec + 2 * (size_t)item + 1);
             srect[threadIdx.x] = prect[item];
         }
-        for (int k = threadIdx.x; k < kTomoChunk * NV; k += kQuadThreads) sacc[k] = 0.0f;
         __syncthreads();
         for (int w0 = 0; w0 < (int)n; w0 += 32) {
             const int jl = w0 + lane;
@@ -321,14 +320,9 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
                     v[6] += G;
                 }
                 const float mine = warp_reduce_scatter<NP>(v, lane);
-                if (swrite && sidx < NV && mine != 0.0f) atomicAdd(&sacc[j * NV + sidx], mine);
+                if (swrite && sidx < NV && mine != 0.0f)
+                    atomicAdd(&grad_acc[(size_t)sitem[j] * kTomoGradN + sidx], mine);
             }
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < (int)n * NV; k += kQuadThreads) {
-            const int jj = k / NV, c = k - jj * NV;
-            const float val = sacc[k];
-            if (val != 0.0f) atomicAdd(&grad_acc[(size_t)sitem[jj] * kTomoGradN + c], val);
         }
         __syncthreads();
     }
