@@ -301,6 +301,18 @@ __device__ __forceinline__ BoxCull box_cull_splat(const WarpBox &b, float alpha_
     return c;
 }
 
+// Asynchronous global-to-shared copies (cp.async): 16 bytes (both addresses 16-byte aligned)
+// and 8 bytes (8-byte aligned); cp_async_wait() waits for all of the thread's copies.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Warp reduce-scatter of NP per-lane values (NP a power of two, 2..32).  Each exchange step
 // with partner lane^w keeps half of the lane's values and sends the other half while more than
 // one value is left (NP/2 + NP/4 + ... shuffles), then plain butterfly adds finish the sum.

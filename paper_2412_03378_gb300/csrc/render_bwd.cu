@@ -21,7 +21,7 @@ namespace vg {
 // [12] sum dL/dln(kappa), [13..15] dL/dcolour.
 constexpr int kGradUsed = 16;
 #ifndef VG_BWD_CHUNK
-#define VG_BWD_CHUNK 192
+#define VG_BWD_CHUNK 128
 #endif
 static_assert(kGradUsed <= kGradN, "accumulator too small");
 
@@ -44,10 +44,11 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     using L = PixLayout<P>;
     constexpr int kThreads = L::kThreads;
     constexpr int kChunk = VG_BWD_CHUNK;   // records per shared-memory chunk
-    __shared__ float4 srec[kChunk * kRecF4];
-    __shared__ uint32_t sitem[kChunk];
-    __shared__ short4 srect[kChunk];
-    __shared__ float4 scull[PIXTEST ? 1 : kChunk * kCullF4];   // Gram matrices for the opacity test
+    // two buffers: the next chunk is staged (cp.async) while the current one is processed
+    __shared__ float4 srec_[2][kChunk * kRecF4];
+    __shared__ uint32_t sitem_[2][kChunk];
+    __shared__ short4 srect_[2][kChunk];
+    __shared__ float4 scull_[2][PIXTEST ? 1 : kChunk * kCullF4];   // Gram matrices for the opacity test
     __shared__ uint32_t s_last;
 
     const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
@@ -102,23 +103,36 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     const float xf = (float)x0, yf = (float)y0;
     unsigned long long pairs = 0, blended = 0;   // evaluated / blended pairs (COUNT only)
 
-    for (uint32_t end = tile_last; end > rg.x;) {
-        const uint32_t start = (end - rg.x > (uint32_t)kChunk) ? end - kChunk : rg.x;
-        const int n = (int)(end - start);
-        for (int r = threadIdx.x; r < n; r += kThreads) {
-            const uint32_t item = sorted_item[start + r];
-            sitem[r] = item;
+    // chunks run back to front: [start, end) with start = max(rg.x, end - kChunk)
+    auto chunk_start = [&](uint32_t e) { return (e - rg.x > (uint32_t)kChunk) ? e - kChunk : rg.x; };
+    auto stage = [&](int b, uint32_t st0, int nn) {   // issue the copies of a chunk into buffer b
+        for (int r = threadIdx.x; r < nn; r += kThreads) {
+            const uint32_t item = sorted_item[st0 + r];
+            sitem_[b][r] = item;
             const float4 *src = rec + (size_t)item * kRecF4;
-            float4 q[kRecF4];
 #pragma unroll
-            for (int k = 0; k < kRecF4; ++k) {
-                q[k] = __ldg(src + k);
-                srec[r * kRecF4 + k] = q[k];
-            }
-            srect[r] = prect[item];
-            if (!PIXTEST) cull_row(q[0], q[1], q[2], q[3], q[4], &scull[r * kCullF4]);
+            for (int k = 0; k < kRecF4; ++k) cp_async16(&srec_[b][r * kRecF4 + k], src + k);
+            cp_async8(&srect_[b][r], prect + item);
         }
-        __syncthreads();
+    };
+    uint32_t end = tile_last, start = chunk_start(end);
+    int buf = 0;
+    if (end > rg.x) stage(0, start, (int)(end - start));
+    while (end > rg.x) {
+        const int n = (int)(end - start);
+        cp_async_wait();   // this thread's copies of the current chunk have landed
+        if (!PIXTEST)
+            for (int r = threadIdx.x; r < n; r += kThreads) {
+                const float4 *q = &srec_[buf][r * kRecF4];
+                cull_row(q[0], q[1], q[2], q[3], q[4], &scull_[buf][r * kCullF4]);
+            }
+        __syncthreads();   // the chunk is staged; every warp is done with the other buffer
+        const uint32_t nend = start, nstart = chunk_start(nend);
+        if (nend > rg.x) stage(buf ^ 1, nstart, (int)(nend - nstart));
+        const float4 *srec = srec_[buf];
+        const uint32_t *sitem = sitem_[buf];
+        const short4 *srect = srect_[buf];
+        const float4 *scull = scull_[buf];
         for (int w0 = (n - 1) & ~31; w0 >= 0; w0 -= 32) {
             const int jl = w0 + lane;
             bool need = jl < n && start + (uint32_t)jl < warp_last && !box_misses(wb, srect[jl]);
@@ -229,9 +243,11 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                 }
             }
         }
-        __syncthreads();   // the chunk's records are restaged next
-        end = start;
+        end = nend;
+        start = nstart;
+        buf ^= 1;
     }
+    cp_async_wait();   // no copy may still target this CTA's shared memory when it exits
     if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
