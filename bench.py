@@ -370,8 +370,9 @@ def graph_step(vg, g, cams, steps, warmup, dev, target_seed=2102):
     t = e0.elapsed_time(e1) / 1e3
     q = ws.query()   # raises if the fixed capacity overflowed during the run
     out = {"views": len(cams), "sizes": sorted({f"{c.width}x{c.height}" for c in cams}),
-           "launch": "fixed-capacity binning, autotuned pixels per thread, whole step replayed as one CUDA graph",
-           "pixels_per_thread": {"fwd": ppt[0], "bwd": ppt[1]},
+           "launch": "fixed-capacity binning, autotuned pixels per thread and chunk depth, whole step replayed as one "
+                     "CUDA graph",
+           "pixels_per_thread": {"fwd": ppt[0], "bwd": ppt[1]}, "chunk": {"fwd": ppt[2], "bwd": ppt[3]},
            "steps_per_s": steps / t, "views_per_s": steps * len(cams) / t, "ms_per_step": t * 1e3 / steps,
            "instances": q["n_instances"], "instance_capacity": q["instance_capacity"],
            "workspace_bytes": q["device_bytes"]}
@@ -635,7 +636,8 @@ def run_ours(args):
     try:   # the same FP32 single-view step replayed as one CUDA graph (fixed capacity, autotuned)
         gs, _, _ = graph_step(vg, g, cams, args.steps, args.warmup, dev)
         out["graph_single_view"] = {"steps_per_s": gs["steps_per_s"], "ms_per_step": gs["ms_per_step"],
-                                    "pixels_per_thread": gs["pixels_per_thread"], "launch": gs["launch"]}
+                                    "pixels_per_thread": gs["pixels_per_thread"], "chunk": gs["chunk"],
+                                    "launch": gs["launch"]}
     except Exception as e:  # a side measurement, never the headline
         out["graph_single_view"] = {"error": str(e)}
     if args.batch_views > 1:

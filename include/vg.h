@@ -113,6 +113,8 @@ typedef struct {
                              this beta, ln(1 + e^(beta x)) / beta (Supp. D uses 10) */
     float splat_dilation; /* VG_FLAG_SPLAT only: added to both variances of the 2D covariance
                              (pixels^2; 0 = Eq. 7 as printed, 0.3 = the 3DGS rasterizer) */
+    int32_t chunk;        /* blend kernels: records staged in shared memory per barrier, 64 or 128;
+                             0 = the autotuned value, else 128.  Results are identical. */
 } vg_opts;
 
 #define VG_FLAG_FIXED_CAPACITY 1u  /* vg_bin_sort never synchronises: the instance count stays
@@ -325,11 +327,14 @@ vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n
 
 /* Autotuner (synchronous; allocates scratch): after vg_bin_sort, times the forward and the
  * backward blend with 1, 2 and 4 pixels per thread (which also sets each warp's pixel box:
- * 8x4, 8x8 or 16x8 pixels) on the binned workload, `reps` timed runs each after one warm-up,
- * and keeps the fastest of each as this workspace's default for vg_opts.pixels_per_thread = 0.
- * The chosen values are written to *ppt_fwd / *ppt_bwd (either may be NULL).  Results of the
- * blend do not depend on the choice.  Call vg_render_fwd again before vg_render_bwd. */
-vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t *ppt_bwd, void *stream);
+ * 8x4, 8x8 or 16x8 pixels) and with 64 and 128 records per staged chunk (the chunk depth) on
+ * the binned workload, `reps` timed runs each after one warm-up, and keeps the fastest of each as
+ * this workspace's default for vg_opts.pixels_per_thread = 0 and vg_opts.chunk = 0.  The chosen
+ * values are written to *ppt_fwd / *ppt_bwd / *chunk_fwd / *chunk_bwd (each may be NULL).  The
+ * tile size stays 16x16: it is part of the binning.  Results of the blend do not depend on the
+ * choice.  Call vg_render_fwd again before vg_render_bwd. */
+vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t *ppt_bwd, int32_t *chunk_fwd,
+                      int32_t *chunk_bwd, void *stream);
 
 /* Statistics of the last calls (synchronises the stream).  *out is filled in every case; the
  * status is the first device-side error latched since the last report (VG_ERR_CAPACITY when

@@ -61,7 +61,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("alpha_min", ctypes.c_float), ("tau_cut", ctypes.c_float), ("tau_max", ctypes.c_float),
                 ("T_stop", ctypes.c_float), ("bg", ctypes.c_float * 3), ("z_near", ctypes.c_float),
                 ("flags", ctypes.c_uint32), ("pixels_per_thread", ctypes.c_int32), ("softplus_beta", ctypes.c_float),
-                ("splat_dilation", ctypes.c_float)]
+                ("splat_dilation", ctypes.c_float), ("chunk", ctypes.c_int32)]
 
 
 class _Grid(ctypes.Structure):
@@ -87,7 +87,7 @@ _SIGS = {
     "vg_workspace_create": [ctypes.c_void_p],
     "vg_workspace_destroy": [ctypes.c_void_p],
     "vg_workspace_reserve": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64],
-    "vg_autotune": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "vg_autotune": [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 5,
     "vg_preprocess": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                       ctypes.c_void_p],
     "vg_bin_sort": [ctypes.c_void_p, ctypes.c_void_p],
@@ -155,6 +155,7 @@ class Opts:
     pixels_per_thread: int = 0
     softplus_beta: float = 0.0
     splat_dilation: float = 0.0
+    chunk: int = 0
 
     @staticmethod
     def exact(**kw):
@@ -176,6 +177,7 @@ class Opts:
         o.z_near, o.flags, o.pixels_per_thread = self.z_near, self.flags, self.pixels_per_thread
         o.softplus_beta = self.softplus_beta
         o.splat_dilation = self.splat_dilation
+        o.chunk = self.chunk
         return o
 
 
@@ -266,10 +268,12 @@ class Workspace:
         self._chk(self._L.vg_workspace_reserve(self.h, n_items, n_instances, n_pixels, n_tiles))
 
     def autotune(self, reps=3, stream=None):
-        """Pick pixels per thread for the blend kernels on the binned workload; returns (fwd, bwd)."""
-        f, b = ctypes.c_int32(0), ctypes.c_int32(0)
-        self._chk(self._L.vg_autotune(self.h, int(reps), ctypes.byref(f), ctypes.byref(b), _stream(stream)))
-        return f.value, b.value
+        """Pick pixels per thread and the chunk depth of the blend kernels on the binned workload;
+        returns (ppt_fwd, ppt_bwd, chunk_fwd, chunk_bwd)."""
+        f, b, cf, cb = (ctypes.c_int32(0) for _ in range(4))
+        self._chk(self._L.vg_autotune(self.h, int(reps), ctypes.byref(f), ctypes.byref(b), ctypes.byref(cf),
+                                      ctypes.byref(cb), _stream(stream)))
+        return f.value, b.value, cf.value, cb.value
 
     def preprocess(self, g: Gaussians, cams, opts: Opts, stream=None):
         self._keep = (g, _cams_array(cams), opts.c())

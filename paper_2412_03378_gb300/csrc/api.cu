@@ -62,6 +62,7 @@ struct vg_workspace {
     uint32_t *tile_order = nullptr;       // longest-first tile order of the last bin_sort
     int ppt_fwd = 2, ppt_bwd = 1;         // pixels per thread of the blend kernels
     int tuned_fwd = 0, tuned_bwd = 0;     // vg_autotune's choice (0: none yet)
+    int tuned_chunk_fwd = 0, tuned_chunk_bwd = 0;
     uint32_t *h_total = nullptr;         // pinned: [0..1] instance total (u64), [2] look-back timeout flag
 
     // per-stage event timing (vg_profile_enable)
@@ -80,6 +81,7 @@ namespace {
 // 0.53 / 0.49 / 0.74 ms and backward 1.32 / 1.16 / 1.19 ms for 1 / 2 / 4 pixels per thread.
 constexpr int kDefaultPixelsFwd = 2;
 constexpr int kDefaultPixelsBwd = 1;
+constexpr int kDefaultChunk = 128;
 
 enum Stage { ST_PRE, ST_DEPTH, ST_SCAN, ST_DUP, ST_TILE, ST_RANGES, ST_FWD, ST_BWD, ST_CHAIN, ST_LOSS, ST_TFWD,
              ST_TBWD, ST_VOXEL, ST_MARCH, ST_COUNT };
@@ -363,6 +365,8 @@ static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const 
     if (opts->pixels_per_thread != 0 && opts->pixels_per_thread != 1 && opts->pixels_per_thread != 2 &&
         opts->pixels_per_thread != 4)
         return fail(ws, VG_ERR_INVALID_ARG, "pixels_per_thread must be 0, 1, 2 or 4");
+    if (opts->chunk != 0 && opts->chunk != 64 && opts->chunk != 128)
+        return fail(ws, VG_ERR_INVALID_ARG, "chunk must be 0, 64 or 128");
     const long long n_items = (long long)g->n * n_views;
     if (n_items >= 0xFFFFFFFFLL) return fail(ws, VG_ERR_INVALID_ARG, "views x Gaussians must be < 2^32");
 
@@ -438,6 +442,8 @@ static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const 
     ws->bp.tau_max = opts->tau_max;
     ws->ppt_fwd = opts->pixels_per_thread ? opts->pixels_per_thread : (ws->tuned_fwd ? ws->tuned_fwd : kDefaultPixelsFwd);
     ws->ppt_bwd = opts->pixels_per_thread ? opts->pixels_per_thread : (ws->tuned_bwd ? ws->tuned_bwd : kDefaultPixelsBwd);
+    ws->bp.chunk_fwd = opts->chunk ? opts->chunk : (ws->tuned_chunk_fwd ? ws->tuned_chunk_fwd : kDefaultChunk);
+    ws->bp.chunk_bwd = opts->chunk ? opts->chunk : (ws->tuned_chunk_bwd ? ws->tuned_chunk_bwd : kDefaultChunk);
     ws->bp.T_stop = opts->T_stop;
     for (int c = 0; c < 3; ++c) ws->bp.bg[c] = opts->bg[c];
     ws->bp.pixel_test = ws->bp.tau_skip < opts->tau_cut ? 1 : 0;
@@ -926,7 +932,8 @@ vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n
     return VG_OK;
 }
 
-vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t *ppt_bwd, void *stream) {
+vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t *ppt_bwd, int32_t *chunk_fwd,
+                      int32_t *chunk_bwd, void *stream) {
     if (!ws) return VG_ERR_INVALID_ARG;
     if (ws->stage < 2) return fail(ws, VG_ERR_STATE, "vg_autotune before vg_bin_sort");
     if (reps < 1) reps = 3;
@@ -947,16 +954,19 @@ vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t 
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    const int cand[3] = {1, 2, 4};
+    const int cand[3] = {1, 2, 4}, chunks[2] = {64, 128};
     float best_f = 1e30f, best_b = 1e30f;
-    int pf = kDefaultPixelsFwd, pb = kDefaultPixelsBwd;
+    int pf = kDefaultPixelsFwd, pb = kDefaultPixelsBwd, cf = kDefaultChunk, cb = kDefaultChunk;
     e = cudaMemsetAsync(dl, 0, px3 * sizeof(float), st);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
+        BlendParams bp = ws->bp;
+        bp.chunk_fwd = bp.chunk_bwd = chunks[i & 1];
+        const int ppt = cand[i >> 1];
         float tf = 0.0f, tb = 0.0f;
         for (int r = 0; r <= reps && e == cudaSuccess; ++r) {   // the first round warms up
             cudaEventRecord(a, st);
             e = launch_render_fwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles, ws->ranges.p,
-                                  ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, cand[i], rgb, nullptr, ws->T_fin.p,
+                                  ws->inst_item, ws->rec.p, ws->prect.p, bp, ppt, rgb, nullptr, ws->T_fin.p,
                                   ws->S_fin.p, ws->nlast.p, nullptr, st, &ws->launches);
             cudaEventRecord(b, st);
             cudaEventSynchronize(b);
@@ -968,15 +978,15 @@ vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t 
             cudaEventRecord(a, st);
             if (e == cudaSuccess)
                 e = launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
-                                      ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, cand[i], ws->T_fin.p,
+                                      ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, bp, ppt, ws->T_fin.p,
                                       ws->S_fin.p, ws->nlast.p, dl, nullptr, ws->grad.p, nullptr, st, &ws->launches);
             cudaEventRecord(b, st);
             cudaEventSynchronize(b);
             cudaEventElapsedTime(&ms, a, b);
             if (r) tb += ms;
         }
-        if (tf < best_f) best_f = tf, pf = cand[i];
-        if (tb < best_b) best_b = tb, pb = cand[i];
+        if (tf < best_f) best_f = tf, pf = ppt, cf = chunks[i & 1];
+        if (tb < best_b) best_b = tb, pb = ppt, cb = chunks[i & 1];
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -985,9 +995,13 @@ vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t 
     if (e != cudaSuccess) return fail(ws, VG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
     ws->tuned_fwd = ws->ppt_fwd = pf;
     ws->tuned_bwd = ws->ppt_bwd = pb;
+    ws->tuned_chunk_fwd = ws->bp.chunk_fwd = cf;
+    ws->tuned_chunk_bwd = ws->bp.chunk_bwd = cb;
     ws->stage = 2;   // the replay state no longer belongs to a vg_render_fwd of the caller
     if (ppt_fwd) *ppt_fwd = pf;
     if (ppt_bwd) *ppt_bwd = pb;
+    if (chunk_fwd) *chunk_fwd = cf;
+    if (chunk_bwd) *chunk_bwd = cb;
     return VG_OK;
 }
 

@@ -20,9 +20,6 @@ namespace vg {
 // Accumulator layout per item: [0..5] sum ga (xx, xy, x, yy, y, 1), [6..11] the same for gq,
 // [12] sum dL/dln(kappa), [13..15] dL/dcolour.
 constexpr int kGradUsed = 16;
-#ifndef VG_BWD_CHUNK
-#define VG_BWD_CHUNK 128
-#endif
 static_assert(kGradUsed <= kGradN, "accumulator too small");
 
 template <int P> struct BwdBounds;
@@ -34,7 +31,7 @@ template <> struct BwdBounds<4> { static constexpr int kMinBlocks = 8; };
 // ballots which records of the staged chunk it needs (some pixel of the warp reached the record,
 // the record's footprint touches the warp's pixels and, when pairs below tau_skip are skipped,
 // its opacity can reach tau_skip there), then visits only those, back to front.
-template <int P, bool COUNT, bool PIXTEST, bool SPLAT>
+template <int P, bool COUNT, bool PIXTEST, bool SPLAT, int CH>
 __global__ void __launch_bounds__(PixLayout<P>::kThreads, BwdBounds<P>::kMinBlocks)
 k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
@@ -43,7 +40,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
              float *__restrict__ grad_acc, unsigned long long *__restrict__ pair_count) {
     using L = PixLayout<P>;
     constexpr int kThreads = L::kThreads;
-    constexpr int kChunk = VG_BWD_CHUNK;   // records per shared-memory chunk
+    constexpr int kChunk = CH;   // records per shared-memory chunk
     // two buffers: the next chunk is staged (cp.async) while the current one is processed
     __shared__ float4 srec_[2][kChunk * kRecF4];
     __shared__ uint32_t sitem_[2][kChunk];
@@ -259,21 +256,35 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
 }
 
+template <int P, bool PIXTEST, bool SPLAT, int CH>
+static void launch_bwd_ptsc(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                            const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                            const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
+                            const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
+                            cudaStream_t st) {
+    const unsigned threads = PixLayout<P>::kThreads;
+    if (pair_count)
+        k_render_bwd<P, true, PIXTEST, SPLAT, CH><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
+            grad_acc, pair_count);
+    else
+        k_render_bwd<P, false, PIXTEST, SPLAT, CH><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
+            grad_acc, nullptr);
+}
+
 template <int P, bool PIXTEST, bool SPLAT>
 static void launch_bwd_pts(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                            const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                            const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
                            const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
                            cudaStream_t st) {
-    const unsigned threads = PixLayout<P>::kThreads;
-    if (pair_count)
-        k_render_bwd<P, true, PIXTEST, SPLAT><<<(unsigned)n_tiles, threads, 0, st>>>(
-            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
-            grad_acc, pair_count);
+    if (bp.chunk_bwd == 64)
+        launch_bwd_ptsc<P, PIXTEST, SPLAT, 64>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
+                                               bp, T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
     else
-        k_render_bwd<P, false, PIXTEST, SPLAT><<<(unsigned)n_tiles, threads, 0, st>>>(
-            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
-            grad_acc, nullptr);
+        launch_bwd_ptsc<P, PIXTEST, SPLAT, 128>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
+                                                bp, T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
 }
 
 template <int P, bool PIXTEST>

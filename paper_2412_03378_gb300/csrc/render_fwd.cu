@@ -12,23 +12,20 @@
 
 namespace vg {
 
-#ifndef VG_FWD_CHUNK
-#define VG_FWD_CHUNK 128
-#endif
 
 template <int P> struct FwdBounds;
 template <> struct FwdBounds<1> { static constexpr int kMinBlocks = 3; };
 template <> struct FwdBounds<2> { static constexpr int kMinBlocks = 7; };
 template <> struct FwdBounds<4> { static constexpr int kMinBlocks = 12; };
 
-template <int P, bool COUNT, bool PIXTEST, bool SPLAT>
+template <int P, bool COUNT, bool PIXTEST, bool SPLAT, int CH>
 __global__ void __launch_bounds__(PixLayout<P>::kThreads, FwdBounds<P>::kMinBlocks)
 k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
              const short4 *__restrict__ prect, BlendParams bp, float *__restrict__ rgb, float *__restrict__ T_user, float *__restrict__ T_ws,
              float *__restrict__ S_out, uint32_t *__restrict__ nlast_out, unsigned long long *__restrict__ pair_count) {
     using L = PixLayout<P>;
-    constexpr int kChunk = VG_FWD_CHUNK > L::kThreads ? VG_FWD_CHUNK : L::kThreads;   // records per barrier
+    constexpr int kChunk = CH;   // records per barrier
     __shared__ float4 srec[kChunk * kRecF4];
     __shared__ short4 srect[kChunk];
     __shared__ float4 scull[PIXTEST ? 1 : kChunk * kCullF4];   // Gram matrices for the opacity test
@@ -161,20 +158,33 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     }
 }
 
+template <int P, bool PIXTEST, bool SPLAT, int CH>
+static void launch_fwd_ptsc(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
+                            const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
+                            const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
+                            uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
+    const unsigned threads = PixLayout<P>::kThreads;
+    if (pair_count)
+        k_render_fwd<P, true, PIXTEST, SPLAT, CH><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
+            pair_count);
+    else
+        k_render_fwd<P, false, PIXTEST, SPLAT, CH><<<(unsigned)n_tiles, threads, 0, st>>>(
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
+            nullptr);
+}
+
 template <int P, bool PIXTEST, bool SPLAT>
 static void launch_fwd_pts(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                            const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                            const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
                            uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
-    const unsigned threads = PixLayout<P>::kThreads;
-    if (pair_count)
-        k_render_fwd<P, true, PIXTEST, SPLAT><<<(unsigned)n_tiles, threads, 0, st>>>(
-            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
-            pair_count);
+    if (bp.chunk_fwd == 64)
+        launch_fwd_ptsc<P, PIXTEST, SPLAT, 64>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
+                                               bp, rgb, T_user, T_ws, S_out, nlast_out, pair_count, st);
     else
-        k_render_fwd<P, false, PIXTEST, SPLAT><<<(unsigned)n_tiles, threads, 0, st>>>(
-            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
-            nullptr);
+        launch_fwd_ptsc<P, PIXTEST, SPLAT, 128>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
+                                                bp, rgb, T_user, T_ws, S_out, nlast_out, pair_count, st);
 }
 
 template <int P, bool PIXTEST>

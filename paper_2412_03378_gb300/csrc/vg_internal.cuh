@@ -49,6 +49,8 @@ struct BlendParams {
     int splat;            // 3DGS comparison mode: alpha = min(o G', alpha_max), skipped below
     float alpha_min;      // alpha_min, instead of the tau bounds above
     float alpha_max;
+    int chunk_fwd;        // records staged per barrier: 64 or 128
+    int chunk_bwd;
 };
 
 // ------------------------------------------------------------------ device helpers

@@ -126,14 +126,16 @@ def test_backward_matches_oracle_gradient(gpu_lib, case, variant):
     check_grads(gg, ref, scene, GRAD_TOL)
 
 
+@pytest.mark.parametrize("chunk", [64, 128])
 @pytest.mark.parametrize("ppt", [1, 2, 4])
 @pytest.mark.parametrize("mode", ["exact", "compat"])
-def test_pixels_per_thread_variants(gpu_lib, ppt, mode):
-    """Every blend-kernel variant (1, 2 or 4 pixels per thread) against the oracle."""
+def test_pixels_per_thread_variants(gpu_lib, ppt, mode, chunk):
+    """Every blend-kernel variant (1, 2 or 4 pixels per thread; 64 or 128 records per chunk)
+    against the oracle."""
     vg = gpu_lib
     scene, cams = _multi_view_scene()
     o = dict(oracle.EXACT if mode == "exact" else oracle.COMPAT, bg=(0.3, 0.2, 0.1))
-    ws, g, rgb, T = run_forward(vg, scene, cams, o, ppt=ppt)
+    ws, g, rgb, T = run_forward(vg, scene, cams, o, ppt=ppt, chunk=chunk)
     ref_rgb, ref_T, _ = oracle.render(scene, cams, o)
     err = np.max(np.abs(rgb - flat(ref_rgb)), axis=1)
     if mode == "exact":
@@ -277,8 +279,8 @@ def test_bins_many_sort_tiles(gpu_lib, mode):
 
 
 def test_autotune_keeps_results(gpu_lib):
-    """vg_autotune times 1/2/4 pixels per thread on the binned workload and keeps the fastest
-    as the workspace default; the blend afterwards still matches the oracle."""
+    """vg_autotune times 1/2/4 pixels per thread x 64/128-record chunks on the binned workload
+    and keeps the fastest as the workspace default; the blend afterwards still matches the oracle."""
     import torch
     vg = gpu_lib
     scene, cams = _multi_view_scene()
@@ -287,8 +289,8 @@ def test_autotune_keeps_results(gpu_lib):
     ws = vg.Workspace()
     ws.preprocess(g, cams, vg_opts(vg, o))
     ws.bin_sort()
-    pf, pb = ws.autotune(reps=2)
-    assert pf in (1, 2, 4) and pb in (1, 2, 4)
+    pf, pb, cf, cb = ws.autotune(reps=2)
+    assert pf in (1, 2, 4) and pb in (1, 2, 4) and cf in (64, 128) and cb in (64, 128)
     P = sum(c.width * c.height for c in cams)
     rgb = torch.empty(P, 3, device="cuda:0")
     with pytest.raises(RuntimeError):
