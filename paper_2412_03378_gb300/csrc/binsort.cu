@@ -205,9 +205,6 @@ constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsItems = VG_RS_ITEMS;                // keys per thread
 constexpr int kRsTile = kRsThreads * kRsItems;      // keys per CTA tile
 constexpr int kRsBins = 256;
-#ifndef VG_HIST_AGG
-#define VG_HIST_AGG 0   // 1: aggregate equal digits over a warp (match_any) before the shared-memory atomic
-#endif
 
 static int rs_passes(int bits) { return (bits + 7) / 8; }
 
@@ -226,22 +223,12 @@ k_digit_hist(const uint32_t *__restrict__ keys, long long n, const unsigned long
     const int passes = (bits + 7) / 8;
     for (int i = threadIdx.x; i < 4 * kRsBins; i += kRsThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    // the loop condition is the same for every lane of a warp (its first index), so that the
-    // per-digit counts can be aggregated over the warp before the shared-memory atomics
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i - lane < n; i += stride) {
-        const bool valid = i < n;
-        const uint32_t k = valid ? keys[i] : 0u;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t k = keys[i];
         for (int p = 0; p < passes; ++p) {
             const int nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
-#if VG_HIST_AGG
-            const uint32_t dg = valid ? ((k >> (8 * p)) & ((1u << nb) - 1u)) : 0xFFFFFFFFu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-            if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&h[p][dg], (uint32_t)__popc(peers));
-#else
-            if (valid) atomicAdd(&h[p][(k >> (8 * p)) & ((1u << nb) - 1u)], 1u);
-#endif
+            atomicAdd(&h[p][(k >> (8 * p)) & ((1u << nb) - 1u)], 1u);
         }
     }
     __syncthreads();

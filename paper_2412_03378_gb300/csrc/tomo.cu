@@ -302,23 +302,33 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
                 const bool full = box_inside(wb, pr);
                 const bool xa = full || (x0 >= pr.x && x0 <= pr.z), xb = full || (x0 + 1 >= pr.x && x0 + 1 <= pr.z);
                 const bool ya = full || (y0 >= pr.y && y0 <= pr.w), yb = full || (y0 + 1 >= pr.y && y0 + 1 <= pr.w);
+                // the quad's pixels sit at (dx0 + (k & 1), dy0 + (k >> 1)): the dx- and dy-weighted
+                // sums follow from the plain sums and those of the odd columns and rows
+                float ox0 = 0.0f, ox1 = 0.0f, oy0 = 0.0f, oy1 = 0.0f;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float dx = (k & 1) ? dx0 + 1.0f : dx0, dy = (k & 2) ? dy0 + 1.0f : dy0;
                     const float y0v = q0[k], y1v = q1[k];
                     const float m2 = fmaf(y0v, y0v, y1v * y1v);
                     const float tau = ex2_approx(fmaf(m2, -kHalfLog2e, r1.z));
                     const bool in = ((k & 1) ? xb : xa) && ((k & 2) ? yb : ya);
                     const float G = in ? gtau[k] * tau : 0.0f;      // dL / d ln(tau)
                     const float gy0 = -G * y0v, gy1 = -G * y1v;
-                    v[0] = fmaf(gy0, dx, v[0]);
-                    v[1] = fmaf(gy1, dx, v[1]);
-                    v[2] = fmaf(gy0, dy, v[2]);
-                    v[3] = fmaf(gy1, dy, v[3]);
+                    if (k & 1) {
+                        ox0 += gy0;
+                        ox1 += gy1;
+                    }
+                    if (k & 2) {
+                        oy0 += gy0;
+                        oy1 += gy1;
+                    }
                     v[4] += gy0;
                     v[5] += gy1;
                     v[6] += G;
                 }
+                v[0] = fmaf(v[4], dx0, ox0);
+                v[1] = fmaf(v[5], dx0, ox1);
+                v[2] = fmaf(v[4], dy0, oy0);
+                v[3] = fmaf(v[5], dy0, oy1);
                 const float mine = warp_reduce_scatter<NP>(v, lane);
                 if (swrite && sidx < NV && mine != 0.0f)
                     atomicAdd(&grad_acc[(size_t)sitem[j] * kTomoGradN + sidx], mine);
