@@ -129,6 +129,7 @@ size_t scan_tmp_words(long long n) {
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_onepass(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm, long long n, uint32_t *__restrict__ out,
                uint32_t *tmp, unsigned long long *total64, unsigned long long cap, uint32_t *err) {
+    pdl_entry();
     __shared__ unsigned long long ws[kScanThreads / 32];
     __shared__ unsigned long long s_prefix;
     __shared__ uint32_t s_tile;
@@ -186,7 +187,7 @@ cudaError_t launch_scan_gather(const uint32_t *count, const uint32_t *perm, uint
         if (e == cudaSuccess) e = cudaMemsetAsync(total64, 0, sizeof(unsigned long long), st);
         return e;
     }
-    k_scan_onepass<<<(unsigned)tiles, kScanThreads, 0, st>>>(count, perm, n, out, tmp, total64, cap, err);
+    pdl_launch(k_scan_onepass, (unsigned)tiles, kScanThreads, 0, st, count, perm, n, out, tmp, total64, cap, err);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -218,6 +219,7 @@ size_t radix_scratch_words(long long n, int bits) {
 __global__ void __launch_bounds__(kRsThreads)
 k_digit_hist(const uint32_t *__restrict__ keys, long long n, const unsigned long long *__restrict__ n_dev, int bits,
              uint32_t *__restrict__ ghist) {
+    pdl_entry();
     if (n_dev && (long long)*n_dev < n) n = (long long)*n_dev;
     __shared__ uint32_t h[4][kRsBins];
     const int passes = (bits + 7) / 8;
@@ -242,6 +244,7 @@ __global__ void __launch_bounds__(kRsThreads)
 k_onesweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, uint32_t *__restrict__ ko,
            uint32_t *__restrict__ vo, long long n, const unsigned long long *__restrict__ n_dev, int shift,
            uint32_t mask, const uint32_t *__restrict__ ghist, uint32_t *status, uint32_t *tile_ctr, uint32_t *err) {
+    pdl_entry();
     __shared__ uint32_t wcnt[kRsWarps][kRsBins];    // per-warp digit counts, then exclusive over warps
     __shared__ uint32_t dig_local[kRsBins];          // first slot of each digit in the ranked tile
     __shared__ uint32_t dig_global[kRsBins];         // first output position of each digit's run
@@ -346,13 +349,13 @@ cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, 
     uint32_t *ghist = scratch, *ctr = scratch + passes * kRsBins, *status = ctr + passes + 8;
     long long hb = (n + kRsThreads - 1) / kRsThreads;
     if (hb > 152 * 8) hb = 152 * 8;
-    k_digit_hist<<<(unsigned)hb, kRsThreads, 0, st>>>(keys_in, n, n_dev, bits, ghist);
+    pdl_launch(k_digit_hist, (unsigned)hb, kRsThreads, 0, st, keys_in, n, n_dev, bits, ghist);
     *launches += 1;
     const uint32_t *ki = keys_in, *vi = vals_in;
     for (int p = 0; p < passes; ++p) {
         uint32_t *kout = (p & 1) ? kb : ka, *vout = (p & 1) ? vb : va;
         const int nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
-        k_onesweep<<<(unsigned)tiles, kRsThreads, 0, st>>>(ki, vi, kout, vout, n, n_dev, 8 * p, (1u << nb) - 1u,
+        pdl_launch(k_onesweep, (unsigned)tiles, kRsThreads, 0, st, ki, vi, kout, vout, n, n_dev, 8 * p, (1u << nb) - 1u,
                                                            ghist + p * kRsBins, status + (size_t)p * tiles * kRsBins,
                                                            ctr + p, err);
         *launches += 1;
@@ -369,6 +372,7 @@ __global__ void __launch_bounds__(256)
 k_duplicate(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ offsets, const short4 *__restrict__ rect,
             const ViewInfo *__restrict__ views, long long n_items, int n_per_view, uint32_t *__restrict__ inst_key,
             uint32_t *__restrict__ inst_val, long long capacity) {
+    pdl_entry();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_items;
          i += (long long)gridDim.x * blockDim.x) {
         const uint32_t off = offsets[i], end = offsets[i + 1];
@@ -393,7 +397,7 @@ cudaError_t launch_duplicate(const uint32_t *perm, const uint32_t *offsets, cons
     long long b = (n_items + 255) / 256;
     if (b > 152 * 32) b = 152 * 32;
     if (b < 1) b = 1;
-    k_duplicate<<<(unsigned)b, 256, 0, st>>>(perm, offsets, rect, views, n_items, n_per_view, inst_key, inst_val,
+    pdl_launch(k_duplicate, (unsigned)b, 256, 0, st, perm, offsets, rect, views, n_items, n_per_view, inst_key, inst_val,
                                             capacity);
     *launches += 1;
     return cudaGetLastError();
@@ -402,6 +406,7 @@ cudaError_t launch_duplicate(const uint32_t *perm, const uint32_t *offsets, cons
 // ---------------------------------------------------------------------------- ranges
 __global__ void k_ranges(const uint32_t *__restrict__ key, long long n, const unsigned long long *__restrict__ n_dev,
                          uint2 *__restrict__ ranges) {
+    pdl_entry();
     if (n_dev && (long long)*n_dev < n) n = (long long)*n_dev;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const uint32_t t = key[i];
@@ -417,7 +422,7 @@ cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, const un
     if (n_inst > 0) {
         long long b = (n_inst + 255) / 256;
         if (b > 152 * 64) b = 152 * 64;
-        k_ranges<<<(unsigned)b, 256, 0, st>>>(sorted_key, n_inst, n_dev, ranges);
+        pdl_launch(k_ranges, (unsigned)b, 256, 0, st, sorted_key, n_inst, n_dev, ranges);
         *launches += 1;
     }
     return cudaGetLastError();
@@ -436,6 +441,7 @@ __device__ __forceinline__ int order_bucket(uint32_t c) {
 }
 
 __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, long long n, uint32_t *__restrict__ order) {
+    pdl_entry();
     __shared__ uint32_t cnt[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -462,7 +468,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
 cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *order, cudaStream_t st,
                               long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
-    k_tile_order<<<1, 1024, 0, st>>>(ranges, n_tiles, order);
+    pdl_launch(k_tile_order, 1, 1024, 0, st, ranges, n_tiles, order);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -470,6 +476,7 @@ cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *
 // ---------------------------------------------------------------------------- L2 loss
 __global__ void k_l2_loss(const float *__restrict__ x, const float *__restrict__ y, long long n, float scale,
                           float *__restrict__ loss, float *__restrict__ grad) {
+    pdl_entry();
     float acc = 0.0f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float d = x[i] - y[i];
@@ -500,7 +507,7 @@ cudaError_t launch_l2_loss_acc(const float *x, const float *y, long long n, floa
     long long b = (n + 255) / 256;
     if (b > 152 * 8) b = 152 * 8;
     if (b < 1) b = 1;
-    k_l2_loss<<<(unsigned)b, 256, 0, st>>>(x, y, n, scale, loss, grad);
+    pdl_launch(k_l2_loss, (unsigned)b, 256, 0, st, x, y, n, scale, loss, grad);
     *launches += 1;
     return cudaGetLastError();
 }

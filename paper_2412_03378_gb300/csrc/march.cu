@@ -27,6 +27,7 @@ template <typename RT>
 __global__ void __launch_bounds__(256)
 k_march_prep(GaussIn g, const ViewInfo *__restrict__ views, long long n_items, const uint32_t *__restrict__ count,
              float4 *__restrict__ E) {
+    pdl_entry();
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < n_items;
          it += (long long)gridDim.x * blockDim.x) {
         float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -54,6 +55,7 @@ k_ray_march(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vie
             const short4 *__restrict__ prect, float t_near, float delta, int n_samples, float T_stop, float bg0,
             float bg1, float bg2, const float *__restrict__ raster, float *__restrict__ rgb, float *__restrict__ T_out,
             float *__restrict__ err) {
+    pdl_entry();
     __shared__ float4 srec[kMarchChunk * (kRecF4 + 1)];
     __shared__ short4 srect[kMarchChunk];
     const int tile = blockIdx.x;
@@ -159,16 +161,16 @@ cudaError_t launch_ray_march(const GaussIn &g, const ViewInfo *views_d, const in
         long long b = (n_items + 255) / 256;
         if (b > 152 * 32) b = 152 * 32;
         if (g.rec_dtype == VG_BF16)
-            k_march_prep<__nv_bfloat16><<<(unsigned)b, 256, 0, st>>>(g, views_d, n_items, count, E);
+            pdl_launch(k_march_prep<__nv_bfloat16>, (unsigned)b, 256, 0, st, g, views_d, n_items, count, E);
         else if (g.rec_dtype == VG_F16)
-            k_march_prep<__half><<<(unsigned)b, 256, 0, st>>>(g, views_d, n_items, count, E);
+            pdl_launch(k_march_prep<__half>, (unsigned)b, 256, 0, st, g, views_d, n_items, count, E);
         else
-            k_march_prep<float><<<(unsigned)b, 256, 0, st>>>(g, views_d, n_items, count, E);
+            pdl_launch(k_march_prep<float>, (unsigned)b, 256, 0, st, g, views_d, n_items, count, E);
         *launches += 1;
     }
     if (n_tiles > 0) {
         const float delta = (t_far - t_near) / (float)n_samples;
-        k_ray_march<<<(unsigned)n_tiles, kTilePix, 0, st>>>(views_d, tile_view, ranges, sorted_item, rec, E, prect, t_near,
+        pdl_launch(k_ray_march, (unsigned)n_tiles, kTilePix, 0, st, views_d, tile_view, ranges, sorted_item, rec, E, prect, t_near,
                                                           delta, n_samples, T_stop, bg[0], bg[1], bg[2], raster, rgb,
                                                           T_out, err);
         *launches += 1;

@@ -13,6 +13,7 @@ __global__ void __launch_bounds__(32 * kPreWarps, 5)
 k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z_near, float tau_cut,
              float4 *__restrict__ rec, uint32_t *__restrict__ depth, uint32_t *__restrict__ count,
              short4 *__restrict__ rect, short4 *__restrict__ prect, unsigned long long *__restrict__ n_visible) {
+    pdl_entry();
     constexpr int kRecStride = 4 * kRecF4 + 1;   // 24 record floats, odd stride
     __shared__ float sbuf[kPreWarps][32 * kRowStride];   // SH rows
     __shared__ float srow[kPreWarps][32 * kRecStride];   // record rows
@@ -106,7 +107,7 @@ static cudaError_t launch_pre_t(const GaussIn &g, const ViewInfo *views_d, int n
     long long blocks = (chunks + kPreWarps - 1) / kPreWarps;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
-    k_preprocess<RT, ST><<<(unsigned)blocks, 32 * kPreWarps, 0, st>>>(g, views_d, n_views, z_near, tau_cut, rec,
+    pdl_launch(k_preprocess<RT, ST>, (unsigned)blocks, 32 * kPreWarps, 0, st, g, views_d, n_views, z_near, tau_cut, rec,
                                                                       depth, count, rect, prect, n_visible);
     return cudaGetLastError();
 }

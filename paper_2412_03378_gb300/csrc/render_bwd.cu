@@ -38,6 +38,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
              const short4 *__restrict__ prect, BlendParams bp, const float *__restrict__ T_fin, const float *__restrict__ S_fin,
              const uint32_t *__restrict__ nlast, const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT,
              float *__restrict__ grad_acc, unsigned long long *__restrict__ pair_count) {
+    pdl_entry();
     using L = PixLayout<P>;
     constexpr int kThreads = L::kThreads;
     constexpr int kChunk = CH;   // records per shared-memory chunk
@@ -264,11 +265,11 @@ static void launch_bwd_ptsc(const ViewInfo *views_d, const int *tile_view, const
                             cudaStream_t st) {
     const unsigned threads = PixLayout<P>::kThreads;
     if (pair_count)
-        k_render_bwd<P, true, PIXTEST, SPLAT, CH><<<(unsigned)n_tiles, threads, 0, st>>>(
+        pdl_launch(k_render_bwd<P, true, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
             views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
             grad_acc, pair_count);
     else
-        k_render_bwd<P, false, PIXTEST, SPLAT, CH><<<(unsigned)n_tiles, threads, 0, st>>>(
+        pdl_launch(k_render_bwd<P, false, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
             views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
             grad_acc, nullptr);
 }
@@ -422,6 +423,7 @@ __global__ void __launch_bounds__(32 * kChainWarps, 8)
 k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float *__restrict__ grad_acc, int zero,
         float *__restrict__ dmu, float *__restrict__ dscale, float *__restrict__ dquat, float *__restrict__ dkappa,
         float *__restrict__ dsh) {
+    pdl_entry();
     __shared__ float ssh[kChainWarps][32 * kRowStride];    // SH coefficients, as float
     __shared__ float sdsh[kChainWarps][32 * kRowStride];   // SH gradient being accumulated
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -632,10 +634,10 @@ static cudaError_t launch_chain_t(const GaussIn &g, const ViewInfo *views_d, int
     if (b > 152 * 64) b = 152 * 64;
     if (b < 1) b = 1;
     if (g.splat)
-        k_chain<RT, ST, true><<<(unsigned)b, 32 * kChainWarps, 0, st>>>(g, views_d, n_views, grad_acc, zero, dmu, dscale,
+        pdl_launch(k_chain<RT, ST, true>, (unsigned)b, 32 * kChainWarps, 0, st, g, views_d, n_views, grad_acc, zero, dmu, dscale,
                                                                         dquat, dkappa, dsh);
     else
-        k_chain<RT, ST, false><<<(unsigned)b, 32 * kChainWarps, 0, st>>>(g, views_d, n_views, grad_acc, zero, dmu, dscale,
+        pdl_launch(k_chain<RT, ST, false>, (unsigned)b, 32 * kChainWarps, 0, st, g, views_d, n_views, grad_acc, zero, dmu, dscale,
                                                                          dquat, dkappa, dsh);
     return cudaGetLastError();
 }

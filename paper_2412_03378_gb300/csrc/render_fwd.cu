@@ -24,6 +24,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
              const short4 *__restrict__ prect, BlendParams bp, float *__restrict__ rgb, float *__restrict__ T_user, float *__restrict__ T_ws,
              float *__restrict__ S_out, uint32_t *__restrict__ nlast_out, unsigned long long *__restrict__ pair_count) {
+    pdl_entry();
     using L = PixLayout<P>;
     constexpr int kChunk = CH;   // records per barrier
     __shared__ float4 srec[kChunk * kRecF4];
@@ -165,11 +166,11 @@ static void launch_fwd_ptsc(const ViewInfo *views_d, const int *tile_view, const
                             uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
     const unsigned threads = PixLayout<P>::kThreads;
     if (pair_count)
-        k_render_fwd<P, true, PIXTEST, SPLAT, CH><<<(unsigned)n_tiles, threads, 0, st>>>(
+        pdl_launch(k_render_fwd<P, true, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
             views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
             pair_count);
     else
-        k_render_fwd<P, false, PIXTEST, SPLAT, CH><<<(unsigned)n_tiles, threads, 0, st>>>(
+        pdl_launch(k_render_fwd<P, false, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
             views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
             nullptr);
 }

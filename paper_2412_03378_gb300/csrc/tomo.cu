@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(256)
 k_tomo_preprocess(GaussIn g, const float *__restrict__ cs, int n_angles, int det_w, int det_h, float pu, float pv,
                   float u0, float v0, float tau_cut, float4 *__restrict__ rec, uint32_t *__restrict__ count,
                   short4 *__restrict__ rect, short4 *__restrict__ prect) {
+    pdl_entry();
     const long long n_items = (long long)g.n * n_angles;
     const int tiles_x = (det_w + kTile - 1) / kTile;
     (void)tiles_x;
@@ -135,13 +136,13 @@ cudaError_t launch_tomo_preprocess(const GaussIn &g, const float *cs_d, int n_an
     if (b < 1) b = 1;
     *launches += 1;
     if (g.rec_dtype == VG_BF16)
-        k_tomo_preprocess<__nv_bfloat16><<<(unsigned)b, 256, 0, st>>>(g, cs_d, n_angles, det_w, det_h, pitch_u, pitch_v,
+        pdl_launch(k_tomo_preprocess<__nv_bfloat16>, (unsigned)b, 256, 0, st, g, cs_d, n_angles, det_w, det_h, pitch_u, pitch_v,
                                                                       u0, v0, tau_cut, rec, count, rect, prect);
     else if (g.rec_dtype == VG_F16)
-        k_tomo_preprocess<__half><<<(unsigned)b, 256, 0, st>>>(g, cs_d, n_angles, det_w, det_h, pitch_u, pitch_v, u0,
+        pdl_launch(k_tomo_preprocess<__half>, (unsigned)b, 256, 0, st, g, cs_d, n_angles, det_w, det_h, pitch_u, pitch_v, u0,
                                                                v0, tau_cut, rec, count, rect, prect);
     else
-        k_tomo_preprocess<float><<<(unsigned)b, 256, 0, st>>>(g, cs_d, n_angles, det_w, det_h, pitch_u, pitch_v, u0,
+        pdl_launch(k_tomo_preprocess<float>, (unsigned)b, 256, 0, st, g, cs_d, n_angles, det_w, det_h, pitch_u, pitch_v, u0,
                                                               v0, tau_cut, rec, count, rect, prect);
     return cudaGetLastError();
 }
@@ -156,6 +157,7 @@ __global__ void __launch_bounds__(kQuadThreads, 12)
 k_tomo_fwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, int det_w, int det_h,
            const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, const short4 *__restrict__ prect,
            float *__restrict__ proj) {
+    pdl_entry();
     __shared__ float4 srec[kTomoChunk * 2];
     __shared__ short4 srect[kTomoChunk];
     const int tile = blockIdx.x;
@@ -232,7 +234,7 @@ cudaError_t launch_tomo_fwd(const uint2 *ranges, long long n_tiles, int tiles_x,
                             int det_h, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                             float *proj, cudaStream_t st, long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
-    k_tomo_fwd<<<(unsigned)n_tiles, kQuadThreads, 0, st>>>(ranges, tiles_x, tiles_per_view, det_w, det_h,
+    pdl_launch(k_tomo_fwd, (unsigned)n_tiles, kQuadThreads, 0, st, ranges, tiles_x, tiles_per_view, det_w, det_h,
                                                            sorted_item, rec, prect, proj);
     *launches += 1;
     return cudaGetLastError();
@@ -247,6 +249,7 @@ __global__ void __launch_bounds__(kQuadThreads, 12)
 k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, int det_w, int det_h,
            const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, const short4 *__restrict__ prect,
            const float *__restrict__ proj, const float *__restrict__ dL_dproj, float *__restrict__ grad_acc) {
+    pdl_entry();
     constexpr int NV = 7, NP = 8;   // partials used, and padded to a power of two
     __shared__ float4 srec[kTomoChunk * 2];
     __shared__ short4 srect[kTomoChunk];
@@ -343,7 +346,7 @@ cudaError_t launch_tomo_bwd(const uint2 *ranges, long long n_tiles, int tiles_x,
                             const float *proj, const float *dL_dproj, float *grad_acc, cudaStream_t st,
                             long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
-    k_tomo_bwd<<<(unsigned)n_tiles, kQuadThreads, 0, st>>>(ranges, tiles_x, tiles_per_view, det_w, det_h,
+    pdl_launch(k_tomo_bwd, (unsigned)n_tiles, kQuadThreads, 0, st, ranges, tiles_x, tiles_per_view, det_w, det_h,
                                                            sorted_item, rec, prect, proj, dL_dproj, grad_acc);
     *launches += 1;
     return cudaGetLastError();
@@ -355,6 +358,7 @@ __global__ void __launch_bounds__(128)
 k_tomo_chain(GaussIn g, const float *__restrict__ cs, int n_angles, long long item0, long long n_items, float pu,
              float pv, float u0, float v0, const float *__restrict__ grad_acc, float *__restrict__ dmu,
              float *__restrict__ dscale, float *__restrict__ dquat, float *__restrict__ dkappa) {
+    pdl_entry();
     (void)n_angles;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_items;
          k += (long long)gridDim.x * blockDim.x) {
@@ -461,13 +465,13 @@ cudaError_t launch_tomo_chain(const GaussIn &g, const float *cs_d, int n_angles,
     if (b < 1) b = 1;
     *launches += 1;
     if (g.rec_dtype == VG_BF16)
-        k_tomo_chain<__nv_bfloat16><<<(unsigned)b, 128, 0, st>>>(g, cs_d, n_angles, item0, n_items, pitch_u, pitch_v, u0,
+        pdl_launch(k_tomo_chain<__nv_bfloat16>, (unsigned)b, 128, 0, st, g, cs_d, n_angles, item0, n_items, pitch_u, pitch_v, u0,
                                                                  v0, grad_acc, dmu, dscale, dquat, dkappa);
     else if (g.rec_dtype == VG_F16)
-        k_tomo_chain<__half><<<(unsigned)b, 128, 0, st>>>(g, cs_d, n_angles, item0, n_items, pitch_u, pitch_v, u0, v0,
+        pdl_launch(k_tomo_chain<__half>, (unsigned)b, 128, 0, st, g, cs_d, n_angles, item0, n_items, pitch_u, pitch_v, u0, v0,
                                                           grad_acc, dmu, dscale, dquat, dkappa);
     else
-        k_tomo_chain<float><<<(unsigned)b, 128, 0, st>>>(g, cs_d, n_angles, item0, n_items, pitch_u, pitch_v, u0, v0,
+        pdl_launch(k_tomo_chain<float>, (unsigned)b, 128, 0, st, g, cs_d, n_angles, item0, n_items, pitch_u, pitch_v, u0, v0,
                                                          grad_acc, dmu, dscale, dquat, dkappa);
     return cudaGetLastError();
 }

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "vg.h"
 
 namespace vg {
@@ -68,6 +70,38 @@ __device__ __forceinline__ float rcp_approx(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Programmatic dependent launch: every kernel of the library is launched with programmatic
+// stream serialisation, so the next kernel's CTAs are scheduled while the previous kernel's
+// last wave drains.  pdl_entry() must run first in every kernel: it blocks until the previous
+// grid has completed and its writes are visible (so the usual stream order holds for all
+// memory accesses after it), then lets the next grid start launching.  VG_PDL=0 at compile
+// time restores plain stream-ordered launches.
+#ifndef VG_PDL
+#define VG_PDL 1
+#endif
+__device__ __forceinline__ void pdl_entry() {
+#if VG_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = VG_PDL ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 template <typename T> __device__ __forceinline__ float ld_f(const T *p, long long i);

@@ -20,6 +20,7 @@ template <typename RT>
 __global__ void __launch_bounds__(256)
 k_voxel_pre(GaussIn g, VoxelGrid grid, float sigma_cut, float4 *__restrict__ rec, short4 *__restrict__ box,
             uint32_t *__restrict__ count) {
+    pdl_entry();
     for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < g.n;
          gi += (long long)gridDim.x * blockDim.x) {
         float mu[3], s[3], q[4], kin, Sig[9], Rq[9], qn[4], smax;
@@ -77,6 +78,7 @@ k_voxel_pre(GaussIn g, VoxelGrid grid, float sigma_cut, float4 *__restrict__ rec
 __global__ void __launch_bounds__(256)
 k_voxel_dup(const uint32_t *__restrict__ offsets, const short4 *__restrict__ box, VoxelGrid grid, long long n,
             uint32_t *__restrict__ inst_key, uint32_t *__restrict__ inst_val, long long capacity) {
+    pdl_entry();
     for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < n;
          gi += (long long)gridDim.x * blockDim.x) {
         const uint32_t off = offsets[gi], end = offsets[gi + 1];
@@ -98,6 +100,7 @@ k_voxel_dup(const uint32_t *__restrict__ offsets, const short4 *__restrict__ box
 __global__ void __launch_bounds__(kVoxThreads)
 k_voxel_eval(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted, const float4 *__restrict__ rec,
              const short4 *__restrict__ box, VoxelGrid grid, float *__restrict__ out) {
+    pdl_entry();
     __shared__ float4 srec[kVoxChunk * kVoxRecF4];
     __shared__ short4 sbox[kVoxChunk * 2];
     const int brick = blockIdx.x;
@@ -166,11 +169,11 @@ cudaError_t launch_voxel_pre(const GaussIn &g, const VoxelGrid &grid, float sigm
     long long b = (g.n + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
     if (g.rec_dtype == VG_BF16)
-        k_voxel_pre<__nv_bfloat16><<<(unsigned)b, 256, 0, st>>>(g, grid, sigma_cut, rec, box, count);
+        pdl_launch(k_voxel_pre<__nv_bfloat16>, (unsigned)b, 256, 0, st, g, grid, sigma_cut, rec, box, count);
     else if (g.rec_dtype == VG_F16)
-        k_voxel_pre<__half><<<(unsigned)b, 256, 0, st>>>(g, grid, sigma_cut, rec, box, count);
+        pdl_launch(k_voxel_pre<__half>, (unsigned)b, 256, 0, st, g, grid, sigma_cut, rec, box, count);
     else
-        k_voxel_pre<float><<<(unsigned)b, 256, 0, st>>>(g, grid, sigma_cut, rec, box, count);
+        pdl_launch(k_voxel_pre<float>, (unsigned)b, 256, 0, st, g, grid, sigma_cut, rec, box, count);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -181,7 +184,7 @@ cudaError_t launch_voxel_dup(const uint32_t *offsets, const short4 *box, const V
     if (n <= 0) return cudaSuccess;
     long long b = (n + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
-    k_voxel_dup<<<(unsigned)b, 256, 0, st>>>(offsets, box, grid, n, inst_key, inst_val, capacity);
+    pdl_launch(k_voxel_dup, (unsigned)b, 256, 0, st, offsets, box, grid, n, inst_key, inst_val, capacity);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -190,7 +193,7 @@ cudaError_t launch_voxel_eval(const uint2 *ranges, const uint32_t *sorted, const
                               const VoxelGrid &grid, float *out, cudaStream_t st, long long *launches) {
     const long long bricks = (long long)grid.bx * grid.by * grid.bz;
     if (bricks <= 0) return cudaSuccess;
-    k_voxel_eval<<<(unsigned)bricks, kVoxThreads, 0, st>>>(ranges, sorted, rec, box, grid, out);
+    pdl_launch(k_voxel_eval, (unsigned)bricks, kVoxThreads, 0, st, ranges, sorted, rec, box, grid, out);
     *launches += 1;
     return cudaGetLastError();
 }
