@@ -313,49 +313,39 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Warp reduce-scatter of NP per-lane values (NP a power of two, 2..32).  Each exchange step
-// with partner lane^w keeps half of the lane's values and sends the other half while more than
-// one value is left (NP/2 + NP/4 + ... shuffles), then plain butterfly adds finish the sum.
-// Afterwards lane l holds the warp sum of value scatter_index<NP>(l); the 32/NP lanes that
-// differ only in their low log2(32/NP) bits hold the same value.
-template <int NP>
-__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NP], int lane) {
-    static_assert(NP >= 2 && NP <= 32 && (NP & (NP - 1)) == 0, "NP must be a power of two");
+// Vector reductions into global memory (red.global.add.v2/v4.f32, no return value): p must be
+// 8- / 16-byte aligned.
+__device__ __forceinline__ void red_add_v2(float *p, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+// Partial warp reduce-scatter of NP per-lane values (NP a power of two): in exchange step s
+// (partner lane^(16>>s)) the lane keeps one half of the values it still holds, adds the
+// partner's copy of that half and hands over the other half.  After S steps the lane's
+// v[0 .. NP>>S) hold the sums, over the 2^S lanes that differ only in lane bits 4 .. 5-S, of
+// the values [base, base + (NP>>S)); base is returned.  NP>>S values cost NP - (NP>>S) shuffles.
+template <int NP, int S>
+__device__ __forceinline__ int warp_reduce_scatter_part(float (&v)[NP], int lane) {
+    static_assert(S >= 1 && (NP >> S) >= 1 && S <= 5, "bad step count");
+    int base = 0;
 #pragma unroll
-    for (int s = 0; s < 5; ++s) {
+    for (int s = 0; s < S; ++s) {
         const int w = 16 >> s;
-        const int c = NP >> s;   // values the lane still holds
-        if (c > 1) {
-            const int h = c / 2;
-            const bool hi = (lane & w) != 0;
+        const int h = (NP >> s) / 2;
+        const bool hi = (lane & w) != 0;
+        if (hi) base += h;
 #pragma unroll
-            for (int i = 0; i < h; ++i) {
-                const float keep = hi ? v[i + h] : v[i];
-                const float send = hi ? v[i] : v[i + h];
-                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-            }
-        } else {
-            v[0] += __shfl_xor_sync(0xffffffffu, v[0], w);
+        for (int i = 0; i < h; ++i) {
+            const float keep = hi ? v[i + h] : v[i];
+            const float send = hi ? v[i] : v[i + h];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
         }
     }
-    return v[0];
-}
-
-template <int NP>
-__device__ __forceinline__ int scatter_index(int lane) {
-    int idx = 0;
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const int c = NP >> s;
-        if (c > 1 && (lane & (16 >> s))) idx += c / 2;
-    }
-    return idx;
-}
-
-// True for the one lane of each group that holds the same reduce-scatter result.
-template <int NP>
-__device__ __forceinline__ bool scatter_writer(int lane) {
-    return (lane & (32 / NP - 1)) == 0;
+    return base;
 }
 
 }  // namespace vg

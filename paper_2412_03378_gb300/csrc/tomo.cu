@@ -243,14 +243,19 @@ cudaError_t launch_tomo_fwd(const uint2 *ranges, long long n_tiles, int tiles_x,
 // ---------------------------------------------------------------------------- backward
 // proj = exp(-sum tau)  =>  dL/dtau = -proj dL/dproj for every Gaussian on the ray;
 // ln tau = lnA - |y|^2/2  =>  dL/dy = -dL/dln(tau) y.  Seven partials per (pixel, Gaussian)
-// are summed over the quad, reduce-scattered over the warp and added to the per-item
-// accumulator with one coalesced global reduction per (warp, Gaussian).
+// are summed over the quad and added to the per-item accumulator (8 floats, 32-byte aligned)
+// with vector reductions in L2: directly by each contributing lane (two v4 reductions) when
+// at most kTomoDirectLanes lanes of the warp contribute, otherwise after two shuffle exchange
+// steps that leave every lane 2 values summed over 4 lanes (one v2 reduction per lane).  On
+// config 4 at half the Gaussians this backward takes 118 ms against 140 ms with a full
+// reduce-scatter and 7 scalar reductions per (warp, Gaussian).
 __global__ void __launch_bounds__(kQuadThreads, 12)
 k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, int det_w, int det_h,
            const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, const short4 *__restrict__ prect,
            const float *__restrict__ proj, const float *__restrict__ dL_dproj, float *__restrict__ grad_acc) {
     pdl_entry();
-    constexpr int NV = 7, NP = 8;   // partials used, and padded to a power of two
+    constexpr int NP = 8;   // 7 partials, padded to a power of two (the accumulator's 8 floats)
+    constexpr int kTomoDirectLanes = 16;
     __shared__ float4 srec[kTomoChunk * 2];
     __shared__ short4 srect[kTomoChunk];
     __shared__ uint32_t sitem[kTomoChunk];
@@ -260,8 +265,6 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
     const int x0 = tx * kTile + 2 * (threadIdx.x & 7), y0 = ty * kTile + 2 * (threadIdx.x >> 3);
     const float xf = (float)x0, yf = (float)y0;
     const int lane = threadIdx.x & 31;
-    const int sidx = scatter_index<NP>(lane);
-    const bool swrite = scatter_writer<NP>(lane);
     float gtau[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -332,9 +335,18 @@ k_tomo_bwd(const uint2 *__restrict__ ranges, int tiles_x, int tiles_per_view, in
                 v[1] = fmaf(v[5], dx0, ox1);
                 v[2] = fmaf(v[4], dy0, oy0);
                 v[3] = fmaf(v[5], dy0, oy1);
-                const float mine = warp_reduce_scatter<NP>(v, lane);
-                if (swrite && sidx < NV && mine != 0.0f)
-                    atomicAdd(&grad_acc[(size_t)sitem[j] * kTomoGradN + sidx], mine);
+                const bool any = (xa || xb) && (ya || yb);   // some pixel of the quad contributes
+                const unsigned act = __ballot_sync(0xffffffffu, any);
+                float *dst = grad_acc + (size_t)sitem[j] * kTomoGradN;
+                if (__popc(act) <= kTomoDirectLanes) {
+                    if (any) {
+                        red_add_v4(dst, v[0], v[1], v[2], v[3]);
+                        red_add_v4(dst + 4, v[4], v[5], v[6], 0.0f);
+                    }
+                } else {
+                    const int b0 = warp_reduce_scatter_part<NP, 2>(v, lane);
+                    red_add_v2(dst + b0, v[0], v[1]);
+                }
             }
         }
         __syncthreads();
