@@ -4,9 +4,10 @@
 // log-transmittance S = sum tau (no per-pair state is kept by the forward):
 //   T_i = exp(-(S_after - tau_i)),  dL/dc_i = g alpha_i T_i,
 //   dL/dtau_i = g . (c_i T_{i+1} - R_i) - gT T_end,  R_i = sum_{j>i} c_j alpha_j T_j + T_end bg,
-// then differentiates tau with respect to the record.  The replay is branch-free: a lane whose pixel does not blend the Gaussian (past its last blended
-// record, outside the footprint or below the skip threshold) takes tau = 0, which leaves its
-// state unchanged and adds zeros (0.421 ms against 0.464 ms with per-lane branches).  d' = A u and o' x d' = C u are linear in
+// then differentiates tau with respect to the record.  The replay is branch-free: a lane whose
+// pixel does not blend the Gaussian (past its last blended record, outside the footprint or
+// below the skip threshold) takes tau = 0, which leaves its state unchanged and adds zeros
+// (0.421 ms against 0.464 ms with per-lane branches).  d' = A u and o' x d' = C u are linear in
 // u = (dx, dy, 1), so with ga = 2 dL/da and gq = 2 dL/dq per pixel (a = |d'|^2, q = |o' x d'|^2)
 //   dL/dA = A sum_p ga u u^T,   dL/dC = C sum_p gq u u^T:
 // per Gaussian only the two symmetric 3x3 moment matrices (6 + 6 values), sum dL/dln(kappa) and
