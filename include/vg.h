@@ -345,6 +345,12 @@ vg_status vg_query(vg_workspace *ws, vg_stats *out, void *stream);
 /* Enable (1) or disable (0) per-stage event timing; enabling clears earlier records. */
 vg_status vg_profile_enable(vg_workspace *ws, int32_t enable);
 
+/* Restrict the event timing to some stages: bit k of stage_mask selects the k-th stage name in
+ * the vg_stage_time list above ("preprocess" = bit 0 ... "ray_march" = bit 13); 0 selects all
+ * (the default).  Fewer recorded stages mean fewer event records between the kernels of a
+ * timed step.  Errors: VG_ERR_INVALID_ARG for a NULL workspace. */
+vg_status vg_profile_stages(vg_workspace *ws, uint32_t stage_mask);
+
 /* Aggregate the recorded stage times (synchronises on the recorded events) into `out`
  * (capacity entries, HOST memory); *n_out receives the number of stages written.  The
  * records are cleared. */

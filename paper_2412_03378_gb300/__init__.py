@@ -27,6 +27,9 @@ FLAG_GRAD_ZERO = 4
 FLAG_DENSITY_THETA = 8
 FLAG_SPLAT = 16
 FLAG_PROJ_GIVEN = 32
+# stage names of the event profiler, in the bit order of vg_profile_stages
+STAGES = ("preprocess", "depth_sort", "scan", "duplicate", "tile_sort", "ranges", "render_fwd", "render_bwd",
+          "chain", "l2_loss", "tomo_fwd", "tomo_bwd", "voxel_eval", "ray_march")
 _STATUS = {0: "VG_OK", 1: "VG_ERR_INVALID_ARG", 2: "VG_ERR_CUDA", 3: "VG_ERR_OOM", 4: "VG_ERR_CAPACITY",
            5: "VG_ERR_TIMEOUT", 6: "VG_ERR_UNSUPPORTED", 7: "VG_ERR_STATE"}
 TILE = 16
@@ -104,6 +107,7 @@ _SIGS = {
     "vg_query": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_read_keys": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_profile_enable": [ctypes.c_void_p, ctypes.c_int32],
+    "vg_profile_stages": [ctypes.c_void_p, ctypes.c_uint32],
     "vg_profile_read": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "vg_read_bins": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_read_bins_range": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -356,7 +360,13 @@ class Workspace:
         self._chk(self._L.vg_query(self.h, ctypes.byref(s), _stream(stream)))
         return s.as_dict()
 
-    def profile_enable(self, on=True):
+    def profile_enable(self, on=True, stages=None):
+        """Per-stage event timing on (clearing earlier records) or off; `stages` (names from
+        STAGES) restricts the recorded stages, None records all."""
+        mask = 0
+        for name in stages or ():
+            mask |= 1 << STAGES.index(name)
+        self._chk(self._L.vg_profile_stages(self.h, mask))
         self._chk(self._L.vg_profile_enable(self.h, 1 if on else 0))
 
     def profile_read(self) -> dict:

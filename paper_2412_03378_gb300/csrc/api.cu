@@ -67,6 +67,7 @@ struct vg_workspace {
 
     // per-stage event timing (vg_profile_enable)
     bool prof_on = false;
+    uint32_t prof_mask = ~0u;             // bit k: stage k is recorded (vg_profile_stages)
     struct ProfRec {
         int stage;
         cudaEvent_t a, b;
@@ -106,7 +107,7 @@ struct ProfScope {
     cudaStream_t st;
     int idx = -1;
     ProfScope(vg_workspace *w, int stage, cudaStream_t s) : ws(w), st(s) {
-        if (!ws->prof_on) return;
+        if (!ws->prof_on || !((ws->prof_mask >> stage) & 1u)) return;
         cudaEvent_t a = prof_event(ws), b = prof_event(ws);
         if (!a || !b) return;
         cudaEventRecord(a, st);
@@ -1041,6 +1042,12 @@ vg_status vg_profile_enable(vg_workspace *ws, int32_t enable) {
     }
     ws->prof.clear();
     ws->prof_on = enable != 0;
+    return VG_OK;
+}
+
+vg_status vg_profile_stages(vg_workspace *ws, uint32_t stage_mask) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    ws->prof_mask = stage_mask ? stage_mask : ~0u;
     return VG_OK;
 }
 
