@@ -404,14 +404,40 @@ cudaError_t launch_duplicate(const uint32_t *perm, const uint32_t *offsets, cons
 }
 
 // ---------------------------------------------------------------------------- ranges
-__global__ void k_ranges(const uint32_t *__restrict__ key, long long n, const unsigned long long *__restrict__ n_dev,
-                         uint2 *__restrict__ ranges) {
+// Four consecutive sorted keys per thread (one 16-byte load plus the two neighbours): a tile's
+// range starts where its key differs from the previous one and ends where the next differs.
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ key, long long n,
+                                                const unsigned long long *__restrict__ n_dev,
+                                                uint2 *__restrict__ ranges) {
     pdl_entry();
     if (n_dev && (long long)*n_dev < n) n = (long long)*n_dev;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const uint32_t t = key[i];
-        if (i == 0 || key[i - 1] != t) ranges[t].x = (uint32_t)i;
-        if (i == n - 1 || key[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    const long long nq = (n + 3) / 4;
+    for (long long qd = (long long)blockIdx.x * blockDim.x + threadIdx.x; qd < nq;
+         qd += (long long)gridDim.x * blockDim.x) {
+        const long long i0 = 4 * qd;
+        uint32_t k[4];
+        if (i0 + 4 <= n) {   // key is 16-byte aligned (a device allocation) and i0 a multiple of 4
+            const uint4 v = *(const uint4 *)(key + i0);
+            k[0] = v.x;
+            k[1] = v.y;
+            k[2] = v.z;
+            k[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? key[i0 + j] : 0u;
+        }
+        const bool has_prev = i0 > 0, has_next = i0 + 4 < n;
+        const uint32_t prev = has_prev ? key[i0 - 1] : 0u, next = has_next ? key[i0 + 4] : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long i = i0 + j;
+            if (i >= n) break;
+            const uint32_t t = k[j];
+            const bool first = j == 0 ? (!has_prev || prev != t) : k[j - 1] != t;
+            const bool last = i + 1 == n || (j == 3 ? next != t : k[j + 1] != t);
+            if (first) ranges[t].x = (uint32_t)i;
+            if (last) ranges[t].y = (uint32_t)(i + 1);
+        }
     }
 }
 
@@ -420,7 +446,7 @@ cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, const un
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, st);
     if (e != cudaSuccess) return e;
     if (n_inst > 0) {
-        long long b = (n_inst + 255) / 256;
+        long long b = ((n_inst + 3) / 4 + 255) / 256;
         if (b > 152 * 64) b = 152 * 64;
         pdl_launch(k_ranges, (unsigned)b, 256, 0, st, sorted_key, n_inst, n_dev, ranges);
         *launches += 1;

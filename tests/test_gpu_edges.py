@@ -115,3 +115,40 @@ def test_degenerate_gaussians_stay_finite(gpu_lib):
     extreme.scale[:, 0] *= 0.1                                      # 10^4 : 1
     _, _, rgb2, T2 = run_forward(vg, extreme, [cam], o)
     assert np.all(np.isfinite(rgb2)) and np.all((T2 >= 0) & (T2 <= 1))
+
+
+def test_stage_profiler_mask(gpu_lib):
+    """vg_profile_stages: with one stage selected only that stage is event-timed; the default
+    (mask 0) records every stage of the step; the rendered image does not depend on either."""
+    vg = gpu_lib
+    import torch
+    scene = synth.uniform_scene(300, 72, log_scale=(-3.5, -2.5), extent=1.0)
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 96, 64, 60.0)
+    o = dict(oracle.EXACT)
+    g = dev_scene(vg, scene)
+    ws = vg.Workspace()
+    P = cam.width * cam.height
+    rgb, T = torch.empty(P, 3, device="cuda:0"), torch.empty(P, device="cuda:0")
+    dl = torch.full((P, 3), 1e-3, device="cuda:0")
+    grads = [torch.zeros(g.n, 3, device="cuda:0"), torch.zeros(g.n, 3, device="cuda:0"),
+             torch.zeros(g.n, 4, device="cuda:0"), torch.zeros(g.n, device="cuda:0"),
+             torch.zeros(tuple(g.sh.shape), device="cuda:0")]
+    images = []
+    for stages in (["render_bwd"], None):
+        ws.profile_enable(True, stages=stages)
+        for _ in range(2):
+            ws.preprocess(g, [cam], vg_opts(vg, o))
+            ws.bin_sort()
+            ws.render_fwd(rgb, T)
+            ws.render_bwd(dl, None, *grads)
+        rec = ws.profile_read()
+        ws.profile_enable(False)
+        images.append(rgb.cpu().numpy().copy())
+        if stages:
+            assert set(rec) == {"render_bwd"} and rec["render_bwd"][0] == 2
+        else:
+            assert {"preprocess", "depth_sort", "tile_sort", "render_fwd", "render_bwd", "chain"} <= set(rec)
+            assert all(c == 2 for c, _ in rec.values())
+    assert np.array_equal(images[0], images[1])
+    with pytest.raises(ValueError):
+        ws.profile_enable(True, stages=["no_such_stage"])
