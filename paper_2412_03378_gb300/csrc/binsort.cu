@@ -368,37 +368,74 @@ cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, 
 }
 
 // ---------------------------------------------------------------------------- duplicate
-__global__ void __launch_bounds__(256)
+// A warp takes 32 consecutive items: their instances fill one contiguous output range
+// [offsets[first], offsets[last + 1]), which the lanes write together, position by position
+// (coalesced stores).  The owner of position o is the last of the warp's items whose first
+// instance is at or before o (items without instances share their successor's offset, so the
+// last one wins); its instance r = o - offset is tile (x0 + r % w, y0 + r / w) of its rectangle,
+// the row-major order of the rectangle.
+constexpr int kDupWarps = 8;
+
+__global__ void __launch_bounds__(32 * kDupWarps)
 k_duplicate(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ offsets, const short4 *__restrict__ rect,
             const ViewInfo *__restrict__ views, long long n_items, int n_per_view, uint32_t *__restrict__ inst_key,
             uint32_t *__restrict__ inst_val, long long capacity) {
     pdl_entry();
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_items;
-         i += (long long)gridDim.x * blockDim.x) {
-        const uint32_t off = offsets[i], end = offsets[i + 1];
-        if (end == off) continue;
-        const uint32_t item = perm ? perm[i] : (uint32_t)i;
-        const short4 rc = rect[item];
-        const int v = (int)(item / (uint32_t)n_per_view);
-        const int tb = views[v].tile_base, tx = views[v].tiles_x;
-        long long o = off;
-        for (int y = rc.y; y <= rc.w; ++y)
-            for (int x = rc.x; x <= rc.z; ++x, ++o)
-                if (o < capacity) {
-                    inst_key[o] = (uint32_t)(tb + y * tx + x);
-                    inst_val[o] = item;
-                }
+    __shared__ uint32_t s_off[kDupWarps][32], s_item[kDupWarps][32];
+    __shared__ short4 s_rc[kDupWarps][32];
+    __shared__ int s_tb[kDupWarps][32], s_tx[kDupWarps][32];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const long long stride = (long long)gridDim.x * kDupWarps * 32;
+    for (long long w0 = ((long long)blockIdx.x * kDupWarps + wi) * 32; w0 < n_items; w0 += stride) {
+        const long long i = w0 + lane;
+        const bool valid = i < n_items;
+        uint32_t off = 0, end = 0, item = 0;
+        short4 rc = make_short4(0, 0, -1, -1);
+        int tb = 0, tx = 0;
+        if (valid) {
+            off = offsets[i];
+            end = offsets[i + 1];
+            item = perm ? perm[i] : (uint32_t)i;
+            if (end > off) {
+                rc = rect[item];
+                const int v = (int)(item / (uint32_t)n_per_view);
+                tb = views[v].tile_base;
+                tx = views[v].tiles_x;
+            }
+        }
+        const int last = (int)min(31LL, n_items - 1 - w0);
+        const uint32_t r0 = __shfl_sync(0xffffffffu, off, 0), r1 = __shfl_sync(0xffffffffu, end, last);
+        s_off[wi][lane] = valid ? off : r1;   // lanes past the end own nothing
+        s_item[wi][lane] = item;
+        s_rc[wi][lane] = rc;
+        s_tb[wi][lane] = tb;
+        s_tx[wi][lane] = tx;
+        __syncwarp();
+        for (uint32_t o = r0 + lane; o < r1; o += 32) {
+            int l = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (s_off[wi][l + step] <= o) l += step;
+            const short4 q = s_rc[wi][l];
+            const uint32_t r = o - s_off[wi][l], w = (uint32_t)(q.z - q.x + 1);
+            const uint32_t ry = r / w, rx = r - ry * w;
+            if ((long long)o < capacity) {
+                inst_key[o] = (uint32_t)(s_tb[wi][l] + ((int)q.y + (int)ry) * s_tx[wi][l] + (int)q.x + (int)rx);
+                inst_val[o] = s_item[wi][l];
+            }
+        }
+        __syncwarp();   // the staged items are reused by the warp's next 32
     }
 }
 
 cudaError_t launch_duplicate(const uint32_t *perm, const uint32_t *offsets, const short4 *rect, const ViewInfo *views,
                              long long n_items, int n_per_view, uint32_t *inst_key, uint32_t *inst_val,
                              long long capacity, cudaStream_t st, long long *launches) {
-    long long b = (n_items + 255) / 256;
+    long long b = (n_items + 32 * kDupWarps - 1) / (32 * kDupWarps);
     if (b > 152 * 32) b = 152 * 32;
     if (b < 1) b = 1;
-    pdl_launch(k_duplicate, (unsigned)b, 256, 0, st, perm, offsets, rect, views, n_items, n_per_view, inst_key, inst_val,
-                                            capacity);
+    pdl_launch(k_duplicate, (unsigned)b, 32 * kDupWarps, 0, st, perm, offsets, rect, views, n_items, n_per_view, inst_key, inst_val,
+               capacity);
     *launches += 1;
     return cudaGetLastError();
 }
