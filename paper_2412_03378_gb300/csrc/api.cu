@@ -64,6 +64,7 @@ struct vg_workspace {
     int tuned_fwd = 0, tuned_bwd = 0;     // vg_autotune's choice (0: none yet)
     int tuned_chunk_fwd = 0, tuned_chunk_bwd = 0;
     uint32_t *h_total = nullptr;         // pinned: [0..1] instance total (u64), [2] look-back timeout flag
+    cudaEvent_t total_ev = nullptr;       // recorded after the copy into h_total (binning ahead of it)
 
     // per-stage event timing (vg_profile_enable)
     bool prof_on = false;
@@ -274,6 +275,7 @@ vg_status vg_workspace_destroy(vg_workspace *ws) {
         cudaEventDestroy(r.b);
     }
     for (auto e : ws->prof_pool) cudaEventDestroy(e);
+    if (ws->total_ev) cudaEventDestroy(ws->total_ev);
     delete ws;
     return VG_OK;
 }
@@ -317,6 +319,22 @@ static vg_status read_total(vg_workspace *ws, cudaStream_t st, long long *total)
     VG_CUDA(ws, cudaMemcpyAsync(ws->h_total, ws->counters.p + 6, 2 * sizeof(unsigned long long),
                                 cudaMemcpyDeviceToHost, st));
     VG_CUDA(ws, cudaStreamSynchronize(st));
+    VG_TRY(latched_status(ws, st));
+    *total = (long long)(((unsigned long long)ws->h_total[1] << 32) | ws->h_total[0]);
+    return VG_OK;
+}
+
+// The same in two halves: the copy and an event now, the wait (on that event only, so that
+// work enqueued after the copy keeps running) later.
+static vg_status read_total_start(vg_workspace *ws, cudaStream_t st) {
+    if (!ws->total_ev) VG_CUDA(ws, cudaEventCreateWithFlags(&ws->total_ev, cudaEventDisableTiming));
+    VG_CUDA(ws, cudaMemcpyAsync(ws->h_total, ws->counters.p + 6, 2 * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, st));
+    VG_CUDA(ws, cudaEventRecord(ws->total_ev, st));
+    return VG_OK;
+}
+static vg_status read_total_finish(vg_workspace *ws, cudaStream_t st, long long *total) {
+    VG_CUDA(ws, cudaEventSynchronize(ws->total_ev));
     VG_TRY(latched_status(ws, st));
     *total = (long long)(((unsigned long long)ws->h_total[1] << 32) | ws->h_total[0]);
     return VG_OK;
@@ -492,40 +510,56 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
     }
     // The instance count: read back (one synchronisation), or, with a fixed capacity, left on
     // the device; the kernels below then cover the capacity and read the count themselves.
-    long long total;
-    const unsigned long long *total_dev = nullptr;
+    // Without a fixed capacity, when an earlier call left instance buffers, the rest of the
+    // binning is enqueued on them first in the same device-count form (kernels stop at the
+    // capacity) and the count is read back afterwards, so the GPU keeps working through the
+    // readback; a step with more instances than the buffers hold is binned again after they grow.
+    auto bin_rest = [&](long long total, const unsigned long long *total_dev) -> vg_status {
+        // 3. duplicate in depth order, 4. stable sort by tile id, 5. per-tile ranges
+        {
+            ProfScope ps(ws, ST_DUP, st);
+            VG_CUDA(ws, launch_duplicate(ws->perm, ws->offsets.p, ws->rect.p, ws->views.p, n, ws->g.n, ws->ikey[0].p,
+                                         ws->ival[0].p, ws->capacity, st, &ws->launches));
+        }
+        {
+            ProfScope ps(ws, ST_TILE, st);
+            VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, ws->ikey[0].p,
+                                          ws->ival[0].p, total, total_dev, bits_for(ws->n_tiles), ws->hist.p,
+                                          lookback_err_ptr(ws), &ws->inst_key, &ws->inst_item, st, &ws->launches));
+        }
+        VG_TRY(ensure(ws, ws->ranges, (size_t)ws->n_tiles, "tile ranges"));
+        VG_TRY(ensure(ws, ws->tord, (size_t)ws->n_tiles, "tile order"));
+        {
+            ProfScope ps(ws, ST_RANGES, st);
+            VG_CUDA(ws, launch_ranges(ws->inst_key, total, total_dev, ws->ranges.p, ws->n_tiles, st, &ws->launches));
+            VG_CUDA(ws, launch_tile_order(ws->ranges.p, ws->n_tiles, ws->tord.p, st, &ws->launches));
+            ws->tile_order = ws->tord.p;
+        }
+        return VG_OK;
+    };
     if (fixed) {
         if (ws->capacity <= 0 || !ws->ikey[1].p)
             return fail(ws, VG_ERR_CAPACITY, "fixed capacity: reserve instances with vg_workspace_reserve first");
-        total = ws->capacity;
-        total_dev = total64_ptr(ws);
         ws->n_inst = -1;   // known on the device only
+        VG_TRY(bin_rest(ws->capacity, total64_ptr(ws)));
     } else {
-        VG_TRY(read_total(ws, st, &total));
+        const bool ahead = ws->capacity > 0 && ws->ikey[1].p != nullptr;
+        long long total;
+        if (ahead) {
+            VG_TRY(read_total_start(ws, st));
+            VG_TRY(reserve_sort_scratch(ws, ws->capacity));
+            VG_TRY(bin_rest(ws->capacity, total64_ptr(ws)));
+            VG_TRY(read_total_finish(ws, st, &total));
+        } else {
+            VG_TRY(read_total(ws, st, &total));
+        }
         if (total > (long long)(1u << 30) - 1)
             return fail(ws, VG_ERR_INVALID_ARG, "more than 2^30 - 1 (tile, Gaussian) instances");
-        VG_TRY(reserve_instances(ws, total));
+        if (!ahead || total > ws->capacity) {
+            VG_TRY(reserve_instances(ws, total));
+            VG_TRY(bin_rest(total, nullptr));
+        }
         ws->n_inst = total;
-    }
-    // 3. duplicate in depth order, 4. stable sort by tile id, 5. per-tile ranges
-    {
-        ProfScope ps(ws, ST_DUP, st);
-        VG_CUDA(ws, launch_duplicate(ws->perm, ws->offsets.p, ws->rect.p, ws->views.p, n, ws->g.n, ws->ikey[0].p,
-                                     ws->ival[0].p, ws->capacity, st, &ws->launches));
-    }
-    {
-        ProfScope ps(ws, ST_TILE, st);
-        VG_CUDA(ws, launch_radix_sort(ws->ikey[0].p, ws->ival[0].p, ws->ikey[1].p, ws->ival[1].p, ws->ikey[0].p,
-                                      ws->ival[0].p, total, total_dev, bits_for(ws->n_tiles), ws->hist.p,
-                                      lookback_err_ptr(ws), &ws->inst_key, &ws->inst_item, st, &ws->launches));
-    }
-    VG_TRY(ensure(ws, ws->ranges, (size_t)ws->n_tiles, "tile ranges"));
-    VG_TRY(ensure(ws, ws->tord, (size_t)ws->n_tiles, "tile order"));
-    {
-        ProfScope ps(ws, ST_RANGES, st);
-        VG_CUDA(ws, launch_ranges(ws->inst_key, total, total_dev, ws->ranges.p, ws->n_tiles, st, &ws->launches));
-        VG_CUDA(ws, launch_tile_order(ws->ranges.p, ws->n_tiles, ws->tord.p, st, &ws->launches));
-        ws->tile_order = ws->tord.p;
     }
     ws->stage = 2;
     return VG_OK;
