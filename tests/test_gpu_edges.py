@@ -152,3 +152,27 @@ def test_stage_profiler_mask(gpu_lib):
     assert np.array_equal(images[0], images[1])
     with pytest.raises(ValueError):
         ws.profile_enable(True, stages=["no_such_stage"])
+
+
+def test_workspace_reuse_growing_and_shrinking_lists(gpu_lib):
+    """One workspace bins three scenes in turn: a small one (the instance buffers are sized to
+    it), a larger one (more instances than the buffers hold: the lists enqueued ahead of the
+    count's readback are rebuilt after the buffers grow) and the small one again (enqueued ahead
+    with spare capacity).  Every time the lists are bit-exact and the image matches the oracle."""
+    vg = gpu_lib
+    small = synth.uniform_scene(200, 73, log_scale=(-3.5, -2.5), extent=1.0)
+    large = synth.uniform_scene(1500, 74, log_scale=(-3.0, -2.0), extent=1.0)
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 160, 112, 60.0)
+    o = dict(oracle.EXACT)
+    ws = vg.Workspace()
+    counts = []
+    for scene in (small, large, small):
+        _, _, rgb, T = run_forward(vg, scene, [cam], o, ws=ws)
+        L = oracle.lists(scene, [cam], o)
+        ts, items = ws.read_bins()
+        assert np.array_equal(ts, L["tile_start"]) and np.array_equal(items, L["sorted_g"])
+        ref_rgb, ref_T, _ = oracle.render(scene, [cam], o, L=L)
+        assert np.max(np.abs(rgb - flat(ref_rgb))) < IMG_TOL
+        assert np.max(np.abs(T - flat(ref_T))) < IMG_TOL
+        counts.append(ws.query()["n_instances"])
+    assert counts[1] > counts[0] and counts[2] == counts[0]
