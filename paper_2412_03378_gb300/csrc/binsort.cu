@@ -116,7 +116,7 @@ __device__ __forceinline__ unsigned long long cta_excl_scan(unsigned long long x
 
 // ---------------------------------------------------------------------------- scan
 constexpr int kScanThreads = 512;
-constexpr int kScanItems = 8;
+constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 size_t scan_tmp_words(long long n) {
