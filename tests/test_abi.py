@@ -54,3 +54,15 @@ def test_oracle_is_not_imported_by_the_package():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "vg_oracle" not in txt and "synth" not in txt, f
+
+
+def test_profiler_stage_order_matches_the_header():
+    """vg_profile_stages selects stages by bit position in the stage-name list documented with
+    vg_stage_time; the binding's STAGES must list them in that order."""
+    import paper_2412_03378_gb300 as vg
+
+    src = open(os.path.join(ROOT, "include", "vg.h")).read()
+    doc = src[src.index("Stage names:"):src.index("typedef struct", src.index("Stage names:"))]
+    doc = doc[:doc.index("(the voxel query")]
+    names = re.findall(r'"([a-z_0-9]+)"', doc)
+    assert tuple(names) == vg.STAGES
