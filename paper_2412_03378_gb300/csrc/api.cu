@@ -491,7 +491,11 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
     if (ws->stage < 1) return fail(ws, VG_ERR_STATE, "vg_bin_sort before vg_preprocess");
     cudaStream_t st = (cudaStream_t)stream;
     const long long n = ws->n_items;
-    VG_TRY(reserve_sort_scratch(ws, n));
+    const bool fixed = (ws->opts.flags & VG_FLAG_FIXED_CAPACITY) != 0;
+    // binning ahead of the count's readback on instance buffers left by an earlier call (below);
+    // the sort scratch for both sorts is reserved before anything is enqueued
+    const bool ahead = !fixed && ws->capacity > 0 && ws->ikey[1].p != nullptr;
+    VG_TRY(reserve_sort_scratch(ws, ahead ? std::max(n, ws->capacity) : n));
     // 1. items by depth key (stable: ties keep index order)
     {
         ProfScope ps(ws, ST_DEPTH, st);
@@ -501,7 +505,6 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
                                       &ws->perm, st, &ws->launches));
     }
     // 2. instance offsets in depth order
-    const bool fixed = (ws->opts.flags & VG_FLAG_FIXED_CAPACITY) != 0;
     {
         ProfScope ps(ws, ST_SCAN, st);
         VG_CUDA(ws, launch_scan_gather(ws->count.p, ws->perm, ws->offsets.p, n, ws->scan_tmp.p, total64_ptr(ws),
@@ -543,11 +546,9 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
         ws->n_inst = -1;   // known on the device only
         VG_TRY(bin_rest(ws->capacity, total64_ptr(ws)));
     } else {
-        const bool ahead = ws->capacity > 0 && ws->ikey[1].p != nullptr;
         long long total;
         if (ahead) {
             VG_TRY(read_total_start(ws, st));
-            VG_TRY(reserve_sort_scratch(ws, ws->capacity));
             VG_TRY(bin_rest(ws->capacity, total64_ptr(ws)));
             VG_TRY(read_total_finish(ws, st, &total));
         } else {
