@@ -40,7 +40,7 @@ typedef enum {
     VG_ERR_OOM = 3,           /* device memory for the workspace could not be allocated       */
     VG_ERR_CAPACITY = 4,      /* fixed-capacity mode: more tile instances than reserved       */
     VG_ERR_TIMEOUT = 5,       /* a bounded device wait gave up                                */
-    VG_ERR_UNSUPPORTED = 6,   /* a valid request this build does not implement                */
+    VG_ERR_UNSUPPORTED = 6,   /* a valid request the library does not implement               */
     VG_ERR_STATE = 7          /* calls out of order (e.g. render before bin_sort)             */
 } vg_status;
 
