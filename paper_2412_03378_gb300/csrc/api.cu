@@ -65,6 +65,8 @@ struct vg_workspace {
     int tuned_chunk_fwd = 0, tuned_chunk_bwd = 0;
     uint32_t *h_total = nullptr;         // pinned: [0..1] instance total (u64), [2] look-back timeout flag
     cudaEvent_t total_ev = nullptr;       // recorded after the copy into h_total (binning ahead of it)
+    const float *grad_zero_p = nullptr;   // grad.p and the leading floats of it known to be zero
+    size_t grad_zero_n = 0;               // (left so by the chain), which a backward need not clear
 
     // per-stage event timing (vg_profile_enable)
     bool prof_on = false;
@@ -600,9 +602,11 @@ static vg_status render_bwd_impl(vg_workspace *ws, const float *dL_drgb, const f
     if ((!dL_drgb && ws->n_pixels > 0 && !drgb_optional) || (ws->g.n > 0 && (!dmu || !dscale || !dquat || !dkappa)))
         return fail(ws, VG_ERR_INVALID_ARG, "a gradient pointer is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    VG_TRY(ensure(ws, ws->grad, (size_t)ws->n_items * kGradN, "gradient accumulators"));
-    if (ws->n_items > 0)
-        VG_CUDA(ws, cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st));
+    const size_t acc_n = (size_t)ws->n_items * kGradN;
+    VG_TRY(ensure(ws, ws->grad, acc_n, "gradient accumulators"));
+    const bool clean = ws->grad_zero_p == ws->grad.p && ws->grad_zero_n >= acc_n;
+    ws->grad_zero_n = 0;   // until the chain below has run
+    if (ws->n_items > 0 && !clean) VG_CUDA(ws, cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * acc_n, st));
     unsigned long long *pc = nullptr;
     if (ws->opts.flags & VG_FLAG_COUNT_PAIRS) {
         pc = ws->counters.p + 3;
@@ -622,6 +626,8 @@ static vg_status render_bwd_impl(vg_workspace *ws, const float *dL_drgb, const f
         VG_CUDA(ws, launch_chain(ws->g, ws->views.p, ws->n_views, ws->grad.p, (ws->opts.flags & VG_FLAG_GRAD_ZERO) ? 1 : 0,
                                  dmu, dscale, dquat, dkappa, dsh, st, &ws->launches));
     }
+    ws->grad_zero_p = ws->grad.p;   // the chain left the accumulator zero
+    ws->grad_zero_n = acc_n;
     return VG_OK;
 }
 
@@ -922,6 +928,7 @@ static vg_status tomo_impl(vg_workspace *ws, const vg_gaussians *g, const vg_bea
         }
         if (backward && items > 0) {
             VG_TRY(ensure(ws, ws->grad, (size_t)items * 8, "gradient accumulators"));
+            ws->grad_zero_n = 0;   // the tomography backward leaves its sums in the accumulator
             VG_CUDA(ws, cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)items * 8, st));
             ProfScope ps(ws, ST_TBWD, st);
             VG_CUDA(ws, launch_tomo_bwd(ws->ranges.p, n_tiles, tiles_x, (int)tpv, beam->det_w, beam->det_h,
@@ -1010,6 +1017,7 @@ vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t 
             cudaEventElapsedTime(&ms, a, b);
             if (r) tf += ms;
             if (e != cudaSuccess) break;
+            ws->grad_zero_n = 0;   // timed backward passes without the chain leave sums behind
             e = cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st);
             cudaEventRecord(a, st);
             if (e == cudaSuccess)

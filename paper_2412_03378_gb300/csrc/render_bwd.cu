@@ -438,7 +438,7 @@ constexpr int kChainWarps = 2;
 
 template <typename RT, typename ST, bool SPLAT>
 __global__ void __launch_bounds__(32 * kChainWarps, 8)
-k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float *__restrict__ grad_acc, int zero,
+k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float *__restrict__ grad_acc, int zero,
         float *__restrict__ dmu, float *__restrict__ dscale, float *__restrict__ dquat, float *__restrict__ dkappa,
         float *__restrict__ dsh) {
     pdl_entry();
@@ -471,7 +471,7 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
         float am[3] = {0.0f, 0.0f, 0.0f}, asc[3] = {0.0f, 0.0f, 0.0f}, aq[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ak = 0.0f;
         for (int v = 0; valid && v < n_views; ++v) {
         const long long it = (long long)v * g.n + gi;
-        const float4 *ga4 = (const float4 *)(grad_acc + it * kGradN);
+        float4 *ga4 = (float4 *)(grad_acc + it * kGradN);
         float ga[kGradN];
         bool any = false;
 #pragma unroll
@@ -484,6 +484,9 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
             any |= (t.x != 0.0f) | (t.y != 0.0f) | (t.z != 0.0f) | (t.w != 0.0f);
         }
         if (!any) continue;
+        // the accumulator is left zero for the next backward (no separate clearing pass)
+#pragma unroll
+        for (int k = 0; k < kGradN / 4; ++k) ga4[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         const ViewInfo &V = views[v];
         float dR[9], dm[3], dsc[3];
         if constexpr (SPLAT) {
@@ -646,7 +649,7 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, const float 
 }
 
 template <typename RT, typename ST>
-static cudaError_t launch_chain_t(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc, int zero,
+static cudaError_t launch_chain_t(const GaussIn &g, const ViewInfo *views_d, int n_views, float *grad_acc, int zero,
                                   float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st) {
     long long b = ((long long)g.n + 32 * kChainWarps - 1) / (32 * kChainWarps);
     if (b > 152 * 64) b = 152 * 64;
@@ -660,7 +663,7 @@ static cudaError_t launch_chain_t(const GaussIn &g, const ViewInfo *views_d, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc, int zero,
+cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, float *grad_acc, int zero,
                          float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st,
                          long long *launches) {
     if (g.n <= 0) return cudaSuccess;

@@ -192,7 +192,9 @@ cudaError_t launch_ray_march(const GaussIn &g, const ViewInfo *views_d, const in
                              int n_samples, float T_stop, const float bg[3], const float *raster, float *rgb,
                              float *T_out, float *err, cudaStream_t st, long long *launches);
 
-cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, const float *grad_acc, int zero,
+// The chain reads grad_acc and leaves every item it reads zero again (an all-zero row is left
+// as it is), so a following backward needs no clearing pass.
+cudaError_t launch_chain(const GaussIn &g, const ViewInfo *views_d, int n_views, float *grad_acc, int zero,
                          float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh, cudaStream_t st,
                          long long *launches);
 
