@@ -559,6 +559,8 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
         if (total > (long long)(1u << 30) - 1)
             return fail(ws, VG_ERR_INVALID_ARG, "more than 2^30 - 1 (tile, Gaussian) instances");
         if (!ahead || total > ws->capacity) {
+            // the binning enqueued ahead still uses the buffers about to be replaced
+            if (ahead) VG_CUDA(ws, cudaStreamSynchronize(st));
             VG_TRY(reserve_instances(ws, total));
             VG_TRY(bin_rest(total, nullptr));
         }
