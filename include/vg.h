@@ -368,6 +368,15 @@ vg_status vg_read_bins(vg_workspace *ws, int64_t *tile_start, int32_t *sorted_it
 vg_status vg_read_bins_range(vg_workspace *ws, int64_t tile0, int64_t tile1, int64_t *counts,
                              int32_t *sorted_item, int64_t cap, int64_t *n_out);
 
+/* Diagnostic read-back of the per-pixel replay state of the last vg_render_fwd into HOST buffers
+ * (synchronous), views concatenated as in the image:
+ *   S [n_pixels] float32: sum of the tau of the pairs the pixel blended (Eq. 14: T = exp(-S)),
+ *   last [n_pixels] uint32: position + 1, within the pixel's tile list, of the last pair the
+ *        pixel blended (0 when it blended none).
+ * Either may be NULL.  Together they identify the pixels where a threshold decision (alpha_min,
+ * T_stop) went differently from another implementation.  VG_ERR_STATE before a forward. */
+vg_status vg_read_pixel_state(vg_workspace *ws, float *S, uint32_t *last);
+
 /* Message of the last failure on this workspace ("" if none).  ws may be NULL for
  * failures of vg_workspace_create. */
 const char *vg_last_error(const vg_workspace *ws);

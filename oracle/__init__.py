@@ -127,7 +127,8 @@ def lib():
         L.orc_tau.restype = None
         L.orc_tau.argtypes = [P, P, P, ctypes.c_double, P, P, P]
         L.orc_render.restype = None
-        L.orc_render.argtypes = [i32, P, P, P, P, P, i32, i32, P, P, i32, i32, P, P, P, P, i32, P, P, P, P, P, P, P]
+        L.orc_render.argtypes = [i32, P, P, P, P, P, i32, i32, P, P, i32, i32, P, P, P, P, i32, P, P, P, P, P, P, P,
+                                 P, P]
         L.orc_render_grad.restype = None
         L.orc_render_grad.argtypes = [i32, P, P, P, P, P, i32, i32, P, P, i32, i32, P, P, P, P, P, P, P, P, P,
                                       P, P, P, P, P]
@@ -254,9 +255,13 @@ def lists(scene, cams, opts=None, tile=(16, 16)):
                 tile_base=base, n_tiles=nt, tile=tile)
 
 
-def render(scene, cams, opts=None, L=None, brute=False, mask=None, tile=(16, 16)):
+def render(scene, cams, opts=None, L=None, brute=False, mask=None, tile=(16, 16), diag=False):
     """Blend every pixel (Eq. 14 with the Eq. 19 alpha).  Returns per-view lists of
-    rgb [H, W, 3] and T_final [H, W] (float64) and the blended-Gaussian count."""
+    rgb [H, W, 3] and T_final [H, W] (float64) and the blended-Gaussian count.  With diag=True a
+    fourth item holds flat per-pixel arrays (views concatenated): "last" = position + 1, within the
+    pixel's tile list, of the last blended pair (0 when none), "S" = sum of the blended tau, and
+    "m_skip" / "m_clamp" / "m_stop" = the relative distance of the pixel's closest alpha_min,
+    tau_max and T_stop decision to its threshold (inf when it met none)."""
     oa, o = _opts_arr(opts)
     if L is None:
         L = lists(scene, cams, o, tile)
@@ -267,17 +272,22 @@ def render(scene, cams, opts=None, L=None, brute=False, mask=None, tile=(16, 16)
     rgb = np.zeros((P, 3), np.float64)
     T = np.zeros(P, np.float64)
     nb = np.zeros(P, np.int32)
+    last = np.zeros(P, np.int64) if diag else None
+    dg = np.zeros((P, 4), np.float64) if diag else None
     m = None if mask is None else _c(mask, np.int32)
     lib().orc_render(scene.n, _p(mu), _p(sc), _p(q), _p(k), _p(sh), scene.sh_degree, len(cams), _p(cf), _p(wh),
                      L["tile"][0], L["tile"][1], _p(oa), _p(L["tile_start"]), _p(L["sorted_g"]),
                      _p(_c(L["tile_base"], np.int32)), int(brute), _p(_c(L["depth"], np.uint32)),
-                     _p(_c(L["prect"], np.int32)), _p(pb), _p(m), _p(rgb), _p(T), _p(nb))
+                     _p(_c(L["prect"], np.int32)), _p(pb), _p(m), _p(rgb), _p(T), _p(nb), _p(last), _p(dg))
     out_rgb, out_T, out_n = [], [], []
     for v, c in enumerate(cams):
         s = slice(pb[v], pb[v] + c.width * c.height)
         out_rgb.append(rgb[s].reshape(c.height, c.width, 3))
         out_T.append(T[s].reshape(c.height, c.width))
         out_n.append(nb[s].reshape(c.height, c.width))
+    if diag:
+        return out_rgb, out_T, out_n, dict(last=last, S=dg[:, 0], m_skip=dg[:, 1], m_clamp=dg[:, 2],
+                                           m_stop=dg[:, 3])
     return out_rgb, out_T, out_n
 
 

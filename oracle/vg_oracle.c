@@ -744,7 +744,7 @@ void orc_render(int n, const double *mu, const double *scale, const double *quat
                 const int64_t *tile_start, const int32_t *sorted_g, const int32_t *view_tile_base,
                 int brute, const uint32_t *depth_bits, const int32_t *prect,
                 const int64_t *pix_base, const int32_t *pix_mask, double *rgb, double *T_final,
-                int32_t *n_blend)
+                int32_t *n_blend, int64_t *last_pos, double *diag)
 {
     const double tau_skip = tau_skip_of(opts[0]);
     const double tau_max = opts[2], T_stop = opts[3];
@@ -795,8 +795,12 @@ void orc_render(int n, const double *mu, const double *scale, const double *quat
                 lo = tile_start[tile];
                 hi = tile_start[tile + 1];
             }
-            double T = 1.0, C[3] = {0, 0, 0};
+            double T = 1.0, C[3] = {0, 0, 0}, S = 0.0;
+            /* how close each threshold decision of this pixel came to going the other way
+             * (relative distance to alpha_min / tau_max / T_stop; INFINITY: no such decision) */
+            double m_skip = INFINITY, m_clamp = INFINITY, m_stop = INFINITY;
             int nb = 0;
+            int64_t last = lo;
             for (int64_t k = lo; k < hi; ++k) {
                 int64_t g = brute ? ord[k].g : sorted_g[k];
                 if (!brute && outside(prect, (int64_t)v * n + g, x, y)) continue;
@@ -805,24 +809,38 @@ void orc_render(int n, const double *mu, const double *scale, const double *quat
                     if (!SP[g].ok) continue;
                     double w[2], q;
                     alpha = splat_alpha(&SP[g], G[g].kap, x, y, w, &q);
+                    if (amax < 1.0) m_clamp = fmin(m_clamp, fabs(alpha - amax) / amax);
                     if (alpha > amax) alpha = amax;
+                    if (opts[0] > 0) m_skip = fmin(m_skip, fabs(alpha - opts[0]) / opts[0]);
                     if (alpha < opts[0]) continue;
                     tau = -log1p(-alpha);
                 } else {
                     double a, b, c, p[3];
                     tau = tau64(&G[g], cam.o, d, &a, &b, &c, p);
+                    if (isfinite(tau_max)) m_clamp = fmin(m_clamp, fabs(tau - tau_max) / tau_max);
                     if (tau > tau_max) tau = tau_max;
+                    if (tau_skip > 0) m_skip = fmin(m_skip, fabs(tau - tau_skip) / tau_skip);
                     if (tau < tau_skip) continue;
                     alpha = -expm1(-tau);
                 }
                 for (int ch = 0; ch < 3; ++ch) C[ch] += col[3 * g + ch] * alpha * T;
                 T *= exp(-tau);
+                S += tau;
                 ++nb;
+                last = k + 1;
+                if (T_stop > 0) m_stop = fmin(m_stop, fabs(T - T_stop) / T_stop);
                 if (T < T_stop) break;
             }
             for (int ch = 0; ch < 3; ++ch) rgb[3 * gp + ch] = C[ch] + T * bg[ch];
             T_final[gp] = T;
             if (n_blend) n_blend[gp] = nb;
+            if (last_pos) last_pos[gp] = last - lo;
+            if (diag) {
+                diag[4 * gp] = S;
+                diag[4 * gp + 1] = m_skip;
+                diag[4 * gp + 2] = m_clamp;
+                diag[4 * gp + 3] = m_stop;
+            }
         }
     }
     free(G);

@@ -62,7 +62,12 @@ void orc_render(int n, const double *mu, const double *scale, const double *quat
                 const int64_t *tile_start, const int32_t *sorted_g, const int32_t *view_tile_base,
                 int brute, const uint32_t *depth_bits, const int32_t *prect,
                 const int64_t *pix_base, const int32_t *pix_mask, double *rgb, double *T_final,
-                int32_t *n_blend);
+                int32_t *n_blend, int64_t *last_pos, double *diag);
+/* Optional per-pixel outputs of orc_render (each may be NULL): n_blend = blended pairs;
+ * last_pos = position + 1, within the pixel's tile list, of the last blended pair (0 when none;
+ * the position in the depth order in brute-force mode); diag[4] = { S = sum of the blended
+ * tau, and the relative distance of the closest skip (alpha_min), clamp (tau_max) and
+ * early-stop (T_stop) decision to its threshold, INFINITY when the pixel met none }. */
 
 void orc_render_grad(int n, const double *mu, const double *scale, const double *quat,
                      const double *kappa, const double *sh, int sh_degree, int n_views,

@@ -110,6 +110,7 @@ _SIGS = {
     "vg_profile_stages": [ctypes.c_void_p, ctypes.c_uint32],
     "vg_profile_read": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "vg_read_bins": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "vg_read_pixel_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_read_bins_range": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                            ctypes.c_int64, ctypes.c_void_p],
 }
@@ -393,6 +394,16 @@ class Workspace:
         self._chk(self._L.vg_read_bins(self.h, ts.ctypes.data_as(ctypes.c_void_p),
                                        si.ctypes.data_as(ctypes.c_void_p)))
         return ts, si[: q["n_instances"]]
+
+    def read_pixel_state(self):
+        """(S [n_pixels] float32, last [n_pixels] uint32) of the last forward (see vg_read_pixel_state)."""
+        import numpy as np
+        n = self.query()["n_pixels"]
+        S = np.zeros(max(1, n), np.float32)
+        last = np.zeros(max(1, n), np.uint32)
+        self._chk(self._L.vg_read_pixel_state(self.h, S.ctypes.data_as(ctypes.c_void_p),
+                                              last.ctypes.data_as(ctypes.c_void_p)))
+        return S[:n], last[:n]
 
     def read_bins_range(self, tile0, tile1, cap):
         """Lists of tiles [tile0, tile1): (counts [tile1 - tile0], items concatenated)."""

@@ -1171,6 +1171,29 @@ vg_status vg_read_bins_range(vg_workspace *ws, int64_t tile0, int64_t tile1, int
     return VG_OK;
 }
 
+vg_status vg_read_pixel_state(vg_workspace *ws, float *S, uint32_t *last) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (ws->stage < 3) return fail(ws, VG_ERR_STATE, "no vg_render_fwd to read");
+    VG_CUDA(ws, cudaDeviceSynchronize());
+    const size_t n = (size_t)ws->n_pixels;
+    if (n == 0) return VG_OK;
+    if (S) VG_CUDA(ws, cudaMemcpy(S, ws->S_fin.p, n * sizeof(float), cudaMemcpyDeviceToHost));
+    if (last) {
+        VG_CUDA(ws, cudaMemcpy(last, ws->nlast.p, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        // the kernels keep positions in the sorted instance array: make them relative to the list
+        std::vector<uint2> rg((size_t)ws->n_tiles);
+        if (ws->n_tiles > 0)
+            VG_CUDA(ws, cudaMemcpy(rg.data(), ws->ranges.p, rg.size() * sizeof(uint2), cudaMemcpyDeviceToHost));
+        for (const ViewInfo &V : ws->views_h)
+            for (int y = 0; y < V.H; ++y)
+                for (int x = 0; x < V.W; ++x) {
+                    const size_t p = (size_t)(V.pix_base + (long long)y * V.W + x);
+                    last[p] -= rg[(size_t)V.tile_base + (size_t)(y / kTile) * V.tiles_x + x / kTile].x;
+                }
+    }
+    return VG_OK;
+}
+
 vg_status vg_read_bins(vg_workspace *ws, int64_t *tile_start, int32_t *sorted_item) {
     if (!ws || !tile_start) return VG_ERR_INVALID_ARG;
     if (ws->stage < 2 && !ws->tomo_read) return fail(ws, VG_ERR_STATE, "no bin_sort to read");

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import check_grads, dev_scene, flat, grad_rel_err, run_backward, run_forward, vg_opts
+from gpu_util import check_grads, compat_check, dev_scene, flat, grad_rel_err, run_backward, run_forward, vg_opts
 
 pytestmark = pytest.mark.gpu
 
@@ -67,15 +67,36 @@ def test_forward_exact_mode(gpu_lib, case):
 @pytest.mark.parametrize("case", list(CASES))
 def test_forward_compat_mode(gpu_lib, case):
     """With alpha_min / tau_max / T_stop the FP32 and FP64 sides may decide a threshold
-    differently at a few pixels; elsewhere the image matches to 1e-4."""
+    differently at a few pixels (identified from the replay state, each near a threshold);
+    every other pixel matches to 1e-4."""
     vg = gpu_lib
     scene, cams = CASES[case]()
     o = oracle.COMPAT
-    _, _, rgb, T = run_forward(vg, scene, cams, o)
-    ref_rgb, ref_T, _ = oracle.render(scene, cams, o)
-    err = np.max(np.abs(rgb - flat(ref_rgb)), axis=1)
-    assert np.mean(err > IMG_TOL) < 0.005
-    assert np.max(err) < 0.02
+    ws, _, rgb, T = run_forward(vg, scene, cams, o)
+    compat_check(ws, scene, cams, o, rgb, T, label=case)
+
+
+@pytest.mark.parametrize("chunk", [64, 128])
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+@pytest.mark.parametrize("case", ["cfg1", "multiview_sh3"])
+def test_backward_compat_mode(gpu_lib, case, ppt, chunk):
+    """The benchmarked backward: the 3DGS thresholds (Sec. 5 swaps only alpha into the 3DGS blend:
+    alpha_min skip, alpha <= 0.99 clamp, T_stop early stop) with the per-warp opacity-bound cull,
+    against the oracle's analytic gradient.  Pixels where FP32 and FP64 took a threshold decision
+    differently, or where a pair lies within 1e-4 of the clamp (its gradient is cut on one side
+    only), get zero loss weight on both sides; the flipped pixels are counted and bounded."""
+    vg = gpu_lib
+    scene, cams = CASES[case]()
+    o = dict(oracle.COMPAT, bg=(0.3, 0.2, 0.1))
+    ws, g, rgb, T = run_forward(vg, scene, cams, o, ppt=ppt, chunk=chunk)
+    keep, L, _ = compat_check(ws, scene, cams, o, rgb, T, label=f"{case} ppt {ppt} chunk {chunk}")
+    rng = np.random.default_rng(100 * ppt + chunk)
+    P = rgb.shape[0]
+    wr = rng.normal(size=(P, 3)) * keep[:, None]
+    wT = rng.normal(size=P) * keep
+    gg = run_backward(vg, ws, g, wr, wT)
+    ref = oracle.render_grad(scene, cams, o, L, wr, wT)
+    check_grads(gg, ref, scene, GRAD_TOL, label=f"compat {case} ppt {ppt} chunk {chunk} ")
 
 
 def test_forward_edge_cases(gpu_lib):
@@ -128,27 +149,22 @@ def test_backward_matches_oracle_gradient(gpu_lib, case, variant):
 
 @pytest.mark.parametrize("chunk", [64, 128])
 @pytest.mark.parametrize("ppt", [1, 2, 4])
-@pytest.mark.parametrize("mode", ["exact", "compat"])
-def test_pixels_per_thread_variants(gpu_lib, ppt, mode, chunk):
-    """Every blend-kernel variant (1, 2 or 4 pixels per thread; 64 or 128 records per chunk)
-    against the oracle."""
+def test_pixels_per_thread_variants(gpu_lib, ppt, chunk):
+    """Every blend-kernel variant (1, 2 or 4 pixels per thread; 64 or 128 records per chunk) in
+    exact mode against the oracle (the compat-mode variants: test_backward_compat_mode)."""
     vg = gpu_lib
     scene, cams = _multi_view_scene()
-    o = dict(oracle.EXACT if mode == "exact" else oracle.COMPAT, bg=(0.3, 0.2, 0.1))
+    o = dict(oracle.EXACT, bg=(0.3, 0.2, 0.1))
     ws, g, rgb, T = run_forward(vg, scene, cams, o, ppt=ppt, chunk=chunk)
     ref_rgb, ref_T, _ = oracle.render(scene, cams, o)
     err = np.max(np.abs(rgb - flat(ref_rgb)), axis=1)
-    if mode == "exact":
-        assert err.max() < IMG_TOL
-    else:
-        assert np.mean(err > IMG_TOL) < 0.005 and err.max() < 0.02
+    assert err.max() < IMG_TOL
     rng = np.random.default_rng(ppt)
     wr = rng.normal(size=(rgb.shape[0], 3))
     wT = rng.normal(size=rgb.shape[0])
     gg = run_backward(vg, ws, g, wr, wT)
-    if mode == "exact":
-        ref = oracle.render_grad(scene, cams, o, oracle.lists(scene, cams, o), wr, wT)
-        check_grads(gg, ref, scene, GRAD_TOL)
+    ref = oracle.render_grad(scene, cams, o, oracle.lists(scene, cams, o), wr, wT)
+    check_grads(gg, ref, scene, GRAD_TOL)
 
 
 @pytest.mark.parametrize("seed", range(1, 7))

@@ -297,6 +297,129 @@ def test_sh_basis_is_orthonormal():
     assert Y[3] < 0
 
 
+def _real_sh_scipy(l, m, d):
+    """Real SH of degree l, order m at unit direction d, from scipy's complex spherical harmonics
+    (which carry the Condon-Shortley phase): sqrt2 Re Y_l^m for m > 0, Y_l^0, sqrt2 Im Y_l^|m| for
+    m < 0 -- the basis whose degree-1 block is proportional to (-y, z, -x)."""
+    import scipy.special as sp
+    theta = math.acos(max(-1.0, min(1.0, d[2])))
+    phi = math.atan2(d[1], d[0])
+    if hasattr(sp, "sph_harm_y"):
+        Y = complex(sp.sph_harm_y(l, abs(m), theta, phi))
+    else:   # older scipy: sph_harm(order, degree, azimuth, polar)
+        Y = complex(sp.sph_harm(abs(m), l, phi, theta))
+    if m > 0:
+        return math.sqrt(2.0) * Y.real
+    if m < 0:
+        return math.sqrt(2.0) * Y.imag
+    return Y.real
+
+
+def test_sh_basis_matches_associated_legendre_definition():
+    """Every function of degree 0-3 (graphics ordering k = l^2 + l + m) equals the real SH built
+    from scipy's associated-Legendre spherical harmonics at fixed and random directions: a swapped
+    pair, a wrong constant or sign of any degree-2 or degree-3 function fails here."""
+    rng = np.random.default_rng(31)
+    dirs = [np.array(v, np.float64) for v in ((0, 0, 1), (1, 0, 0), (0, 1, 0), (0.6, -0.48, 0.64), (-0.3, 0.4, -0.866))]
+    dirs += [v / np.linalg.norm(v) for v in rng.normal(size=(12, 3))]
+    for d in dirs:
+        d = d / np.linalg.norm(d)
+        Y = oracle.sh_basis(3, d)
+        for l in range(4):
+            for m in range(-l, l + 1):
+                assert abs(Y[l * l + l + m] - _real_sh_scipy(l, m, d)) < 1e-12, (l, m, d)
+
+
+# ------------------------------------------------------------------ thresholds (reading 8)
+def _on_axis_scene(taus, colours, s=0.1):
+    """Isotropic Gaussians of scale s centred on the optical axis of _axis_camera, front to back;
+    along that ray each has tau = kappa sqrt(2 pi) s exactly (Eq. 19 with the ray through the mean)."""
+    y00 = 0.5 / math.sqrt(math.pi)
+    gs = [one_gaussian((0.0, 0.0, -1.0 + 0.5 * i), (s, s, s), (1.0, 0.0, 0.0, 0.0), t / (math.sqrt(2 * math.pi) * s),
+                       sh0=tuple((np.asarray(c) - 0.5) / y00)) for i, (t, c) in enumerate(zip(taus, colours))]
+    return concat(*gs)
+
+
+def _stored_taus_colours(scene):
+    """tau along the axis and the colour of each Gaussian from the stored (float32) parameters."""
+    y00 = 0.5 / math.sqrt(math.pi)
+    taus = [float(scene.kappa[i]) * math.sqrt(2 * math.pi) * float(scene.scale[i, 0]) for i in range(scene.n)]
+    cols = [np.maximum(scene.sh[i, 0].astype(np.float64) * y00 + 0.5, 0.0) for i in range(scene.n)]
+    return taus, cols
+
+
+def _axis_camera():
+    """One pixel whose centre ray is the optical axis (0, 0, 1) from the centre (0, 0, -4)."""
+    return synth.Camera(np.eye(3, dtype=np.float32), np.array([0.0, 0.0, 4.0], np.float32), 100.0, 100.0, 0.5, 0.5,
+                        1, 1)
+
+
+def _blend_reading8(taus, colours, o, slip=None):
+    """Eq. 14 with the thresholds as read (reading 8), written independently of the oracle: clamp tau
+    at tau_max, skip when the clamped tau < -ln(1 - alpha_min), blend, then stop once T < T_stop.
+    `slip` plants one plausible mistake."""
+    tau_skip = -math.log1p(-o["alpha_min"]) if o["alpha_min"] > 0 else 0.0
+    T, C, n = 1.0, np.zeros(3), 0
+    for t, c in zip(taus, colours):
+        if slip != "no_clamp" and slip != "skip_before_clamp":
+            t = min(t, o["tau_max"])
+        if slip != "no_skip" and t < tau_skip:
+            continue
+        if slip == "skip_before_clamp":
+            t = min(t, o["tau_max"])
+        if slip == "stop_before_blend" and T * math.exp(-t) < o["T_stop"]:
+            break
+        C = C + np.asarray(c) * (-math.expm1(-t)) * T
+        T *= math.exp(-t)
+        n += 1
+        if slip != "no_stop" and T < o["T_stop"]:
+            break
+    return C + T * np.asarray(o["bg"]), T, n
+
+
+def test_volumetric_thresholds_follow_reading_8():
+    """The compat thresholds on one ray through six Gaussians where each rule changes the result:
+    tau 0.002 (skipped: below -ln(1 - 1/255)), 6 (clamped to ln 100), 0.003 (skipped), 3, 2 (blended;
+    T crosses 1e-4 here, so the pixel stops after it), 1.5 (never reached).  The oracle equals the
+    independent blend to 1e-12, and every planted slip of the blend moves the result."""
+    taus = [0.002, 6.0, 0.003, 3.0, 2.0, 1.5]
+    cols = [(0.9, 0.1, 0.1), (0.1, 0.8, 0.2), (0.2, 0.2, 0.9), (0.7, 0.7, 0.1), (0.3, 0.9, 0.6), (0.95, 0.4, 0.05)]
+    o = dict(oracle.COMPAT, tau_cut=1e-6, bg=(0.25, 0.5, 0.75))   # footprints keep even the skipped pairs
+    scene, cam = _on_axis_scene(taus, cols), _axis_camera()
+    taus, cols = _stored_taus_colours(scene)
+    rgb, T, nb = oracle.render(scene, [cam], o)
+    C, Tw, n = _blend_reading8(taus, cols, o)
+    assert n == 3 and nb[0][0, 0] == 3
+    assert np.max(np.abs(rgb[0][0, 0] - C)) < 1e-12 and abs(T[0][0, 0] - Tw) < 1e-15
+    for slip in ("no_clamp", "no_skip", "stop_before_blend", "no_stop"):
+        Cs, Ts, _ = _blend_reading8(taus, cols, o, slip)
+        assert np.max(np.abs(Cs - C)) > 1e-6 or abs(Ts - Tw) > 1e-9, slip
+    # clamp, then skip: with tau_max below the skip threshold every clamped pair is skipped
+    o2 = dict(o, tau_max=0.003)
+    rgb2, T2, nb2 = oracle.render(scene, [cam], o2)
+    C2, T2w, n2 = _blend_reading8(taus, cols, o2)
+    assert n2 == 0 and nb2[0][0, 0] == 0 and T2[0][0, 0] == 1.0
+    assert np.max(np.abs(rgb2[0][0, 0] - C2)) < 1e-12
+    Cs, _, ns = _blend_reading8(taus, cols, o2, "skip_before_clamp")
+    assert ns > 0 and np.max(np.abs(Cs - C2)) > 1e-6
+
+
+def test_early_stop_is_strict():
+    """T_stop ends a pixel only once T < T_stop (strictly): with T_stop set to the oracle's own T
+    after two blends the pixel goes on to blend the third (whose T is below it) and stops there; one
+    ulp above it, it stops after those two."""
+    taus = [1.0, 2.0, 0.5, 0.7]
+    cols = [(0.9, 0.1, 0.1), (0.1, 0.8, 0.2), (0.2, 0.2, 0.9), (0.7, 0.7, 0.1)]
+    scene, cam = _on_axis_scene(taus, cols), _axis_camera()
+    o = dict(oracle.EXACT, tau_cut=1e-6)
+    _, T2, _ = oracle.render(scene.subset([0, 1]), [cam], o)
+    t2 = float(T2[0][0, 0])
+    _, _, nb = oracle.render(scene, [cam], dict(o, T_stop=t2))
+    assert nb[0][0, 0] == 3
+    _, T, nb = oracle.render(scene, [cam], dict(o, T_stop=float(np.nextafter(t2, 1.0))))
+    assert nb[0][0, 0] == 2 and T[0][0, 0] == t2
+
+
 # ------------------------------------------------------------------ gradients
 def _fd_check(f, x, g_an, idx, h_rel=1e-5, rtol=1e-6):
     scale = max(1e-300, float(np.max(np.abs(g_an))))
