@@ -34,7 +34,14 @@ if ROOT not in sys.path:
 METRIC = "fwd+bwd steps/s & frames/s, 1M Gaussians @1280×832, vs plain FP32, % of pipe peak"
 WORKLOAD = "1M Gaussians (64-cluster mixture, 20% flattened, SH deg 3), 1280x832, fwd+bwd, L2 loss, FP32"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SMS, FP32_LANES, MUFU_PER_SM = 152, 128, 16
+SMS = 152
+# HBM-bound stages, algorithmic bytes per Gaussian of the FP32 workload (SH degree 3): parameters
+# 236 B (mu 12, scale 12, quat 16, kappa 4, SH 192); the preprocess writes the 96 B blend record and
+# 24 B of keys per item; the chain reads the parameters and the 64 B accumulator and writes 236 B of
+# gradients
+PARAM_BYTES = 236
+PRE_WRITE_BYTES = 120
+CHAIN_ACC_BYTES = 64
 # Algorithmic FP32 work, FMA counted as 2 and each transcendental (rsqrt, exp2) as 1:
 # evaluating the closed-form tau of one (pixel, Gaussian) pair (d' and o' x d' from the pixel
 # offset, both squared norms, rsqrt, exponent, exp2), then for pairs with tau >= tau_skip the
@@ -43,7 +50,15 @@ SMS, FP32_LANES, MUFU_PER_SM = 152, 128, 16
 FLOPS_EVAL_PAIR = 44
 FLOPS_FWD_BLEND = 12
 FLOPS_BWD_BLEND = 64
-CPU_SAMPLE_TILES = 96
+# of which transcendental-unit (MUFU) operations: rsqrt and ex2 per evaluated pair; the ex2 of
+# alpha (and, in the backward, of the replayed transmittance) per blended pair
+XU_EVAL_PAIR = 2
+XU_FWD_BLEND = 1
+XU_BWD_BLEND = 2
+# the CPU baseline's bounded sample: the same seeded tiles in the GPU arm's cpu_baseline and in
+# every step of --impl reference
+CPU_SAMPLE_TILES = 64
+CPU_SAMPLE_SEED = 5
 
 
 def log(*a):
@@ -148,6 +163,28 @@ def peaks():
         return json.load(open(PEAKS_PATH))
     except Exception:
         return {}
+
+
+# ----------------------------------------------------------------------------- pipe peaks
+def measure_pipe_peaks(vg, gpu_id, min_ms=50.0):
+    """Measured FP32 FMA and ex2 (MUFU) rates of this GPU (vg_pipe_peak) with the SM clock sampled
+    during the measurement: the denominators of the blend kernels' roofline."""
+    ws = vg.Workspace()
+    clk = ClockSampler(gpu_id)
+    clk.start()
+    fma, fma_ms = ws.pipe_peak("fma", min_ms)
+    ex2, ex2_ms = ws.pipe_peak("ex2", min_ms)
+    fma2, _ = ws.pipe_peak("fma", min_ms)   # again, after the ex2 run: the clock may have moved
+    c = clk.stop()
+    fma = max(fma, fma2)
+    out = {"fma_tflops": 2.0 * fma / 1e12, "ex2_tops": ex2 / 1e12, "fma_launch_ms": fma_ms, "ex2_launch_ms": ex2_ms,
+           "clocks": c, "method": "vg_pipe_peak: 8 independent FMA (or ex2.approx) chains per thread, grid at the "
+                                  "occupancy limit on every SM, fastest of 3 event-timed launches"}
+    if c and c.get("sm_mhz"):
+        mhz = c["sm_mhz"]
+        out["fma_per_sm_per_clk"] = fma / (SMS * mhz * 1e6)
+        out["ex2_per_sm_per_clk"] = ex2 / (SMS * mhz * 1e6)
+    return out
 
 
 # ----------------------------------------------------------------------------- cone beam
@@ -635,31 +672,53 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel (the backward blend), measured live
+    # ---- roofline of the dominant kernel (the backward blend), measured live, against the
+    # measured FMA and ex2 rates of this GPU
     calls_bwd, ms_bwd = stages_timed.get("render_bwd", (0, 0.0))
-    dominant = "render_bwd"
     per_launch_s = (ms_bwd / max(1, calls_bwd)) / 1e3
-    flops = q["n_pairs_bwd"] * FLOPS_EVAL_PAIR + q["n_blend_bwd"] * FLOPS_BWD_BLEND
-    achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else None
-    pk = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    peak_tf = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    pp = measure_pipe_peaks(vg, gpu_id)
     traffic = traffic_record()
-    roofline = {"bound": "alu", "kernel": "k_render_bwd", "achieved": achieved, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": (achieved / peak_tf) if achieved else None, "traffic": traffic,
-                "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
-                "pairs_per_launch": q["n_pairs_bwd"], "blended_pairs_per_launch": q["n_blend_bwd"],
-                "flops_per_launch": flops,
-                "flops_basis": f"{FLOPS_EVAL_PAIR} per evaluated pair + {FLOPS_BWD_BLEND} per blended pair",
-                "launch_ms": per_launch_s * 1e3}
-    if clk and clk.get("sm_mhz"):
-        roofline["frac_at_observed_clock"] = achieved / (peak_tf * clk["sm_mhz"] / sm_max) if achieved else None
+
+    def alu_roofline(kernel, pairs, blended, f_blend, xu_blend, t_s):
+        flops = pairs * FLOPS_EVAL_PAIR + blended * f_blend
+        xu = pairs * XU_EVAL_PAIR + blended * xu_blend
+        fma_flops = flops - xu               # FP32-pipe work: FMA = 2 flop, other FP32 operations 1
+        ach = fma_flops / t_s / 1e12 if t_s > 0 else None
+        xu_rate = xu / t_s / 1e12 if t_s > 0 else None
+        return {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": pp["fma_tflops"], "unit": "TFLOP/s",
+                "frac": ach / pp["fma_tflops"] if ach else None,
+                "peak_basis": "measured FP32 FMA rate x 2 flop (vg_pipe_peak, clocks in pipe_peaks)",
+                "xu": {"achieved_tops": xu_rate, "peak_tops": pp["ex2_tops"],
+                       "frac": xu_rate / pp["ex2_tops"] if xu_rate else None,
+                       "basis": "rsqrt + ex2 per evaluated pair, ex2 per blended pair (x2 in the backward) "
+                                "against the measured ex2 rate"},
+                "pairs_per_launch": pairs, "blended_pairs_per_launch": blended, "flops_per_launch": flops,
+                "fma_pipe_flops_per_launch": fma_flops, "xu_ops_per_launch": xu,
+                "flops_basis": f"{FLOPS_EVAL_PAIR} per evaluated pair + {f_blend} per blended pair (FMA = 2, "
+                               f"transcendental = 1; {XU_EVAL_PAIR} + {xu_blend} of them on the MUFU)",
+                "launch_ms": t_s * 1e3}
+
+    roofline = alu_roofline("k_render_bwd", q["n_pairs_bwd"], q["n_blend_bwd"], FLOPS_BWD_BLEND, XU_BWD_BLEND,
+                            per_launch_s)
+    roofline["traffic"] = traffic
+    hbm_peak = float(peaks().get("hbm_gbs", 6788.6))
+
+    def hbm_roofline(stage, nbytes):
+        calls, ms_tot = stages.get(stage, (0, 0.0))
+        if not calls or ms_tot <= 0:
+            return None
+        gbs = nbytes / (ms_tot / calls / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "bytes_per_launch": nbytes, "launch_ms": ms_tot / calls,
+                "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy)"}
+
+    roofline_hbm = {"k_preprocess": hbm_roofline("preprocess", g.n * (PARAM_BYTES + PRE_WRITE_BYTES)),
+                    "k_chain": hbm_roofline("chain", g.n * (2 * PARAM_BYTES + CHAIN_ACC_BYTES))}
 
     stage_ms = {k: round(v[1] / max(1, v[0]), 4) for k, v in stages.items()}
-    fwd_pairs = q["n_pairs"]
     calls_f, ms_f = stages.get("render_fwd", (0, 0.0))
-    fwd_flops = fwd_pairs * FLOPS_EVAL_PAIR + q["n_blend"] * FLOPS_FWD_BLEND
-    fwd_tf = fwd_flops / ((ms_f / max(1, calls_f)) / 1e3) / 1e12 if ms_f > 0 else None
+    fwd_roof = alu_roofline("k_render_fwd", q["n_pairs"], q["n_blend"], FLOPS_FWD_BLEND, XU_FWD_BLEND,
+                            (ms_f / max(1, calls_f)) / 1e3)
 
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -674,7 +733,9 @@ def run_ours(args):
         "stages_basis": "event-timed per stage over a separate pass of the same steps; inside the timed "
                         "region only k_render_bwd is bracketed by events",
         "roofline": roofline,
-        "fwd_blend_tflops": fwd_tf,
+        "roofline_fwd": fwd_roof,
+        "roofline_hbm": roofline_hbm,
+        "pipe_peaks": pp,
         "counts": {"visible": q["n_visible"], "instances": q["n_instances"], "pairs_fwd": q["n_pairs"],
                    "blend_fwd": q["n_blend"], "pairs_bwd": q["n_pairs_bwd"], "blend_bwd": q["n_blend_bwd"],
                    "workspace_bytes": q["device_bytes"]},
@@ -820,13 +881,20 @@ def oracle_step(scene, cams, target, n_sample, seed, oracle):
 
 
 def cpu_baseline(scene, cams, target, n_sample=CPU_SAMPLE_TILES):
+    """The oracle on the fixed seeded tile sample, on all host cores and on one core."""
     import oracle
 
-    est, wall, k, n_tiles = oracle_step(scene, cams, target, n_sample, 5, oracle)
-    return {"value": 1.0 / est, "unit": "steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.set_threads(0)
+    est, wall, k, n_tiles = oracle_step(scene, cams, target, n_sample, CPU_SAMPLE_SEED, oracle)
+    oracle.set_threads(1)
+    est1, wall1, _, _ = oracle_step(scene, cams, target, n_sample, CPU_SAMPLE_SEED, oracle)
+    oracle.set_threads(0)
+    return {"value": 1.0 / est, "unit": "steps/s", "cores": cores, "kind": "oracle", "extrapolated": True,
             "sample": f"FP64 oracle: keys+binning of all {scene.n} Gaussians, forward+gradient on {k} of "
-                      f"{n_tiles} tiles (seeded), per-tile time extrapolated to the full frame; "
-                      f"{wall:.1f} s wall for the sample"}
+                      f"{n_tiles} tiles (seed {CPU_SAMPLE_SEED}, the sample of --impl reference), per-tile time "
+                      f"extrapolated to the full frame; {wall:.1f} s wall for the sample",
+            "single_core": {"value": 1.0 / est1, "unit": "steps/s", "cores": 1, "extrapolated": True,
+                            "sample_wall_s": wall1}}
 
 
 def run_reference(args):
@@ -837,13 +905,14 @@ def run_reference(args):
     import oracle
 
     oracle.build()
+    cores = oracle.set_threads(0)
     scene, cams, target = make_workload(args.frac)
     for w in range(args.warmup):
         oracle_step(scene, cams, target, 8, 100 + w, oracle)
     ests = []
     t0 = time.perf_counter()
     for k in range(args.steps):
-        est, _, _, n_tiles = oracle_step(scene, cams, target, 16, 200 + k, oracle)
+        est, _, n_pick, n_tiles = oracle_step(scene, cams, target, CPU_SAMPLE_TILES, CPU_SAMPLE_SEED, oracle)
         ests.append(est)
     wall = time.perf_counter() - t0
     value = args.steps / sum(ests)
@@ -852,10 +921,12 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "gaussians": scene.n, "width": cams[0].width,
                       "height": cams[0].height, "frac": args.frac},
-           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                            "extrapolated": True,
                             "sample": f"each step: keys+binning of all {scene.n} Gaussians, forward+gradient "
-                                      f"on 16 seeded tiles of {n_tiles}, extrapolated to the full frame; "
-                                      f"{wall:.1f} s wall in total"},
+                                      f"on the same {n_pick} tiles of {n_tiles} (seed {CPU_SAMPLE_SEED}, the GPU "
+                                      f"arm's cpu_baseline sample), extrapolated to the full frame; ms_per_step is "
+                                      f"that extrapolation; {wall:.1f} s wall for all {args.steps} sampled steps"},
            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

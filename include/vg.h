@@ -245,8 +245,12 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
  *    larger requests return VG_ERR_INVALID_ARG and launch nothing.
  *  - The array (VG_NOALLOC_MAX_ITEMS x 64 bytes = 4 MiB) is a static device allocation of
  *    the library: every GPU that loads the library holds it until the process exits.
- *  - The first call on a device looks up the array's device address with that device
- *    current; make that first call before any stream capture.
+ *  - Every call looks up the array's device address in the current context (no allocation),
+ *    so the address stays valid after cudaDeviceReset.  The first call on a device, and the
+ *    first after a cudaDeviceReset, loads the library's module onto it: make that call before
+ *    any stream capture.
+ *  - VG_FLAG_COUNT_PAIRS and the stage profiler ("render_bwd", "chain") work as in
+ *    vg_render_bwd; the pair counters are the workspace's own.
  *  - Every call shares the one array.  Each call clears the part it uses before
  *    accumulating, but calls whose work overlaps on the GPU (different streams or
  *    workspaces in flight at once) race on it: serialise them.
@@ -256,6 +260,25 @@ vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_
 vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const float *dL_dT,
                                 float *dmu, float *dscale, float *dquat, float *dkappa,
                                 float *dsh, void *stream);
+
+/* Measured pipe peaks, the denominators of the blend and tomography kernels' roofline
+ * (synchronous; allocates nothing).  pipe 0: FP32 FMA instructions per second (one FFMA = 2 flop);
+ * pipe 1: ex2.approx instructions per second (the transcendental unit the closed-form opacity
+ * uses).  Every thread of a grid at the occupancy limit on every SM runs 8 independent
+ * dependency chains with no memory traffic; after a warm-up, three launches of about min_ms each
+ * (0 < min_ms <= 10000) are event-timed on `stream` and the fastest is returned in *ops_per_s
+ * (lane operations per second) and its duration in *ms (may be NULL).  The SM clock during the
+ * run is the caller's to sample. */
+vg_status vg_pipe_peak(vg_workspace *ws, int32_t pipe, float min_ms, double *ops_per_s, float *ms, void *stream);
+
+/* Failure-path check of the bounded device waits (no counterpart in the paper: it tests the
+ * library's own failure detection).  Runs one look-back wait of the binning -- which = 0: the
+ * instance scan's warp-cooperative walk, 1: a radix pass's walk -- whose predecessor never
+ * publishes its status, with a limit of spin_limit polls (1..2^20; a few dozen take
+ * microseconds).  The wait gives up, latches VG_ERR_TIMEOUT in the workspace and the kernel
+ * returns; the next vg_query reports the timeout (and clears it) and the workspace stays usable.
+ * Uses the workspace's scan scratch; nothing a later call reads is left changed. */
+vg_status vg_selftest_timeout(vg_workspace *ws, int32_t which, int32_t spin_limit, void *stream);
 
 /* Tomography (Sec. 6.2, Eq. 21): for every angle and detector pixel,
  *   proj[a][j][i] = exp(-sum_g tau_g(ray)),  float32 device buffer [n_angles][det_h][det_w].

@@ -149,12 +149,19 @@ def lib():
         L.orc_voxel_density.restype = None
         L.orc_voxel_density.argtypes = [i32, P, P, P, P, P, i32, P, P, P, P, P]
         L.orc_num_threads.restype = i32
+        L.orc_set_threads.restype = i32
+        L.orc_set_threads.argtypes = [i32]
         _LIB = L
     return _LIB
 
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's later calls (n < 1: all cores); returns the count in use."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _p(a):

@@ -46,6 +46,18 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the following parallel regions (n < 1: all cores); returns the count now in use. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* =============================== FP32 key function =============================== */
 
 /* Validity, unit quaternion, rotation and world covariance Sigma = R S^2 R^T, all FP32. */

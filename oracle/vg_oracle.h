@@ -117,6 +117,7 @@ void orc_tomo_grad(int n, const double *mu, const double *scale, const double *q
                    const double *dL_dproj, const int32_t *pix_mask, double *dmu, double *dscale, double *dquat, double *dkappa);
 
 int orc_num_threads(void);
+int orc_set_threads(int n);   /* threads of later parallel regions (n < 1: all cores) */
 
 #ifdef __cplusplus
 }

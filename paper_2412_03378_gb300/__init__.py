@@ -111,6 +111,9 @@ _SIGS = {
     "vg_profile_read": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "vg_read_bins": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_read_pixel_state": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "vg_selftest_timeout": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p],
+    "vg_pipe_peak": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
+                     ctypes.c_void_p],
     "vg_read_bins_range": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                            ctypes.c_int64, ctypes.c_void_p],
 }
@@ -300,6 +303,19 @@ class Workspace:
         """vg_render_bwd_noalloc: the backward without any device allocation (see vg.h)."""
         self._chk(self._L.vg_render_bwd_noalloc(self.h, _ptr(dL_drgb), _ptr(dL_dT), _ptr(dmu), _ptr(dscale),
                                                 _ptr(dquat), _ptr(dkappa), _ptr(dsh), _stream(stream)))
+
+    def pipe_peak(self, pipe, min_ms=50.0, stream=None):
+        """Measured peak of one pipe ("fma": FP32 FMA instructions/s, "ex2": ex2 instructions/s,
+        per lane) and the duration of the timed launch in ms (see vg_pipe_peak)."""
+        r, ms = ctypes.c_double(0.0), ctypes.c_float(0.0)
+        self._chk(self._L.vg_pipe_peak(self.h, {"fma": 0, "ex2": 1}[pipe], float(min_ms), ctypes.byref(r),
+                                       ctypes.byref(ms), _stream(stream)))
+        return r.value, ms.value
+
+    def selftest_timeout(self, which=0, spin_limit=64, stream=None):
+        """Run one bounded look-back wait that must give up (see vg_selftest_timeout); the next
+        query() raises VGError with VG_ERR_TIMEOUT."""
+        self._chk(self._L.vg_selftest_timeout(self.h, int(which), int(spin_limit), _stream(stream)))
 
     def project_tomo(self, g: Gaussians, beam, opts: Opts, proj, dL_dproj=None, dmu=None, dscale=None, dquat=None,
                      dkappa=None, stream=None):

@@ -4,7 +4,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -311,6 +310,7 @@ static vg_status latched_status(vg_workspace *ws, cudaStream_t st) {
     const uint32_t e = ws->h_total[2];
     if (e == 0) return VG_OK;
     ws->h_total[2] = 0;
+    ws->grad_zero_n = 0;   // after a device-side failure the next backward clears its accumulator
     cudaMemsetAsync(lookback_err_ptr(ws), 0, sizeof(uint32_t), st);
     if (e & kDevErrTimeout) return fail(ws, VG_ERR_TIMEOUT, "a look-back wait of the scan or sort timed out");
     return fail(ws, VG_ERR_CAPACITY, "more (tile, Gaussian) instances than the fixed capacity");
@@ -763,27 +763,19 @@ vg_status vg_query_density(vg_workspace *ws, const vg_gaussians *g, const vg_gri
 // The per-item gradient accumulator of vg_render_bwd_noalloc: a fixed array that the
 // library's module brings onto every device it is loaded on.  Host code must not pass the
 // symbol itself to a kernel (in host code it names a host-side stand-in); the device
-// address comes from cudaGetSymbolAddress, looked up once per device.
+// address comes from cudaGetSymbolAddress, looked up in the current context on every call.
 static __device__ __align__(256) float g_noalloc_acc[(size_t)VG_NOALLOC_MAX_ITEMS * kGradN];
 
 namespace {
-std::mutex g_noalloc_mu;
-constexpr int kNoallocMaxDevices = 64;
-float *g_noalloc_ptr[kNoallocMaxDevices] = {};
-
+// The array's device address in the current context.  cudaGetSymbolAddress allocates nothing; it
+// is called on every call, so the address stays right after cudaDeviceReset (which unloads the
+// module: the next call loads it again, with the array possibly elsewhere).
 vg_status noalloc_scratch(vg_workspace *ws, float **out) {
-    int dev = -1;
-    VG_CUDA(ws, cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(ws, VG_ERR_UNSUPPORTED, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_acc);
-        if (e != cudaSuccess || !p)
-            return fail(ws, VG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = (float *)p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_acc);
+    if (e != cudaSuccess || !p)
+        return fail(ws, VG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = (float *)p;
     return VG_OK;
 }
 }  // namespace
@@ -803,12 +795,77 @@ vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const fl
     VG_TRY(noalloc_scratch(ws, &acc));
     // the array keeps the previous call's sums: clear the part this call accumulates into
     if (ws->n_items > 0) VG_CUDA(ws, cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st));
-    VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
-                                  ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_bwd, ws->T_fin.p,
-                                  ws->S_fin.p,
-                                  ws->nlast.p, dL_drgb, dL_dT, acc, nullptr, st, &ws->launches));
-    VG_CUDA(ws, launch_chain(ws->g, ws->views.p, ws->n_views, acc, (ws->opts.flags & VG_FLAG_GRAD_ZERO) ? 1 : 0, dmu,
-                             dscale, dquat, dkappa, dsh, st, &ws->launches));
+    unsigned long long *pc = nullptr;   // the workspace's own counters: nothing is allocated for them
+    if (ws->opts.flags & VG_FLAG_COUNT_PAIRS) {
+        pc = ws->counters.p + 3;
+        VG_CUDA(ws, cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), st));
+    }
+    {
+        ProfScope ps(ws, ST_BWD, st);
+        VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
+                                      ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_bwd,
+                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, acc, pc, st,
+                                      &ws->launches));
+    }
+    {
+        ProfScope ps(ws, ST_CHAIN, st);
+        VG_CUDA(ws, launch_chain(ws->g, ws->views.p, ws->n_views, acc, (ws->opts.flags & VG_FLAG_GRAD_ZERO) ? 1 : 0,
+                                 dmu, dscale, dquat, dkappa, dsh, st, &ws->launches));
+    }
+    return VG_OK;
+}
+
+vg_status vg_pipe_peak(vg_workspace *ws, int32_t pipe, float min_ms, double *ops_per_s, float *ms, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if ((pipe != 0 && pipe != 1) || !ops_per_s || !(min_ms > 0.0f) || !(min_ms <= 10000.0f))
+        return fail(ws, VG_ERR_INVALID_ARG, "pipe must be 0 (FMA) or 1 (ex2), min_ms in (0, 10000]");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    VG_CUDA(ws, cudaEventCreate(&a));
+    cudaError_t e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(ws, VG_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    }
+    // one short launch to warm up and size the timed ones, then three timed launches of about
+    // min_ms each; the fastest counts
+    int iters = 64;
+    double ops = 0.0, best = 0.0;
+    float best_ms = 0.0f;
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(a, st);
+        if (e == cudaSuccess) e = launch_pipe_peak(pipe, iters, &ops, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        ws->launches += 1;
+        if (e != cudaSuccess) break;
+        if (r >= 2 && t > 0.0f && ops / (t * 1e-3) > best) {
+            best = ops / (t * 1e-3);
+            best_ms = t;
+        }
+        if (r < 2 && t > 0.0f)   // resize towards min_ms per launch
+            iters = (int)std::min(1.0e8, std::max(16.0, iters * (double)min_ms / t));
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return fail(ws, VG_ERR_CUDA, std::string("pipe peak: ") + cudaGetErrorString(e));
+    *ops_per_s = best;
+    if (ms) *ms = best_ms;
+    return VG_OK;
+}
+
+vg_status vg_selftest_timeout(vg_workspace *ws, int32_t which, int32_t spin_limit, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (which != 0 && which != 1) return fail(ws, VG_ERR_INVALID_ARG, "which must be 0 (scan) or 1 (radix pass)");
+    if (spin_limit < 1 || spin_limit > (1 << 20)) return fail(ws, VG_ERR_INVALID_ARG, "spin_limit must be 1..2^20");
+    cudaStream_t st = (cudaStream_t)stream;
+    VG_TRY(ensure(ws, ws->scan_tmp, 4, "self-test status words"));
+    // a predecessor that never publishes: its status word stays zero for the whole wait
+    VG_CUDA(ws, cudaMemsetAsync(ws->scan_tmp.p, 0, 4 * sizeof(uint32_t), st));
+    VG_CUDA(ws, launch_lookback_selftest(ws->scan_tmp.p, which, spin_limit, lookback_err_ptr(ws), ws->counters.p + 5,
+                                         st, &ws->launches));
     return VG_OK;
 }
 

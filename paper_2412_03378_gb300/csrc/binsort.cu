@@ -35,7 +35,7 @@ constexpr unsigned long long kFlagAgg64 = 1ull << 62, kFlagPre64 = 2ull << 62, k
 constexpr int kLookWin = VG_LOOK_WIN;
 
 __device__ __forceinline__ uint32_t lookback32(const uint32_t *status, long long tile, int stride, int col,
-                                               uint32_t *err) {
+                                               uint32_t *err, int spin_limit = kSpinLimit) {
     uint32_t prefix = 0;
     for (long long t = tile - 1; t >= 0; t -= kLookWin) {
         uint32_t s[kLookWin];
@@ -44,7 +44,7 @@ __device__ __forceinline__ uint32_t lookback32(const uint32_t *status, long long
 #pragma unroll
         for (int k = 0; k < kLookWin; ++k) {
             for (int spins = 0; (s[k] >> 30) == 0; ++spins) {
-                if (spins >= kSpinLimit) {
+                if (spins >= spin_limit) {
                     atomicOr(err, kErrTimeout);
                     return prefix;
                 }
@@ -61,7 +61,7 @@ __device__ __forceinline__ uint32_t lookback32(const uint32_t *status, long long
 // round trip covers 32 predecessors; the walk stops at the nearest inclusive prefix once every
 // tile up to it has published.
 __device__ __forceinline__ unsigned long long warp_lookback64(const unsigned long long *status, long long tile,
-                                                              uint32_t *err) {
+                                                              uint32_t *err, int spin_limit = kSpinLimit) {
     const int lane = threadIdx.x & 31;
     unsigned long long prefix = 0;
     for (long long t = tile - 1; t >= 0; t -= 32) {
@@ -73,7 +73,7 @@ __device__ __forceinline__ unsigned long long warp_lookback64(const unsigned lon
             need = pre ? ((pre & (0u - pre)) << 1) - 1u : 0xffffffffu;   // lanes up to the nearest prefix
             const unsigned waiting = __ballot_sync(0xffffffffu, (s >> 62) == 0) & need;
             if (waiting == 0) break;
-            if (spins >= kSpinLimit) {
+            if (spins >= spin_limit) {
                 if (lane == 0) atomicOr(err, kErrTimeout);
                 break;
             }
@@ -571,6 +571,29 @@ cudaError_t launch_l2_loss_acc(const float *x, const float *y, long long n, floa
     if (b > 152 * 8) b = 152 * 8;
     if (b < 1) b = 1;
     pdl_launch(k_l2_loss, (unsigned)b, 256, 0, st, x, y, n, scale, loss, grad);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- bounded-wait self-test
+// One look-back of tile 1 over a status array whose tile 0 never publishes (all words zero), with
+// a spin limit of `spin_limit` polls: the wait gives up, latches kErrTimeout in *err and returns.
+// which = 0: the scan's warp-cooperative walk (64-bit status); 1: the radix pass's walk (32-bit).
+__global__ void k_lookback_selftest(const unsigned long long *status64, const uint32_t *status32, int which,
+                                    int spin_limit, uint32_t *err, unsigned long long *out) {
+    pdl_entry();
+    unsigned long long v;
+    if (which == 0)
+        v = warp_lookback64(status64, 1, err, spin_limit);
+    else
+        v = lookback32(status32, 1, 1, 0, err, spin_limit);
+    if (threadIdx.x == 0) *out = v;
+}
+
+cudaError_t launch_lookback_selftest(void *status, int which, int spin_limit, uint32_t *err, unsigned long long *out,
+                                     cudaStream_t st, long long *launches) {
+    pdl_launch(k_lookback_selftest, 1, which == 0 ? 32 : 1, 0, st, (const unsigned long long *)status,
+               (const uint32_t *)status, which, spin_limit, err, out);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -146,6 +146,15 @@ cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, 
                               uint32_t *scratch, uint32_t *err, uint32_t **keys_out, uint32_t **vals_out,
                               cudaStream_t st, long long *launches);
 
+// A look-back over a status array (4 zero words, device) whose predecessor never publishes, with a
+// spin limit of spin_limit polls; the wait gives up and sets kDevErrTimeout in *err (test path).
+cudaError_t launch_lookback_selftest(void *status, int which, int spin_limit, uint32_t *err, unsigned long long *out,
+                                     cudaStream_t st, long long *launches);
+
+// Pipe-peak microbenchmark (peaks.cu): pipe 0 = FP32 FMA, 1 = ex2 (MUFU); *ops receives the
+// instructions (per lane) one launch executes.
+cudaError_t launch_pipe_peak(int pipe, int iters, double *ops, cudaStream_t st);
+
 // Duplicate items into (tile key, item) instances, in the order given by perm (NULL = item
 // order).  offsets[i] is the first instance slot of the i-th item in that order.
 cudaError_t launch_duplicate(const uint32_t *perm, const uint32_t *offsets, const short4 *rect,

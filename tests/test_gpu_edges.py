@@ -176,3 +176,19 @@ def test_workspace_reuse_growing_and_shrinking_lists(gpu_lib):
         assert np.max(np.abs(T - flat(ref_T))) < IMG_TOL
         counts.append(ws.query()["n_instances"])
     assert counts[1] > counts[0] and counts[2] == counts[0]
+
+
+def test_pipe_peak_microbenchmark(gpu_lib):
+    """vg_pipe_peak's FP32 FMA rate cannot exceed 152 SMs x 128 lanes at the maximum SM clock and a
+    healthy GPU reaches most of it; the ex2 rate is positive and below the FMA rate."""
+    vg = gpu_lib
+    ws = vg.Workspace()
+    fma, ms = ws.pipe_peak("fma", 5.0)
+    ex2, ms2 = ws.pipe_peak("ex2", 5.0)
+    ceiling = 152 * 128 * 2.07e9
+    print(f"FMA {fma / 1e12:.2f} T/s ({fma / ceiling:.3f} of 152 x 128 x 2070 MHz), ex2 {ex2 / 1e12:.2f} T/s")
+    assert 0.3 * ceiling < fma <= 1.01 * ceiling
+    assert 1e11 < ex2 < fma
+    assert ms > 0 and ms2 > 0
+    with pytest.raises(vg.VGError):
+        ws.pipe_peak("fma", 0.0)

@@ -1,11 +1,12 @@
 """Fixed-capacity binning (no host synchronisation) and a whole training step captured in a
-CUDA graph, against the oracle and the eager path."""
+CUDA graph, against the oracle and the eager path; failures reported by the device (capacity
+overflow, a bounded wait that gave up) without a GPU fault."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from gpu_util import check_grads, dev_scene, flat, vg_opts
+from gpu_util import check_grads, dev_scene, flat, run_forward, vg_opts
 
 pytestmark = pytest.mark.gpu
 
@@ -122,3 +123,23 @@ def test_graph_captured_step_matches_eager(gpu_lib, mode):
     ge = {k: eb[k].cpu().numpy().astype(np.float64) for k in ("mu", "scale", "quat", "kappa", "sh")}
     check_grads(gg, ge, scene, 1e-4)
     assert ws.query()["n_instances"] == n_inst
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_wait_gives_up_and_is_reported(gpu_lib, which):
+    """Failure detection of the binning's look-back waits, without a GPU fault: a wait whose
+    predecessor never publishes gives up after a few dozen polls, latches VG_ERR_TIMEOUT and
+    returns; vg_query reports it once, and the workspace then renders as before (bit for bit)."""
+    vg = gpu_lib
+    scene, cams = synth.config1(0.25)
+    o = oracle.EXACT
+    ws, g, rgb0, T0 = run_forward(vg, scene, cams, o)
+    ws.selftest_timeout(which, spin_limit=48)
+    with pytest.raises(vg.VGError) as ei:
+        ws.query()
+    assert ei.value.status == 5 and "timed out" in str(ei.value)
+    assert ws.query()["n_items"] == scene.n          # reported once, then cleared
+    _, _, rgb1, T1 = run_forward(vg, scene, cams, o, ws=ws, g=g)
+    assert np.array_equal(rgb0, rgb1) and np.array_equal(T0, T1)
+    with pytest.raises(vg.VGError):
+        ws.selftest_timeout(which, spin_limit=0)    # rejected on the host, nothing launched
