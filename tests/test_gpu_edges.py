@@ -147,7 +147,7 @@ def test_stage_profiler_mask(gpu_lib):
         if stages:
             assert set(rec) == {"render_bwd"} and rec["render_bwd"][0] == 2
         else:
-            assert {"preprocess", "depth_sort", "tile_sort", "render_fwd", "render_bwd", "chain"} <= set(rec)
+            assert {"preprocess", "depth_sort", "scan", "duplicate", "tile_sort", "render_fwd", "render_bwd", "chain"} <= set(rec)
             assert all(c == 2 for c, _ in rec.values())
     assert np.array_equal(images[0], images[1])
     with pytest.raises(ValueError):

@@ -274,8 +274,8 @@ def test_reduced_precision_storage(gpu_lib, rec_dtype, sh_dtype):
 
 @pytest.mark.parametrize("mode", ["exact", "compat"])
 def test_bins_many_sort_tiles(gpu_lib, mode):
-    """50,000 Gaussians at 1280x832: the depth sort, the instance scan and the tile sort span
-    dozens of look-back tiles; keys, per-tile ranges and lists stay bit-exact."""
+    """50,000 Gaussians at 1280x832: the tile counts, their scan (dozens of look-back tiles),
+    the placement and the per-tile sorts; keys, per-tile ranges and lists stay bit-exact."""
     vg = gpu_lib
     scene, cams, _ = synth.config2(0.05)
     o = oracle.EXACT if mode == "exact" else oracle.COMPAT
@@ -292,6 +292,26 @@ def test_bins_many_sort_tiles(gpu_lib, mode):
     assert len(items) > 20 * 2048
     assert np.array_equal(ts, L["tile_start"])
     assert np.array_equal(items, L["sorted_g"])
+
+
+@pytest.mark.parametrize("n", [12000, 30000])
+def test_long_tile_lists(gpu_lib, n):
+    """Long lists: n Gaussians crowded onto the centre tile of a 48x40 view (9,000 and 23,000
+    instances in one tile, most of the same few depth-key bits); the lists stay bit-exact and the
+    image matches the oracle."""
+    vg = gpu_lib
+    rng = np.random.default_rng(n)
+    scene = synth.uniform_scene(n, n + 1, log_scale=(-5.0, -4.0), kappa=(0.05, 0.5), extent=1.0)
+    scene.mu = (rng.normal(size=(n, 3)) * np.array([0.02, 0.02, 0.5])).astype(np.float32)
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 48, 40, 60.0)
+    o = dict(oracle.EXACT, bg=(0.1, 0.2, 0.3))
+    ws, g, rgb, T = run_forward(vg, scene, [cam], o)
+    ts, items = ws.read_bins()
+    L = oracle.lists(scene, [cam], o)
+    assert np.diff(L["tile_start"]).max() > 8192 * (1 if n < 20000 else 2)
+    assert np.array_equal(ts, L["tile_start"]) and np.array_equal(items, L["sorted_g"])
+    ref_rgb, ref_T, _ = oracle.render(scene, [cam], o, L=L)
+    assert np.max(np.abs(rgb - flat(ref_rgb))) < IMG_TOL
 
 
 def test_autotune_keeps_results(gpu_lib):
