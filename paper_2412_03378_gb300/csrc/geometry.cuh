@@ -2,6 +2,8 @@
 // backward chain kernel, so that both see bit-identical records.
 #pragma once
 
+#include <type_traits>
+
 #include <float.h>
 
 #include "vg_internal.cuh"
@@ -658,6 +660,70 @@ __device__ __forceinline__ void warp_store_rows(float *dst, int rows, int w, con
     for (uint32_t e = lane; e < total; e += 32) {
         const uint32_t r = (e * inv) >> 20, c = e - r * (uint32_t)w;
         dst[e] = buf[r * (uint32_t)stride + c];
+    }
+}
+
+// FP32 rows of degree-3 SH (48 floats = 12 x 16 bytes per Gaussian) in 16-byte pieces: a warp's
+// 32 rows are one contiguous 6,144-byte block, copied piece by piece with consecutive lanes on
+// consecutive pieces (coalesced), into rows of kRow16 float4 -- an odd count, so that 8 lanes
+// reading their own rows' piece j with 128-bit loads hit 8 different bank groups.
+constexpr int kRow16 = 13;
+constexpr int kSh3Pieces = 12;   // 16-byte pieces of one degree-3 FP32 SH row
+
+// piece c of the block: row c / 12, piece c % 12 (c < 384: (c * 2731) >> 15 == c / 12)
+__device__ __forceinline__ void sh3_piece(uint32_t c, uint32_t &r, uint32_t &j) {
+    r = (c * 2731u) >> 15;
+    j = c - r * (uint32_t)kSh3Pieces;
+}
+
+// Whether the SH rows of g take the 16-byte path: FP32, degree 3, a 16-byte aligned array.
+template <typename ST>
+inline bool sh3_rows(const GaussIn &g) {
+    return std::is_same<ST, float>::value && g.sh != nullptr && g.sh_degree == 3 &&
+           ((uintptr_t)g.sh & 15u) == 0;
+}
+
+// Asynchronous copies of `rows` rows (src 16-byte aligned); wait with rows_wait() before __syncwarp().
+__device__ __forceinline__ void warp_load_sh3(const float *src, int rows, float4 *buf, int lane) {
+    const uint32_t total = (uint32_t)rows * kSh3Pieces;
+    for (uint32_t c = lane; c < total; c += 32) {
+        uint32_t r, j;
+        sh3_piece(c, r, j);
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(buf + r * kRow16 + j);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src + 4 * c) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void warp_store_sh3(float *dst, int rows, const float4 *buf, int lane) {
+    const uint32_t total = (uint32_t)rows * kSh3Pieces;
+    for (uint32_t c = lane; c < total; c += 32) {
+        uint32_t r, j;
+        sh3_piece(c, r, j);
+        reinterpret_cast<float4 *>(dst)[c] = buf[r * kRow16 + j];
+    }
+}
+
+// the colour of eval_colour_row from a degree-3 row staged by warp_load_sh3, in the same
+// operation order (coefficient k, channel c), read 4 coefficients (three float4) at a time
+__device__ __forceinline__ void eval_colour_sh3(const float4 *row, const float dir[3], float rgb[3], float raw[3],
+                                                float beta = 0.0f) {
+    float Y[16];
+    sh_basis(3, dir[0], dir[1], dir[2], Y);
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 a = row[3 * q], b = row[3 * q + 1], c = row[3 * q + 2];
+        const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) acc[ch] = fmaf(v[3 * kk + ch], Y[4 * q + kk], acc[ch]);
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        raw[ch] = acc[ch];
+        rgb[ch] = colour_act(acc[ch], beta);
     }
 }
 

@@ -1,25 +1,26 @@
 // Per-(view, Gaussian) preprocessing: key function (depth key + conservative tile
 // rectangle), view-dependent colour and the blend record.  One thread per item, a warp per 32
-// consecutive Gaussians of one view; SH rows in and records out go through shared memory so
-// that the HBM traffic (the kernel's bound) is moved by coalesced instructions.
+// consecutive Gaussians of one view.  The SH rows come in through shared memory so that the HBM
+// reads (the kernel's bound) are coalesced: FP32 degree-3 rows (SH3) as 16-byte pieces, other rows
+// element by element.  Each visible item's 96-byte record goes out from registers as six 16-byte
+// stores (records of culled items are never read and are not written).
 #include "geometry.cuh"
 
 namespace vg {
 
 constexpr int kPreWarps = 4;   // warps per CTA; each owns 32 consecutive Gaussians of one view at a time
 
-template <typename RT, typename ST>
+template <typename RT, typename ST, bool SH3>
 __global__ void __launch_bounds__(32 * kPreWarps, 5)
 k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z_near, float tau_cut,
              float4 *__restrict__ rec, uint32_t *__restrict__ depth, uint32_t *__restrict__ count,
              short4 *__restrict__ rect, short4 *__restrict__ prect, unsigned long long *__restrict__ n_visible) {
     pdl_entry();
-    constexpr int kRecStride = 4 * kRecF4 + 1;   // 24 record floats, odd stride
-    __shared__ float sbuf[kPreWarps][32 * kRowStride];   // SH rows
-    __shared__ float srow[kPreWarps][32 * kRecStride];   // record rows
+    // SH rows: kRowStride floats per row, or (SH3) kRow16 float4
+    __shared__ __align__(16) float sbuf[kPreWarps][32 * (SH3 ? 4 * kRow16 : kRowStride)];
     const int lane = threadIdx.x & 31;
-    float *buf = sbuf[threadIdx.x >> 5], *rbuf = srow[threadIdx.x >> 5];
-    float *row = buf + lane * kRowStride, *rrow = rbuf + lane * kRecStride;
+    float *buf = sbuf[threadIdx.x >> 5];
+    float *row = buf + lane * (SH3 ? 4 * kRow16 : kRowStride);
     const int K3 = 3 * (g.sh_degree + 1) * (g.sh_degree + 1);
     const long long per_view = ((long long)g.n + 31) / 32;
     const long long n_chunks = per_view * n_views;
@@ -32,7 +33,10 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
         const long long it = (long long)v * g.n + gi;
         // the SH rows of the warp's Gaussians, coalesced, before (and independent of) the key; the
         // parameter loads are issued before the wait so that both round trips overlap
-        if (g.sh) warp_load_rows<ST>((const ST *)g.sh + gbase * K3, nloc, K3, buf, lane);
+        if (SH3)
+            warp_load_sh3((const float *)g.sh + gbase * K3, nloc, reinterpret_cast<float4 *>(buf), lane);
+        else if (g.sh)
+            warp_load_rows<ST>((const ST *)g.sh + gbase * K3, nloc, K3, buf, lane);
         float mu[3], s[3], q[4], kin;
         if (lane < nloc) load_gauss<RT>(g, gi, mu, s, q, kin);
         rows_wait();
@@ -53,8 +57,12 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
             if (state == 2) {
                 cnt = (uint32_t)(rc.z - rc.x + 1) * (uint32_t)(rc.w - rc.y + 1);
                 float dir[3], len, rgb[3] = {0.0f, 0.0f, 0.0f}, raw[3];
+                float rrow[4 * kRecF4];
                 view_dir(V, mu, dir, len);
-                if (g.sh) eval_colour_row(g.sh_degree, row, dir, rgb, raw, g.softplus_beta);   // else density only
+                if (SH3)
+                    eval_colour_sh3(reinterpret_cast<const float4 *>(row), dir, rgb, raw, g.softplus_beta);
+                else if (g.sh)
+                    eval_colour_row(g.sh_degree, row, dir, rgb, raw, g.softplus_beta);   // else density only
                 if (g.splat) {
                     SplatGeom SG;
                     if (splat_geom(V, mu, s, Rq, g.splat_dil, SG)) {
@@ -79,6 +87,10 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
                 rrow[21] = rgb[0];
                 rrow[22] = rgb[1];
                 rrow[23] = rgb[2];
+                float4 *dst = rec + it * kRecF4;
+#pragma unroll
+                for (int k = 0; k < kRecF4; ++k)
+                    dst[k] = make_float4(rrow[4 * k], rrow[4 * k + 1], rrow[4 * k + 2], rrow[4 * k + 3]);
             } else {
                 rc = make_short4(-1, -1, -1, -1);
                 prc = rc;
@@ -88,11 +100,6 @@ k_preprocess(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float z
             rect[it] = rc;
             prect[it] = prc;
         }
-        __syncwarp();
-        // records of the warp's items are contiguous: write them coalesced (rows of invisible
-        // items carry stale values that no tile list references)
-        warp_store_rows((float *)(rec + ((long long)v * g.n + gbase) * kRecF4), nloc, 4 * kRecF4, rbuf, lane,
-                        kRecStride);
         const unsigned vis = __ballot_sync(0xffffffffu, state == 2);
         if (lane == 0 && vis) atomicAdd(n_visible, (unsigned long long)__popc(vis));
         __syncwarp();   // the buffer is reused by the next chunk
@@ -107,8 +114,13 @@ static cudaError_t launch_pre_t(const GaussIn &g, const ViewInfo *views_d, int n
     long long blocks = (chunks + kPreWarps - 1) / kPreWarps;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
-    pdl_launch(k_preprocess<RT, ST>, (unsigned)blocks, 32 * kPreWarps, 0, st, g, views_d, n_views, z_near, tau_cut, rec,
-                                                                      depth, count, rect, prect, n_visible);
+    // FP32 degree-3 SH rows of a 16-byte aligned array: 16-byte copies
+    if (sh3_rows<ST>(g))
+        pdl_launch(k_preprocess<RT, ST, true>, (unsigned)blocks, 32 * kPreWarps, 0, st, g, views_d, n_views, z_near,
+                   tau_cut, rec, depth, count, rect, prect, n_visible);
+    else
+        pdl_launch(k_preprocess<RT, ST, false>, (unsigned)blocks, 32 * kPreWarps, 0, st, g, views_d, n_views, z_near,
+                   tau_cut, rec, depth, count, rect, prect, n_visible);
     return cudaGetLastError();
 }
 

@@ -436,28 +436,42 @@ __device__ __forceinline__ void splat_chain(const ViewInfo &V, const float mu[3]
 // SH-gradient rows accumulated and written, through shared memory with coalesced instructions.
 constexpr int kChainWarps = 2;
 
-template <typename RT, typename ST, bool SPLAT>
+template <typename RT, typename ST, bool SPLAT, bool SH3>
 __global__ void __launch_bounds__(32 * kChainWarps, 8)
 k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float *__restrict__ grad_acc, int zero,
         float *__restrict__ dmu, float *__restrict__ dscale, float *__restrict__ dquat, float *__restrict__ dkappa,
         float *__restrict__ dsh) {
     pdl_entry();
-    __shared__ float ssh[kChainWarps][32 * kRowStride];    // SH coefficients, as float
-    __shared__ float sdsh[kChainWarps][32 * kRowStride];   // SH gradient being accumulated
+    // SH coefficients (as float) and the SH gradient being accumulated: kRowStride floats per row,
+    // or (SH3: FP32 degree-3 rows and a 16-byte aligned dsh) kRow16 float4 per row
+    constexpr int kStride = SH3 ? 4 * kRow16 : kRowStride;
+    __shared__ __align__(16) float ssh[kChainWarps][32 * kStride];
+    __shared__ __align__(16) float sdsh[kChainWarps][32 * kStride];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int K = (g.sh_degree + 1) * (g.sh_degree + 1), K3 = 3 * K;
-    float *shrow = ssh[wi] + lane * kRowStride, *dshrow = sdsh[wi] + lane * kRowStride;
+    float *shrow = ssh[wi] + lane * kStride, *dshrow = sdsh[wi] + lane * kStride;
     const long long n_chunks = ((long long)g.n + 31) / 32;
     for (long long ch = (long long)blockIdx.x * kChainWarps + wi; ch < n_chunks; ch += (long long)gridDim.x * kChainWarps) {
         const long long gbase = ch * 32;
         const int nloc = (int)min(32LL, (long long)g.n - gbase);
         const long long gi = gbase + lane;
-        if (g.sh != nullptr) warp_load_rows<ST>((const ST *)g.sh + gbase * K3, nloc, K3, ssh[wi], lane);
-        if (dsh != nullptr) {
+        if (SH3) {
+            warp_load_sh3((const float *)g.sh + gbase * K3, nloc, reinterpret_cast<float4 *>(ssh[wi]), lane);
             if (zero) {
-                for (int k = 0; k < K3; ++k) dshrow[k] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < kSh3Pieces; ++j)
+                    reinterpret_cast<float4 *>(dshrow)[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             } else {
-                warp_load_rows<float>(dsh + gbase * K3, nloc, K3, sdsh[wi], lane);
+                warp_load_sh3(dsh + gbase * K3, nloc, reinterpret_cast<float4 *>(sdsh[wi]), lane);
+            }
+        } else {
+            if (g.sh != nullptr) warp_load_rows<ST>((const ST *)g.sh + gbase * K3, nloc, K3, ssh[wi], lane);
+            if (dsh != nullptr) {
+                if (zero) {
+                    for (int k = 0; k < K3; ++k) dshrow[k] = 0.0f;
+                } else {
+                    warp_load_rows<float>(dsh + gbase * K3, nloc, K3, sdsh[wi], lane);
+                }
             }
         }
         rows_wait();
@@ -583,23 +597,59 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float *__res
             float Y[16];
             sh_basis(g.sh_degree, dir[0], dir[1], dir[2], Y);
             float raw[3] = {0.5f, 0.5f, 0.5f};   // colour before the clamp (same order as eval_colour_row)
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                if (k >= K) break;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) raw[c] = fmaf(shrow[3 * k + c], Y[k], raw[c]);
-            }
             float gc[3], w[16], gd[3];
+            if constexpr (SH3) {
+                const float4 *r4 = reinterpret_cast<const float4 *>(shrow);
+                float4 *d4 = reinterpret_cast<float4 *>(dshrow);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) gc[c] = ga[13 + c] * colour_act_grad(raw[c], g.softplus_beta);
+                for (int qd = 0; qd < 4; ++qd) {   // 4 coefficients (three float4) at a time
+                    const float4 a = r4[3 * qd], b = r4[3 * qd + 1], c = r4[3 * qd + 2];
+                    const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                w[k] = 0.0f;
-                if (k >= K) continue;
+                    for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    w[k] = fmaf(gc[c], shrow[3 * k + c], w[k]);
-                    if (dsh != nullptr) dshrow[3 * k + c] += gc[c] * Y[k];
+                        for (int ch = 0; ch < 3; ++ch) raw[ch] = fmaf(v[3 * kk + ch], Y[4 * qd + kk], raw[ch]);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gc[c] = ga[13 + c] * colour_act_grad(raw[c], g.softplus_beta);
+#pragma unroll
+                for (int qd = 0; qd < 4; ++qd) {
+                    const float4 a = r4[3 * qd], b = r4[3 * qd + 1], c = r4[3 * qd + 2];
+                    const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+                    float4 e[3] = {d4[3 * qd], d4[3 * qd + 1], d4[3 * qd + 2]};
+                    float *ev = reinterpret_cast<float *>(e);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int k = 4 * qd + kk;
+                        w[k] = 0.0f;
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            w[k] = fmaf(gc[ch], v[3 * kk + ch], w[k]);
+                            ev[3 * kk + ch] += gc[ch] * Y[k];
+                        }
+                    }
+                    d4[3 * qd] = e[0];
+                    d4[3 * qd + 1] = e[1];
+                    d4[3 * qd + 2] = e[2];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    if (k >= K) break;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) raw[c] = fmaf(shrow[3 * k + c], Y[k], raw[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gc[c] = ga[13 + c] * colour_act_grad(raw[c], g.softplus_beta);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    w[k] = 0.0f;
+                    if (k >= K) continue;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        w[k] = fmaf(gc[c], shrow[3 * k + c], w[k]);
+                        if (dsh != nullptr) dshrow[3 * k + c] += gc[c] * Y[k];
+                    }
                 }
             }
             sh_grad_dot(g.sh_degree, dir[0], dir[1], dir[2], w, gd);
@@ -643,7 +693,10 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float *__res
         }
         }
         __syncwarp();
-        if (dsh != nullptr) warp_store_rows(dsh + gbase * K3, nloc, K3, sdsh[wi], lane);
+        if (SH3)
+            warp_store_sh3(dsh + gbase * K3, nloc, reinterpret_cast<const float4 *>(sdsh[wi]), lane);
+        else if (dsh != nullptr)
+            warp_store_rows(dsh + gbase * K3, nloc, K3, sdsh[wi], lane);
         __syncwarp();   // the buffers are reused by the next chunk
     }
 }
@@ -654,12 +707,23 @@ static cudaError_t launch_chain_t(const GaussIn &g, const ViewInfo *views_d, int
     long long b = ((long long)g.n + 32 * kChainWarps - 1) / (32 * kChainWarps);
     if (b > 152 * 64) b = 152 * 64;
     if (b < 1) b = 1;
-    if (g.splat)
-        pdl_launch(k_chain<RT, ST, true>, (unsigned)b, 32 * kChainWarps, 0, st, g, views_d, n_views, grad_acc, zero, dmu, dscale,
-                                                                        dquat, dkappa, dsh);
-    else
-        pdl_launch(k_chain<RT, ST, false>, (unsigned)b, 32 * kChainWarps, 0, st, g, views_d, n_views, grad_acc, zero, dmu, dscale,
-                                                                         dquat, dkappa, dsh);
+    // FP32 degree-3 SH rows and a 16-byte aligned SH gradient: 16-byte pieces
+    const bool sh3 = sh3_rows<ST>(g) && dsh != nullptr && ((uintptr_t)dsh & 15u) == 0;
+#define VG_CHAIN_LAUNCH(SPL, S3)                                                                                     \
+    pdl_launch(k_chain<RT, ST, SPL, S3>, (unsigned)b, 32 * kChainWarps, 0, st, g, views_d, n_views, grad_acc, zero, dmu, \
+               dscale, dquat, dkappa, dsh)
+    if (g.splat) {
+        if (sh3)
+            VG_CHAIN_LAUNCH(true, true);
+        else
+            VG_CHAIN_LAUNCH(true, false);
+    } else {
+        if (sh3)
+            VG_CHAIN_LAUNCH(false, true);
+        else
+            VG_CHAIN_LAUNCH(false, false);
+    }
+#undef VG_CHAIN_LAUNCH
     return cudaGetLastError();
 }
 
