@@ -115,6 +115,10 @@ typedef struct {
                              (pixels^2; 0 = Eq. 7 as printed, 0.3 = the 3DGS rasterizer) */
     int32_t chunk;        /* blend kernels: records staged in shared memory per barrier, 64 or 128;
                              0 = the autotuned value, else 128.  Results are identical. */
+    int32_t tile_w, tile_h; /* screen tile in pixels: 16x16, 32x16 or 16x8; 0x0 = the autotuned
+                               shape, else 16x16.  Images and gradients are identical; the
+                               tile lists (and with them the instance count) follow the shape,
+                               each list still in depth order. */
 } vg_opts;
 
 #define VG_FLAG_FIXED_CAPACITY 1u  /* vg_bin_sort never synchronises: the instance count stays
@@ -350,14 +354,20 @@ vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n
 
 /* Autotuner (synchronous; allocates scratch): after vg_bin_sort, times the forward and the
  * backward blend with 1, 2 and 4 pixels per thread (which also sets each warp's pixel box:
- * 8x4, 8x8 or 16x8 pixels) and with 64 and 128 records per staged chunk (the chunk depth) on
- * the binned workload, `reps` timed runs each after one warm-up, and keeps the fastest of each as
- * this workspace's default for vg_opts.pixels_per_thread = 0 and vg_opts.chunk = 0.  The chosen
- * values are written to *ppt_fwd / *ppt_bwd / *chunk_fwd / *chunk_bwd (each may be NULL).  The
- * tile size stays 16x16: it is part of the binning.  Results of the blend do not depend on the
- * choice.  Call vg_render_fwd again before vg_render_bwd. */
+ * 8x4, 8x8 or 16x8 pixels) and with 64 and 128 records per staged chunk (the chunk depth),
+ * `reps` timed runs each after one warm-up, for each tile shape 32x16, 16x16 and 16x8: the
+ * views of the last vg_preprocess are preprocessed and binned again for each shape (binning
+ * timed too, in the form VG_FLAG_FIXED_CAPACITY selects; the instance buffers grow to the
+ * largest count), unless that call fixed vg_opts.tile_w / tile_h, which are then kept.  The
+ * shape with the least binning + forward + backward time and its fastest settings become this
+ * workspace's defaults for vg_opts.pixels_per_thread = 0, vg_opts.chunk = 0 and
+ * vg_opts.tile_w = tile_h = 0, and the workspace is left binned with that shape.  The chosen
+ * values are written to *ppt_fwd / *ppt_bwd / *chunk_fwd / *chunk_bwd / *tile_w / *tile_h (each
+ * may be NULL).  Images and gradients do not depend on the choice; instance counts do (a
+ * fixed capacity reserved for one shape may not hold another's: reserve after tuning).  Call
+ * vg_render_fwd again before vg_render_bwd. */
 vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t *ppt_bwd, int32_t *chunk_fwd,
-                      int32_t *chunk_bwd, void *stream);
+                      int32_t *chunk_bwd, int32_t *tile_w, int32_t *tile_h, void *stream);
 
 /* Statistics of the last calls (synchronises the stream).  *out is filled in every case; the
  * status is the first device-side error latched since the last report (VG_ERR_CAPACITY when

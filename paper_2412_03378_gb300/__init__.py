@@ -64,7 +64,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("alpha_min", ctypes.c_float), ("tau_cut", ctypes.c_float), ("tau_max", ctypes.c_float),
                 ("T_stop", ctypes.c_float), ("bg", ctypes.c_float * 3), ("z_near", ctypes.c_float),
                 ("flags", ctypes.c_uint32), ("pixels_per_thread", ctypes.c_int32), ("softplus_beta", ctypes.c_float),
-                ("splat_dilation", ctypes.c_float), ("chunk", ctypes.c_int32)]
+                ("splat_dilation", ctypes.c_float), ("chunk", ctypes.c_int32), ("tile_w", ctypes.c_int32),
+                ("tile_h", ctypes.c_int32)]
 
 
 class _Grid(ctypes.Structure):
@@ -90,7 +91,7 @@ _SIGS = {
     "vg_workspace_create": [ctypes.c_void_p],
     "vg_workspace_destroy": [ctypes.c_void_p],
     "vg_workspace_reserve": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64],
-    "vg_autotune": [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 5,
+    "vg_autotune": [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 7,
     "vg_preprocess": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                       ctypes.c_void_p],
     "vg_bin_sort": [ctypes.c_void_p, ctypes.c_void_p],
@@ -164,6 +165,8 @@ class Opts:
     softplus_beta: float = 0.0
     splat_dilation: float = 0.0
     chunk: int = 0
+    tile_w: int = 0
+    tile_h: int = 0
 
     @staticmethod
     def exact(**kw):
@@ -186,6 +189,7 @@ class Opts:
         o.softplus_beta = self.softplus_beta
         o.splat_dilation = self.splat_dilation
         o.chunk = self.chunk
+        o.tile_w, o.tile_h = self.tile_w, self.tile_h
         return o
 
 
@@ -276,12 +280,12 @@ class Workspace:
         self._chk(self._L.vg_workspace_reserve(self.h, n_items, n_instances, n_pixels, n_tiles))
 
     def autotune(self, reps=3, stream=None):
-        """Pick pixels per thread and the chunk depth of the blend kernels on the binned workload;
-        returns (ppt_fwd, ppt_bwd, chunk_fwd, chunk_bwd)."""
-        f, b, cf, cb = (ctypes.c_int32(0) for _ in range(4))
-        self._chk(self._L.vg_autotune(self.h, int(reps), ctypes.byref(f), ctypes.byref(b), ctypes.byref(cf),
-                                      ctypes.byref(cb), _stream(stream)))
-        return f.value, b.value, cf.value, cb.value
+        """Pick the tile shape, pixels per thread and the chunk depth of the blend kernels on the
+        binned workload (left binned with the chosen shape); returns
+        (ppt_fwd, ppt_bwd, chunk_fwd, chunk_bwd, tile_w, tile_h)."""
+        v = [ctypes.c_int32(0) for _ in range(6)]
+        self._chk(self._L.vg_autotune(self.h, int(reps), *(ctypes.byref(x) for x in v), _stream(stream)))
+        return tuple(x.value for x in v)
 
     def preprocess(self, g: Gaussians, cams, opts: Opts, stream=None):
         self._keep = (g, _cams_array(cams), opts.c())

@@ -62,6 +62,7 @@ struct vg_workspace {
     int ppt_fwd = 2, ppt_bwd = 1;         // pixels per thread of the blend kernels
     int tuned_fwd = 0, tuned_bwd = 0;     // vg_autotune's choice (0: none yet)
     int tuned_chunk_fwd = 0, tuned_chunk_bwd = 0;
+    int tuned_tw = 0, tuned_th = 0;        // vg_autotune's tile shape (0: none yet)
     uint32_t *h_total = nullptr;         // pinned: [0..1] instance total (u64), [2] look-back timeout flag
     cudaEvent_t total_ev = nullptr;       // recorded after the copy into h_total (binning ahead of it)
     const float *grad_zero_p = nullptr;   // grad.p and the leading floats of it known to be zero
@@ -170,6 +171,8 @@ void release(DBuf<T> &b) {
 }
 
 bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
+// the tile shapes the blend kernels' pixel layouts cover (widths a multiple of 16, heights of 8)
+bool tile_shape_ok(int tw, int th) { return (tw == 16 && th == 16) || (tw == 32 && th == 16) || (tw == 16 && th == 8); }
 
 int bits_for(long long n) {
     int b = 1;
@@ -372,6 +375,10 @@ vg_status vg_workspace_reserve(vg_workspace *ws, int64_t n_items, int64_t n_inst
     return s;
 }
 
+static vg_status upload_views(vg_workspace *ws, const std::vector<ViewInfo> &vh, const std::vector<int> &tv,
+                              cudaStream_t st);
+static vg_status run_preprocess(vg_workspace *ws, cudaStream_t st);
+
 static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams, int32_t n_views,
                                  const vg_opts *opts, void *stream, bool need_sh) {
     if (!ws) return VG_ERR_INVALID_ARG;
@@ -388,6 +395,13 @@ static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const 
         return fail(ws, VG_ERR_INVALID_ARG, "pixels_per_thread must be 0, 1, 2 or 4");
     if (opts->chunk != 0 && opts->chunk != 64 && opts->chunk != 128)
         return fail(ws, VG_ERR_INVALID_ARG, "chunk must be 0, 64 or 128");
+    int tw = opts->tile_w, th = opts->tile_h;
+    if (tw == 0 && th == 0) {
+        tw = ws->tuned_tw ? ws->tuned_tw : kTile;
+        th = ws->tuned_th ? ws->tuned_th : kTile;
+    } else if (!tile_shape_ok(tw, th)) {
+        return fail(ws, VG_ERR_INVALID_ARG, "tile_w x tile_h must be 0 x 0, 16 x 16, 32 x 16 or 16 x 8");
+    }
     const long long n_items = (long long)g->n * n_views;
     if (n_items >= 0xFFFFFFFFLL) return fail(ws, VG_ERR_INVALID_ARG, "views x Gaussians must be < 2^32");
 
@@ -417,8 +431,10 @@ static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const 
         }
         V.W = c.width;
         V.H = c.height;
-        V.tiles_x = (c.width + kTile - 1) / kTile;
-        V.tiles_y = (c.height + kTile - 1) / kTile;
+        V.tw = tw;
+        V.th = th;
+        V.tiles_x = (c.width + tw - 1) / tw;
+        V.tiles_y = (c.height + th - 1) / th;
         if (c.width > 32767 || c.height > 32767) return fail(ws, VG_ERR_INVALID_ARG, "image wider or taller than 32767");
         V.tile_base = (int)tile_base;
         V.pix_base = pix_base;
@@ -442,19 +458,7 @@ static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const 
     ws->g.splat_dil = splat ? opts->splat_dilation : 0.0f;
     ws->tomo_read = false;
     VG_TRY(reserve_items(ws, n_items));
-    VG_TRY(ensure(ws, ws->views, (size_t)n_views, "views"));
-    VG_TRY(ensure(ws, ws->tile_view, (size_t)tile_base, "tile views"));
-    const bool same = ws->views_valid && ws->n_views == n_views && ws->views_h.size() == vh.size() &&
-                      memcmp(ws->views_h.data(), vh.data(), vh.size() * sizeof(ViewInfo)) == 0;
-    if (!same) {
-        // pageable sources: the runtime stages them before returning, so the host vectors
-        // may change afterwards
-        VG_CUDA(ws, cudaMemcpyAsync(ws->views.p, vh.data(), vh.size() * sizeof(ViewInfo), cudaMemcpyHostToDevice, st));
-        VG_CUDA(ws, cudaMemcpyAsync(ws->tile_view.p, tv.data(), tv.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-        ws->views_h = vh;
-        ws->tile_view_h = tv;
-        ws->views_valid = true;
-    }
+    VG_TRY(upload_views(ws, vh, tv, st));
     ws->n_views = n_views;
     ws->n_items = n_items;
     ws->n_tiles = tile_base;
@@ -466,6 +470,7 @@ static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const 
     ws->bp.chunk_fwd = opts->chunk ? opts->chunk : (ws->tuned_chunk_fwd ? ws->tuned_chunk_fwd : kDefaultChunk);
     ws->bp.chunk_bwd = opts->chunk ? opts->chunk : (ws->tuned_chunk_bwd ? ws->tuned_chunk_bwd : kDefaultChunk);
     ws->bp.T_stop = opts->T_stop;
+    ws->bp.tile_px = tw * th;
     for (int c = 0; c < 3; ++c) ws->bp.bg[c] = opts->bg[c];
     ws->bp.pixel_test = ws->bp.tau_skip < opts->tau_cut ? 1 : 0;
     // splat mode: alpha <= min(1 - exp(-tau_max), 1 - 2^-24) keeps 1 - alpha and S = sum tau finite
@@ -473,14 +478,62 @@ static vg_status preprocess_impl(vg_workspace *ws, const vg_gaussians *g, const 
     ws->bp.alpha_min = opts->alpha_min;
     ws->bp.alpha_max = (float)std::min(-std::expm1(-(double)opts->tau_max), 1.0 - 5.9604644775390625e-8);
     if (splat) ws->bp.pixel_test = opts->alpha_min < opts->tau_cut ? 1 : 0;
+    return run_preprocess(ws, st);
+}
+
+// The view table and the tile -> view map on the device (copied only when they changed).
+static vg_status upload_views(vg_workspace *ws, const std::vector<ViewInfo> &vh, const std::vector<int> &tv,
+                              cudaStream_t st) {
+    VG_TRY(ensure(ws, ws->views, vh.size(), "views"));
+    VG_TRY(ensure(ws, ws->tile_view, tv.size(), "tile views"));
+    const bool same = ws->views_valid && ws->views_h.size() == vh.size() &&
+                      memcmp(ws->views_h.data(), vh.data(), vh.size() * sizeof(ViewInfo)) == 0;
+    if (!same) {
+        // pageable sources: the runtime stages them before returning, so the host vectors
+        // may change afterwards
+        VG_CUDA(ws, cudaMemcpyAsync(ws->views.p, vh.data(), vh.size() * sizeof(ViewInfo), cudaMemcpyHostToDevice, st));
+        VG_CUDA(ws, cudaMemcpyAsync(ws->tile_view.p, tv.data(), tv.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        ws->views_h = vh;
+        ws->tile_view_h = tv;
+        ws->views_valid = true;
+    }
+    return VG_OK;
+}
+
+// Per-item records, depth keys and tile footprints of the workspace's Gaussians and views.
+static vg_status run_preprocess(vg_workspace *ws, cudaStream_t st) {
     VG_CUDA(ws, cudaMemsetAsync(ws->counters.p, 0, sizeof(unsigned long long), st));
-    if (n_items > 0) {
+    if (ws->n_items > 0) {
         ProfScope ps(ws, ST_PRE, st);
-        VG_CUDA(ws, launch_preprocess(ws->g, ws->views.p, n_views, opts->z_near, opts->tau_cut, ws->rec.p, ws->depth.p,
-                                      ws->count.p, ws->rect.p, ws->prect.p, ws->counters.p, st, &ws->launches));
+        VG_CUDA(ws, launch_preprocess(ws->g, ws->views.p, ws->n_views, ws->opts.z_near, ws->opts.tau_cut, ws->rec.p,
+                                      ws->depth.p, ws->count.p, ws->rect.p, ws->prect.p, ws->counters.p, st,
+                                      &ws->launches));
     }
     ws->stage = 1;
     return VG_OK;
+}
+
+// The views of the last vg_preprocess cut into tw x th tiles, preprocessed again (the tile
+// footprints depend on the shape; the records do not).
+static vg_status retile(vg_workspace *ws, int tw, int th, cudaStream_t st) {
+    std::vector<ViewInfo> vh = ws->views_h;
+    std::vector<int> tv;
+    long long tile_base = 0;
+    for (size_t v = 0; v < vh.size(); ++v) {
+        ViewInfo &V = vh[v];
+        V.tw = tw;
+        V.th = th;
+        V.tiles_x = (V.W + tw - 1) / tw;
+        V.tiles_y = (V.H + th - 1) / th;
+        V.tile_base = (int)tile_base;
+        tile_base += (long long)V.tiles_x * V.tiles_y;
+        if (tile_base >= (1LL << 30)) return fail(ws, VG_ERR_INVALID_ARG, "too many tiles");
+        tv.insert(tv.end(), (size_t)V.tiles_x * V.tiles_y, (int)v);
+    }
+    VG_TRY(upload_views(ws, vh, tv, st));
+    ws->n_tiles = tile_base;
+    ws->bp.tile_px = tw * th;
+    return run_preprocess(ws, st);
 }
 
 vg_status vg_preprocess(vg_workspace *ws, const vg_gaussians *g, const vg_camera *cams, int32_t n_views,
@@ -675,7 +728,8 @@ vg_status vg_ray_march(vg_workspace *ws, float t_near, float t_far, int32_t n_sa
     cudaStream_t st = (cudaStream_t)stream;
     VG_TRY(ensure(ws, ws->march_E, (size_t)ws->n_items, "ray-march scratch"));
     ProfScope ps(ws, ST_MARCH, st);
-    VG_CUDA(ws, launch_ray_march(ws->g, ws->views.p, ws->tile_view.p, ws->n_tiles, ws->n_items, ws->ranges.p,
+    VG_CUDA(ws, launch_ray_march(ws->g, ws->views.p, ws->tile_view.p, ws->n_tiles, ws->bp.tile_px, ws->n_items,
+                                 ws->ranges.p,
                                  ws->inst_item, ws->rec.p, ws->count.p, ws->prect.p, ws->march_E.p, t_near, t_far,
                                  n_samples, ws->opts.T_stop, ws->opts.bg, raster_rgb, rgb, T, err_map, st,
                                  &ws->launches));
@@ -931,6 +985,8 @@ static vg_status tomo_impl(vg_workspace *ws, const vg_gaussians *g, const vg_bea
             memset(&vh[v], 0, sizeof(ViewInfo));
             vh[v].W = beam->det_w;
             vh[v].H = beam->det_h;
+            vh[v].tw = kTile;
+            vh[v].th = kTile;
             vh[v].tiles_x = tiles_x;
             vh[v].tiles_y = tiles_y;
             vh[v].tile_base = (int)(v * tpv);
@@ -1035,9 +1091,9 @@ vg_status vg_l2_loss(vg_workspace *ws, const float *x, const float *y, int64_t n
 }
 
 vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t *ppt_bwd, int32_t *chunk_fwd,
-                      int32_t *chunk_bwd, void *stream) {
+                      int32_t *chunk_bwd, int32_t *tile_w, int32_t *tile_h, void *stream) {
     if (!ws) return VG_ERR_INVALID_ARG;
-    if (ws->stage < 2) return fail(ws, VG_ERR_STATE, "vg_autotune before vg_bin_sort");
+    if (ws->stage < 2 || !ws->views_valid) return fail(ws, VG_ERR_STATE, "vg_autotune before vg_bin_sort");
     if (reps < 1) reps = 3;
     cudaStream_t st = (cudaStream_t)stream;
     VG_TRY(ensure(ws, ws->S_fin, (size_t)ws->n_pixels, "pixel state"));
@@ -1056,55 +1112,104 @@ vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t 
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
+    auto elapsed = [&]() {
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    };
+    // The default tile shape first, another one taken only when it is faster by more than 2%
+    // (the measured differences between shapes are often within the run-to-run spread); a
+    // shape set in the options of the last vg_preprocess is kept.
+    const int shapes[3][2] = {{16, 16}, {32, 16}, {16, 8}};
+    const int cur_tw = ws->views_h[0].tw, cur_th = ws->views_h[0].th;
+    const bool fixed_shape = ws->opts.tile_w != 0;
+    const int n_shapes = fixed_shape ? 1 : 3;
+    const unsigned flags = ws->opts.flags;
     const int cand[3] = {1, 2, 4}, chunks[2] = {64, 128};
-    float best_f = 1e30f, best_b = 1e30f;
+    float best_total = 1e30f;
     int pf = kDefaultPixelsFwd, pb = kDefaultPixelsBwd, cf = kDefaultChunk, cb = kDefaultChunk;
+    int tw = cur_tw, th = cur_th, last_tw = cur_tw, last_th = cur_th;
+    vg_status vs = VG_OK;
     e = cudaMemsetAsync(dl, 0, px3 * sizeof(float), st);
-    for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
-        BlendParams bp = ws->bp;
-        bp.chunk_fwd = bp.chunk_bwd = chunks[i & 1];
-        const int ppt = cand[i >> 1];
-        float tf = 0.0f, tb = 0.0f;
-        for (int r = 0; r <= reps && e == cudaSuccess; ++r) {   // the first round warms up
-            cudaEventRecord(a, st);
-            e = launch_render_fwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles, ws->ranges.p,
-                                  ws->inst_item, ws->rec.p, ws->prect.p, bp, ppt, rgb, nullptr, ws->T_fin.p,
-                                  ws->S_fin.p, ws->nlast.p, nullptr, st, &ws->launches);
-            cudaEventRecord(b, st);
-            cudaEventSynchronize(b);
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, a, b);
-            if (r) tf += ms;
-            if (e != cudaSuccess) break;
-            ws->grad_zero_n = 0;   // timed backward passes without the chain leave sums behind
-            e = cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st);
-            cudaEventRecord(a, st);
-            if (e == cudaSuccess)
-                e = launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
-                                      ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, bp, ppt, ws->T_fin.p,
-                                      ws->S_fin.p, ws->nlast.p, dl, nullptr, ws->grad.p, nullptr, st, &ws->launches);
-            cudaEventRecord(b, st);
-            cudaEventSynchronize(b);
-            cudaEventElapsedTime(&ms, a, b);
-            if (r) tb += ms;
+    for (int s = 0; s < n_shapes && e == cudaSuccess && vs == VG_OK; ++s) {
+        const int sw = fixed_shape ? cur_tw : shapes[s][0], sh = fixed_shape ? cur_th : shapes[s][1];
+        float t_bin = 0.0f;
+        if (!fixed_shape) {
+            // one binning that may grow the instance buffers, then the timed ones in the
+            // fixed-capacity form (the device work of either form, without the count's readback)
+            ws->opts.flags = flags & ~VG_FLAG_FIXED_CAPACITY;
+            vs = retile(ws, sw, sh, st);
+            if (vs == VG_OK) vs = vg_bin_sort(ws, st);
+            ws->opts.flags = flags | VG_FLAG_FIXED_CAPACITY;
+            last_tw = sw, last_th = sh;
+            t_bin = 1e30f;
+            for (int r = 0; r < reps && vs == VG_OK; ++r) {
+                cudaEventRecord(a, st);
+                vs = run_preprocess(ws, st);
+                if (vs == VG_OK) vs = vg_bin_sort(ws, st);
+                t_bin = std::min(t_bin, elapsed());
+            }
+            ws->opts.flags = flags;
+            if (vs != VG_OK) break;
         }
-        if (tf < best_f) best_f = tf, pf = ppt, cf = chunks[i & 1];
-        if (tb < best_b) best_b = tb, pb = ppt, cb = chunks[i & 1];
+        float best_f = 1e30f, best_b = 1e30f;
+        int spf = pf, spb = pb, scf = cf, scb = cb;
+        for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
+            BlendParams bp = ws->bp;
+            bp.chunk_fwd = bp.chunk_bwd = chunks[i & 1];
+            const int ppt = cand[i >> 1];
+            float tf = 1e30f, tb = 1e30f;   // the fastest of the timed runs
+            for (int r = 0; r <= reps && e == cudaSuccess; ++r) {   // the first round warms up
+                cudaEventRecord(a, st);
+                e = launch_render_fwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
+                                      ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, bp, ppt, rgb, nullptr,
+                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, nullptr, st, &ws->launches);
+                float ms = elapsed();
+                if (r) tf = std::min(tf, ms);
+                if (e != cudaSuccess) break;
+                ws->grad_zero_n = 0;   // timed backward passes without the chain leave sums behind
+                e = cudaMemsetAsync(ws->grad.p, 0, sizeof(float) * (size_t)ws->n_items * kGradN, st);
+                cudaEventRecord(a, st);
+                if (e == cudaSuccess)
+                    e = launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
+                                          ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, bp, ppt, ws->T_fin.p,
+                                          ws->S_fin.p, ws->nlast.p, dl, nullptr, ws->grad.p, nullptr, st, &ws->launches);
+                ms = elapsed();
+                if (r) tb = std::min(tb, ms);
+            }
+            if (tf < best_f) best_f = tf, spf = ppt, scf = chunks[i & 1];
+            if (tb < best_b) best_b = tb, spb = ppt, scb = chunks[i & 1];
+        }
+        const float total = t_bin + best_f + best_b;
+        if (s == 0 || total < 0.98f * best_total)
+            best_total = total, pf = spf, pb = spb, cf = scf, cb = scb, tw = sw, th = sh;
+    }
+    if (vs == VG_OK && e == cudaSuccess && (tw != last_tw || th != last_th)) {   // leave the chosen tiling binned
+        ws->opts.flags = flags & ~VG_FLAG_FIXED_CAPACITY;
+        vs = retile(ws, tw, th, st);
+        if (vs == VG_OK) vs = vg_bin_sort(ws, st);
+        ws->opts.flags = flags;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(rgb);
     cudaFree(dl);
+    if (vs != VG_OK) return vs;
     if (e != cudaSuccess) return fail(ws, VG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
     ws->tuned_fwd = ws->ppt_fwd = pf;
     ws->tuned_bwd = ws->ppt_bwd = pb;
     ws->tuned_chunk_fwd = ws->bp.chunk_fwd = cf;
     ws->tuned_chunk_bwd = ws->bp.chunk_bwd = cb;
+    if (!fixed_shape) ws->tuned_tw = tw, ws->tuned_th = th;
     ws->stage = 2;   // the replay state no longer belongs to a vg_render_fwd of the caller
     if (ppt_fwd) *ppt_fwd = pf;
     if (ppt_bwd) *ppt_bwd = pb;
     if (chunk_fwd) *chunk_fwd = cf;
     if (chunk_bwd) *chunk_bwd = cb;
+    if (tile_w) *tile_w = tw;
+    if (tile_h) *tile_h = th;
     return VG_OK;
 }
 
@@ -1245,7 +1350,7 @@ vg_status vg_read_pixel_state(vg_workspace *ws, float *S, uint32_t *last) {
             for (int y = 0; y < V.H; ++y)
                 for (int x = 0; x < V.W; ++x) {
                     const size_t p = (size_t)(V.pix_base + (long long)y * V.W + x);
-                    last[p] -= rg[(size_t)V.tile_base + (size_t)(y / kTile) * V.tiles_x + x / kTile].x;
+                    last[p] -= rg[(size_t)V.tile_base + (size_t)(y / V.th) * V.tiles_x + x / V.tw].x;
                 }
     }
     return VG_OK;

@@ -54,28 +54,34 @@ __device__ __forceinline__ void eval_pair(const float4 &r0, const float4 &r1, co
     e.tau = __fmul_rn(ex2_approx(fmaf(e.m2, -kHalfLog2e, __fadd_rn(r5.x, p.Lp))), e.rs);
 }
 
-// A thread owns P pixels of a 16x16 tile (P = 1, 2 or 4); 256 / P threads per tile.  Warps own
-// near-square pixel boxes, which the footprint tests below cull best.  With w = t / 32, l = t % 32:
-//   P = 1: pixel (8 (w % 2) + l % 8, 4 (w / 2) + l / 8)               (a warp covers 8 x 4 pixels)
-//   P = 2: pixels (8 (w % 2) + l % 8, 8 (w / 2) + 2 (l / 8) + k)      (8 x 8)
-//   P = 4: pixels (2 (t % 8) + (k & 1), 2 (t / 8) + (k >> 1))         (16 x 8)
+// A thread owns P pixels of a tile of tw x th pixels (16 x 16, 32 x 16 or 16 x 8; P = 1, 2 or 4);
+// tw th / P threads per tile.  Warps own near-square pixel boxes, which the footprint tests below
+// cull best, laid out row by row over the tile; with w = t / 32, l = t % 32, the warp's box column
+// wx = w % (tw / bw) and row wy = w / (tw / bw):
+//   P = 1: box 8 x 4,  pixel (8 wx + l % 8, 4 wy + l / 8)
+//   P = 2: box 8 x 8,  pixels (8 wx + l % 8, 8 wy + 2 (l / 8) + k)
+//   P = 4: box 16 x 8, pixels (16 wx + 2 (l % 8) + (k & 1), 8 wy + 2 (l / 8) + (k >> 1))
 // d' and o' x d' are affine in the pixel offset, so a thread's other pixels follow from its
 // first by one add per component.  Forward and backward both use pair_eval_at(), so they
 // compute the same bits and take the same skip decisions.
 template <int P>
 struct PixLayout {
-    static constexpr int kThreads = kTilePix / P;
-    __device__ static void origin(int t, int &x, int &y) {
+    static constexpr int kBoxW = P == 4 ? 16 : 8;
+    // register caps that keep the occupancy of 16 x 16 tiles (forward / backward)
+    static constexpr int kFwdRegs = P == 2 ? 73 : 85;
+    static constexpr int kBwdRegs = P == 1 ? 64 : 128;
+    __device__ static void origin(int t, int tw, int &x, int &y) {
         const int w = t >> 5, l = t & 31;
+        const int nwx = tw / kBoxW, wx = w % nwx, wy = w / nwx;
         if (P == 1) {
-            x = 8 * (w & 1) + (l & 7);
-            y = 4 * (w >> 1) + (l >> 3);
+            x = 8 * wx + (l & 7);
+            y = 4 * wy + (l >> 3);
         } else if (P == 2) {
-            x = 8 * (w & 1) + (l & 7);
-            y = 8 * (w >> 1) + 2 * (l >> 3);
+            x = 8 * wx + (l & 7);
+            y = 8 * wy + 2 * (l >> 3);
         } else {
-            x = 2 * (t & 7);
-            y = 2 * (t >> 3);
+            x = 16 * wx + 2 * (l & 7);
+            y = 8 * wy + 2 * (l >> 3);
         }
     }
     __host__ __device__ static constexpr int ox(int k) { return P == 4 ? (k & 1) : 0; }

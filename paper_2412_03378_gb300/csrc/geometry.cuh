@@ -205,7 +205,7 @@ __device__ __forceinline__ int key_persp(const ViewInfo &V, const float mu[3], c
     pixel_span(xlo, xhi, V.W, ix0, ix1);
     pixel_span(ylo, yhi, V.H, iy0, iy1);
     if (ix0 > ix1 || iy0 > iy1) return 1;
-    rect = make_short4((short)(ix0 / kTile), (short)(iy0 / kTile), (short)(ix1 / kTile), (short)(iy1 / kTile));
+    rect = make_short4((short)(ix0 / V.tw), (short)(iy0 / V.th), (short)(ix1 / V.tw), (short)(iy1 / V.th));
     prect = make_short4((short)ix0, (short)iy0, (short)ix1, (short)iy1);
     return 2;
 }
@@ -254,7 +254,7 @@ __device__ __forceinline__ int key_splat(const ViewInfo &V, const float mu[3], c
     pixel_span(VG_SUB(mx, hx), VG_ADD(mx, hx), V.W, ix0, ix1);
     pixel_span(VG_SUB(my, hy), VG_ADD(my, hy), V.H, iy0, iy1);
     if (ix0 > ix1 || iy0 > iy1) return 1;
-    rect = make_short4((short)(ix0 / kTile), (short)(iy0 / kTile), (short)(ix1 / kTile), (short)(iy1 / kTile));
+    rect = make_short4((short)(ix0 / V.tw), (short)(iy0 / V.th), (short)(ix1 / V.tw), (short)(iy1 / V.th));
     prect = make_short4((short)ix0, (short)iy0, (short)ix1, (short)iy1);
     return 2;
 }

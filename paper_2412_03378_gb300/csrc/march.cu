@@ -49,7 +49,7 @@ k_march_prep(GaussIn g, const ViewInfo *__restrict__ views, long long n_items, c
     }
 }
 
-__global__ void __launch_bounds__(kTilePix)
+__global__ void __launch_bounds__(kMaxTilePix)
 k_ray_march(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const uint2 *__restrict__ ranges,
             const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec, const float4 *__restrict__ E,
             const short4 *__restrict__ prect, float t_near, float delta, int n_samples, float T_stop, float bg0,
@@ -62,7 +62,7 @@ k_ray_march(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vie
     const ViewInfo &V = views[tile_view[tile]];
     const int local = tile - V.tile_base;
     const int tyi = local / V.tiles_x, txi = local - tyi * V.tiles_x;
-    const int x = txi * kTile + (threadIdx.x & (kTile - 1)), y = tyi * kTile + (threadIdx.x / kTile);
+    const int x = txi * V.tw + (int)(threadIdx.x % V.tw), y = tyi * V.th + (int)(threadIdx.x / V.tw);
     const bool inside = x < V.W && y < V.H;
     const float xf = (float)x, yf = (float)y;
     const float pu = ((float)x + 0.5f - V.cx) / V.fx, pv = ((float)y + 0.5f - V.cy) / V.fy;
@@ -79,7 +79,7 @@ k_ray_march(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vie
         for (uint32_t base = rg.x; base < rg.y; base += kMarchChunk) {
             const int n = (int)min((uint32_t)kMarchChunk, rg.y - base);
             __syncthreads();
-            for (int r = threadIdx.x; r < n; r += kTilePix) {
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
                 const uint32_t item = sorted_item[base + r];
 #pragma unroll
                 for (int c = 0; c < kRecF4; ++c) srec[r * (kRecF4 + 1) + c] = __ldg(rec + (size_t)item * kRecF4 + c);
@@ -153,6 +153,7 @@ k_ray_march(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vie
 }
 
 cudaError_t launch_ray_march(const GaussIn &g, const ViewInfo *views_d, const int *tile_view, long long n_tiles,
+                             int tile_px,
                              long long n_items, const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
                              const uint32_t *count, const short4 *prect, float4 *E, float t_near, float t_far,
                              int n_samples, float T_stop, const float bg[3], const float *raster, float *rgb,
@@ -170,7 +171,7 @@ cudaError_t launch_ray_march(const GaussIn &g, const ViewInfo *views_d, const in
     }
     if (n_tiles > 0) {
         const float delta = (t_far - t_near) / (float)n_samples;
-        pdl_launch(k_ray_march, (unsigned)n_tiles, kTilePix, 0, st, views_d, tile_view, ranges, sorted_item, rec, E, prect, t_near,
+        pdl_launch(k_ray_march, (unsigned)n_tiles, (unsigned)tile_px, 0, st, views_d, tile_view, ranges, sorted_item, rec, E, prect, t_near,
                                                           delta, n_samples, T_stop, bg[0], bg[1], bg[2], raster, rgb,
                                                           T_out, err);
         *launches += 1;

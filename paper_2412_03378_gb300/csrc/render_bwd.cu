@@ -32,17 +32,15 @@ constexpr int kGradUsed = 16;
 static_assert(kGradUsed == kGradN, "the vector reductions cover the whole 16-float accumulator");
 constexpr int kDirectLanes = 16;   // at most this many contributing lanes: direct reductions
 
-template <int P> struct BwdBounds;
-template <> struct BwdBounds<1> { static constexpr int kMinBlocks = 4; };
-template <> struct BwdBounds<2> { static constexpr int kMinBlocks = 4; };
-template <> struct BwdBounds<4> { static constexpr int kMinBlocks = 8; };
 
-// One CTA per tile (longest list first), 256/P threads owning P pixels each.  Each warp first
+// One CTA per tile (longest list first), tw th / P threads owning P pixels each.  Each warp first
 // ballots which records of the staged chunk it needs (some pixel of the warp reached the record,
 // the record's footprint touches the warp's pixels and, when pairs below tau_skip are skipped,
 // its opacity can reach tau_skip there), then visits only those, back to front.
+// The register cap is that of 4 / 4 / 8 CTAs of a 16 x 16 tile per SM for P = 1 / 2 / 4, whatever
+// the tile shape.
 template <int P, bool COUNT, bool PIXTEST, bool SPLAT, int CH>
-__global__ void __launch_bounds__(PixLayout<P>::kThreads, BwdBounds<P>::kMinBlocks)
+__global__ void __maxnreg__(PixLayout<P>::kBwdRegs)
 k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
              const short4 *__restrict__ prect, BlendParams bp, const float *__restrict__ T_fin, const float *__restrict__ S_fin,
@@ -50,7 +48,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
              float *__restrict__ grad_acc, unsigned long long *__restrict__ pair_count) {
     pdl_entry();
     using L = PixLayout<P>;
-    constexpr int kThreads = L::kThreads;
+    const int kThreads = blockDim.x;
     constexpr int kChunk = CH;   // records per shared-memory chunk
     // two buffers: the next chunk is staged (cp.async) while the current one is processed
     __shared__ float4 srec_[2][kChunk * kRecF4];
@@ -64,8 +62,8 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     const int local = tile - V.tile_base;
     const int tyi = local / V.tiles_x, txi = local - tyi * V.tiles_x;
     int ix, iy;
-    L::origin(threadIdx.x, ix, iy);
-    const int x0 = txi * kTile + ix, y0 = tyi * kTile + iy;
+    L::origin(threadIdx.x, V.tw, ix, iy);
+    const int x0 = txi * V.tw + ix, y0 = tyi * V.th + iy;
     const uint2 rg = ranges[tile];
     const int lane = threadIdx.x & 31;
 
@@ -281,7 +279,7 @@ static void launch_bwd_ptsc(const ViewInfo *views_d, const int *tile_view, const
                             const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
                             const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
                             cudaStream_t st) {
-    const unsigned threads = PixLayout<P>::kThreads;
+    const unsigned threads = (unsigned)(bp.tile_px / P);
     if (pair_count)
         pdl_launch(k_render_bwd<P, true, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
             views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,

@@ -1,7 +1,7 @@
 // Front-to-back blend of the depth-sorted per-tile lists (Eq. 14 with the Eq. 19 alpha).
 //
-// One CTA per 16x16 tile, tiles taken longest list first; each of the 256/P threads owns P
-// pixels (P = 1, 2, 4).  Records of the tile's Gaussians are staged through shared memory in
+// One CTA per tile (16 x 16, 32 x 16 or 16 x 8 pixels), tiles taken longest list first; each of
+// the tw th / P threads owns P pixels (P = 1, 2, 4).  Records of the tile's Gaussians are staged through shared memory in
 // depth-ordered chunks (one record per thread); every record is read once per thread and
 // serves its P pixels, whose d' and o' x d' follow from the first pixel's by one add per
 // component.  The closed form is evaluated in FP32 (FMA pipe + 3 MUFU ops per pair); the CTA
@@ -16,13 +16,10 @@
 namespace vg {
 
 
-template <int P> struct FwdBounds;
-template <> struct FwdBounds<1> { static constexpr int kMinBlocks = 3; };
-template <> struct FwdBounds<2> { static constexpr int kMinBlocks = 7; };
-template <> struct FwdBounds<4> { static constexpr int kMinBlocks = 12; };
-
+// One CTA of tw th / P threads per tile.  The register cap is that of 3 / 7 / 12 CTAs of a 16 x 16
+// tile per SM for P = 1 / 2 / 4 (the occupancy measured fastest), whatever the tile shape.
 template <int P, bool COUNT, bool PIXTEST, bool SPLAT, int CH>
-__global__ void __launch_bounds__(PixLayout<P>::kThreads, FwdBounds<P>::kMinBlocks)
+__global__ void __maxnreg__(PixLayout<P>::kFwdRegs)
 k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
              const short4 *__restrict__ prect, BlendParams bp, float *__restrict__ rgb, float *__restrict__ T_user, float *__restrict__ T_ws,
@@ -38,8 +35,8 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     const int local = tile - V.tile_base;
     const int tyi = local / V.tiles_x, txi = local - tyi * V.tiles_x;
     int ix, iy;
-    L::origin(threadIdx.x, ix, iy);
-    const int x0 = txi * kTile + ix, y0 = tyi * kTile + iy;
+    L::origin(threadIdx.x, V.tw, ix, iy);
+    const int x0 = txi * V.tw + ix, y0 = tyi * V.th + iy;
     float Lp[P], T[P], S[P], c0[P], c1[P], c2[P];
     uint32_t last[P];
     const uint2 rg = ranges[tile];
@@ -60,7 +57,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     unsigned long long pairs = 0, blended = 0;   // evaluated / blended pairs (COUNT only)
     for (uint32_t base = rg.x; base < rg.y; base += kChunk) {
         const uint32_t n = min((uint32_t)kChunk, rg.y - base);
-        for (uint32_t r = threadIdx.x; r < n; r += L::kThreads) {
+        for (uint32_t r = threadIdx.x; r < n; r += blockDim.x) {
             const uint32_t item = sorted_item[base + r];
             const float4 *src = rec + (size_t)item * kRecF4;
             float4 q[kRecF4];
@@ -168,7 +165,7 @@ static void launch_fwd_ptsc(const ViewInfo *views_d, const int *tile_view, const
                             const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                             const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
                             uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
-    const unsigned threads = PixLayout<P>::kThreads;
+    const unsigned threads = (unsigned)(bp.tile_px / P);
     if (pair_count)
         pdl_launch(k_render_fwd<P, true, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
             views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,

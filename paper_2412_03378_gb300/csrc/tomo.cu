@@ -150,7 +150,7 @@ cudaError_t launch_tomo_preprocess(const GaussIn &g, const float *cs_d, int n_an
 // ---------------------------------------------------------------------------- projector
 // One CTA of 64 threads per detector tile, a 2x2 pixel quad per thread; y advances by c0 or c1
 // from one quad pixel to the next.
-constexpr int kQuadThreads = PixLayout<4>::kThreads;   // 64 threads, a 2x2 quad each
+constexpr int kQuadThreads = kTilePix / 4;   // 64 threads, a 2x2 quad each
 constexpr int kTomoChunk = kQuadThreads;
 
 __global__ void __launch_bounds__(kQuadThreads, 12)

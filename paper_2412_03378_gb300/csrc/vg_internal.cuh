@@ -13,8 +13,9 @@
 
 namespace vg {
 
-constexpr int kTile = 16;                 // square pixel tiles
-constexpr int kTilePix = kTile * kTile;   // one thread per pixel in the blend kernels
+constexpr int kTile = 16;                 // the default tile (16 x 16 pixels); tomography's tiles
+constexpr int kTilePix = kTile * kTile;
+constexpr int kMaxTilePix = 512;          // the largest tile the blend kernels take (32 x 16)
 constexpr int kRecF4 = 6;                 // blend record: 6 x float4 = 96 bytes
 constexpr int kGradN = 16;                // per-item gradient accumulator (moments, dln kappa, colour)
 constexpr int kTomoRecF4 = 2;             // tomography record: 2 x float4
@@ -27,6 +28,7 @@ struct ViewInfo {
     double od[3];         // camera centre, FP64
     int W, H, tiles_x, tiles_y;
     int tile_base;        // first global tile id of this view
+    int tw, th;           // tile width and height in pixels (16 x 16, 32 x 16 or 16 x 8)
     int pad;
     long long pix_base;   // first pixel of this view in the concatenated image
 };
@@ -53,6 +55,7 @@ struct BlendParams {
     float alpha_max;
     int chunk_fwd;        // records staged per barrier: 64 or 128
     int chunk_bwd;
+    int tile_px;          // pixels per tile (the blend kernels' block is tile_px / P threads)
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -193,9 +196,11 @@ cudaError_t launch_voxel_dup(const uint32_t *offsets, const short4 *box, const V
 cudaError_t launch_voxel_eval(const uint2 *ranges, const uint32_t *sorted, const float4 *rec, const short4 *box,
                               const VoxelGrid &grid, float *out, cudaStream_t st, long long *launches);
 
-// Ray-marching reference (march.cu): E receives (o'.A0, o'.A1, o'.A2) per item (scratch);
+// Ray-marching reference (march.cu): one CTA of tile_px threads per tile (one pixel each); E
+// receives (o'.A0, o'.A1, o'.A2) per item (scratch);
 // rgb / T_out / err (max over channels of |rgb - raster|) are each optional.
 cudaError_t launch_ray_march(const GaussIn &g, const ViewInfo *views_d, const int *tile_view, long long n_tiles,
+                             int tile_px,
                              long long n_items, const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec,
                              const uint32_t *count, const short4 *prect, float4 *E, float t_near, float t_far,
                              int n_samples, float T_stop, const float bg[3], const float *raster, float *rgb,

@@ -12,7 +12,7 @@ def dev_scene(vg, scene, rec_dtype=torch.float32, sh_dtype=torch.float32, mu_dty
                         t(scene.kappa, rec_dtype), t(scene.sh, sh_dtype), scene.sh_degree)
 
 
-def vg_opts(vg, o, flags=0, ppt=0, chunk=0):
+def vg_opts(vg, o, flags=0, ppt=0, chunk=0, tile=(0, 0)):
     if o.get("density_theta"):
         flags |= vg.FLAG_DENSITY_THETA
     if o.get("splat"):
@@ -20,16 +20,16 @@ def vg_opts(vg, o, flags=0, ppt=0, chunk=0):
     return vg.Opts(alpha_min=o["alpha_min"], tau_cut=o["tau_cut"], tau_max=o["tau_max"], T_stop=o["T_stop"],
                    bg=tuple(o["bg"]), z_near=o["z_near"], flags=flags, pixels_per_thread=ppt,
                    softplus_beta=o.get("softplus_beta", 0.0), splat_dilation=o.get("splat_dilation", 0.0),
-                   chunk=chunk)
+                   chunk=chunk, tile_w=tile[0], tile_h=tile[1])
 
 
-def run_forward(vg, scene, cams, o, ws=None, flags=0, g=None, ppt=0, chunk=0):
+def run_forward(vg, scene, cams, o, ws=None, flags=0, g=None, ppt=0, chunk=0, tile=(0, 0)):
     ws = ws or vg.Workspace()
     g = g or dev_scene(vg, scene)
     P = sum(c.width * c.height for c in cams)
     rgb = torch.full((P, 3), float("nan"), device="cuda:0")
     T = torch.full((P,), float("nan"), device="cuda:0")
-    ws.preprocess(g, cams, vg_opts(vg, o, flags, ppt, chunk))
+    ws.preprocess(g, cams, vg_opts(vg, o, flags, ppt, chunk, tile))
     ws.bin_sort()
     ws.render_fwd(rgb, T)
     torch.cuda.synchronize()

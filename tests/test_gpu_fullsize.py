@@ -15,11 +15,12 @@ IMG_TOL = 1e-4
 GRAD_TOL = 1e-3
 
 
-def _bases(cams):
+def _bases(cams, tile=(16, 16)):
+    tw, th = tile
     pb, tb = [0], [0]
     for c in cams:
         pb.append(pb[-1] + c.width * c.height)
-        tb.append(tb[-1] + ((c.width + 15) // 16) * ((c.height + 15) // 16))
+        tb.append(tb[-1] + ((c.width + tw - 1) // tw) * ((c.height + th - 1) // th))
     return pb, tb
 
 
@@ -39,26 +40,28 @@ def _pixel_sample(cams, n_per_view, seed, whole_tiles=2):
     return out
 
 
-def _check_subset(vg, ws, scene, cams, views, o, rgb_gpu, seed, compat, n_key=200_000, n_tiles=40, grad_g=None):
+def _check_subset(vg, ws, scene, cams, views, o, rgb_gpu, seed, compat, n_key=200_000, n_tiles=40, grad_g=None,
+                  tile=(16, 16)):
     """keys of sampled Gaussians, lists of sampled tiles and sampled pixels, per view; with compat,
     every sampled pixel whose threshold decisions agree with the oracle's within 1e-4 and the
     flipped ones counted (compat_check).  With grad_g (the device Gaussians), the gradient of a loss on the sampled pixels
     of these views (flipped pixels weighted zero) against the oracle's analytic gradient."""
     sub = [cams[v] for v in views]
-    L = oracle.lists(scene, sub, o)
+    tw, th = tile
+    L = oracle.lists(scene, sub, o, tile=tile)
     N = scene.n
     depth, rect = ws.read_keys()
     rng = np.random.default_rng(seed)
     pick = rng.choice(N, size=min(n_key, N), replace=False)
-    pb_gpu, tb_gpu = _bases(cams)
-    pb_sub, _ = _bases(sub)
+    pb_gpu, tb_gpu = _bases(cams, tile)
+    pb_sub, _ = _bases(sub, tile)
     masks = _pixel_sample(sub, 1500, seed)
     for i, v in enumerate(views):
         od = L["depth"][i].reshape(-1)
         orc = L["rect"][i].reshape(-1, 4)
         assert np.array_equal(depth[v * N + pick], od[pick]), v
         assert np.array_equal(rect[v * N + pick], orc[pick]), v
-        ntv = ((cams[v].width + 15) // 16) * ((cams[v].height + 15) // 16)
+        ntv = ((cams[v].width + tw - 1) // tw) * ((cams[v].height + th - 1) // th)
         for t in rng.choice(ntv, size=min(n_tiles, ntv), replace=False):
             a = int(L["tile_start"][L["tile_base"][i] + t])
             b = int(L["tile_start"][L["tile_base"][i] + t + 1])
@@ -160,13 +163,15 @@ def test_config3_graph_batched_bf16(gpu_lib):
     scene, rec_dt, sh_dt = _dequantised(scene32, "bf16", "f16")
     o = oracle.COMPAT
     g = dev_scene(vg, scene, rec_dtype=rec_dt, sh_dtype=sh_dt)
-    pb, tb = _bases(cams)
-    P, tiles = pb[-1], tb[-1]
     ws = vg.Workspace()
     ws.preprocess(g, cams, vg_opts(vg, o))
     ws.bin_sort()
-    n_inst = ws.query()["n_instances"]
-    ws.autotune(reps=1)
+    tile = ws.autotune(reps=1)[4:]   # left binned with the chosen tile shape
+    q = ws.query()
+    n_inst = q["n_instances"]
+    pb, tb = _bases(cams, tile)
+    P, tiles = pb[-1], tb[-1]
+    assert q["n_tiles"] == tiles
     ws.reserve(scene.n * len(cams), int(n_inst * 1.05) + 4096, P, tiles)
     opts = vg_opts(vg, o, flags=vg.FLAG_FIXED_CAPACITY | vg.FLAG_GRAD_ZERO)
     dev = torch.device("cuda:0")
@@ -198,7 +203,7 @@ def test_config3_graph_batched_bf16(gpu_lib):
     # the graph's forward state stays in the workspace: the backward (its autotuned launch) of a
     # loss on sampled pixels of views 0, 7 and 15 against the oracle
     _check_subset(vg, ws, scene, cams, [0, 7, 15], o, rgb.cpu().numpy().astype(np.float64), 31, compat=True,
-                  grad_g=g)
+                  grad_g=g, tile=tile)
 
 
 def test_config4_full_size_tomography(gpu_lib):

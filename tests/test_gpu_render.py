@@ -314,9 +314,50 @@ def test_long_tile_lists(gpu_lib, n):
     assert np.max(np.abs(rgb - flat(ref_rgb))) < IMG_TOL
 
 
+@pytest.mark.parametrize("tile", [(16, 16), (32, 16), (16, 8)])
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+@pytest.mark.parametrize("mode", ["exact", "compat"])
+def test_tile_shapes(gpu_lib, tile, ppt, mode):
+    """Every tile shape: the per-tile lists are those of the oracle binned with the same shape
+    (bit-exact), the image equals the 16 x 16 one bit for bit (each pixel blends the same
+    Gaussians in the same order with the same arithmetic) and matches the oracle, and the
+    gradients match the oracle's."""
+    vg = gpu_lib
+    scene, cams = _multi_view_scene()
+    o = dict(oracle.EXACT if mode == "exact" else oracle.COMPAT, bg=(0.3, 0.2, 0.1))
+    ws, g, rgb, T = run_forward(vg, scene, cams, o, ppt=ppt, tile=tile)
+    ts, items = ws.read_bins()
+    L = oracle.lists(scene, cams, o, tile=tile)
+    assert np.array_equal(ts, L["tile_start"]) and np.array_equal(items % scene.n, L["sorted_g"])
+    tile_of = np.repeat(np.arange(L["n_tiles"]), np.diff(L["tile_start"]))
+    assert np.array_equal(items // scene.n, np.searchsorted(L["tile_base"], tile_of, side="right") - 1)
+    assert ws.query()["n_tiles"] == L["n_tiles"]
+    _, _, rgb16, T16 = run_forward(vg, scene, cams, o, g=g, ppt=ppt, tile=(16, 16))
+    assert np.array_equal(rgb, rgb16) and np.array_equal(T, T16)
+    ref_rgb, ref_T, _ = oracle.render(scene, cams, o, L=L)
+    assert np.max(np.abs(rgb - flat(ref_rgb))) < IMG_TOL and np.max(np.abs(T - flat(ref_T))) < IMG_TOL
+    ws, g, rgb, T = run_forward(vg, scene, cams, o, g=g, ppt=ppt, tile=tile)
+    wr = np.random.default_rng(11).normal(size=rgb.shape)
+    gg = run_backward(vg, ws, g, wr)
+    ref = oracle.render_grad(scene, cams, o, L, wr)
+    check_grads(gg, ref, scene, GRAD_TOL, label=f"tile {tile} ppt {ppt} {mode}")
+
+
+def test_tile_shape_rejected(gpu_lib):
+    vg = gpu_lib
+    scene, cams = _multi_view_scene()
+    g = dev_scene(vg, scene)
+    ws = vg.Workspace()
+    for tile in [(8, 8), (16, 32), (24, 16), (0, 16)]:
+        with pytest.raises(RuntimeError, match="tile_w"):
+            ws.preprocess(g, cams, vg_opts(vg, oracle.EXACT, tile=tile))
+
+
 def test_autotune_keeps_results(gpu_lib):
-    """vg_autotune times 1/2/4 pixels per thread x 64/128-record chunks on the binned workload
-    and keeps the fastest as the workspace default; the blend afterwards still matches the oracle."""
+    """vg_autotune times the tile shapes 32x16 / 16x16 / 16x8 (binning included) and 1/2/4
+    pixels per thread x 64/128-record chunks on the binned workload and keeps the fastest as
+    the workspace default, binned with the chosen shape; the blend afterwards still matches the
+    oracle, and a shape fixed in the options is kept."""
     import torch
     vg = gpu_lib
     scene, cams = _multi_view_scene()
@@ -325,8 +366,12 @@ def test_autotune_keeps_results(gpu_lib):
     ws = vg.Workspace()
     ws.preprocess(g, cams, vg_opts(vg, o))
     ws.bin_sort()
-    pf, pb, cf, cb = ws.autotune(reps=2)
+    pf, pb, cf, cb, tw, th = ws.autotune(reps=2)
     assert pf in (1, 2, 4) and pb in (1, 2, 4) and cf in (64, 128) and cb in (64, 128)
+    assert (tw, th) in [(16, 16), (32, 16), (16, 8)]
+    ts, items = ws.read_bins()   # left binned with the chosen shape
+    L = oracle.lists(scene, cams, o, tile=(tw, th))
+    assert np.array_equal(ts, L["tile_start"]) and np.array_equal(items % scene.n, L["sorted_g"])
     P = sum(c.width * c.height for c in cams)
     rgb = torch.empty(P, 3, device="cuda:0")
     with pytest.raises(RuntimeError):
@@ -341,6 +386,13 @@ def test_autotune_keeps_results(gpu_lib):
     gg = run_backward(vg, ws, g, wr)
     ref = oracle.render_grad(scene, cams, o, oracle.lists(scene, cams, o), wr)
     check_grads(gg, ref, scene, GRAD_TOL)
+    ws.preprocess(g, cams, vg_opts(vg, o))   # the tuned shape is this workspace's default now
+    ws.bin_sort()
+    assert np.array_equal(ws.read_bins()[0], L["tile_start"])
+    fixed = vg.Workspace()
+    fixed.preprocess(g, cams, vg_opts(vg, o, tile=(16, 8)))
+    fixed.bin_sort()
+    assert fixed.autotune(reps=1)[4:] == (16, 8)
 
 
 @pytest.mark.parametrize("variant", ["theta", "softplus", "theta_softplus"])
