@@ -315,7 +315,7 @@ static vg_status latched_status(vg_workspace *ws, cudaStream_t st) {
     ws->h_total[2] = 0;
     ws->grad_zero_n = 0;   // after a device-side failure the next backward clears its accumulator
     cudaMemsetAsync(lookback_err_ptr(ws), 0, sizeof(uint32_t), st);
-    if (e & kDevErrTimeout) return fail(ws, VG_ERR_TIMEOUT, "a look-back wait of the scan or sort timed out");
+    if (e & kDevErrTimeout) return fail(ws, VG_ERR_TIMEOUT, "a bounded device wait (scan or sort look-back, backward ring) timed out");
     return fail(ws, VG_ERR_CAPACITY, "more (tile, Gaussian) instances than the fixed capacity");
 }
 
@@ -672,8 +672,8 @@ static vg_status render_bwd_impl(vg_workspace *ws, const float *dL_drgb, const f
         VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
                                       ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_bwd,
                                       ws->T_fin.p,
-                                      ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, ws->grad.p, pc, st,
-                                      &ws->launches));
+                                      ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, ws->grad.p, pc, lookback_err_ptr(ws),
+                                      st, &ws->launches));
     }
     {
         // the chain writes every Gaussian's gradient: overwriting with VG_FLAG_GRAD_ZERO, else adding
@@ -858,8 +858,8 @@ vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const fl
         ProfScope ps(ws, ST_BWD, st);
         VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
                                       ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_bwd,
-                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, acc, pc, st,
-                                      &ws->launches));
+                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, acc, pc,
+                                      lookback_err_ptr(ws), st, &ws->launches));
     }
     {
         ProfScope ps(ws, ST_CHAIN, st);
@@ -1175,7 +1175,8 @@ vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t 
                 if (e == cudaSuccess)
                     e = launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
                                           ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, bp, ppt, ws->T_fin.p,
-                                          ws->S_fin.p, ws->nlast.p, dl, nullptr, ws->grad.p, nullptr, st, &ws->launches);
+                                          ws->S_fin.p, ws->nlast.p, dl, nullptr, ws->grad.p, nullptr,
+                                          lookback_err_ptr(ws), st, &ws->launches);
                 ms = elapsed();
                 if (r) tb = std::min(tb, ms);
             }

@@ -69,7 +69,7 @@ struct PixLayout {
     static constexpr int kBoxW = P == 4 ? 16 : 8;
     // register caps that keep the occupancy of 16 x 16 tiles (forward / backward)
     static constexpr int kFwdRegs = P == 2 ? 73 : 85;
-    static constexpr int kBwdRegs = P == 1 ? 64 : 128;
+    static constexpr int kBwdRegs = P == 1 ? 56 : (P == 2 ? 96 : 128);
     __device__ static void origin(int t, int tw, int &x, int &y) {
         const int w = t >> 5, l = t & 31;
         const int nwx = tw / kBoxW, wx = w % nwx, wy = w / nwx;
@@ -318,6 +318,41 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// mbarrier objects in shared memory (CTA scope).  arrive has release semantics and try_wait
+// acquire semantics (the PTX defaults), so stores before an arrive are visible to a thread whose
+// wait saw that phase complete, and loads before an arrive are done before any store that
+// follows such a wait.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the completion of the barrier phase of the given parity: returns false
+// once limit_ns have passed, or as soon as *abort is set by another warp of the CTA that gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned long long limit_ns,
+                                          const volatile int *abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (*abort || globaltimer_ns() - t0 > limit_ns) return false;
+    return true;
+}
 
 // Vector reductions into global memory (red.global.add.v2/v4.f32, no return value): p must be
 // 8- / 16-byte aligned.

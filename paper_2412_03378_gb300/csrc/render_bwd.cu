@@ -33,39 +33,70 @@ static_assert(kGradUsed == kGradN, "the vector reductions cover the whole 16-flo
 constexpr int kDirectLanes = 16;   // at most this many contributing lanes: direct reductions
 
 
-// One CTA per tile (longest list first), tw th / P threads owning P pixels each.  Each warp first
-// ballots which records of the staged chunk it needs (some pixel of the warp reached the record,
-// the record's footprint touches the warp's pixels and, when pairs below tau_skip are skipped,
-// its opacity can reach tau_skip there), then visits only those, back to front.
-// The register cap is that of 4 / 4 / 8 CTAs of a 16 x 16 tile per SM for P = 1 / 2 / 4, whatever
-// the tile shape.
+// Records are staged through a ring of kGroup-record slots in shared memory, back to front: the
+// CTA's last warp is the producer, gathering each group's records (and, for the opacity test,
+// their Gram rows) into a free slot; the other warps consume the slots in order.  Slots
+// complete on mbarriers (full: the producer's 32 lanes arrive once the slot is written;
+// empty: every consumer lane arrives once its warp is done with it), so a consumer warp waits
+// only for data and never for the other consumers: warps whose pixels need few of a group's
+// records run ahead by up to the ring's depth.  Every wait is bounded (kWaitLimitNs): a wait
+// that runs out latches kDevErrTimeout in *err and the warp returns, and the CTA's other warps
+// give up at their next wait.
+constexpr int kGroup = 32;                               // records per ring slot
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
+
+template <bool PIXTEST>
+struct RingSlot {
+    float4 rec[kGroup * kRecF4];                // the records, one after another
+    float4 cull[PIXTEST ? 1 : kCullF4][kGroup];  // Gram rows for the opacity test, by row
+    float4 ref[PIXTEST ? 1 : kGroup];            // (px0, py0, log2 K) for the opacity test
+    short4 rect[kGroup];                         // pixel footprint rectangles
+    uint32_t item[kGroup];                       // item ids (accumulator rows)
+};
+
+// One CTA per tile (longest list first): tw th / P consumer threads owning P pixels each, plus
+// the producer warp.  For each group a consumer warp first ballots which records it needs (some
+// pixel of the warp reached the record, the record's footprint touches the warp's pixels and,
+// when pairs below tau_skip are skipped, its opacity can reach tau_skip there), then visits only
+// those, back to front.  The chunk setting CH gives the ring depth: CH / 16 slots (4 or 8, i.e.
+// 128 or 256 records in flight).  The register cap is that of 4 / 4 / 5 CTAs of a 16 x 16 tile
+// (with its producer warp) per SM for P = 1 / 2 / 4, whatever the tile shape.
 template <int P, bool COUNT, bool PIXTEST, bool SPLAT, int CH>
 __global__ void __maxnreg__(PixLayout<P>::kBwdRegs)
 k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
              const short4 *__restrict__ prect, BlendParams bp, const float *__restrict__ T_fin, const float *__restrict__ S_fin,
              const uint32_t *__restrict__ nlast, const float *__restrict__ dL_drgb, const float *__restrict__ dL_dT,
-             float *__restrict__ grad_acc, unsigned long long *__restrict__ pair_count) {
+             float *__restrict__ grad_acc, unsigned long long *__restrict__ pair_count, uint32_t *__restrict__ err) {
     pdl_entry();
     using L = PixLayout<P>;
-    const int kThreads = blockDim.x;
-    constexpr int kChunk = CH;   // records per shared-memory chunk
-    // two buffers: the next chunk is staged (cp.async) while the current one is processed
-    __shared__ float4 srec_[2][kChunk * kRecF4];
-    __shared__ uint32_t sitem_[2][kChunk];
-    __shared__ short4 srect_[2][kChunk];
-    __shared__ float4 scull_[2][PIXTEST ? 1 : kChunk * kCullF4];   // Gram matrices for the opacity test
+    constexpr int kSlots = CH / 16;
+    using Slot = RingSlot<PIXTEST>;
+    __shared__ Slot ring[kSlots];
+    __shared__ __align__(8) uint64_t full[kSlots], empty[kSlots];
     __shared__ uint32_t s_last;
+    __shared__ int s_abort;
 
+    const int n_cons = (int)blockDim.x - 32;   // consumer threads; the last warp produces
+    const bool producer = (int)threadIdx.x >= n_cons;
     const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
     const ViewInfo &V = views[tile_view[tile]];
     const int local = tile - V.tile_base;
     const int tyi = local / V.tiles_x, txi = local - tyi * V.tiles_x;
     int ix, iy;
-    L::origin(threadIdx.x, V.tw, ix, iy);
+    L::origin(producer ? 0 : (int)threadIdx.x, V.tw, ix, iy);
     const int x0 = txi * V.tw + ix, y0 = tyi * V.th + iy;
     const uint2 rg = ranges[tile];
     const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_last = rg.x;
+        s_abort = 0;
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k) {
+            mbar_init(&full[k], 32);
+            mbar_init(&empty[k], (unsigned)n_cons);
+        }
+    }
 
     float Lp[P], S[P], Tafter[P], R0[P], R1[P], R2[P], g0[P], g1[P], g2[P], gTterm[P];
     uint32_t my_last[P];
@@ -78,7 +109,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
         S[k] = 0.0f;
         float Tend = 1.0f;
         g0[k] = g1[k] = g2[k] = gTterm[k] = 0.0f;
-        if (x < V.W && y < V.H) {
+        if (!producer && x < V.W && y < V.H) {
             const long long pix = V.pix_base + (long long)y * V.W + x;
             my_last[k] = nlast[pix];
             S[k] = S_fin[pix];
@@ -96,70 +127,91 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
         R2[k] = Tend * bp.bg[2];
         thr_last = max(thr_last, my_last[k]);
     }
-    if (threadIdx.x == 0) s_last = rg.x;
-    __syncthreads();
+    __syncthreads();   // s_last and the barriers are initialised
     if (thr_last > rg.x) atomicMax(&s_last, thr_last);
-    __syncthreads();
+    __syncthreads();   // the last such barrier of the kernel: warps proceed independently below
     const uint32_t tile_last = s_last;
+    const uint32_t n_groups = (tile_last - rg.x + kGroup - 1) / kGroup;
+    // group g covers [start, end) with end = tile_last - g kGroup, start = max(rg.x, end - kGroup)
+    auto group_range = [&](uint32_t g, uint32_t &start, uint32_t &end) {
+        end = tile_last - g * kGroup;
+        start = (end - rg.x > (uint32_t)kGroup) ? end - kGroup : rg.x;
+    };
+    auto give_up = [&]() {
+        if (lane == 0) atomicOr(err, kDevErrTimeout);
+        s_abort = 1;
+    };
+
+    if (producer) {
+        for (uint32_t g = 0; g < n_groups; ++g) {
+            const int sl = (int)(g % kSlots);
+            if (!mbar_wait(&empty[sl], ((g / kSlots) & 1u) ^ 1u, kWaitLimitNs, &s_abort)) {
+                give_up();
+                return;
+            }
+            uint32_t start, end;
+            group_range(g, start, end);
+            Slot &Sl = ring[sl];
+            if (lane < (int)(end - start)) {
+                const uint32_t item = sorted_item[start + lane];
+                const float4 *src = rec + (size_t)item * kRecF4;
+                float4 q[kRecF4];
+#pragma unroll
+                for (int k = 0; k < kRecF4; ++k) q[k] = __ldg(src + k);
+                const short4 pr = prect[item];
+#pragma unroll
+                for (int k = 0; k < kRecF4; ++k) Sl.rec[lane * kRecF4 + k] = q[k];
+                Sl.rect[lane] = pr;
+                Sl.item[lane] = item;
+                if (!PIXTEST) {
+                    float4 c[kCullF4];
+                    cull_row(q[0], q[1], q[2], q[3], q[4], c);
+#pragma unroll
+                    for (int k = 0; k < kCullF4; ++k) Sl.cull[k][lane] = c[k];
+                    Sl.ref[lane] = make_float4(q[4].z, q[4].w, q[5].x, 0.0f);
+                }
+            }
+            mbar_arrive(&full[sl]);
+        }
+        return;
+    }
+
     const uint32_t warp_last = __reduce_max_sync(0xffffffffu, thr_last);
     const WarpBox wb = warp_box<P>(x0, y0);
     const BoxCull bc = SPLAT ? box_cull_splat(wb, bp.alpha_min) : box_cull(V, wb, bp.tau_skip);
     const float xf = (float)x0, yf = (float)y0;
     unsigned long long pairs = 0, blended = 0;   // evaluated / blended pairs (COUNT only)
-
-    // chunks run back to front: [start, end) with start = max(rg.x, end - kChunk)
-    auto chunk_start = [&](uint32_t e) { return (e - rg.x > (uint32_t)kChunk) ? e - kChunk : rg.x; };
-    auto stage = [&](int b, uint32_t st0, int nn) {   // issue the copies of a chunk into buffer b
-        for (int r = threadIdx.x; r < nn; r += kThreads) {
-            const uint32_t item = sorted_item[st0 + r];
-            sitem_[b][r] = item;
-            const float4 *src = rec + (size_t)item * kRecF4;
-#pragma unroll
-            for (int k = 0; k < kRecF4; ++k) cp_async16(&srec_[b][r * kRecF4 + k], src + k);
-            cp_async8(&srect_[b][r], prect + item);
+    for (uint32_t g = 0; g < n_groups; ++g) {
+        const int sl = (int)(g % kSlots);
+        uint32_t start, end;
+        group_range(g, start, end);
+        if (!mbar_wait(&full[sl], (g / kSlots) & 1u, kWaitLimitNs, &s_abort)) {
+            give_up();
+            return;
         }
-    };
-    uint32_t end = tile_last, start = chunk_start(end);
-    int buf = 0;
-    if (end > rg.x) stage(0, start, (int)(end - start));
-    while (end > rg.x) {
-        const int n = (int)(end - start);
-        cp_async_wait();   // this thread's copies of the current chunk have landed
-        if (!PIXTEST)
-            for (int r = threadIdx.x; r < n; r += kThreads) {
-                const float4 *q = &srec_[buf][r * kRecF4];
-                cull_row(q[0], q[1], q[2], q[3], q[4], &scull_[buf][r * kCullF4]);
-            }
-        __syncthreads();   // the chunk is staged; every warp is done with the other buffer
-        const uint32_t nend = start, nstart = chunk_start(nend);
-        if (nend > rg.x) stage(buf ^ 1, nstart, (int)(nend - nstart));
-        const float4 *srec = srec_[buf];
-        const uint32_t *sitem = sitem_[buf];
-        const short4 *srect = srect_[buf];
-        const float4 *scull = scull_[buf];
-        for (int w0 = (n - 1) & ~31; w0 >= 0; w0 -= 32) {
-            const int jl = w0 + lane;
-            bool need = jl < n && start + (uint32_t)jl < warp_last && !box_misses(wb, srect[jl]);
+        if (start < warp_last) {
+            const Slot &Sl = ring[sl];
+            const int n = (int)(end - start);
+            bool need = lane < n && start + (uint32_t)lane < warp_last && !box_misses(wb, Sl.rect[lane]);
             if (!PIXTEST && need) {   // skip records whose opacity stays below tau_skip on this warp
-                const float4 *q = &scull[jl * kCullF4];
-                const float4 r4 = srec[jl * kRecF4 + 4];
-                need = box_may_blend(q[0], q[1], q[2], r4.z, r4.w, srec[jl * kRecF4 + 5].x, bc);
+                const float4 r = Sl.ref[lane];
+                need = box_may_blend(Sl.cull[0][lane], Sl.cull[1][lane], Sl.cull[2][lane], r.x, r.y, r.z, bc);
             }
             unsigned m = __ballot_sync(0xffffffffu, need);
             while (m) {
                 const int b = 31 - __clz(m);
                 m ^= 1u << b;
-                const int j = w0 + b;
+                const int j = b;
                 const uint32_t idx = start + (uint32_t)j;
                 float gv[kGradUsed];
 #pragma unroll
                 for (int k = 0; k < kGradUsed; ++k) gv[k] = 0.0f;
                 bool any = false;
                 {
-                    const float4 *r = &srec[j * kRecF4];
+                    const float4 *r = &Sl.rec[j * kRecF4];
                     const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
                     short4 pr;
-                    if (PIXTEST) pr = srect[j];
+                    if (PIXTEST) pr = Sl.rect[j];
                     QuadBase qb;
                     SplatBase sb;
                     if constexpr (SPLAT)
@@ -242,7 +294,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                 }
                 const unsigned act = __ballot_sync(0xffffffffu, any);
                 if (act) {
-                    float *dst = grad_acc + (size_t)sitem[j] * kGradN;   // 64-byte aligned
+                    float *dst = grad_acc + (size_t)Sl.item[j] * kGradN;   // 64-byte aligned
                     if (__popc(act) <= kDirectLanes) {
                         if (any) {
                             red_add_v4(dst, gv[0], gv[1], gv[2], gv[3]);
@@ -257,11 +309,8 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                 }
             }
         }
-        end = nend;
-        start = nstart;
-        buf ^= 1;
+        mbar_arrive(&empty[sl]);   // this warp is done with the slot
     }
-    cp_async_wait();   // no copy may still target this CTA's shared memory when it exits
     if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -278,16 +327,16 @@ static void launch_bwd_ptsc(const ViewInfo *views_d, const int *tile_view, const
                             const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                             const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
                             const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
-                            cudaStream_t st) {
-    const unsigned threads = (unsigned)(bp.tile_px / P);
+                            uint32_t *err, cudaStream_t st) {
+    const unsigned threads = (unsigned)(bp.tile_px / P + 32);   // consumers + the producer warp
     if (pair_count)
         pdl_launch(k_render_bwd<P, true, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
             views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
-            grad_acc, pair_count);
+            grad_acc, pair_count, err);
     else
         pdl_launch(k_render_bwd<P, false, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
             views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast, dL_drgb, dL_dT,
-            grad_acc, nullptr);
+            grad_acc, nullptr, err);
 }
 
 template <int P, bool PIXTEST, bool SPLAT>
@@ -295,13 +344,13 @@ static void launch_bwd_pts(const ViewInfo *views_d, const int *tile_view, const 
                            const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                            const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
                            const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
-                           cudaStream_t st) {
+                           uint32_t *err, cudaStream_t st) {
     if (bp.chunk_bwd == 64)
         launch_bwd_ptsc<P, PIXTEST, SPLAT, 64>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
-                                               bp, T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
+                                               bp, T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, err, st);
     else
         launch_bwd_ptsc<P, PIXTEST, SPLAT, 128>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
-                                                bp, T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
+                                                bp, T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, err, st);
 }
 
 template <int P, bool PIXTEST>
@@ -309,13 +358,13 @@ static void launch_bwd_pt(const ViewInfo *views_d, const int *tile_view, const i
                           const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                           const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
                           const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
-                          cudaStream_t st) {
+                          uint32_t *err, cudaStream_t st) {
     if (bp.splat)
         launch_bwd_pts<P, PIXTEST, true>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp,
-                                         T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
+                                         T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, err, st);
     else
         launch_bwd_pts<P, PIXTEST, false>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
-                                          bp, T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
+                                          bp, T_fin, S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, err, st);
 }
 
 template <int P>
@@ -323,30 +372,30 @@ static void launch_bwd_p(const ViewInfo *views_d, const int *tile_view, const in
                          const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                          const BlendParams &bp, const float *T_fin, const float *S_fin, const uint32_t *nlast,
                          const float *dL_drgb, const float *dL_dT, float *grad_acc, unsigned long long *pair_count,
-                         cudaStream_t st) {
+                         uint32_t *err, cudaStream_t st) {
     if (bp.pixel_test)
         launch_bwd_pt<P, true>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, T_fin,
-                               S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
+                               S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, err, st);
     else
         launch_bwd_pt<P, false>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, T_fin,
-                                S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, st);
+                                S_fin, nlast, dL_drgb, dL_dT, grad_acc, pair_count, err, st);
 }
 
 cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                               const BlendParams &bp, int ppt, const float *T_fin, const float *S_fin,
                               const uint32_t *nlast, const float *dL_drgb, const float *dL_dT, float *grad_acc,
-                              unsigned long long *pair_count, cudaStream_t st, long long *launches) {
+                              unsigned long long *pair_count, uint32_t *err, cudaStream_t st, long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
     if (ppt == 1)
         launch_bwd_p<1>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast,
-                        dL_drgb, dL_dT, grad_acc, pair_count, st);
+                        dL_drgb, dL_dT, grad_acc, pair_count, err, st);
     else if (ppt == 4)
         launch_bwd_p<4>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast,
-                        dL_drgb, dL_dT, grad_acc, pair_count, st);
+                        dL_drgb, dL_dT, grad_acc, pair_count, err, st);
     else
         launch_bwd_p<2>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, T_fin, S_fin, nlast,
-                        dL_drgb, dL_dT, grad_acc, pair_count, st);
+                        dL_drgb, dL_dT, grad_acc, pair_count, err, st);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -177,7 +177,7 @@ cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, con
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                               const BlendParams &bp, int ppt, const float *T_fin, const float *S_fin,
                               const uint32_t *nlast, const float *dL_drgb, const float *dL_dT, float *grad_acc,
-                              unsigned long long *pair_count, cudaStream_t st, long long *launches);
+                              unsigned long long *pair_count, uint32_t *err, cudaStream_t st, long long *launches);
 
 // Longest-first tile order: order[] lists the tiles by descending instance count (bucketed).
 cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *order, cudaStream_t st,
