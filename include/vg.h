@@ -276,12 +276,14 @@ vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const fl
 vg_status vg_pipe_peak(vg_workspace *ws, int32_t pipe, float min_ms, double *ops_per_s, float *ms, void *stream);
 
 /* Failure-path check of the bounded device waits (no counterpart in the paper: it tests the
- * library's own failure detection).  Runs one look-back wait of the binning -- which = 0: the
- * instance scan's warp-cooperative walk, 1: a radix pass's walk -- whose predecessor never
- * publishes its status, with a limit of spin_limit polls (1..2^20; a few dozen take
- * microseconds).  The wait gives up, latches VG_ERR_TIMEOUT in the workspace and the kernel
- * returns; the next vg_query reports the timeout (and clears it) and the workspace stays usable.
- * Uses the workspace's scan scratch; nothing a later call reads is left changed. */
+ * library's own failure detection).  Runs one bounded wait that can never be satisfied --
+ * which = 0: the instance scan's warp-cooperative look-back, 1: a radix pass's look-back, both
+ * on a predecessor that never publishes its status, with a limit of spin_limit polls (1..2^20;
+ * a few dozen take microseconds); 2: the backward blend's ring wait on a full barrier no
+ * producer arrives on, with a limit of spin_limit microseconds (1..2^20).  The wait gives up,
+ * latches VG_ERR_TIMEOUT in the workspace and the kernel returns; the next vg_query reports the
+ * timeout (and clears it) and the workspace stays usable.  Uses the workspace's scan scratch;
+ * nothing a later call reads is left changed. */
 vg_status vg_selftest_timeout(vg_workspace *ws, int32_t which, int32_t spin_limit, void *stream);
 
 /* Tomography (Sec. 6.2, Eq. 21): for every angle and detector pixel,

@@ -9,6 +9,12 @@
 
 #include "vg_internal.cuh"
 
+namespace vg {
+// csrc/peaks.cu: one bounded mbarrier wait of the backward's ring that must give up after
+// limit_us microseconds (latching kDevErrTimeout in *err).
+cudaError_t launch_ring_selftest(int limit_us, uint32_t *err, cudaStream_t st, long long *launches);
+}  // namespace vg
+
 using namespace vg;
 
 namespace {
@@ -912,9 +918,14 @@ vg_status vg_pipe_peak(vg_workspace *ws, int32_t pipe, float min_ms, double *ops
 
 vg_status vg_selftest_timeout(vg_workspace *ws, int32_t which, int32_t spin_limit, void *stream) {
     if (!ws) return VG_ERR_INVALID_ARG;
-    if (which != 0 && which != 1) return fail(ws, VG_ERR_INVALID_ARG, "which must be 0 (scan) or 1 (radix pass)");
+    if (which < 0 || which > 2)
+        return fail(ws, VG_ERR_INVALID_ARG, "which must be 0 (scan), 1 (radix pass) or 2 (backward ring)");
     if (spin_limit < 1 || spin_limit > (1 << 20)) return fail(ws, VG_ERR_INVALID_ARG, "spin_limit must be 1..2^20");
     cudaStream_t st = (cudaStream_t)stream;
+    if (which == 2) {
+        VG_CUDA(ws, launch_ring_selftest(spin_limit, lookback_err_ptr(ws), st, &ws->launches));
+        return VG_OK;
+    }
     VG_TRY(ensure(ws, ws->scan_tmp, 4, "self-test status words"));
     // a predecessor that never publishes: its status word stays zero for the whole wait
     VG_CUDA(ws, cudaMemsetAsync(ws->scan_tmp.p, 0, 4 * sizeof(uint32_t), st));

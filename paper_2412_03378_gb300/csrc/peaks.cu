@@ -8,7 +8,8 @@
 //   EX2: x <- ex2.approx(-x)     one MUFU ex2 per step (x stays in (0, 1])
 // The chains' final values feed a store that never happens (the compiler cannot drop them).
 // Launched plainly (no programmatic dependent launch): nothing else runs beside a measurement.
-#include "vg_internal.cuh"
+// Also here: the self-test of the backward ring's bounded mbarrier wait.
+#include "blend.cuh"
 
 namespace vg {
 
@@ -68,6 +69,25 @@ cudaError_t launch_pipe_peak(int pipe, int iters, double *ops, cudaStream_t st) 
     else
         k_peak_ex2<<<blocks, kPeakThreads, 0, st>>>(iters);
     *ops = (double)blocks * kPeakThreads * (double)iters * kPeakUnroll * kPeakChains;
+    return cudaGetLastError();
+}
+
+// Failure-path check of the backward ring's bounded wait: one warp waits on a full barrier that
+// no producer ever arrives on; the wait gives up after limit_ns, latches kDevErrTimeout and returns.
+__global__ void k_ring_selftest(unsigned long long limit_ns, uint32_t *__restrict__ err) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        s_abort = 0;
+    }
+    __syncthreads();
+    if (!mbar_wait(&bar, 0, limit_ns, &s_abort) && threadIdx.x == 0) atomicOr(err, kDevErrTimeout);
+}
+
+cudaError_t launch_ring_selftest(int limit_us, uint32_t *err, cudaStream_t st, long long *launches) {
+    k_ring_selftest<<<1, 32, 0, st>>>((unsigned long long)limit_us * 1000ull, err);
+    *launches += 1;
     return cudaGetLastError();
 }
 

@@ -125,11 +125,13 @@ def test_graph_captured_step_matches_eager(gpu_lib, mode):
     assert ws.query()["n_instances"] == n_inst
 
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_bounded_wait_gives_up_and_is_reported(gpu_lib, which):
-    """Failure detection of the binning's look-back waits, without a GPU fault: a wait whose
-    predecessor never publishes gives up after a few dozen polls, latches VG_ERR_TIMEOUT and
-    returns; vg_query reports it once, and the workspace then renders as before (bit for bit)."""
+    """Failure detection of the bounded device waits, without a GPU fault: a binning look-back
+    whose predecessor never publishes (which 0, 1) gives up after a few dozen polls, and the
+    backward ring's wait on a full barrier no producer arrives on (which 2) after 48 us; each
+    latches VG_ERR_TIMEOUT and returns; vg_query reports it once, and the workspace then renders
+    as before (bit for bit)."""
     vg = gpu_lib
     scene, cams = synth.config1(0.25)
     o = oracle.EXACT
