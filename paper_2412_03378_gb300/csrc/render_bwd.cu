@@ -15,7 +15,9 @@
 // with vector reductions (red.global.add.v4/v2).  When at most kDirectLanes lanes of the warp
 // contribute to a Gaussian, each of them adds its 16 values directly (four v4 reductions);
 // otherwise three shuffle exchange steps leave every lane with 2 values summed over 8 lanes,
-// and all 32 lanes add those (one v2 reduction each).  Measured on the 1M-Gaussian 1280x832
+// and all 32 lanes add those (one v2 reduction each).  Thresholds 8 / 12 / 16 / 24 measured
+// 0.411 / 0.403 / 0.411 / 0.470 ms on the 1M-Gaussian 1280x832 step (the ring kernel); two more
+// butterfly steps before v2 reductions from 8 lanes only measured 0.417 ms.  Earlier, on the same
 // step: 0.465 ms against 0.539 ms for a full reduce-scatter with 16 scalar reductions; a full
 // reduce-scatter per Gaussian waits on five dependent shuffle rounds, while the L2 reduction
 // units absorb the extra (unreturned) reductions; shared-memory float atomics measured slower
@@ -30,7 +32,7 @@ namespace vg {
 // [12] sum dL/dln(kappa), [13..15] dL/dcolour.
 constexpr int kGradUsed = 16;
 static_assert(kGradUsed == kGradN, "the vector reductions cover the whole 16-float accumulator");
-constexpr int kDirectLanes = 16;   // at most this many contributing lanes: direct reductions
+constexpr int kDirectLanes = 12;   // at most this many contributing lanes: direct reductions
 
 
 // Records are staged through a ring of kGroup-record slots in shared memory, back to front: the
