@@ -139,6 +139,14 @@ def kernel_source_sha1():
     return h.hexdigest()
 
 
+def step_config(scene, cams, world, frac):
+    """The workload of the headline line, the same for both arms."""
+    return {"workload": WORKLOAD, "gaussians": scene.n, "width": cams[0].width, "height": cams[0].height,
+            "sh_degree": scene.sh_degree, "mode": "alpha_min 1/255, tau_max ln100, T_stop 1e-4",
+            "l2": "inputs larger than L2 (236 MB Gaussian parameters + 12.8 MB target per step)",
+            "parallelism": f"replicas x{world}", "frac": frac}
+
+
 def traffic_record():
     """DRAM bytes per launch of the backward blend kernel from the committed ncu summary,
     valid only while the kernel's sources are unchanged (null otherwise)."""
@@ -780,11 +788,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "gaussians": g.n, "width": cams[0].width, "height": cams[0].height,
-                   "sh_degree": scene.sh_degree, "mode": "alpha_min 1/255, tau_max ln100, T_stop 1e-4",
-                   "l2": "inputs larger than L2 (236 MB Gaussian parameters + 12.8 MB target per step)",
-                   "parallelism": f"replicas x{world}", "frac": args.frac,
-                   "binning": f"fixed capacity: {capacity} instances reserved from one tuned eager binning + 10%"},
+        "config": step_config(scene, cams, world, args.frac),
+        "binning": f"fixed capacity: {capacity} instances reserved from one tuned eager binning + 10%",
         "tuned": {"tile": f"{tuned[4]}x{tuned[5]}", "pixels_per_thread": {"fwd": tuned[0], "bwd": tuned[1]},
                   "chunk": {"fwd": tuned[2], "bwd": tuned[3]}, "by": "vg_autotune, once before the warm-up"},
         "frames_per_s": frames,
@@ -984,8 +989,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ests) / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "gaussians": scene.n, "width": cams[0].width,
-                      "height": cams[0].height, "frac": args.frac},
+           "config": step_config(scene, cams, world, args.frac),
            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
                             "extrapolated": True,
                             "sample": f"each step: keys+binning of all {scene.n} Gaussians, forward+gradient "
