@@ -153,6 +153,27 @@ def test_config2_full_size_compat(gpu_lib):
                   n_key=scene.n, n_tiles=200, grad_g=g)
 
 
+@pytest.mark.parametrize("tile", [(16, 8), (32, 16)])
+def test_config2_full_size_tile_shapes(gpu_lib, tile):
+    """The other tile shapes on the full 1M-Gaussian workload with the compat thresholds and the
+    default layouts: sampled keys, sampled tiles' lists against the oracle binned with the same
+    shape, sampled pixels, and the gradient of a loss on them."""
+    import torch
+    vg = gpu_lib
+    scene, cams, _ = synth.config2(1.0)
+    o = oracle.COMPAT
+    g = dev_scene(vg, scene)
+    ws = vg.Workspace()
+    P = cams[0].width * cams[0].height
+    rgb = torch.empty(P, 3, device="cuda:0")
+    ws.preprocess(g, cams, vg_opts(vg, o, flags=vg.FLAG_GRAD_ZERO, tile=tile))
+    ws.bin_sort()
+    assert ws.query()["n_tiles"] == _bases(cams, tile)[1][-1]
+    ws.render_fwd(rgb)
+    _check_subset(vg, ws, scene, cams, [0], o, rgb.cpu().numpy().astype(np.float64), 17, compat=True,
+                  n_key=100_000, n_tiles=60, grad_g=g, tile=tile)
+
+
 def test_config3_graph_batched_bf16(gpu_lib):
     """3M Gaussians (BF16 records, FP16 SH), 16 views 640x416..1920x1080 in one launch per stage,
     fixed capacity, autotuned, the step replayed as a CUDA graph; views 0, 7 and 15 against the
