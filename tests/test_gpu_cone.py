@@ -12,7 +12,7 @@ IMG_TOL = 1e-4
 GRAD_TOL = 1e-3
 
 
-def _run(vg, scene, cams, o, dL=None, ws=None, g=None):
+def _run(vg, scene, cams, o, dL=None, ws=None, g=None, tile=(0, 0)):
     import torch
     dev = torch.device("cuda:0")
     g = g or dev_scene(vg, scene)
@@ -23,10 +23,10 @@ def _run(vg, scene, cams, o, dL=None, ws=None, g=None):
     if dL is not None:
         grads = [torch.zeros(scene.n, 3, device=dev), torch.zeros(scene.n, 3, device=dev),
                  torch.zeros(scene.n, 4, device=dev), torch.zeros(scene.n, device=dev)]
-        ws.project_cone(g, cams, vg_opts(vg, o), proj, torch.as_tensor(np.ascontiguousarray(dL, np.float32)).to(dev),
-                        *grads)
+        ws.project_cone(g, cams, vg_opts(vg, o, tile=tile), proj,
+                        torch.as_tensor(np.ascontiguousarray(dL, np.float32)).to(dev), *grads)
     else:
-        ws.project_cone(g, cams, vg_opts(vg, o), proj)
+        ws.project_cone(g, cams, vg_opts(vg, o, tile=tile), proj)
     torch.cuda.synchronize()
     out = proj.cpu().numpy().astype(np.float64)
     if grads is not None:
@@ -34,8 +34,8 @@ def _run(vg, scene, cams, o, dL=None, ws=None, g=None):
     return ws, out, grads
 
 
-@pytest.mark.parametrize("theta", [False, True])
-def test_cone_projection_and_gradient(gpu_lib, theta):
+@pytest.mark.parametrize("theta,tile", [(False, (0, 0)), (True, (0, 0)), (False, (16, 8)), (True, (32, 16))])
+def test_cone_projection_and_gradient(gpu_lib, theta, tile):
     vg = gpu_lib
     scene = synth.tomo_scene(400, 95, log_scale=(-4.0, -2.5))
     o = dict(oracle.EXACT, density_theta=theta)
@@ -45,8 +45,8 @@ def test_cone_projection_and_gradient(gpu_lib, theta):
     cams = synth.cone_beam(3, det=48) + [synth.look_at((0.5, -3.0, 1.0), (0, 0, 0), 37, 29, 45.0)]
     P = sum(c.width * c.height for c in cams)
     dL = rng.normal(size=P)
-    ws, proj, gg = _run(vg, scene, cams, o, dL)
-    L = oracle.lists(scene, cams, o)
+    ws, proj, gg = _run(vg, scene, cams, o, dL, tile=tile)
+    L = oracle.lists(scene, cams, o, tile=tile if tile[0] else (16, 16))
     depth, rect = ws.read_keys()
     assert np.array_equal(depth, L["depth"].reshape(-1)) and np.array_equal(rect, L["rect"].reshape(-1, 4))
     ts, items = ws.read_bins()

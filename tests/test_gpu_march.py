@@ -40,8 +40,9 @@ def _scene(n, seed):
     return sc
 
 
-@pytest.mark.parametrize("theta", [False, True])
-def test_ray_march_matches_oracle(gpu_lib, theta):
+@pytest.mark.parametrize("theta,tile", [(False, (0, 0)), (True, (0, 0)), (False, (32, 16)), (False, (16, 8))])
+def test_ray_march_matches_oracle(gpu_lib, theta, tile):
+    """The march over each tile shape's lists (one CTA per tile, one pixel per thread)."""
     vg = gpu_lib
     sc = _scene(300, 61)
     o = dict(oracle.EXACT, bg=(0.2, 0.1, 0.4))
@@ -50,7 +51,7 @@ def test_ray_march_matches_oracle(gpu_lib, theta):
         o["density_theta"] = True
     cams = [synth.look_at((0.3, -0.4, -4.0), (0, 0, 0), 53, 37, 50.0),
             synth.look_at((-3.5, 0.5, 1.0), (0, 0, 0), 40, 30, 45.0)]
-    ws, g, raster, _ = run_forward(vg, sc, cams, o)
+    ws, g, raster, _ = run_forward(vg, sc, cams, o, tile=tile)
     P = raster.shape[0]
     rgb, T, err = _march(vg, ws, P, 1.5, 7.0, 300, raster)
     ref_rgb, ref_T = oracle.ray_march(sc, cams, o, 1.5, 7.0, 300)
