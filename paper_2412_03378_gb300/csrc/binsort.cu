@@ -269,22 +269,35 @@ k_onesweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
         return;
     }
     // 1. stable rank inside the tile: warp w ranks keys [w*256, (w+1)*256) of the tile in order,
-    //    32 at a time, with __match_any_sync
+    //    32 at a time: the peers of every key first (__match_any_sync, independent of one another),
+    //    then per key group the lowest lane adds the group's size to the warp's digit count with a
+    //    shared-memory atomic, whose old value the group's lanes read by shuffle (a warp's atomics on
+    //    one address take effect in program order, so the ranks stay stable; tile sort 0.088 ->
+    //    0.085 ms against the previous load / store of the count between two __syncwarp)
     const long long base = tile * kRsTile + w * (kRsItems * 32);
-    uint32_t k[kRsItems], v[kRsItems], r[kRsItems];
+    uint32_t k[kRsItems], v[kRsItems], r[kRsItems], pm[kRsItems];
 #pragma unroll
     for (int it = 0; it < kRsItems; ++it) {
         const long long i = base + it * 32 + lane;
         const bool valid = i < n;
         k[it] = valid ? keys[i] : 0u;
         v[it] = valid ? (vals ? vals[i] : (uint32_t)i) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {
+        const bool valid = base + it * 32 + lane < n;
         const uint32_t dg = valid ? ((k[it] >> shift) & mask) : 0xFFFFFFFFu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t lower = peers & ((1u << lane) - 1u);
-        const uint32_t prev = valid ? wcnt[w][dg] : 0u;
-        __syncwarp();
-        if (valid && lower == 0u) wcnt[w][dg] = prev + __popc(peers);
-        __syncwarp();
+        pm[it] = __match_any_sync(0xffffffffu, dg);
+    }
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {
+        const bool valid = base + it * 32 + lane < n;
+        const uint32_t dg = valid ? ((k[it] >> shift) & mask) : 0u;
+        const uint32_t lower = pm[it] & ((1u << lane) - 1u);
+        const int leader = __ffs(pm[it]) - 1;
+        uint32_t prev = 0u;
+        if (valid && lower == 0u) prev = atomicAdd(&wcnt[w][dg], (uint32_t)__popc(pm[it]));
+        prev = __shfl_sync(0xffffffffu, prev, leader);
         r[it] = prev + __popc(lower);
     }
     __syncthreads();
