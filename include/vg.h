@@ -113,7 +113,8 @@ typedef struct {
                              this beta, ln(1 + e^(beta x)) / beta (Supp. D uses 10) */
     float splat_dilation; /* VG_FLAG_SPLAT only: added to both variances of the 2D covariance
                              (pixels^2; 0 = Eq. 7 as printed, 0.3 = the 3DGS rasterizer) */
-    int32_t chunk;        /* blend kernels: records staged in shared memory per barrier, 64 or 128;
+    int32_t chunk;        /* blend kernels: records staged in shared memory per barrier, 64 or 128
+                             (the backward: a ring of chunk / 16 slots of 32 records);
                              0 = the autotuned value, else 128.  Results are identical. */
     int32_t tile_w, tile_h; /* screen tile in pixels: 16x16, 32x16 or 16x8; 0x0 = the autotuned
                                shape, else 16x16.  Images and gradients are identical; the
@@ -228,7 +229,10 @@ vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stre
  *   dL_drgb [pixels][3] float32, dL_dT [pixels] float32 or NULL.
  * Accumulates into float32 device buffers shaped like the inputs of vg_preprocess:
  *   dmu [n][3], dscale [n][3], dquat [n][4] (w.r.t. the unnormalised input), dkappa [n],
- *   dsh [n][K][3] (may be NULL to skip colour gradients). */
+ *   dsh [n][K][3] (may be NULL to skip colour gradients).
+ * Device-side waits of the blend kernel are bounded: one that gives up (it cannot under
+ * normal operation) latches VG_ERR_TIMEOUT, which the next vg_query or synchronising call
+ * reports; the gradients of that call are then not valid. */
 vg_status vg_render_bwd(vg_workspace *ws, const float *dL_drgb, const float *dL_dT,
                         float *dmu, float *dscale, float *dquat, float *dkappa, float *dsh,
                         void *stream);
