@@ -225,14 +225,41 @@ k_digit_hist(const uint32_t *__restrict__ keys, long long n, const unsigned long
     const int passes = (bits + 7) / 8;
     for (int i = threadIdx.x; i < 4 * kRsBins; i += kRsThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t k = keys[i];
-        for (int p = 0; p < passes; ++p) {
-            const int nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
-            atomicAdd(&h[p][(k >> (8 * p)) & ((1u << nb) - 1u)], 1u);
+    // each thread reads 4 consecutive keys at a time (16-byte loads; the key arrays are
+    // allocation bases) and counts runs of equal digits in registers, flushing a run to the shared
+    // histogram when its digit changes: a digit shared by most keys (the depth keys' exponent
+    // byte) no longer serialises on one shared counter (depth sort 0.0835 -> 0.0806 ms)
+    uint32_t run_d[4], run_c[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) run_d[p] = 0u, run_c[p] = 0u;
+    auto add = [&](uint32_t k) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            if (p < passes) {
+                const int nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
+                const uint32_t dg = (k >> (8 * p)) & ((1u << nb) - 1u);
+                if (dg != run_d[p]) {
+                    if (run_c[p]) atomicAdd(&h[p][run_d[p]], run_c[p]);
+                    run_d[p] = dg;
+                    run_c[p] = 0u;
+                }
+                ++run_c[p];
+            }
         }
+    };
+    const long long n4 = n / 4;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const uint4 q = reinterpret_cast<const uint4 *>(keys)[i];
+        add(q.x);
+        add(q.y);
+        add(q.z);
+        add(q.w);
     }
+    for (long long i = 4 * n4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) add(keys[i]);
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        if (p < passes && run_c[p]) atomicAdd(&h[p][run_d[p]], run_c[p]);
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRsBins; i += kRsThreads) {
         const uint32_t c = (&h[0][0])[i];
