@@ -383,6 +383,7 @@ cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, 
     *vals_out = const_cast<uint32_t *>(vals_in);
     if (n <= 0 || passes == 0) return cudaSuccess;
     if (n > (long long)kCountMask) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(keys_in) & 15u) return cudaErrorMisalignedAddress;   // 16-byte key loads
     const long long tiles = (n + kRsTile - 1) / kRsTile;
     cudaError_t e = cudaMemsetAsync(scratch, 0, radix_scratch_words(n, bits) * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
