@@ -289,7 +289,14 @@ k_onesweep(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
     // identity permutation: every CTA sees the same digit count and copies its tile instead
     if (ghist[(keys[tile * kRsTile] >> shift) & mask] == (uint32_t)n) {
         const long long t0 = tile * kRsTile, t1 = min(t0 + kRsTile, n);
-        for (long long i = t0 + threadIdx.x; i < t1; i += kRsThreads) {
+        // 16-byte copies (tile starts are multiples of 2048 keys of allocation-based arrays)
+        const long long q0 = t0 / 4, q1 = t1 / 4;
+        for (long long q = q0 + threadIdx.x; q < q1; q += kRsThreads) {
+            reinterpret_cast<uint4 *>(ko)[q] = reinterpret_cast<const uint4 *>(keys)[q];
+            const uint32_t i = (uint32_t)(4 * q);
+            reinterpret_cast<uint4 *>(vo)[q] = vals ? reinterpret_cast<const uint4 *>(vals)[q] : make_uint4(i, i + 1, i + 2, i + 3);
+        }
+        for (long long i = 4 * q1 + threadIdx.x; i < t1; i += kRsThreads) {
             ko[i] = keys[i];
             vo[i] = vals ? vals[i] : (uint32_t)i;
         }
