@@ -65,6 +65,8 @@ struct vg_workspace {
     DBuf<float4> march_E;                 // ray march: o'.A_k per item
     DBuf<float> tomo_dl;                  // fused tomography step: dL/dproj of one angle batch
     uint32_t *tile_order = nullptr;       // longest-first tile order of the last bin_sort
+    uint32_t *tile_order_bwd = nullptr;   // longest replay first, from the last forward (NULL: none)
+    DBuf<uint32_t> treplay, tord_bwd;     // per-tile replay lengths and their order
     int ppt_fwd = 2, ppt_bwd = 1;         // pixels per thread of the blend kernels
     int tuned_fwd = 0, tuned_bwd = 0;     // vg_autotune's choice (0: none yet)
     int tuned_chunk_fwd = 0, tuned_chunk_bwd = 0;
@@ -276,6 +278,8 @@ vg_status vg_workspace_destroy(vg_workspace *ws) {
     release(ws->counters);
     release(ws->tomo_cs);
     release(ws->tord);
+    release(ws->treplay);
+    release(ws->tord_bwd);
     release(ws->vbox);
     release(ws->march_E);
     release(ws->tomo_dl);
@@ -312,6 +316,8 @@ static vg_status reserve_sort_scratch(vg_workspace *ws, long long n) {
 
 static unsigned long long *total64_ptr(vg_workspace *ws) { return ws->counters.p + 6; }
 static uint32_t *lookback_err_ptr(vg_workspace *ws) { return (uint32_t *)(ws->counters.p + 7); }
+// The backward's tile order: by the replay lengths the last forward measured, else the binning's.
+static const uint32_t *bwd_order(vg_workspace *ws) { return ws->tile_order_bwd ? ws->tile_order_bwd : ws->tile_order; }
 
 // Reports (and clears) error bits latched on the device: a look-back timeout, a capacity
 // overflow.  Reads h_total[2] as filled by the last copy of counters[6..7].
@@ -596,8 +602,9 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
         {
             ProfScope ps(ws, ST_RANGES, st);
             VG_CUDA(ws, launch_ranges(ws->inst_key, total, total_dev, ws->ranges.p, ws->n_tiles, st, &ws->launches));
-            VG_CUDA(ws, launch_tile_order(ws->ranges.p, ws->n_tiles, ws->tord.p, st, &ws->launches));
+            VG_CUDA(ws, launch_tile_order(ws->ranges.p, nullptr, ws->n_tiles, ws->tord.p, st, &ws->launches));
             ws->tile_order = ws->tord.p;
+            ws->tile_order_bwd = nullptr;   // until a forward has measured the replay lengths
         }
         return VG_OK;
     };
@@ -642,11 +649,17 @@ static vg_status render_fwd_impl(vg_workspace *ws, float *rgb, float *T_final, v
         pc = ws->counters.p + 1;
         VG_CUDA(ws, cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), st));
     }
+    VG_TRY(ensure(ws, ws->treplay, (size_t)std::max<long long>(ws->n_tiles, 1), "tile replay lengths"));
+    VG_TRY(ensure(ws, ws->tord_bwd, (size_t)std::max<long long>(ws->n_tiles, 1), "backward tile order"));
     {
         ProfScope ps(ws, ST_FWD, st);
+        VG_CUDA(ws, cudaMemsetAsync(ws->treplay.p, 0, sizeof(uint32_t) * (size_t)ws->n_tiles, st));
         VG_CUDA(ws, launch_render_fwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
                                       ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_fwd, rgb, T_final,
-                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, pc, st, &ws->launches));
+                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, ws->treplay.p, pc, st, &ws->launches));
+        // the backward's order: longest replay (largest last blended position in the tile) first
+        VG_CUDA(ws, launch_tile_order(nullptr, ws->treplay.p, ws->n_tiles, ws->tord_bwd.p, st, &ws->launches));
+        ws->tile_order_bwd = ws->tord_bwd.p;
     }
     ws->stage = 3;
     return VG_OK;
@@ -675,7 +688,7 @@ static vg_status render_bwd_impl(vg_workspace *ws, const float *dL_drgb, const f
     }
     {
         ProfScope ps(ws, ST_BWD, st);
-        VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
+        VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)bwd_order(ws), ws->n_tiles,
                                       ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_bwd,
                                       ws->T_fin.p,
                                       ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, ws->grad.p, pc, lookback_err_ptr(ws),
@@ -862,7 +875,7 @@ vg_status vg_render_bwd_noalloc(vg_workspace *ws, const float *dL_drgb, const fl
     }
     {
         ProfScope ps(ws, ST_BWD, st);
-        VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
+        VG_CUDA(ws, launch_render_bwd(ws->views.p, ws->tile_view.p, (const int *)bwd_order(ws), ws->n_tiles,
                                       ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_bwd,
                                       ws->T_fin.p, ws->S_fin.p, ws->nlast.p, dL_drgb, dL_dT, acc, pc,
                                       lookback_err_ptr(ws), st, &ws->launches));
@@ -1176,7 +1189,7 @@ vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t 
                 cudaEventRecord(a, st);
                 e = launch_render_fwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
                                       ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, bp, ppt, rgb, nullptr,
-                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, nullptr, st, &ws->launches);
+                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, nullptr, nullptr, st, &ws->launches);
                 float ms = elapsed();
                 if (r) tf = std::min(tf, ms);
                 if (e != cudaSuccess) break;

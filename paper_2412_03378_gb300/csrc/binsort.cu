@@ -551,15 +551,19 @@ __device__ __forceinline__ int order_bucket(uint32_t c) {
     return b < kOrderBuckets - 1 ? b : kOrderBuckets - 1;
 }
 
-__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, long long n, uint32_t *__restrict__ order) {
+__device__ __forceinline__ uint32_t tile_len(const uint2 *ranges, const uint32_t *lens, long long t) {
+    if (lens) return lens[t];
+    const uint2 r = ranges[t];
+    return r.y - r.x;
+}
+
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ lens,
+                                                     long long n, uint32_t *__restrict__ order) {
     pdl_entry();
     __shared__ uint32_t cnt[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (long long t = threadIdx.x; t < n; t += blockDim.x) {
-        const uint2 r = ranges[t];
-        atomicAdd(&cnt[order_bucket(r.y - r.x)], 1u);
-    }
+    for (long long t = threadIdx.x; t < n; t += blockDim.x) atomicAdd(&cnt[order_bucket(tile_len(ranges, lens, t))], 1u);
     __syncthreads();
     if (threadIdx.x == 0) {   // descending: largest bucket first
         uint32_t run = 0;
@@ -570,16 +574,14 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
         }
     }
     __syncthreads();
-    for (long long t = threadIdx.x; t < n; t += blockDim.x) {
-        const uint2 r = ranges[t];
-        order[atomicAdd(&cnt[order_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
-    }
+    for (long long t = threadIdx.x; t < n; t += blockDim.x)
+        order[atomicAdd(&cnt[order_bucket(tile_len(ranges, lens, t))], 1u)] = (uint32_t)t;
 }
 
-cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *order, cudaStream_t st,
-                              long long *launches) {
+cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *lens, long long n_tiles, uint32_t *order,
+                              cudaStream_t st, long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
-    pdl_launch(k_tile_order, 1, 1024, 0, st, ranges, n_tiles, order);
+    pdl_launch(k_tile_order, 1, 1024, 0, st, ranges, lens, n_tiles, order);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -23,7 +23,8 @@ __global__ void __maxnreg__(PixLayout<P>::kFwdRegs)
 k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_view, const int *__restrict__ tile_order,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
              const short4 *__restrict__ prect, BlendParams bp, float *__restrict__ rgb, float *__restrict__ T_user, float *__restrict__ T_ws,
-             float *__restrict__ S_out, uint32_t *__restrict__ nlast_out, unsigned long long *__restrict__ pair_count) {
+             float *__restrict__ S_out, uint32_t *__restrict__ nlast_out, uint32_t *__restrict__ tile_replay,
+             unsigned long long *__restrict__ pair_count) {
     pdl_entry();
     using L = PixLayout<P>;
     constexpr int kChunk = CH;   // records per barrier
@@ -149,6 +150,13 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
         S_out[pix] = S[k];
         nlast_out[pix] = last[k];
     }
+    if (tile_replay) {   // the backward's replay length of this tile: its largest last blended position
+        uint32_t m = rg.x;
+#pragma unroll
+        for (int k = 0; k < P; ++k) m = max(m, last[k]);
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0 && m > rg.x) atomicMax(tile_replay + tile, m - rg.x);
+    }
     if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -164,15 +172,15 @@ template <int P, bool PIXTEST, bool SPLAT, int CH>
 static void launch_fwd_ptsc(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                             const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                             const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
-                            uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
+                            uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count, cudaStream_t st) {
     const unsigned threads = (unsigned)(bp.tile_px / P);
     if (pair_count)
         pdl_launch(k_render_fwd<P, true, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
-            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out, tile_replay,
             pair_count);
     else
         pdl_launch(k_render_fwd<P, false, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
-            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out,
+            views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out, tile_replay,
             nullptr);
 }
 
@@ -180,56 +188,56 @@ template <int P, bool PIXTEST, bool SPLAT>
 static void launch_fwd_pts(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                            const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                            const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
-                           uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
+                           uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count, cudaStream_t st) {
     if (bp.chunk_fwd == 64)
         launch_fwd_ptsc<P, PIXTEST, SPLAT, 64>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
-                                               bp, rgb, T_user, T_ws, S_out, nlast_out, pair_count, st);
+                                               bp, rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
     else
         launch_fwd_ptsc<P, PIXTEST, SPLAT, 128>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
-                                                bp, rgb, T_user, T_ws, S_out, nlast_out, pair_count, st);
+                                                bp, rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
 }
 
 template <int P, bool PIXTEST>
 static void launch_fwd_pt(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                           const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                           const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
-                          uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
+                          uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count, cudaStream_t st) {
     if (bp.splat)
         launch_fwd_pts<P, PIXTEST, true>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp,
-                                         rgb, T_user, T_ws, S_out, nlast_out, pair_count, st);
+                                         rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
     else
         launch_fwd_pts<P, PIXTEST, false>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp,
-                                          rgb, T_user, T_ws, S_out, nlast_out, pair_count, st);
+                                          rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
 }
 
 template <int P>
 static void launch_fwd_p(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                          const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                          const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
-                         uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st) {
+                         uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count, cudaStream_t st) {
     if (bp.pixel_test)
         launch_fwd_pt<P, true>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb,
-                               T_user, T_ws, S_out, nlast_out, pair_count, st);
+                               T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
     else
         launch_fwd_pt<P, false>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb,
-                                T_user, T_ws, S_out, nlast_out, pair_count, st);
+                                T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
 }
 
 cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                               const BlendParams &bp, int ppt, float *rgb, float *T_user, float *T_ws, float *S_out,
-                              uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st,
-                              long long *launches) {
+                              uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count,
+                              cudaStream_t st, long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
     if (ppt == 1)
         launch_fwd_p<1>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out,
-                        nlast_out, pair_count, st);
+                        nlast_out, tile_replay, pair_count, st);
     else if (ppt == 4)
         launch_fwd_p<4>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out,
-                        nlast_out, pair_count, st);
+                        nlast_out, tile_replay, pair_count, st);
     else
         launch_fwd_p<2>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out,
-                        nlast_out, pair_count, st);
+                        nlast_out, tile_replay, pair_count, st);
     *launches += 1;
     return cudaGetLastError();
 }

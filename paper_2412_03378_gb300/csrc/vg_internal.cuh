@@ -170,8 +170,8 @@ cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, const un
 cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                               const BlendParams &bp, int ppt, float *rgb, float *T_user, float *T_ws, float *S_out,
-                              uint32_t *nlast_out, unsigned long long *pair_count, cudaStream_t st,
-                              long long *launches);
+                              uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count,
+                              cudaStream_t st, long long *launches);
 
 cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
@@ -179,9 +179,10 @@ cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, con
                               const uint32_t *nlast, const float *dL_drgb, const float *dL_dT, float *grad_acc,
                               unsigned long long *pair_count, uint32_t *err, cudaStream_t st, long long *launches);
 
-// Longest-first tile order: order[] lists the tiles by descending instance count (bucketed).
-cudaError_t launch_tile_order(const uint2 *ranges, long long n_tiles, uint32_t *order, cudaStream_t st,
-                              long long *launches);
+// Longest-first tile order: order[] lists the tiles by descending length (bucketed): the instance
+// count from ranges, or (ranges NULL) the lengths in lens.
+cudaError_t launch_tile_order(const uint2 *ranges, const uint32_t *lens, long long n_tiles, uint32_t *order,
+                              cudaStream_t st, long long *launches);
 
 // Voxel density query (voxel.cu): grid origin, voxel size, voxel and brick (8^3) counts.
 struct VoxelGrid {
