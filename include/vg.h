@@ -107,8 +107,11 @@ typedef struct {
     uint32_t flags;      /* VG_FLAG_* */
     int32_t pixels_per_thread;  /* blend kernels: pixels owned by one thread, 1, 2 or 4;
                                    0 = the library defaults (forward 2, backward 1, the
-                                   fastest measured).  Results are identical; only speed
-                                   differs. */
+                                   fastest measured).  Every pixel is evaluated by the same
+                                   operations in every layout: images and per-pixel state are
+                                   bit-identical, forward and backward take the same skip and
+                                   clamp decisions, and gradients differ only in the order of
+                                   the accumulator's additions. */
     float softplus_beta;  /* 0: rgb = max(sh . Y + 0.5, 0); > 0: rgb = softplus of the same with
                              this beta, ln(1 + e^(beta x)) / beta (Supp. D uses 10) */
     float splat_dilation; /* VG_FLAG_SPLAT only: added to both variances of the 2D covariance

@@ -31,28 +31,17 @@ __device__ __forceinline__ PixelRay pixel_ray(const ViewInfo &V, int x, int y) {
 //   r3 = (C1.x, C1.y, C1.z, C2.x)  r4 = (C2.y, C2.z, px0, py0)     r5 = (log2(kappa sqrt(2pi)), r, g, b)
 // d' = A0 dx + A1 dy + A2, o' x d' = C0 dx + C1 dy + C2 with (dx, dy) = pixel - (px0, py0);
 //   tau = kappa sqrt(2 pi) |d_c| / |d'| exp(-|o' x d'|^2 / (2 |d'|^2))   (Eq. 19, unit-ray form).
+// Every pixel is evaluated by the same operations, whatever the pixel layout of the kernel:
+//   dx = x - px0, dy = y - py0 (rounded), d'_c = fma(A1_c, dy, fma(A0_c, dx, A2_c)) and the same
+//   for o' x d' with C.
+// The inner term depends on the pixel column only, so the pixels of a thread that share a column
+// share it (ColBase), and forward and backward compute identical bits for a pixel -- and take
+// identical skip and clamp decisions -- with any pixels-per-thread setting of either kernel.
 struct PairEval {
     float dx, dy;
     float dp[3], cr[3];
     float rs, m2, tau;
 };
-
-__device__ __forceinline__ void eval_pair(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
-                                          const float4 &r4, const float4 &r5, const PixelRay &p, PairEval &e) {
-    e.dx = __fsub_rn(p.xf, r4.z);
-    e.dy = __fsub_rn(p.yf, r4.w);
-    e.dp[0] = fmaf(r0.x, e.dx, fmaf(r0.w, e.dy, r1.z));
-    e.dp[1] = fmaf(r0.y, e.dx, fmaf(r1.x, e.dy, r1.w));
-    e.dp[2] = fmaf(r0.z, e.dx, fmaf(r1.y, e.dy, r2.x));
-    e.cr[0] = fmaf(r2.y, e.dx, fmaf(r3.x, e.dy, r3.w));
-    e.cr[1] = fmaf(r2.z, e.dx, fmaf(r3.y, e.dy, r4.x));
-    e.cr[2] = fmaf(r2.w, e.dx, fmaf(r3.z, e.dy, r4.y));
-    const float a = fmaf(e.dp[0], e.dp[0], fmaf(e.dp[1], e.dp[1], __fmul_rn(e.dp[2], e.dp[2])));
-    const float q = fmaf(e.cr[0], e.cr[0], fmaf(e.cr[1], e.cr[1], __fmul_rn(e.cr[2], e.cr[2])));
-    e.rs = rsqrt_approx(a);
-    e.m2 = __fmul_rn(q, __fmul_rn(e.rs, e.rs));
-    e.tau = __fmul_rn(ex2_approx(fmaf(e.m2, -kHalfLog2e, __fadd_rn(r5.x, p.Lp))), e.rs);
-}
 
 // A thread owns P pixels of a tile of tw x th pixels (16 x 16, 32 x 16 or 16 x 8; P = 1, 2 or 4);
 // tw th / P threads per tile.  Warps own near-square pixel boxes, which the footprint tests below
@@ -61,9 +50,8 @@ __device__ __forceinline__ void eval_pair(const float4 &r0, const float4 &r1, co
 //   P = 1: box 8 x 4,  pixel (8 wx + l % 8, 4 wy + l / 8)
 //   P = 2: box 8 x 8,  pixels (8 wx + l % 8, 8 wy + 2 (l / 8) + k)
 //   P = 4: box 16 x 8, pixels (16 wx + 2 (l % 8) + (k & 1), 8 wy + 2 (l / 8) + (k >> 1))
-// d' and o' x d' are affine in the pixel offset, so a thread's other pixels follow from its
-// first by one add per component.  Forward and backward both use pair_eval_at(), so they
-// compute the same bits and take the same skip decisions.
+// A thread's pixels lie in one column (P = 1, 2) or two (P = 4), and it forms each
+// column's inner terms (col_base) once per record.
 template <int P>
 struct PixLayout {
     static constexpr int kBoxW = P == 4 ? 16 : 8;
@@ -208,46 +196,33 @@ __device__ __forceinline__ bool box_may_blend(const float4 &ga, const float4 &gb
     return q <= 0.0f;
 }
 
-struct QuadBase {
-    float dx, dy;          // offset of the thread's first pixel from the reference pixel
-    float dp[3], cr[3];    // d' and o' x d' there
+struct ColBase {
+    float dx;              // x - px0 of the column
+    float ip[3], ic[3];    // fma(A0, dx, A2) and fma(C0, dx, C2)
 };
 
-__device__ __forceinline__ void quad_base(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
-                                          const float4 &r4, float x0, float y0, QuadBase &b) {
-    b.dx = __fsub_rn(x0, r4.z);
-    b.dy = __fsub_rn(y0, r4.w);
-    b.dp[0] = fmaf(r0.x, b.dx, fmaf(r0.w, b.dy, r1.z));
-    b.dp[1] = fmaf(r0.y, b.dx, fmaf(r1.x, b.dy, r1.w));
-    b.dp[2] = fmaf(r0.z, b.dx, fmaf(r1.y, b.dy, r2.x));
-    b.cr[0] = fmaf(r2.y, b.dx, fmaf(r3.x, b.dy, r3.w));
-    b.cr[1] = fmaf(r2.z, b.dx, fmaf(r3.y, b.dy, r4.x));
-    b.cr[2] = fmaf(r2.w, b.dx, fmaf(r3.z, b.dy, r4.y));
+__device__ __forceinline__ void col_base(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
+                                         const float4 &r4, float x, ColBase &b) {
+    b.dx = __fsub_rn(x, r4.z);
+    b.ip[0] = fmaf(r0.x, b.dx, r1.z);
+    b.ip[1] = fmaf(r0.y, b.dx, r1.w);
+    b.ip[2] = fmaf(r0.z, b.dx, r2.x);
+    b.ic[0] = fmaf(r2.y, b.dx, r3.w);
+    b.ic[1] = fmaf(r2.z, b.dx, r4.x);
+    b.ic[2] = fmaf(r2.w, b.dx, r4.y);
 }
 
-// d', o' x d', (dx, dy) of the pixel at offset (sx, sy) from the thread's first pixel, and
-// its tau (unclamped).
-__device__ __forceinline__ void pair_eval_at(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
-                                             const float4 &r5, const QuadBase &b, bool sx, bool sy, float Lp,
-                                             PairEval &e) {
-    const float A0[3] = {r0.x, r0.y, r0.z}, A1[3] = {r0.w, r1.x, r1.y};
-    const float C0[3] = {r2.y, r2.z, r2.w}, C1[3] = {r3.x, r3.y, r3.z};
-    e.dx = sx ? __fadd_rn(b.dx, 1.0f) : b.dx;
-    e.dy = sy ? __fadd_rn(b.dy, 1.0f) : b.dy;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float dpc = b.dp[c], crc = b.cr[c];
-        if (sx) {
-            dpc = __fadd_rn(dpc, A0[c]);
-            crc = __fadd_rn(crc, C0[c]);
-        }
-        if (sy) {
-            dpc = __fadd_rn(dpc, A1[c]);
-            crc = __fadd_rn(crc, C1[c]);
-        }
-        e.dp[c] = dpc;
-        e.cr[c] = crc;
-    }
+// d', o' x d', (dx, dy) and tau (unclamped) of the pixel in row y of the column b.
+__device__ __forceinline__ void pair_eval_col(const float4 &r0, const float4 &r1, const float4 &r3, const float4 &r4,
+                                              const float4 &r5, const ColBase &b, float y, float Lp, PairEval &e) {
+    e.dx = b.dx;
+    e.dy = __fsub_rn(y, r4.w);
+    e.dp[0] = fmaf(r0.w, e.dy, b.ip[0]);
+    e.dp[1] = fmaf(r1.x, e.dy, b.ip[1]);
+    e.dp[2] = fmaf(r1.y, e.dy, b.ip[2]);
+    e.cr[0] = fmaf(r3.x, e.dy, b.ic[0]);
+    e.cr[1] = fmaf(r3.y, e.dy, b.ic[1]);
+    e.cr[2] = fmaf(r3.z, e.dy, b.ic[2]);
     const float a = fmaf(e.dp[0], e.dp[0], fmaf(e.dp[1], e.dp[1], __fmul_rn(e.dp[2], e.dp[2])));
     const float q = fmaf(e.cr[0], e.cr[0], fmaf(e.cr[1], e.cr[1], __fmul_rn(e.cr[2], e.cr[2])));
     e.rs = rsqrt_approx(a);
@@ -262,34 +237,24 @@ __device__ __forceinline__ void pair_eval_at(const float4 &r0, const float4 &r1,
 // The blend runs on tau = -ln(1 - alpha) (log1pf, exact to rounding for small alpha), so the
 // transmittance update, the stored S = sum tau and the backward's log-space replay are those
 // of the default mode.  Forward and backward evaluate with the same operations.
-struct SplatBase {
-    float dx, dy;    // offset of the thread's first pixel from the reference pixel
-    float c0, c1;    // C u there (two components)
+struct SplatCol {
+    float dx;        // x - px0 of the column
+    float i0, i1;    // fma(C0, dx, C2), two components
 };
 
-__device__ __forceinline__ void splat_base(const float4 &r2, const float4 &r3, const float4 &r4, float x0, float y0,
-                                           SplatBase &b) {
-    b.dx = __fsub_rn(x0, r4.z);
-    b.dy = __fsub_rn(y0, r4.w);
-    b.c0 = fmaf(r2.y, b.dx, fmaf(r3.x, b.dy, r3.w));
-    b.c1 = fmaf(r2.z, b.dx, fmaf(r3.y, b.dy, r4.x));
+__device__ __forceinline__ void splat_col(const float4 &r2, const float4 &r3, const float4 &r4, float x, SplatCol &b) {
+    b.dx = __fsub_rn(x, r4.z);
+    b.i0 = fmaf(r2.y, b.dx, r3.w);
+    b.i1 = fmaf(r2.z, b.dx, r4.x);
 }
 
-// (dx, dy) and q = |C u|^2 of the pixel at offset (sx, sy) from the thread's first pixel;
-// returns the unclamped opacity o G'(p).
-__device__ __forceinline__ float splat_at(const float4 &r2, const float4 &r3, const float4 &r5, const SplatBase &b,
-                                          bool sx, bool sy, float &dx, float &dy, float &q) {
-    float c0 = b.c0, c1 = b.c1;
-    dx = sx ? __fadd_rn(b.dx, 1.0f) : b.dx;
-    dy = sy ? __fadd_rn(b.dy, 1.0f) : b.dy;
-    if (sx) {
-        c0 = __fadd_rn(c0, r2.y);
-        c1 = __fadd_rn(c1, r2.z);
-    }
-    if (sy) {
-        c0 = __fadd_rn(c0, r3.x);
-        c1 = __fadd_rn(c1, r3.y);
-    }
+// (dx, dy) and q = |C u|^2 of the pixel in row y of the column b (the same operations for every
+// pixel layout); returns the unclamped opacity o G'(p).
+__device__ __forceinline__ float splat_at(const float4 &r3, const float4 &r4, const float4 &r5, const SplatCol &b,
+                                          float y, float &dx, float &dy, float &q) {
+    dx = b.dx;
+    dy = __fsub_rn(y, r4.w);
+    const float c0 = fmaf(r3.x, dy, b.i0), c1 = fmaf(r3.y, dy, b.i1);
     q = fmaf(c0, c0, __fmul_rn(c1, c1));
     return ex2_approx(fmaf(q, -kHalfLog2e, r5.x));
 }

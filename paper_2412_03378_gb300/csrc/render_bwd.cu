@@ -214,12 +214,16 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                     const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
                     short4 pr;
                     if (PIXTEST) pr = Sl.rect[j];
-                    QuadBase qb;
-                    SplatBase sb;
-                    if constexpr (SPLAT)
-                        splat_base(r2, r3, r4, xf, yf, sb);
-                    else
-                        quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
+                    constexpr int kCols = P == 4 ? 2 : 1;   // pixel columns of the thread
+                    ColBase cb[kCols];
+                    SplatCol sc[kCols];
+#pragma unroll
+                    for (int c = 0; c < kCols; ++c) {
+                        if constexpr (SPLAT)
+                            splat_col(r2, r3, r4, c ? xf + 1.0f : xf, sc[c]);
+                        else
+                            col_base(r0, r1, r2, r3, r4, c ? xf + 1.0f : xf, cb[c]);
+                    }
 #pragma unroll
                     for (int k = 0; k < P; ++k) {
                         bool valid = idx < my_last[k];
@@ -227,7 +231,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                         float tau, e2, alpha, pdx, pdy, kG, ca, cq;
                         if constexpr (SPLAT) {
                             float q;
-                            const float ar = splat_at(r2, r3, r5, sb, L::ox(k) != 0, L::oy(k) != 0, pdx, pdy, q);
+                            const float ar = splat_at(r3, r4, r5, sc[L::ox(k)], L::oy(k) ? yf + (float)L::oy(k) : yf, pdx, pdy, q);
                             if (COUNT) pairs += valid;
                             const bool clamped = ar > bp.alpha_max;
                             const float a_c = fminf(ar, bp.alpha_max);
@@ -241,7 +245,7 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                             cq = -1.0f;        // ln(o G') = ln o - q/2
                         } else {
                             PairEval e;
-                            pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
+                            pair_eval_col(r0, r1, r3, r4, r5, cb[L::ox(k)], L::oy(k) ? yf + (float)L::oy(k) : yf, Lp[k], e);
                             if (COUNT) pairs += valid;
                             const bool clamped = e.tau > bp.tau_max;
                             const float t_c = fminf(e.tau, bp.tau_max);
@@ -523,11 +527,16 @@ k_chain(GaussIn g, const ViewInfo *__restrict__ views, int n_views, float *__res
                 }
             }
         }
+        // the parameters are requested before the wait, so that their round trip overlaps the SH
+        // rows' copies
+        float mu[3], s[3], q[4], kin;
+        if (lane < nloc) {
+            load_gauss<RT>(g, gi, mu, s, q, kin);
+        }
         rows_wait();
         __syncwarp();
         if (lane < nloc) {
-        float mu[3], s[3], q[4], kin, Sig[9], Rq[9], qn[4], smax;
-        load_gauss<RT>(g, gi, mu, s, q, kin);
+        float Sig[9], Rq[9], qn[4], smax;
         const Density dn = density_of(g, kin, s);
         const float kap = dn.kap;
         const bool valid = key_cov(mu, s, q, dn.kap_key, Sig, Rq, qn, smax);

@@ -3,8 +3,8 @@
 // One CTA per tile (16 x 16, 32 x 16 or 16 x 8 pixels), tiles taken longest list first; each of
 // the tw th / P threads owns P pixels (P = 1, 2, 4).  Records of the tile's Gaussians are staged through shared memory in
 // depth-ordered chunks (one record per thread); every record is read once per thread and
-// serves its P pixels, whose d' and o' x d' follow from the first pixel's by one add per
-// component.  The closed form is evaluated in FP32 (FMA pipe + 3 MUFU ops per pair); the CTA
+// serves its P pixels, which share the record's per-column inner terms (col_base: the pixels
+// of a thread lie in one or two columns).  The closed form is evaluated in FP32 (FMA pipe + 3 MUFU ops per pair); the CTA
 // leaves once all of its pixels have reached T < T_stop.  The per-pixel update is branch-free: a
 // pixel that does not blend the visited Gaussian (finished, outside the image or the footprint,
 // or below the skip threshold) takes tau = 0 (alpha = 0), which leaves its colour, T and S
@@ -91,12 +91,16 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                 const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
                 short4 pr;
                 if (PIXTEST) pr = srect[j];
-                QuadBase qb;
-                SplatBase sb;
-                if constexpr (SPLAT)
-                    splat_base(r2, r3, r4, xf, yf, sb);
-                else
-                    quad_base(r0, r1, r2, r3, r4, xf, yf, qb);
+                constexpr int kCols = P == 4 ? 2 : 1;   // pixel columns of the thread
+                ColBase cb[kCols];
+                SplatCol sc[kCols];
+#pragma unroll
+                for (int c = 0; c < kCols; ++c) {
+                    if constexpr (SPLAT)
+                        splat_col(r2, r3, r4, c ? xf + 1.0f : xf, sc[c]);
+                    else
+                        col_base(r0, r1, r2, r3, r4, c ? xf + 1.0f : xf, cb[c]);
+                }
 #pragma unroll
                 for (int k = 0; k < P; ++k) {
                     bool valid = (live >> k) & 1u;
@@ -105,7 +109,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                     if constexpr (SPLAT) {   // Eq. 6: alpha = min(o G'(p), alpha_max)
                         float dx, dy, q;
                         const float a_c =
-                            fminf(splat_at(r2, r3, r5, sb, L::ox(k) != 0, L::oy(k) != 0, dx, dy, q), bp.alpha_max);
+                            fminf(splat_at(r3, r4, r5, sc[L::ox(k)], L::oy(k) ? yf + (float)L::oy(k) : yf, dx, dy, q), bp.alpha_max);
                         if (COUNT) pairs += valid;
                         valid = valid && a_c >= bp.alpha_min;
                         const float alpha = valid ? a_c : 0.0f;
@@ -114,7 +118,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                         w = __fmul_rn(alpha, T[k]);
                     } else {
                         PairEval e;
-                        pair_eval_at(r0, r1, r2, r3, r5, qb, L::ox(k) != 0, L::oy(k) != 0, Lp[k], e);
+                        pair_eval_col(r0, r1, r3, r4, r5, cb[L::ox(k)], L::oy(k) ? yf + (float)L::oy(k) : yf, Lp[k], e);
                         if (COUNT) pairs += valid;
                         const float t_c = fminf(e.tau, bp.tau_max);
                         valid = valid && t_c >= bp.tau_skip;

@@ -426,3 +426,36 @@ def test_density_reparam_and_softplus_colour(gpu_lib, variant):
     # dtau/ds_min ~ +tau/s_min along the thin axis, both carrying the FP32 error of the per-pixel
     # sums: the flattened Gaussians' scale gradient is held to 1e-2
     check_grads(gg, ref, scene, GRAD_TOL, flat_tol={"scale": 1e-2} if o.get("density_theta") else None)
+
+
+@pytest.mark.parametrize("splat", [False, True])
+@pytest.mark.parametrize("mode", ["exact", "compat"])
+def test_pixel_layouts_compute_identical_bits(gpu_lib, mode, splat):
+    """Every pixel is evaluated by the same FP32 operations whatever the pixels-per-thread layout
+    of the kernel, so the forward's image, transmittance, log-transmittance and last blended index
+    are bit-identical for 1, 2 and 4 pixels per thread, and the backward (one pixel per thread by
+    default) replays the forward (two by default) with the same skip and clamp decisions: the
+    blended pairs it counts are exactly the forward's."""
+    vg = gpu_lib
+    scene, cams, _ = synth.config2(0.1, 640, 416)
+    o = dict(oracle.COMPAT if mode == "compat" else oracle.EXACT, bg=(0.3, 0.2, 0.1))
+    if splat:
+        o.update(splat=True, splat_dilation=0.3)
+    g = dev_scene(vg, scene)
+    ref = None
+    for ppt in (1, 2, 4):
+        ws, _, rgb, T = run_forward(vg, scene, cams, o, g=g, ppt=ppt)
+        S, last = ws.read_pixel_state()
+        got = (rgb, T, S.copy(), last.copy())
+        if ref is None:
+            ref = got
+            continue
+        for a, b, name in zip(ref, got, ("rgb", "T", "S", "last")):
+            assert np.array_equal(a, b), f"{name} differs between 1 and {ppt} pixels per thread"
+    rng = np.random.default_rng(5)
+    wr = rng.normal(size=(ref[0].shape[0], 3))
+    for ppt in (0, 1, 2, 4):   # 0: the library defaults (forward 2, backward 1 pixels per thread)
+        ws, _, _, _ = run_forward(vg, scene, cams, o, g=g, ppt=ppt, flags=vg.FLAG_COUNT_PAIRS)
+        run_backward(vg, ws, g, wr)
+        q = ws.query()
+        assert q["n_blend"] == q["n_blend_bwd"] > 0, (ppt, q["n_blend"], q["n_blend_bwd"])
