@@ -310,3 +310,53 @@ def test_config5_full_size_bf16(gpu_lib):
     assert torch.isfinite(grads[0]).all()
     _check_subset(vg, ws, scene, cams, [3], o, rgb.cpu().numpy().astype(np.float64), 51, compat=True,
                   n_key=300_000, n_tiles=30, grad_g=g)
+
+
+@pytest.mark.parametrize("mode", ["exact", "compat"])
+def test_gradient_accuracy_every_pixel(gpu_lib, mode):
+    """100,000 Gaussians of the 1M-Gaussian workload's generator (20% flattened 100:1) at 640x416,
+    with a loss on every pixel, against the oracle's analytic gradient, per Gaussian and parameter
+    block.  Means, densities and SH meet the render tests' bars (1e-3, 5e-3 flattened) on every
+    Gaussian; so do the scales of every Gaussian whose thin axis spans at least 0.01 px on screen.
+    Below that width (about half of the flattened Gaussians here: axes of 4e-5 at depth 4, a
+    conditioning z / s_min near 1e5) the scale gradient is a large cancellation in the moment form
+    the backward accumulates, and a few of them reach 1e-1; quaternion gradients of a few
+    Gaussians with nearly equal scales (a rotation direction that changes almost nothing) exceed
+    1e-3.  Those outliers are counted and bounded here, and listed in the design notes."""
+    vg = gpu_lib
+    scene, cams, _ = synth.config2(0.1, 640, 416)
+    o = dict(oracle.COMPAT if mode == "compat" else oracle.EXACT, bg=(0.3, 0.2, 0.1))
+    g = dev_scene(vg, scene)
+    ws = vg.Workspace()
+    P = cams[0].width * cams[0].height
+    import torch
+    rgb = torch.empty(P, 3, device="cuda:0")
+    ws.preprocess(g, cams, vg_opts(vg, o))
+    ws.bin_sort()
+    ws.render_fwd(rgb)
+    rng = np.random.default_rng(5)
+    wr = rng.normal(size=(P, 3))
+    if mode == "compat":   # pixels whose threshold decisions FP32 and FP64 took differently weigh 0
+        keep, L, _ = compat_check(ws, scene, cams, o, rgb.cpu().numpy().astype(np.float64), label="every pixel")
+        wr = wr * keep[:, None]
+    else:
+        L = oracle.lists(scene, cams, o)
+    gg = run_backward(vg, ws, g, wr)
+    ref = oracle.render_grad(scene, cams, o, L, wr)
+    from gpu_util import FLAT_ANISO, FLAT_TOL, grad_block_err
+    aniso = scene.scale.max(1) / scene.scale.min(1)
+    flat = aniso > FLAT_ANISO
+    bar = np.where(flat, FLAT_TOL, GRAD_TOL)
+    depth = (scene.mu.astype(np.float64) @ np.asarray(cams[0].R).T + np.asarray(cams[0].t))[:, 2]
+    width = cams[0].fx * scene.scale.min(1) / depth   # the thin axis on screen, in pixels
+    err = {k: grad_block_err(gg[k], ref[k], scene.n) for k in ("mu", "scale", "quat", "kappa", "sh")}
+    print(f"{mode}: worst block errors", {k: f"{v.max():.2e}" for k, v in err.items()},
+          "above the bar:", {k: int(np.sum(v > bar)) for k, v in err.items()})
+    for k in ("mu", "kappa", "sh"):
+        assert np.all(err[k] <= bar), (k, float(err[k].max()))
+    wide = width >= 0.01
+    assert np.all(err["scale"][wide] <= bar[wide]), float(err["scale"][wide].max())
+    thin_bad = err["scale"][~wide] > bar[~wide]
+    assert thin_bad.sum() <= 10 and err["scale"].max() < 0.5, (int(thin_bad.sum()), float(err["scale"].max()))
+    q_bad = err["quat"] > bar
+    assert q_bad.sum() <= 10 and err["quat"].max() < 1e-2, (int(q_bad.sum()), float(err["quat"].max()))
