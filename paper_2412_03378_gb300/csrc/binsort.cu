@@ -193,7 +193,7 @@ cudaError_t launch_scan_gather(const uint32_t *count, const uint32_t *perm, uint
 }
 
 // ---------------------------------------------------------------------------- radix sort
-// Stable LSD radix sort, one kernel per 8-bit digit (Adinets, Merrill: "Onesweep: A Faster
+// Stable LSD radix sort, one kernel per digit of at most 8 bits (Adinets, Merrill: "Onesweep: A Faster
 // Least Significant Digit Radix Sort for GPUs", 2022): the digit totals of every pass come
 // from one histogram kernel up front; per pass a CTA ranks its 2048-key tile stably in shared
 // memory, finds each digit's offset from the tiles before it by decoupled look-back, and
@@ -208,6 +208,19 @@ constexpr int kRsTile = kRsThreads * kRsItems;      // keys per CTA tile
 constexpr int kRsBins = 256;
 
 static int rs_passes(int bits) { return (bits + 7) / 8; }
+
+// Digit widths: the bits are shared out as evenly as the pass count allows, low digits first
+// (13 bits: 7 + 6 rather than 8 + 5), so that no pass scatters a tile over all 256 buckets when
+// fewer suffice: a wider low digit spreads each tile's keys over more, shorter output runs.
+__host__ __device__ __forceinline__ int rs_width(int bits, int p) {
+    const int passes = (bits + 7) / 8;
+    return bits / passes + (p < bits % passes ? 1 : 0);
+}
+__host__ __device__ __forceinline__ int rs_shift(int bits, int p) {
+    int s = 0;
+    for (int q = 0; q < p; ++q) s += rs_width(bits, q);
+    return s;
+}
 
 size_t radix_scratch_words(long long n, int bits) {
     const long long tiles = (n + kRsTile - 1) / kRsTile;
@@ -229,15 +242,19 @@ k_digit_hist(const uint32_t *__restrict__ keys, long long n, const unsigned long
     // allocation bases) and counts runs of equal digits in registers, flushing a run to the shared
     // histogram when its digit changes: a digit shared by most keys (the depth keys' exponent
     // byte) no longer serialises on one shared counter (depth sort 0.0835 -> 0.0806 ms)
-    uint32_t run_d[4], run_c[4];
+    uint32_t run_d[4], run_c[4], dmask[4];
+    int dshift[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) run_d[p] = 0u, run_c[p] = 0u;
+    for (int p = 0; p < 4; ++p) {
+        run_d[p] = 0u, run_c[p] = 0u;
+        dshift[p] = rs_shift(bits, p);
+        dmask[p] = (1u << rs_width(bits, p)) - 1u;
+    }
     auto add = [&](uint32_t k) {
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             if (p < passes) {
-                const int nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
-                const uint32_t dg = (k >> (8 * p)) & ((1u << nb) - 1u);
+                const uint32_t dg = (k >> dshift[p]) & dmask[p];
                 if (dg != run_d[p]) {
                     if (run_c[p]) atomicAdd(&h[p][run_d[p]], run_c[p]);
                     run_d[p] = dg;
@@ -402,10 +419,9 @@ cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, 
     const uint32_t *ki = keys_in, *vi = vals_in;
     for (int p = 0; p < passes; ++p) {
         uint32_t *kout = (p & 1) ? kb : ka, *vout = (p & 1) ? vb : va;
-        const int nb = bits - 8 * p < 8 ? bits - 8 * p : 8;
-        pdl_launch(k_onesweep, (unsigned)tiles, kRsThreads, 0, st, ki, vi, kout, vout, n, n_dev, 8 * p, (1u << nb) - 1u,
-                                                           ghist + p * kRsBins, status + (size_t)p * tiles * kRsBins,
-                                                           ctr + p, err);
+        const int nb = rs_width(bits, p);
+        pdl_launch(k_onesweep, (unsigned)tiles, kRsThreads, 0, st, ki, vi, kout, vout, n, n_dev, rs_shift(bits, p),
+                   (1u << nb) - 1u, ghist + p * kRsBins, status + (size_t)p * tiles * kRsBins, ctr + p, err);
         *launches += 1;
         ki = kout;
         vi = vout;
