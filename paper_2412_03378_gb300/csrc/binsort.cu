@@ -214,7 +214,7 @@ static int rs_passes(int bits) { return (bits + 7) / 8; }
 // fewer suffice: a wider low digit spreads each tile's keys over more, shorter output runs.
 __host__ __device__ __forceinline__ int rs_width(int bits, int p) {
     const int passes = (bits + 7) / 8;
-    return bits / passes + (p < bits % passes ? 1 : 0);
+    return passes ? bits / passes + (p < bits % passes ? 1 : 0) : 0;
 }
 __host__ __device__ __forceinline__ int rs_shift(int bits, int p) {
     int s = 0;
