@@ -118,9 +118,12 @@ typedef struct {
                              (pixels^2; 0 = Eq. 7 as printed, 0.3 = the 3DGS rasterizer) */
     int32_t chunk;        /* blend kernels: records staged in shared memory per barrier, 64 or 128
                              (the backward: a ring of chunk / 16 slots of 32 records);
-                             0 = the autotuned value, else 128.  Results are identical. */
+                             0 = the autotuned value, else 128.  Images are bit-identical;
+                             gradients differ only in the order of the accumulator's
+                             additions. */
     int32_t tile_w, tile_h; /* screen tile in pixels: 16x16, 32x16 or 16x8; 0x0 = the autotuned
-                               shape, else 16x16.  Images and gradients are identical; the
+                               shape, else 16x16.  Images are bit-identical and gradients
+                               differ only in the order of the accumulator's additions; the
                                tile lists (and with them the instance count) follow the shape,
                                each list still in depth order. */
 } vg_opts;
