@@ -362,7 +362,7 @@ def run_march(args):
 
 # ----------------------------------------------------------------------------- batched graph path
 def graph_step(vg, g, cams, steps, warmup, dev, target_seed=2102):
-    """A whole training step over all `cams` (preprocess, bin/sort, forward, L2 loss, backward)
+    """A whole training step over all `cams` (preprocess, bin/sort, forward with the L2 loss fused, backward)
     with fixed-capacity binning, autotuned pixels per thread, captured once as a CUDA graph and
     replayed `steps` times.  Returns the timing, the rendered images and the workspace."""
     import torch
@@ -390,8 +390,7 @@ def graph_step(vg, g, cams, steps, warmup, dev, target_seed=2102):
     def step():
         ws.preprocess(g, cams, opts)
         ws.bin_sort()
-        ws.render_fwd(rgb, T)
-        ws.l2_loss(rgb, tgt, scale, loss, dl)
+        ws.render_fwd_l2(rgb, T, tgt, scale, loss, dl)
         ws.render_bwd(dl, None, *grads)
 
     side = torch.cuda.Stream()
@@ -581,8 +580,7 @@ def run_ours(args):
     def step(gg=g, target_dev=None):
         ws.preprocess(gg, cams, opts)
         ws.bin_sort()
-        ws.render_fwd(rgb, T)
-        ws.l2_loss(rgb, tgt if target_dev is None else target_dev, scale, loss, dldrgb)
+        ws.render_fwd_l2(rgb, T, tgt if target_dev is None else target_dev, scale, loss, dldrgb)
         ws.render_bwd(dldrgb, None, *grads)
 
     def fwd_only():
@@ -659,8 +657,7 @@ def run_ours(args):
     # ---- pair counts for the roofline (separate, counted launches outside the timed region)
     ws.preprocess(g, cams, vg.Opts.compat(flags=vg.FLAG_GRAD_ZERO | vg.FLAG_COUNT_PAIRS))
     ws.bin_sort()
-    ws.render_fwd(rgb, T)
-    ws.l2_loss(rgb, tgt, scale, loss, dldrgb)
+    ws.render_fwd_l2(rgb, T, tgt, scale, loss, dldrgb)
     ws.render_bwd(dldrgb, None, *grads)
     q = ws.query()
 
@@ -795,7 +792,8 @@ def run_ours(args):
         "frames_per_s": frames,
         "stages_ms": stage_ms,
         "stages_basis": "event-timed per stage over a separate pass of the same steps; inside the timed "
-                        "region only k_render_bwd is bracketed by events",
+                        "region only k_render_bwd is bracketed by events; the L2 loss is fused into the "
+                        "forward (vg_render_fwd_l2), so render_fwd includes it",
         "roofline": roofline,
         "roofline_fwd": fwd_roof,
         "roofline_hbm": roofline_hbm,
@@ -886,8 +884,9 @@ def splat_ab(vg, scene, cams, tgt, steps, warmup, dev, vol_step_ms, vol_frames):
         ws.render_fwd(rgb, T)
 
     def step():
-        fwd()
-        ws.l2_loss(rgb, tgt, 1.0 / float(rgb.numel()), loss, dl)
+        ws.preprocess(g, cams, opts)
+        ws.bin_sort()
+        ws.render_fwd_l2(rgb, T, tgt, 1.0 / float(rgb.numel()), loss, dl)
         ws.render_bwd(dl, None, *grads)
 
     def timed(fn):

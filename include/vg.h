@@ -230,6 +230,20 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream);
  * vg_render_bwd. */
 vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stream);
 
+/* vg_render_fwd with the L2 image loss of vg_l2_loss fused into the blend's epilogue: each
+ * pixel's colour is compared with the target where the blend writes it, so no second kernel
+ * reads the image back.  The loss is the training loss of the benchmark workloads (an L2 loss
+ * against a target image); the paper's own training losses (Supp. D) are out of scope.
+ *   rgb, T_final  as vg_render_fwd (rgb must not be NULL)
+ *   target   [sum_v H_v W_v][3] float32, device, the layout of rgb
+ *   *loss    = scale * sum (rgb - target)^2, a device scalar (overwritten)
+ *   dL_drgb  [sum_v H_v W_v][3] float32, device: 2 scale (rgb - target) (overwritten)
+ * rgb, T_final and dL_drgb are bit-identical to vg_render_fwd followed by vg_l2_loss; the loss
+ * differs from vg_l2_loss's only in the order of its additions.  NULL rgb, target, loss or
+ * dL_drgb: VG_ERR_INVALID_ARG. */
+vg_status vg_render_fwd_l2(vg_workspace *ws, float *rgb, float *T_final, const float *target, float scale,
+                           float *loss, float *dL_drgb, void *stream);
+
 /* Backward of the last vg_render_fwd on this workspace (derived from Eq. 14 and Eq. 19 by
  * the chain rule; the forward is replayed back to front, nothing per pair is stored).
  *   dL_drgb [pixels][3] float32, dL_dT [pixels] float32 or NULL.

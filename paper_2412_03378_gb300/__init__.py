@@ -96,6 +96,8 @@ _SIGS = {
                       ctypes.c_void_p],
     "vg_bin_sort": [ctypes.c_void_p, ctypes.c_void_p],
     "vg_render_fwd": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "vg_render_fwd_l2": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
+                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vg_render_bwd": [ctypes.c_void_p] + [ctypes.c_void_p] * 7 + [ctypes.c_void_p],
     "vg_render_bwd_noalloc": [ctypes.c_void_p] + [ctypes.c_void_p] * 7 + [ctypes.c_void_p],
     "vg_project_tomo": [ctypes.c_void_p] * 11,
@@ -298,6 +300,11 @@ class Workspace:
 
     def render_fwd(self, rgb, T_final=None, stream=None):
         self._chk(self._L.vg_render_fwd(self.h, _ptr(rgb), _ptr(T_final), _stream(stream)))
+
+    def render_fwd_l2(self, rgb, T_final, target, scale, loss, dL_drgb, stream=None):
+        """vg_render_fwd_l2: the forward with the L2 loss against `target` fused into it."""
+        self._chk(self._L.vg_render_fwd_l2(self.h, _ptr(rgb), _ptr(T_final), _ptr(target), float(scale), _ptr(loss),
+                                           _ptr(dL_drgb), _stream(stream)))
 
     def render_bwd(self, dL_drgb, dL_dT, dmu, dscale, dquat, dkappa, dsh, stream=None):
         self._chk(self._L.vg_render_bwd(self.h, _ptr(dL_drgb), _ptr(dL_dT), _ptr(dmu), _ptr(dscale), _ptr(dquat),

@@ -636,11 +636,13 @@ vg_status vg_bin_sort(vg_workspace *ws, void *stream) {
     return VG_OK;
 }
 
-static vg_status render_fwd_impl(vg_workspace *ws, float *rgb, float *T_final, void *stream, bool rgb_optional) {
+static vg_status render_fwd_impl(vg_workspace *ws, float *rgb, float *T_final, void *stream, bool rgb_optional,
+                                 const L2Fused &l2 = L2Fused{}) {
     if (!ws) return VG_ERR_INVALID_ARG;
     if (ws->stage < 2) return fail(ws, VG_ERR_STATE, "vg_render_fwd before vg_bin_sort");
     if (!rgb && ws->n_pixels > 0 && !rgb_optional) return fail(ws, VG_ERR_INVALID_ARG, "rgb is NULL");
     cudaStream_t st = (cudaStream_t)stream;
+    if (l2.target) VG_CUDA(ws, cudaMemsetAsync(l2.loss, 0, sizeof(float), st));
     VG_TRY(ensure(ws, ws->S_fin, (size_t)ws->n_pixels, "pixel state"));
     VG_TRY(ensure(ws, ws->T_fin, (size_t)ws->n_pixels, "pixel state"));
     VG_TRY(ensure(ws, ws->nlast, (size_t)ws->n_pixels, "pixel state"));
@@ -656,7 +658,7 @@ static vg_status render_fwd_impl(vg_workspace *ws, float *rgb, float *T_final, v
         VG_CUDA(ws, cudaMemsetAsync(ws->treplay.p, 0, sizeof(uint32_t) * (size_t)ws->n_tiles, st));
         VG_CUDA(ws, launch_render_fwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
                                       ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, ws->bp, ws->ppt_fwd, rgb, T_final,
-                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, ws->treplay.p, pc, st, &ws->launches));
+                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, ws->treplay.p, pc, l2, st, &ws->launches));
         // the backward's order: longest replay (largest last blended position in the tile) first
         VG_CUDA(ws, launch_tile_order(nullptr, ws->treplay.p, ws->n_tiles, ws->tord_bwd.p, st, &ws->launches));
         ws->tile_order_bwd = ws->tord_bwd.p;
@@ -667,6 +669,18 @@ static vg_status render_fwd_impl(vg_workspace *ws, float *rgb, float *T_final, v
 
 vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stream) {
     return render_fwd_impl(ws, rgb, T_final, stream, false);
+}
+
+vg_status vg_render_fwd_l2(vg_workspace *ws, float *rgb, float *T_final, const float *target, float scale,
+                           float *loss, float *dL_drgb, void *stream) {
+    if (!ws) return VG_ERR_INVALID_ARG;
+    if (!loss || (ws->n_pixels > 0 && (!rgb || !target || !dL_drgb)))
+        return fail(ws, VG_ERR_INVALID_ARG, "invalid loss arguments");
+    if (ws->n_pixels == 0) {   // no pixel: the loss is zero (the forward still records its state)
+        VG_CUDA(ws, cudaMemsetAsync(loss, 0, sizeof(float), (cudaStream_t)stream));
+        return render_fwd_impl(ws, rgb, T_final, stream, false);
+    }
+    return render_fwd_impl(ws, rgb, T_final, stream, false, L2Fused{target, dL_drgb, loss, scale});
 }
 
 static vg_status render_bwd_impl(vg_workspace *ws, const float *dL_drgb, const float *dL_dT, float *dmu, float *dscale,
@@ -1189,7 +1203,8 @@ vg_status vg_autotune(vg_workspace *ws, int32_t reps, int32_t *ppt_fwd, int32_t 
                 cudaEventRecord(a, st);
                 e = launch_render_fwd(ws->views.p, ws->tile_view.p, (const int *)ws->tile_order, ws->n_tiles,
                                       ws->ranges.p, ws->inst_item, ws->rec.p, ws->prect.p, bp, ppt, rgb, nullptr,
-                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, nullptr, nullptr, st, &ws->launches);
+                                      ws->T_fin.p, ws->S_fin.p, ws->nlast.p, nullptr, nullptr, L2Fused{}, st,
+                                      &ws->launches);
                 float ms = elapsed();
                 if (r) tf = std::min(tf, ms);
                 if (e != cudaSuccess) break;

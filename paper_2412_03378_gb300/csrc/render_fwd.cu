@@ -24,7 +24,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ sorted_item, const float4 *__restrict__ rec,
              const short4 *__restrict__ prect, BlendParams bp, float *__restrict__ rgb, float *__restrict__ T_user, float *__restrict__ T_ws,
              float *__restrict__ S_out, uint32_t *__restrict__ nlast_out, uint32_t *__restrict__ tile_replay,
-             unsigned long long *__restrict__ pair_count) {
+             unsigned long long *__restrict__ pair_count, L2Fused l2) {
     pdl_entry();
     using L = PixLayout<P>;
     constexpr int kChunk = CH;   // records per barrier
@@ -139,20 +139,33 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
         }
         if (__syncthreads_count(live != 0) == 0) break;
     }
+    float l2acc = 0.0f;   // this thread's share of sum (rgb - target)^2 (fused loss only)
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         const int x = x0 + L::ox(k), y = y0 + L::oy(k);
         if (x >= V.W || y >= V.H) continue;
         const long long pix = V.pix_base + (long long)y * V.W + x;
         if (rgb) {   // absent for the cone-beam projection, which needs T alone
-            rgb[3 * pix + 0] = fmaf(T[k], bp.bg[0], c0[k]);
-            rgb[3 * pix + 1] = fmaf(T[k], bp.bg[1], c1[k]);
-            rgb[3 * pix + 2] = fmaf(T[k], bp.bg[2], c2[k]);
+            const float o[3] = {fmaf(T[k], bp.bg[0], c0[k]), fmaf(T[k], bp.bg[1], c1[k]), fmaf(T[k], bp.bg[2], c2[k])};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                rgb[3 * pix + c] = o[c];
+                if (l2.target) {   // the operations of k_l2_loss: the same gradient bits
+                    const float d = o[c] - l2.target[3 * pix + c];
+                    l2.grad[3 * pix + c] = 2.0f * l2.scale * d;
+                    l2acc = fmaf(d, d, l2acc);
+                }
+            }
         }
         T_ws[pix] = T[k];
         if (T_user) T_user[pix] = T[k];
         S_out[pix] = S[k];
         nlast_out[pix] = last[k];
+    }
+    if (l2.target) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l2acc += __shfl_xor_sync(0xffffffffu, l2acc, o);
+        if (lane == 0 && l2acc != 0.0f) atomicAdd(l2.loss, l2acc * l2.scale);
     }
     if (tile_replay) {   // the backward's replay length of this tile: its largest last blended position
         uint32_t m = rg.x;
@@ -176,72 +189,76 @@ template <int P, bool PIXTEST, bool SPLAT, int CH>
 static void launch_fwd_ptsc(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                             const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                             const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
-                            uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count, cudaStream_t st) {
+                            uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count,
+                            const L2Fused &l2, cudaStream_t st) {
     const unsigned threads = (unsigned)(bp.tile_px / P);
     if (pair_count)
         pdl_launch(k_render_fwd<P, true, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
             views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out, tile_replay,
-            pair_count);
+            pair_count, l2);
     else
         pdl_launch(k_render_fwd<P, false, PIXTEST, SPLAT, CH>, (unsigned)n_tiles, threads, 0, st,
             views_d, tile_view, tile_order, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out, nlast_out, tile_replay,
-            nullptr);
+            nullptr, l2);
 }
 
 template <int P, bool PIXTEST, bool SPLAT>
 static void launch_fwd_pts(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                            const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                            const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
-                           uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count, cudaStream_t st) {
+                           uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count,
+                           const L2Fused &l2, cudaStream_t st) {
     if (bp.chunk_fwd == 64)
         launch_fwd_ptsc<P, PIXTEST, SPLAT, 64>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
-                                               bp, rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
+                                               bp, rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, l2, st);
     else
         launch_fwd_ptsc<P, PIXTEST, SPLAT, 128>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect,
-                                                bp, rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
+                                                bp, rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, l2, st);
 }
 
 template <int P, bool PIXTEST>
 static void launch_fwd_pt(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                           const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                           const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
-                          uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count, cudaStream_t st) {
+                          uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count,
+                          const L2Fused &l2, cudaStream_t st) {
     if (bp.splat)
         launch_fwd_pts<P, PIXTEST, true>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp,
-                                         rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
+                                         rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, l2, st);
     else
         launch_fwd_pts<P, PIXTEST, false>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp,
-                                          rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
+                                          rgb, T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, l2, st);
 }
 
 template <int P>
 static void launch_fwd_p(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                          const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                          const BlendParams &bp, float *rgb, float *T_user, float *T_ws, float *S_out,
-                         uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count, cudaStream_t st) {
+                         uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count,
+                         const L2Fused &l2, cudaStream_t st) {
     if (bp.pixel_test)
         launch_fwd_pt<P, true>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb,
-                               T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
+                               T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, l2, st);
     else
         launch_fwd_pt<P, false>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb,
-                                T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, st);
+                                T_user, T_ws, S_out, nlast_out, tile_replay, pair_count, l2, st);
 }
 
 cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                               const BlendParams &bp, int ppt, float *rgb, float *T_user, float *T_ws, float *S_out,
                               uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count,
-                              cudaStream_t st, long long *launches) {
+                              const L2Fused &l2, cudaStream_t st, long long *launches) {
     if (n_tiles <= 0) return cudaSuccess;
     if (ppt == 1)
         launch_fwd_p<1>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out,
-                        nlast_out, tile_replay, pair_count, st);
+                        nlast_out, tile_replay, pair_count, l2, st);
     else if (ppt == 4)
         launch_fwd_p<4>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out,
-                        nlast_out, tile_replay, pair_count, st);
+                        nlast_out, tile_replay, pair_count, l2, st);
     else
         launch_fwd_p<2>(views_d, tile_view, tile_order, n_tiles, ranges, sorted_item, rec, prect, bp, rgb, T_user, T_ws, S_out,
-                        nlast_out, tile_replay, pair_count, st);
+                        nlast_out, tile_replay, pair_count, l2, st);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -167,11 +167,20 @@ cudaError_t launch_duplicate(const uint32_t *perm, const uint32_t *offsets, cons
 cudaError_t launch_ranges(const uint32_t *sorted_key, long long n_inst, const unsigned long long *n_dev, uint2 *ranges,
                           long long n_tiles, cudaStream_t st, long long *launches);
 
+// The L2 image loss fused into the forward's epilogue (target NULL: none): *loss +=
+// scale sum (rgb - target)^2 and grad = 2 scale (rgb - target), per pixel where rgb is written.
+struct L2Fused {
+    const float *target;
+    float *grad;
+    float *loss;
+    float scale;
+};
+
 cudaError_t launch_render_fwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,
                               const BlendParams &bp, int ppt, float *rgb, float *T_user, float *T_ws, float *S_out,
                               uint32_t *nlast_out, uint32_t *tile_replay, unsigned long long *pair_count,
-                              cudaStream_t st, long long *launches);
+                              const L2Fused &l2, cudaStream_t st, long long *launches);
 
 cudaError_t launch_render_bwd(const ViewInfo *views_d, const int *tile_view, const int *tile_order, long long n_tiles,
                               const uint2 *ranges, const uint32_t *sorted_item, const float4 *rec, const short4 *prect,

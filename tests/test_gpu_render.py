@@ -459,3 +459,42 @@ def test_pixel_layouts_compute_identical_bits(gpu_lib, mode, splat):
         run_backward(vg, ws, g, wr)
         q = ws.query()
         assert q["n_blend"] == q["n_blend_bwd"] > 0, (ppt, q["n_blend"], q["n_blend_bwd"])
+
+
+@pytest.mark.parametrize("mode", ["exact", "compat"])
+@pytest.mark.parametrize("case", ["cfg1_ragged", "multiview_sh3"])
+def test_forward_with_fused_l2_loss(gpu_lib, case, mode):
+    """vg_render_fwd_l2 against vg_render_fwd followed by vg_l2_loss on the same workspace: image,
+    transmittance and loss gradient bit-identical, the loss equal up to the order of its additions
+    (and to the FP64 sum over the image); the backward that follows sees the same state."""
+    import torch
+    vg = gpu_lib
+    scene, cams = CASES[case]()
+    o = dict(oracle.COMPAT if mode == "compat" else oracle.EXACT, bg=(0.3, 0.2, 0.1))
+    g = dev_scene(vg, scene)
+    P = sum(c.width * c.height for c in cams)
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(3)
+    tgt = torch.as_tensor(rng.uniform(size=(P, 3)).astype(np.float32)).to(dev)
+    scale = 1.0 / (3 * P)
+    ws = vg.Workspace()
+    ws.preprocess(g, cams, vg_opts(vg, o))
+    ws.bin_sort()
+    rgb1, T1 = torch.empty(P, 3, device=dev), torch.empty(P, device=dev)
+    ws.render_fwd(rgb1, T1)
+    l1, d1 = torch.zeros(1, device=dev), torch.empty(P, 3, device=dev)
+    ws.l2_loss(rgb1, tgt, scale, l1, d1)
+    nan = float("nan")
+    rgb2, T2 = torch.full((P, 3), nan, device=dev), torch.full((P,), nan, device=dev)
+    l2, d2 = torch.full((1,), nan, device=dev), torch.full((P, 3), nan, device=dev)
+    ws.render_fwd_l2(rgb2, T2, tgt, scale, l2, d2)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb1, rgb2) and torch.equal(T1, T2) and torch.equal(d1, d2)
+    ref = scale * float(np.sum((rgb1.cpu().numpy().astype(np.float64) - tgt.cpu().numpy().astype(np.float64)) ** 2))
+    assert abs(float(l1) - ref) <= 1e-5 * ref and abs(float(l2) - ref) <= 1e-5 * ref
+    grads = run_backward(vg, ws, g, d2.cpu().numpy())
+    ws.render_fwd(rgb1, T1)
+    ref_g = run_backward(vg, ws, g, d1.cpu().numpy())
+    check_grads(grads, ref_g, scene, GRAD_TOL, label="fused loss against separate ")
+    with pytest.raises(RuntimeError, match="loss"):
+        ws.render_fwd_l2(rgb2, T2, None, scale, l2, d2)
