@@ -239,8 +239,8 @@ vg_status vg_render_fwd(vg_workspace *ws, float *rgb, float *T_final, void *stre
  *   *loss    = scale * sum (rgb - target)^2, a device scalar (overwritten)
  *   dL_drgb  [sum_v H_v W_v][3] float32, device: 2 scale (rgb - target) (overwritten)
  * rgb, T_final and dL_drgb are bit-identical to vg_render_fwd followed by vg_l2_loss; the loss
- * differs from vg_l2_loss's only in the order of its additions.  NULL rgb, target, loss or
- * dL_drgb: VG_ERR_INVALID_ARG. */
+ * differs from vg_l2_loss's only in the order of its additions.  A NULL loss, or a NULL rgb,
+ * target or dL_drgb while the views have pixels: VG_ERR_INVALID_ARG. */
 vg_status vg_render_fwd_l2(vg_workspace *ws, float *rgb, float *T_final, const float *target, float scale,
                            float *loss, float *dL_drgb, void *stream);
 
