@@ -165,16 +165,18 @@ __device__ __forceinline__ void cull_row(const float4 &r0, const float4 &r1, con
     out[2] = make_float4(dot(C0, C2), dot(C1, C1), dot(C1, C2), dot(C2, C2));
 }
 
-// The test of the record (px0, py0, log2 K from the record; Gram matrices from cull_row).
+// The test of the record (px0, py0, log2 K from the record; Gram matrices from cull_row; sg00 =
+// sqrtf(g00) = |A0| and sg11 = sqrtf(g11) = |A1|, formed once per staged record by the thread that
+// stages it rather than once per warp that tests it).
 __device__ __forceinline__ bool box_may_blend(const float4 &ga, const float4 &gb, const float4 &gc, float px0,
-                                              float py0, float l2K, const BoxCull &bc) {
+                                              float py0, float l2K, float sg00, float sg11, const BoxCull &bc) {
     const float g00 = ga.x, g01 = ga.y, g02 = ga.z, g11 = ga.w, g12 = gb.x, g22 = gb.y;
     const float k00 = gb.z, k01 = gb.w, k02 = gc.x, k11 = gc.y, k12 = gc.z, k22 = gc.w;
     const float ex0 = bc.x0 - px0, ex1 = bc.x1 - px0, ey0 = bc.y0 - py0, ey1 = bc.y1 - py0;
     const float cx = 0.5f * (ex0 + ex1), cy = 0.5f * (ey0 + ey1), hx = 0.5f * (ex1 - ex0), hy = 0.5f * (ey1 - ey0);
     // |A u_c|^2 = u_c^T G u_c with u_c = (cx, cy, 1)
     const float au2 = fmaf(cx, fmaf(g00, cx, 2.0f * fmaf(g01, cy, g02)), fmaf(cy, fmaf(g11, cy, 2.0f * g12), g22));
-    const float low = sqrtf(fmaxf(au2, 0.0f)) * 0.9999f - sqrtf(g00) * hx - sqrtf(g11) * hy;
+    const float low = sqrtf(fmaxf(au2, 0.0f)) * 0.9999f - sg00 * hx - sg11 * hy;
     if (!(low > 0.0f)) return true;                      // no useful amplitude bound: keep
     const float t = l2K + bc.l2dmax - __log2f(low) - bc.l2tskip;   // log2(Amax / tau_skip)
     if (!(t > -1e-3f)) return false;                     // Amax < tau_skip: no pixel blends

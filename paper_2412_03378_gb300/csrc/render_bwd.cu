@@ -51,7 +51,8 @@ template <bool PIXTEST>
 struct RingSlot {
     float4 rec[kGroup * kRecF4];                // the records, one after another
     float4 cull[PIXTEST ? 1 : kCullF4][kGroup];  // Gram rows for the opacity test, by row
-    float4 ref[PIXTEST ? 1 : kGroup];            // (px0, py0, log2 K) for the opacity test
+    float4 ref[PIXTEST ? 1 : kGroup];            // (px0, py0, log2 K, |A0|) for the opacity test
+    float sa1[PIXTEST ? 1 : kGroup];             // |A1| for the opacity test
     short4 rect[kGroup];                         // pixel footprint rectangles
     uint32_t item[kGroup];                       // item ids (accumulator rows)
 };
@@ -170,7 +171,8 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                     cull_row(q[0], q[1], q[2], q[3], q[4], c);
 #pragma unroll
                     for (int k = 0; k < kCullF4; ++k) Sl.cull[k][lane] = c[k];
-                    Sl.ref[lane] = make_float4(q[4].z, q[4].w, q[5].x, 0.0f);
+                    Sl.ref[lane] = make_float4(q[4].z, q[4].w, q[5].x, sqrtf(c[0].x));
+                    Sl.sa1[lane] = sqrtf(c[0].w);
                 }
             }
             mbar_arrive(&full[sl]);
@@ -197,7 +199,8 @@ k_render_bwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             bool need = lane < n && start + (uint32_t)lane < warp_last && !box_misses(wb, Sl.rect[lane]);
             if (!PIXTEST && need) {   // skip records whose opacity stays below tau_skip on this warp
                 const float4 r = Sl.ref[lane];
-                need = box_may_blend(Sl.cull[0][lane], Sl.cull[1][lane], Sl.cull[2][lane], r.x, r.y, r.z, bc);
+                need = box_may_blend(Sl.cull[0][lane], Sl.cull[1][lane], Sl.cull[2][lane], r.x, r.y, r.z, r.w,
+                                     Sl.sa1[lane], bc);
             }
             unsigned m = __ballot_sync(0xffffffffu, need);
             while (m) {

@@ -31,6 +31,7 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     __shared__ float4 srec[kChunk * kRecF4];
     __shared__ short4 srect[kChunk];
     __shared__ float4 scull[PIXTEST ? 1 : kChunk * kCullF4];   // Gram matrices for the opacity test
+    __shared__ float2 ssq[PIXTEST ? 1 : kChunk];                 // |A0|, |A1| for the opacity test
     const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
     const ViewInfo &V = views[tile_view[tile]];
     const int local = tile - V.tile_base;
@@ -68,7 +69,13 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                 srec[r * kRecF4 + k] = q[k];
             }
             srect[r] = prect[item];
-            if (!PIXTEST) cull_row(q[0], q[1], q[2], q[3], q[4], &scull[r * kCullF4]);
+            if (!PIXTEST) {
+                float4 c[kCullF4];
+                cull_row(q[0], q[1], q[2], q[3], q[4], c);
+#pragma unroll
+                for (int k = 0; k < kCullF4; ++k) scull[r * kCullF4 + k] = c[k];
+                ssq[r] = make_float2(sqrtf(c[0].x), sqrtf(c[0].w));
+            }
         }
         __syncthreads();
         // the warp ballots the records whose footprint touches its pixels (and, when pairs below
@@ -80,7 +87,8 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             if (!PIXTEST && need) {   // skip records whose opacity stays below tau_skip on this warp
                 const float4 *q = &scull[jl * kCullF4];
                 const float4 r4 = srec[jl * kRecF4 + 4];
-                need = box_may_blend(q[0], q[1], q[2], r4.z, r4.w, srec[jl * kRecF4 + 5].x, bc);
+                const float2 sq = ssq[jl];
+                need = box_may_blend(q[0], q[1], q[2], r4.z, r4.w, srec[jl * kRecF4 + 5].x, sq.x, sq.y, bc);
             }
             unsigned m = __ballot_sync(0xffffffffu, need);
             while (m) {
