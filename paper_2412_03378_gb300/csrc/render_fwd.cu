@@ -31,7 +31,9 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
     __shared__ float4 srec[kChunk * kRecF4];
     __shared__ short4 srect[kChunk];
     __shared__ float4 scull[PIXTEST ? 1 : kChunk * kCullF4];   // Gram matrices for the opacity test
-    __shared__ float2 ssq[PIXTEST ? 1 : kChunk];                 // |A0|, |A1| for the opacity test
+    // per record, contiguous for the opacity test: (px0, py0, log2 K, |A0|) and |A1|
+    __shared__ float4 sref[PIXTEST ? 1 : kChunk];
+    __shared__ float ssq1[PIXTEST ? 1 : kChunk];
     const int tile = tile_order ? tile_order[blockIdx.x] : (int)blockIdx.x;
     const ViewInfo &V = views[tile_view[tile]];
     const int local = tile - V.tile_base;
@@ -74,7 +76,8 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
                 cull_row(q[0], q[1], q[2], q[3], q[4], c);
 #pragma unroll
                 for (int k = 0; k < kCullF4; ++k) scull[r * kCullF4 + k] = c[k];
-                ssq[r] = make_float2(sqrtf(c[0].x), sqrtf(c[0].w));
+                sref[r] = make_float4(q[4].z, q[4].w, q[5].x, sqrtf(c[0].x));
+                ssq1[r] = sqrtf(c[0].w);
             }
         }
         __syncthreads();
@@ -86,9 +89,8 @@ k_render_fwd(const ViewInfo *__restrict__ views, const int *__restrict__ tile_vi
             bool need = jl < (int)n && !box_misses(wb, srect[jl]);
             if (!PIXTEST && need) {   // skip records whose opacity stays below tau_skip on this warp
                 const float4 *q = &scull[jl * kCullF4];
-                const float4 r4 = srec[jl * kRecF4 + 4];
-                const float2 sq = ssq[jl];
-                need = box_may_blend(q[0], q[1], q[2], r4.z, r4.w, srec[jl * kRecF4 + 5].x, sq.x, sq.y, bc);
+                const float4 rf = sref[jl];
+                need = box_may_blend(q[0], q[1], q[2], rf.x, rf.y, rf.z, rf.w, ssq1[jl], bc);
             }
             unsigned m = __ballot_sync(0xffffffffu, need);
             while (m) {
