@@ -413,7 +413,7 @@ cudaError_t launch_radix_sort(const uint32_t *keys_in, const uint32_t *vals_in, 
     if (e != cudaSuccess) return e;
     uint32_t *ghist = scratch, *ctr = scratch + passes * kRsBins, *status = ctr + passes + 8;
     long long hb = (n + kRsThreads - 1) / kRsThreads;
-    if (hb > 152 * 8) hb = 152 * 8;
+    if (hb > 152 * 4) hb = 152 * 4;   // fewer CTAs: fewer same-address flushes of the digit totals
     pdl_launch(k_digit_hist, (unsigned)hb, kRsThreads, 0, st, keys_in, n, n_dev, bits, ghist);
     *launches += 1;
     const uint32_t *ki = keys_in, *vi = vals_in;
